@@ -1,0 +1,204 @@
+/*
+ * tdq.h -- C ABI of libtdq, a GB300 (sm_103a) implementation of the distance
+ * threshold search over trajectory databases of Gowanlock & Casanova,
+ * "Parallel Distance Threshold Query Processing for Spatiotemporal
+ * Trajectory Databases on the GPU" (arXiv 1405.7461).
+ *
+ * Problem (Sec. 3): the database D holds n 4-D line segments (x,y,z,t of a
+ * start point and of an end point, a segment id and a trajectory id).  A
+ * query is a set of query segments, a distance d and a time window [t0,t1].
+ * The result holds, for every (query segment, entry segment) pair that comes
+ * within distance d during the common time span of both segments inside the
+ * window, that pair and the sub-interval [t_enter, t_exit] in absolute time.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a tdq_status; on error no output is produced (output
+ *    handles are left NULL) and tdq_last_error() gives a message.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work of a call is ordered on that stream.
+ *  - Device pointers refer to memory of the CUDA device that is current on
+ *    the calling thread; an index is bound to the device it was built on.
+ *  - Readings of the paper that these calls implement:
+ *      * two segments form a pair only if their common span has positive
+ *        length (a < b); segments that only touch at an instant do not;
+ *      * "within d" is inclusive (distance <= d);
+ *      * the window clips the common span; a window with t0 > t1 is invalid;
+ *      * at most one interval per pair (the squared distance of two linearly
+ *        moving points is a convex quadratic in time, Sec. 5).
+ *  - One search at a time per index (calls on one index must not overlap).
+ */
+#ifndef TDQ_H
+#define TDQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDQ_OK = 0,
+    TDQ_ERR_INVALID = 1,  /* NULL argument, non-finite value, t_end <= t_start, d < 0 or NaN, t0 > t1 */
+    TDQ_ERR_NOMEM = 2,    /* a device or host allocation failed; nothing leaked */
+    TDQ_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    TDQ_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    TDQ_ERR_OVERFLOW = 5  /* a caller-provided result buffer is too small (see tdq_search_device) */
+} tdq_status;
+
+/* A segment set in structure-of-arrays form (Sec. 3).  Columns are float64
+ * (start point xs,ys,zs at time ts; end point xe,ye,ze at time te) and int64
+ * ids, n entries each.  on_device = 0: host memory; 1: device memory.
+ * traj_id may be NULL (ids then read as 0).  The library copies what it
+ * needs; the caller keeps ownership of these arrays. */
+typedef struct {
+    const double *xs, *ys, *zs, *ts;
+    const double *xe, *ye, *ze, *te;
+    const int64_t *seg_id;
+    const int64_t *traj_id;
+    uint64_t n;
+    int on_device;
+} tdq_segments;
+
+/* Temporal-bin index parameters (Sec. 4).  bin_count = m, the number of
+ * fixed-width bins over the database's temporal extent; 0 selects 10,000,
+ * the value used in the paper's experiments (Sec. 7.2). */
+typedef struct {
+    uint32_t bin_count;
+} tdq_index_params;
+
+/* Opaque index: the entry segments sorted by t_start in device memory (SoA)
+ * and the bin table, plus the search workspace.  Owns its device memory. */
+typedef struct tdq_index tdq_index;
+
+/* Search modes. */
+enum {
+    TDQ_MODE_FP64 = 0,        /* every temporal-overlap pair in FP64 (plain method) */
+    TDQ_MODE_FP32_FILTER = 1  /* conservative FP32 pre-test, FP64 for the survivors */
+};
+
+/* Search tuning.  Zero fields select defaults. */
+typedef struct {
+    uint32_t query_tile;  /* query segments per tile (multiple of 32, <= 32; default 32) */
+    uint32_t entry_chunk; /* entry segments per work item (multiple of 256; default 512) */
+    int mode;             /* TDQ_MODE_* (default TDQ_MODE_FP64) */
+} tdq_search_params;
+
+/* Host-side results, owned by the library (release with tdq_results_free).
+ * Item k: query segment query_seg_id[k] (the caller's id) is within d of
+ * entry segment entry_seg_id[k] over [t_enter[k], t_exit[k]].  Order is
+ * unspecified. */
+typedef struct {
+    int64_t *query_seg_id;
+    int64_t *entry_seg_id;
+    double *t_enter;
+    double *t_exit;
+    uint64_t count;
+} tdq_results;
+
+/* Device-side result buffer provided by the caller: four device arrays of
+ * `capacity` items each (same meaning as tdq_results). */
+typedef struct {
+    int64_t *query_seg_id;
+    int64_t *entry_seg_id;
+    double *t_enter;
+    double *t_exit;
+    uint64_t capacity;
+} tdq_result_buffer;
+
+/* Counters of the last search on an index (Sec. 8.1 splits interactions into
+ * hits, temporal misses and temporal-hit/spatial-misses). */
+typedef struct {
+    uint64_t query_segments;    /* query segments searched (after validation) */
+    uint64_t interactions;      /* candidate pairs visited by the kernel (tile x chunk) */
+    uint64_t overlap_pairs;     /* pairs whose common span (inside the window) has positive length */
+    uint64_t fp64_pairs;        /* pairs evaluated in FP64 (all overlap pairs in FP64 mode) */
+    uint64_t results;           /* pairs within d (alpha * interactions) */
+    uint64_t work_items;        /* (query tile, entry chunk) work items */
+    uint64_t kernel_launches;   /* CUDA kernels the library launched for the search */
+    double pair_kernel_ms;      /* device time of the pair kernel (CUDA events) */
+    double total_ms;            /* device time of the whole search on its stream */
+} tdq_stats;
+
+/*
+ * Build the temporal-bin index of Sec. 4 over `entries`: entry segments sorted
+ * by non-decreasing t_start (ties by input position), m fixed-width bins over
+ * [min t_start, max t_end], per bin the largest t_end and the range of sorted
+ * positions.  Sorting, binning and the per-segment velocity are computed on
+ * the device.  n = 0 is allowed (every search then returns no results).
+ * Errors: TDQ_ERR_INVALID for a NULL argument or an invalid segment
+ * (non-finite value, t_end <= t_start).  *out is set only on TDQ_OK.
+ */
+tdq_status tdq_build_index(const tdq_segments *entries, const tdq_index_params *params, void *stream,
+                           tdq_index **out);
+
+/* Release an index and all its device memory (NULL is ignored). */
+void tdq_index_free(tdq_index *idx);
+
+/* Number of entry segments in the index. */
+uint64_t tdq_index_size(const tdq_index *idx);
+
+/*
+ * Copy the bin table of Sec. 4 (Fig. 1) to host arrays of *m items each:
+ * bin_start = smallest t_start in the bin, bin_end = largest t_end,
+ * bin_first/bin_last = sorted positions of the bin's first and last entry;
+ * an empty bin has first = last = -1 and start = end = NaN.  *width receives
+ * the bin width b and *t_min the lower end of the extent.  Pass NULL arrays
+ * to query *m only.  sorted_index (n items, may be NULL) receives the input
+ * position of each sorted entry.  Synchronous.
+ */
+tdq_status tdq_index_bins(const tdq_index *idx, uint32_t *m, double *width, double *t_min, double *bin_start,
+                          double *bin_end, int64_t *bin_first, int64_t *bin_last, int64_t *sorted_index);
+
+/*
+ * Search (Sec. 4 lookup + Sec. 5 kernel): every query segment against the
+ * candidate entry segments its bins select, with threshold d and window
+ * [t0, t1] (use -INFINITY/INFINITY for no window).  Queries may be on the
+ * host or the device; results are returned in host memory, owned by the
+ * library.  The result buffer is grown and the kernel re-run when the
+ * results do not fit (the retry of Sec. 5).  Blocks until done.
+ * Errors: TDQ_ERR_INVALID (NULL, invalid query segment, d < 0 or NaN,
+ * t0 > t1, NaN window).  n = 0 queries gives an empty result.
+ */
+tdq_status tdq_search(tdq_index *idx, const tdq_segments *queries, double d, double t0, double t1,
+                      const tdq_search_params *params, void *stream, tdq_results **out);
+
+/* Release results from tdq_search (NULL is ignored). */
+void tdq_results_free(tdq_results *res);
+
+/*
+ * Device-resident search: queries in device memory, results written into the
+ * caller's device buffer.  *count receives the number of results; when it
+ * exceeds out->capacity only the first capacity items are written and the
+ * call returns TDQ_ERR_OVERFLOW, so the caller can grow the buffer and call
+ * again (Sec. 5).  Blocks until the count is known.
+ */
+tdq_status tdq_search_device(tdq_index *idx, const tdq_segments *queries, double d, double t0, double t1,
+                             const tdq_search_params *params, void *stream, const tdq_result_buffer *out,
+                             uint64_t *count);
+
+/*
+ * Same as tdq_search_device with a threshold and a window per query segment:
+ * d_per_query, t0_per_query, t1_per_query are device arrays of queries->n
+ * items (the batched form, where each query trajectory of a batch carries
+ * its own d and window).
+ */
+tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries, const double *d_per_query,
+                                     const double *t0_per_query, const double *t1_per_query,
+                                     const tdq_search_params *params, void *stream,
+                                     const tdq_result_buffer *out, uint64_t *count);
+
+/* Counters of the last completed search on idx. */
+tdq_status tdq_get_stats(const tdq_index *idx, tdq_stats *out);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *tdq_last_error(void);
+
+/* Library version string. */
+const char *tdq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDQ_H */

@@ -1,0 +1,33 @@
+// Error reporting and version of libtdq.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "tdq_internal.cuh"
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+namespace tdq {
+
+tdq_status set_error(tdq_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+tdq_status cuda_error(cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear a non-sticky error
+    if (e == cudaErrorMemoryAllocation) return set_error(TDQ_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(TDQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace tdq
+
+extern "C" const char *tdq_last_error(void) { return g_err; }
+
+extern "C" const char *tdq_version(void) { return "tdq 0.1 (sm_103a)"; }

@@ -1,0 +1,764 @@
+// Distance threshold search on the device: candidate lookup in the
+// temporal-bin index (Sec. 4) and the pair kernel (Sec. 5, Algorithm 1).
+//
+// Pipeline of one search, all on the caller's stream:
+//   query_prep    validate, clip each query segment to the window, velocity,
+//                 start position at the clipped start, sort key
+//   radix sort    query segments by clipped start (Sec. 4 sorts Q by t_start)
+//   query_gather  sorted query SoA + candidate range [lo, hi) of sorted entry
+//                 positions per query segment, from the bin table
+//   tile_plan     tiles of 32 consecutive sorted query segments; a tile's
+//                 range is the union of its members' ranges, cut into chunks
+//                 of `entry_chunk` entries; one work item per (tile, chunk)
+//   scan          work-item offsets per tile
+//   traj_dist_search_kernel
+//                 persistent CTAs take work items from an atomic counter,
+//                 stage the tile's queries and the chunk's entries in shared
+//                 memory, enumerate the pairs whose spans overlap with
+//                 integer time keys, compact them so that all 32 lanes of a
+//                 warp evaluate a real pair, and append every pair within d
+//                 with one atomic per warp.
+//
+// Design notes for GB300: the FP64 pipe issues ~2 DFMA per clock per SM, so
+// FP64 lane-slots are the scarce resource.  Temporal tests and every
+// comparison run on the integer pipe; a lane never issues FP64 work for a
+// pair whose spans do not overlap; the interval roots (sqrt, two divisions)
+// run only for pairs that are within d.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "tdq_internal.cuh"
+
+namespace tdq {
+namespace {
+
+constexpr int kQT = 32;             // query segments per tile (one bit each in a lane mask)
+constexpr int kPairThreads = 256;   // threads of the pair kernel
+constexpr int kBlock = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+inline unsigned grid_for(uint64_t n, int block = kBlock)
+{
+    uint64_t g = (n + block - 1) / block;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+struct QueryInput {
+    const double *c[8];  // xs ys zs ts xe ye ze te
+    const int64_t *seg_id;
+    double d, t0, t1;                            // one threshold and window ...
+    const double *d_arr, *t0_arr, *t1_arr;       // ... or one per query segment
+};
+
+__device__ __forceinline__ bool is_nan_bits(double x)
+{
+    int64_t b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+    return b > 0x7ff0000000000000LL;
+}
+
+// Validate and clip every query segment.  pre[] columns: px py pz vx vy vz d2
+// ts_key te_key (keys stored bitwise in the double arrays).
+__global__ void query_prep(QueryInput in, uint64_t nq, double *const *pre, uint64_t *keys, uint32_t *vals,
+                           DevCounters *ctr)
+{
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false;
+    if (i < nq) {
+        bool ok = true;
+        double c[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            c[k] = in.c[k][i];
+            ok &= finite_bits(c[k]);
+        }
+        double d = in.d_arr ? in.d_arr[i] : in.d;
+        double t0 = in.t0_arr ? in.t0_arr[i] : in.t0;
+        double t1 = in.t1_arr ? in.t1_arr[i] : in.t1;
+        ok &= finite_bits(d) && ge0(d);
+        ok &= !is_nan_bits(t0) && !is_nan_bits(t1);
+        int64_t ks = okey(c[3]), ke = okey(c[7]);
+        ok &= ke > ks;
+        int64_t k0 = ok ? okey(t0) : 0, k1 = ok ? okey(t1) : 0;
+        ok &= k0 <= k1;
+        if (!ok) atomicOr(&ctr->error, 1u);
+        int64_t cs = max(ks, k0), ce = min(ke, k1);
+        valid = ok && cs < ce;
+        double dt = c[7] - c[3];
+        double vx = (c[4] - c[0]) / dt, vy = (c[5] - c[1]) / dt, vz = (c[6] - c[2]) / dt;
+        double px = c[0], py = c[1], pz = c[2];
+        if (valid && cs != ks) {  // the window cuts the start: position at the clipped start
+            double shift = key_double(cs) - c[3];
+            px = fma(vx, shift, px);
+            py = fma(vy, shift, py);
+            pz = fma(vz, shift, pz);
+        }
+        pre[0][i] = px; pre[1][i] = py; pre[2][i] = pz;
+        pre[3][i] = vx; pre[4][i] = vy; pre[5][i] = vz;
+        pre[6][i] = d * d;
+        pre[7][i] = __longlong_as_double(cs);
+        pre[8][i] = __longlong_as_double(ce);
+        keys[i] = valid ? ((uint64_t)cs ^ 0x8000000000000000ULL) : ~0ULL;
+        vals[i] = (uint32_t)i;
+    }
+    unsigned vm = __ballot_sync(kFull, valid);
+    if ((threadIdx.x & 31) == 0 && vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
+}
+
+__device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
+{
+    double f = floor((t - t_min) / width);
+    if (!(f < (double)(m - 1))) return (int64_t)m - 1;
+    if (f < 0.0) return 0;
+    return (int64_t)f;
+}
+
+struct BinView {
+    const int64_t *bin_begin, *bin_pmax_key;
+    double t_min, width;
+    uint32_t m;
+};
+
+// Sorted query SoA and the candidate range of each query segment.
+__global__ void query_gather(const double *const *pre, const int64_t *seg_id, const uint32_t *order, uint64_t nq,
+                             const DevCounters *ctr, BinView bins, QuerySoA q)
+{
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nq || k >= ctr->valid_queries) return;
+    uint32_t i = order[k];
+    q.px[k] = pre[0][i]; q.py[k] = pre[1][i]; q.pz[k] = pre[2][i];
+    q.vx[k] = pre[3][i]; q.vy[k] = pre[4][i]; q.vz[k] = pre[5][i];
+    q.d2[k] = pre[6][i];
+    int64_t cs = __double_as_longlong(pre[7][i]);
+    int64_t ce = __double_as_longlong(pre[8][i]);
+    q.ts_key[k] = cs;
+    q.te_key[k] = ce;
+    q.qid[k] = seg_id[i];
+    // First bin whose extent reaches past the query start: the prefix maximum
+    // of bin ends is non-decreasing, so this is a binary search (Sec. 4 uses
+    // an index tree over the bin extents for the same lookup).
+    uint32_t lo = 0, hi = bins.m;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (bins.bin_pmax_key[mid] > cs) hi = mid; else lo = mid + 1;
+    }
+    int64_t jlo = lo;
+    // Last bin that can hold an entry starting before the query end.
+    double te = key_double(ce);
+    int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
+    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
+    if (jlo < (int64_t)bins.m && jlo <= jhi) {
+        rlo = bins.bin_begin[jlo];
+        rhi = bins.bin_begin[jhi + 1];
+        if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
+    }
+    q.lo[k] = rlo;
+    q.hi[k] = rhi;
+}
+
+// One warp per tile of kQT sorted query segments.
+__global__ void tile_plan(const QuerySoA q, uint64_t ntiles, const DevCounters *ctr, uint32_t chunk,
+                          int64_t *tile_lo, int64_t *tile_hi, unsigned long long *tile_work)
+{
+    uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    uint64_t nv = ctr->valid_queries;
+    uint64_t k = t * kQT + lane;
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    if (k < nv) { lo = q.lo[k]; hi = q.hi[k]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, (int64_t)__shfl_xor_sync(kFull, (long long)lo, o));
+        hi = max(hi, (int64_t)__shfl_xor_sync(kFull, (long long)hi, o));
+    }
+    if (lane == 0) {
+        unsigned long long w = 0;
+        if (hi > lo) {
+            w = (unsigned long long)((hi - lo + chunk - 1) / chunk);
+        } else {
+            lo = 0;
+            hi = 0;
+        }
+        tile_lo[t] = lo;
+        tile_hi[t] = hi;
+        tile_work[t] = w;
+        if (t == 0) tile_work[ntiles] = 0;  // the scan turns this slot into the total
+    }
+}
+
+// n-th (0-based) set bit of m; m must have more than r bits set.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r)
+{
+    int p = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        int c = __popc(m & ((1u << s) - 1u));
+        if (r >= c) {
+            r -= c;
+            m >>= s;
+            p += s;
+        }
+    }
+    return p;
+}
+
+// Shared-memory staging of one work item.
+struct PairSmem {
+    double qp[3][kQT], qv[3][kQT], qd2[kQT];
+    int64_t qts[kQT], qte[kQT], qid[kQT];
+    long long item;
+    long long tile;
+    // followed by the entry chunk: 6 double columns + 2 key columns of `chunk` items
+};
+
+struct PairArgs {
+    EntrySoA e;
+    QuerySoA q;
+    const int64_t *tile_lo, *tile_hi;
+    const unsigned long long *tile_work;
+    uint64_t ntiles;
+    DevCounters *ctr;
+    tdq_result_buffer out;
+    uint32_t chunk;
+};
+
+// calcTimeInterval for a pair that is within d: the roots of
+// A tau^2 + 2 Bh tau + C over tau in [0, L] (tau = time since a), by the
+// cancellation-free quadratic formula; a tangent contact that rounding pushes
+// out of the root bracket collapses to the closest point.
+__device__ __noinline__ void pair_interval(double A, double Bh, double C, double disc, double a, double b,
+                                           double *tin, double *tout)
+{
+    double L = b - a;
+    double tlo, thi;
+    if (le0(A)) {  // no relative motion: the whole span
+        tlo = 0.0;
+        thi = L;
+    } else {
+        double sq = sqrt(lt0(disc) ? 0.0 : disc);
+        double qq = -(Bh + copysign(sq, Bh));
+        double r1, r2;
+        if (qq == 0.0) {
+            r1 = 0.0;
+            r2 = 0.0;
+        } else {
+            r1 = qq / A;
+            r2 = C / qq;
+        }
+        double lo = fmin(r1, r2), hi = fmax(r1, r2);
+        tlo = fmax(lo, 0.0);
+        thi = fmin(hi, L);
+        if (tlo > thi) {
+            double ts = fmin(fmax(-Bh / A, 0.0), L);
+            tlo = ts;
+            thi = ts;
+        }
+    }
+    *tin = le0(tlo) ? a : (tlo >= L ? b : a + tlo);
+    *tout = thi >= L ? b : (le0(thi) ? a : a + thi);
+}
+
+__global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PairSmem &S = *reinterpret_cast<PairSmem *>(smem_raw);
+    const uint32_t EC = args.chunk;
+    double *ecol = reinterpret_cast<double *>(smem_raw + ((sizeof(PairSmem) + 15) & ~(size_t)15));
+    double *epx = ecol, *epy = ecol + EC, *epz = ecol + 2 * EC;
+    double *evx = ecol + 3 * EC, *evy = ecol + 4 * EC, *evz = ecol + 5 * EC;
+    int64_t *ets = reinterpret_cast<int64_t *>(ecol + 6 * EC);
+    int64_t *ete = ets + EC;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    DevCounters *ctr = args.ctr;
+    const unsigned long long total = args.tile_work[args.ntiles];
+    const uint64_t nvalid = ctr->valid_queries;
+    const uint64_t cap = args.out.capacity;
+
+    unsigned long long n_inter = 0, n_overlap = 0;
+
+    for (;;) {
+        if (tid == 0) {
+            long long item = (long long)atomicAdd(&ctr->work_next, 1ULL);
+            long long t = -1;
+            if ((unsigned long long)item < total) {
+                // last tile whose first work item is <= item
+                uint64_t lo = 0, hi = args.ntiles;
+                while (hi - lo > 1) {
+                    uint64_t mid = (lo + hi) >> 1;
+                    if (args.tile_work[mid] <= (unsigned long long)item) lo = mid; else hi = mid;
+                }
+                t = (long long)lo;
+            }
+            S.item = item;
+            S.tile = t;
+        }
+        __syncthreads();
+        const long long item = S.item;
+        if ((unsigned long long)item >= total) break;
+        const uint64_t t = (uint64_t)S.tile;
+        const int64_t e0 = args.tile_lo[t] + (int64_t)(item - (long long)args.tile_work[t]) * EC;
+        const int64_t e1 = min(e0 + (int64_t)EC, args.tile_hi[t]);
+        const int ne = (int)(e1 - e0);
+        const uint64_t q0 = t * kQT;
+        const int nqt = (int)min((uint64_t)kQT, nvalid - q0);
+
+        // stage the tile's query segments
+        if (tid < kQT) {
+            if (tid < nqt) {
+                uint64_t k = q0 + tid;
+                S.qp[0][tid] = args.q.px[k]; S.qp[1][tid] = args.q.py[k]; S.qp[2][tid] = args.q.pz[k];
+                S.qv[0][tid] = args.q.vx[k]; S.qv[1][tid] = args.q.vy[k]; S.qv[2][tid] = args.q.vz[k];
+                S.qd2[tid] = args.q.d2[k];
+                S.qts[tid] = args.q.ts_key[k];
+                S.qte[tid] = args.q.te_key[k];
+                S.qid[tid] = args.q.qid[k];
+            } else {  // padding: a span that overlaps nothing
+                S.qts[tid] = INT64_MAX;
+                S.qte[tid] = INT64_MIN;
+            }
+        }
+        // stage the chunk's entry segments (coalesced column loads)
+        for (int i = tid; i < (int)EC; i += kPairThreads) {
+            if (i < ne) {
+                int64_t k = e0 + i;
+                epx[i] = args.e.px[k]; epy[i] = args.e.py[k]; epz[i] = args.e.pz[k];
+                evx[i] = args.e.vx[k]; evy[i] = args.e.vy[k]; evz[i] = args.e.vz[k];
+                ets[i] = args.e.ts_key[k];
+                ete[i] = args.e.te_key[k];
+            } else {
+                ets[i] = INT64_MAX;
+                ete[i] = INT64_MIN;
+            }
+        }
+        if (tid == 0) n_inter += (unsigned long long)ne * (unsigned long long)nqt;
+        __syncthreads();
+
+        for (int g = 0; g < (int)EC; g += kPairThreads) {
+            const int el = g + warp * 32 + lane;
+            // temporal intersection of this lane's entry with every query of
+            // the tile, as a 32-bit mask (integer keys: strict overlap a < b)
+            const int64_t my_ts = ets[el], my_te = ete[el];
+            unsigned mask = 0;
+#pragma unroll
+            for (int j = 0; j < kQT; j++) {
+                bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
+                mask |= (unsigned)ov << j;
+            }
+            const int cnt = __popc(mask);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - cnt;
+            const int npairs = __shfl_sync(kFull, incl, 31);
+            if (lane == 0) n_overlap += (unsigned long long)npairs;
+
+            // evaluate the overlapping pairs 32 at a time, one per lane
+            for (int base = 0; base < npairs; base += 32) {
+                const int kk = base + lane;
+                const bool active = kk < npairs;
+                int owner = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    int v = __shfl_sync(kFull, incl, owner + s - 1);
+                    if (v <= kk) owner += s;
+                }
+                const unsigned mo = __shfl_sync(kFull, mask, owner);
+                const int eo = __shfl_sync(kFull, excl, owner);
+                const int j = active ? nth_set_bit(mo, kk - eo) : 0;
+                const int ei = active ? (g + warp * 32 + owner) : el;
+
+                // temporalIntersection: common span [a, b]; S = the segment
+                // that starts at a, O = the other one
+                const int64_t ets_k = ets[ei], ete_k = ete[ei];
+                const int64_t qts_k = S.qts[j], qte_k = S.qte[j];
+                const bool e_later = ets_k >= qts_k;
+                const int64_t a_k = e_later ? ets_k : qts_k;
+                const int64_t b_k = min(ete_k, qte_k);
+                const int64_t o_k = e_later ? qts_k : ets_k;
+                const double a = key_double(a_k), b = key_double(b_k), o_ts = key_double(o_k);
+                const double epx_ = epx[ei], epy_ = epy[ei], epz_ = epz[ei];
+                const double evx_ = evx[ei], evy_ = evy[ei], evz_ = evz[ei];
+                const double qpx_ = S.qp[0][j], qpy_ = S.qp[1][j], qpz_ = S.qp[2][j];
+                const double qvx_ = S.qv[0][j], qvy_ = S.qv[1][j], qvz_ = S.qv[2][j];
+                const double opx = e_later ? qpx_ : epx_, opy = e_later ? qpy_ : epy_, opz = e_later ? qpz_ : epz_;
+                const double ovx = e_later ? qvx_ : evx_, ovy = e_later ? qvy_ : evy_, ovz = e_later ? qvz_ : evz_;
+                const double spx = e_later ? epx_ : qpx_, spy = e_later ? epy_ : qpy_, spz = e_later ? epz_ : qpz_;
+                const double svx = e_later ? evx_ : qvx_, svy = e_later ? evy_ : qvy_, svz = e_later ? evz_ : qvz_;
+
+                // relative position O - S at a, and relative velocity
+                const double dt = a - o_ts;
+                const double dpx = fma(ovx, dt, opx) - spx;
+                const double dpy = fma(ovy, dt, opy) - spy;
+                const double dpz = fma(ovz, dt, opz) - spz;
+                const double dvx = ovx - svx, dvy = ovy - svy, dvz = ovz - svz;
+                // calcTimeInterval: |dp + dv tau|^2 - d^2 = A tau^2 + 2 Bh tau + C
+                const double A = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
+                const double Bh = fma(dpz, dvz, fma(dpy, dvy, dpx * dvx));
+                const double C = fma(dpz, dpz, fma(dpy, dpy, fma(dpx, dpx, -S.qd2[j])));
+                const double disc = fma(Bh, Bh, -(A * C));
+                // Minimum over [0, L] <= 0 without dividing: C <= 0 (in range
+                // at a), or approaching (Bh < 0) with a real root pair
+                // (disc >= 0) whose closest point lies inside the span or
+                // whose value at L is <= 0.
+                bool hit = le0(C);
+                const bool need_L = !hit && lt0(Bh) && ge0(disc);
+                if (__any_sync(kFull, active && need_L)) {
+                    const double L = b - a;
+                    const double gL = fma(A, L, Bh);
+                    const double fL = fma(gL + Bh, L, C);
+                    hit = hit || (need_L && (gt0(gL) || le0(fL)));
+                }
+                hit = hit && active;
+
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (hm) {
+                    unsigned long long rbase = 0;
+                    const int leader = __ffs(hm) - 1;
+                    if (lane == leader) rbase = atomicAdd(&ctr->results, (unsigned long long)__popc(hm));
+                    rbase = __shfl_sync(kFull, rbase, leader);
+                    if (hit) {
+                        double tin, tout;
+                        pair_interval(A, Bh, C, disc, a, b, &tin, &tout);
+                        const unsigned long long pos = rbase + __popc(hm & lt_mask);
+                        if (pos < cap) {
+                            args.out.query_seg_id[pos] = S.qid[j];
+                            args.out.entry_seg_id[pos] = args.e.seg_id[e0 + ei];
+                            args.out.t_enter[pos] = tin;
+                            args.out.t_exit[pos] = tout;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the chunk is about to be restaged
+    }
+    // counters: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_inter += __shfl_xor_sync(kFull, n_inter, o);
+        n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
+    }
+    if (lane == 0) {
+        if (n_inter) atomicAdd(&ctr->interactions, n_inter);
+        if (n_overlap) {
+            atomicAdd(&ctr->overlap_pairs, n_overlap);
+            atomicAdd(&ctr->fp64_pairs, n_overlap);
+        }
+    }
+}
+
+size_t pair_smem_bytes(uint32_t chunk)
+{
+    return ((sizeof(PairSmem) + 15) & ~(size_t)15) + (size_t)chunk * 8 * sizeof(double);
+}
+
+template <typename T>
+T *carve(char *&p, uint64_t count)
+{
+    T *r = (T *)p;
+    p += (count * sizeof(T) + 255) & ~(uint64_t)255;
+    return r;
+}
+inline uint64_t cb(uint64_t count, uint64_t size) { return (count * size + 255) & ~(uint64_t)255; }
+
+tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
+{
+    Workspace &w = idx->ws;
+    if (nq <= w.q_cap && w.q_block) return TDQ_OK;
+    uint64_t cap = nq > 2 * w.q_cap ? nq : 2 * w.q_cap;
+    if (cap < 1024) cap = 1024;
+    uint64_t bytes = 9 * cb(cap, 8)                    // staged host input
+                     + 9 * cb(cap, 8)                  // pre
+                     + 2 * cb(cap, 8) + 2 * cb(cap, 4) // sort
+                     + 12 * cb(cap, 8)                 // sorted query SoA
+                     + cb(9, sizeof(double *));        // pre pointer table
+    uint64_t ntiles = (cap + kQT - 1) / kQT;
+    uint64_t tbytes = 2 * cb(ntiles, 8) + cb(ntiles + 1, 8);
+    uint64_t hwords = sort_hist_words(cap);
+    cudaFree(w.q_block);
+    cudaFree(w.t_block);
+    cudaFree(w.sort_hist);
+    w.q_block = w.t_block = nullptr;
+    w.sort_hist = nullptr;
+    w.q_cap = 0;
+    if (cudaMalloc(&w.q_block, bytes) != cudaSuccess || cudaMalloc(&w.t_block, tbytes) != cudaSuccess ||
+        cudaMalloc(&w.sort_hist, hwords * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(w.q_block);
+        cudaFree(w.t_block);
+        cudaFree(w.sort_hist);
+        w.q_block = w.t_block = nullptr;
+        w.sort_hist = nullptr;
+        return set_error(TDQ_ERR_NOMEM, "search workspace: device allocation of %llu bytes failed",
+                         (unsigned long long)(bytes + tbytes + hwords * 4));
+    }
+    char *p = (char *)w.q_block;
+    for (int c = 0; c < 8; c++) w.in_cols[c] = carve<double>(p, cap);
+    w.in_seg = carve<int64_t>(p, cap);
+    for (int c = 0; c < 9; c++) w.pre[c] = carve<double>(p, cap);
+    w.keys = carve<uint64_t>(p, cap);
+    w.keys_alt = carve<uint64_t>(p, cap);
+    w.vals = carve<uint32_t>(p, cap);
+    w.vals_alt = carve<uint32_t>(p, cap);
+    QuerySoA &q = w.q;
+    q.px = carve<double>(p, cap); q.py = carve<double>(p, cap); q.pz = carve<double>(p, cap);
+    q.vx = carve<double>(p, cap); q.vy = carve<double>(p, cap); q.vz = carve<double>(p, cap);
+    q.d2 = carve<double>(p, cap);
+    q.ts_key = carve<int64_t>(p, cap); q.te_key = carve<int64_t>(p, cap);
+    q.qid = carve<int64_t>(p, cap); q.lo = carve<int64_t>(p, cap); q.hi = carve<int64_t>(p, cap);
+    w.pre_dev = carve<double *>(p, 9);
+    if (cudaMemcpy(w.pre_dev, w.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cuda_error(cudaGetLastError(), "search workspace: pointer table");
+    char *tp = (char *)w.t_block;
+    w.tile_lo = carve<int64_t>(tp, ntiles);
+    w.tile_hi = carve<int64_t>(tp, ntiles);
+    w.tile_work = carve<unsigned long long>(tp, ntiles + 1);
+    w.q_cap = cap;
+    w.t_cap = ntiles;
+    w.s_cap = hwords;
+    return TDQ_OK;
+}
+
+struct SearchSpec {
+    double d, t0, t1;
+    const double *d_arr, *t0_arr, *t1_arr;
+};
+
+tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchSpec &spec,
+                      const tdq_search_params *params, cudaStream_t stream, const tdq_result_buffer &out,
+                      uint64_t *count)
+{
+    const uint64_t nq = queries->n;
+    Workspace &w = idx->ws;
+    idx->last = tdq_stats{};
+    *count = 0;
+    if (nq == 0) return TDQ_OK;
+    if (nq > 0xffffffffULL) return set_error(TDQ_ERR_INVALID, "tdq_search: more than 2^32-1 query segments");
+    const double *cols[8] = {queries->xs, queries->ys, queries->zs, queries->ts,
+                             queries->xe, queries->ye, queries->ze, queries->te};
+    for (int c = 0; c < 8; c++)
+        if (!cols[c]) return set_error(TDQ_ERR_INVALID, "tdq_search: query column %d is NULL", c);
+    if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_search: query seg_id is NULL");
+
+    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
+    if (chunk % kPairThreads != 0 || chunk > 2048)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
+    if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: query_tile must be 32");
+    if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
+
+    tdq_status st = ensure_queries(idx, nq);
+    if (st != TDQ_OK) return st;
+
+    QueryInput in{};
+    if (!queries->on_device) {
+        for (int c = 0; c < 8; c++) {
+            TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, cudaMemcpyHostToDevice, stream));
+            in.c[c] = w.in_cols[c];
+        }
+        TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, cudaMemcpyHostToDevice, stream));
+        in.seg_id = w.in_seg;
+    } else {
+        for (int c = 0; c < 8; c++) in.c[c] = cols[c];
+        in.seg_id = queries->seg_id;
+    }
+    in.d = spec.d;
+    in.t0 = spec.t0;
+    in.t1 = spec.t1;
+    in.d_arr = spec.d_arr;
+    in.t0_arr = spec.t0_arr;
+    in.t1_arr = spec.t1_arr;
+
+    TDQ_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream));
+    TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
+    double *const *pre = w.pre_dev;
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, pre, w.keys, w.vals, w.ctr);
+    const uint64_t ntiles = (nq + kQT - 1) / kQT;
+    if (idx->n > 0) {
+        TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream));
+        BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
+        tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, chunk, w.tile_lo, w.tile_hi,
+                                                                 w.tile_work);
+        TDQ_CUDA(exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream));
+        TDQ_CUDA(cudaGetLastError());
+        const size_t smem = pair_smem_bytes(chunk);
+        static int smem_set = 0;
+        if (smem > 48 * 1024 && smem_set < (int)smem) {
+            TDQ_CUDA(cudaFuncSetAttribute(traj_dist_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            smem_set = (int)smem;
+        }
+        int per_sm = 0;
+        TDQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_search_kernel, kPairThreads, smem));
+        if (per_sm < 1) per_sm = 1;
+        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, chunk};
+        TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
+        traj_dist_search_kernel<<<idx->sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
+        TDQ_CUDA(cudaGetLastError());
+        TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
+    } else {
+        TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
+        TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
+    }
+    TDQ_CUDA(cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream));
+    TDQ_CUDA(cudaEventRecord(w.ev[3], stream));
+    TDQ_CUDA(cudaStreamSynchronize(stream));
+    const DevCounters &h = *w.ctr_host;
+    if (h.error & 1u)
+        return set_error(TDQ_ERR_INVALID,
+                         "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
+                         "NaN window or t0 > t1)");
+    tdq_stats &s = idx->last;
+    s.query_segments = h.valid_queries;
+    s.interactions = h.interactions;
+    s.overlap_pairs = h.overlap_pairs;
+    s.fp64_pairs = h.fp64_pairs;
+    s.results = h.results;
+    s.work_items = h.work_items;
+    // query_prep; with entries: 8 sort passes x 3 kernels, query_gather,
+    // tile_plan, scan, pair kernel
+    s.kernel_launches = idx->n > 0 ? 1 + 24 + 4 : 1;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s.pair_kernel_ms = ms;
+    if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s.total_ms = ms;
+    *count = h.results;
+    return h.results > out.capacity ? TDQ_ERR_OVERFLOW : TDQ_OK;
+}
+
+tdq_status check_scalars(double d, double t0, double t1)
+{
+    if (!(d >= 0.0) || isinf(d)) return set_error(TDQ_ERR_INVALID, "tdq_search: d must be finite and >= 0");
+    if (isnan(t0) || isnan(t1) || t0 > t1) return set_error(TDQ_ERR_INVALID, "tdq_search: invalid window");
+    return TDQ_OK;
+}
+
+tdq_status ensure_results(tdq_index *idx, uint64_t cap)
+{
+    Workspace &w = idx->ws;
+    if (cap <= w.r_cap && w.r_block) return TDQ_OK;
+    cudaFree(w.r_block);
+    w.r_block = nullptr;
+    w.r_cap = 0;
+    if (cudaMalloc(&w.r_block, 4 * cb(cap, 8)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(TDQ_ERR_NOMEM, "tdq_search: result buffer of %llu items", (unsigned long long)cap);
+    }
+    char *p = (char *)w.r_block;
+    w.r.query_seg_id = carve<int64_t>(p, cap);
+    w.r.entry_seg_id = carve<int64_t>(p, cap);
+    w.r.t_enter = carve<double>(p, cap);
+    w.r.t_exit = carve<double>(p, cap);
+    w.r.capacity = cap;
+    w.r_cap = cap;
+    return TDQ_OK;
+}
+
+}  // namespace
+}  // namespace tdq
+
+using namespace tdq;
+
+extern "C" tdq_status tdq_search_device(tdq_index *idx, const tdq_segments *queries, double d, double t0, double t1,
+                                        const tdq_search_params *params, void *stream, const tdq_result_buffer *out,
+                                        uint64_t *count)
+{
+    if (!idx || !queries || !out || !count) return set_error(TDQ_ERR_INVALID, "tdq_search_device: NULL argument");
+    if (!queries->on_device)
+        return set_error(TDQ_ERR_INVALID, "tdq_search_device: queries must be in device memory");
+    if (out->capacity && (!out->query_seg_id || !out->entry_seg_id || !out->t_enter || !out->t_exit))
+        return set_error(TDQ_ERR_INVALID, "tdq_search_device: NULL result array");
+    tdq_status st = check_scalars(d, t0, t1);
+    if (st != TDQ_OK) return st;
+    SearchSpec spec{d, t0, t1, nullptr, nullptr, nullptr};
+    return run_search(idx, queries, spec, params, (cudaStream_t)stream, *out, count);
+}
+
+extern "C" tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries,
+                                                const double *d_per_query, const double *t0_per_query,
+                                                const double *t1_per_query, const tdq_search_params *params,
+                                                void *stream, const tdq_result_buffer *out, uint64_t *count)
+{
+    if (!idx || !queries || !out || !count || !d_per_query || !t0_per_query || !t1_per_query)
+        return set_error(TDQ_ERR_INVALID, "tdq_search_device_batched: NULL argument");
+    if (!queries->on_device)
+        return set_error(TDQ_ERR_INVALID, "tdq_search_device_batched: queries must be in device memory");
+    if (out->capacity && (!out->query_seg_id || !out->entry_seg_id || !out->t_enter || !out->t_exit))
+        return set_error(TDQ_ERR_INVALID, "tdq_search_device_batched: NULL result array");
+    SearchSpec spec{0.0, 0.0, 0.0, d_per_query, t0_per_query, t1_per_query};
+    return run_search(idx, queries, spec, params, (cudaStream_t)stream, *out, count);
+}
+
+extern "C" tdq_status tdq_search(tdq_index *idx, const tdq_segments *queries, double d, double t0, double t1,
+                                 const tdq_search_params *params, void *stream_, tdq_results **out)
+{
+    if (!out) return set_error(TDQ_ERR_INVALID, "tdq_search: out is NULL");
+    *out = nullptr;
+    if (!idx || !queries) return set_error(TDQ_ERR_INVALID, "tdq_search: NULL argument");
+    tdq_status st = check_scalars(d, t0, t1);
+    if (st != TDQ_OK) return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    // Statically sized result buffer, |D| items by default (Sec. 5), grown and
+    // the search re-run when the results do not fit.
+    uint64_t want = idx->ws.r_cap ? idx->ws.r_cap : (idx->n > 65536 ? idx->n : 65536);
+    SearchSpec spec{d, t0, t1, nullptr, nullptr, nullptr};
+    uint64_t count = 0;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        st = ensure_results(idx, want);
+        if (st != TDQ_OK) return st;
+        st = run_search(idx, queries, spec, params, stream, idx->ws.r, &count);
+        if (st != TDQ_ERR_OVERFLOW) break;
+        want = count + count / 8 + 1024;
+    }
+    if (st != TDQ_OK) return st;
+    tdq_results *r = (tdq_results *)calloc(1, sizeof(tdq_results));
+    if (!r) return set_error(TDQ_ERR_NOMEM, "tdq_search: host allocation failed");
+    r->count = count;
+    if (count) {
+        r->query_seg_id = (int64_t *)malloc(count * 8);
+        r->entry_seg_id = (int64_t *)malloc(count * 8);
+        r->t_enter = (double *)malloc(count * 8);
+        r->t_exit = (double *)malloc(count * 8);
+        if (!r->query_seg_id || !r->entry_seg_id || !r->t_enter || !r->t_exit) {
+            tdq_results_free(r);
+            return set_error(TDQ_ERR_NOMEM, "tdq_search: host allocation failed");
+        }
+        const Workspace &w = idx->ws;
+        cudaError_t e = cudaMemcpyAsync(r->query_seg_id, w.r.query_seg_id, count * 8, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->entry_seg_id, w.r.entry_seg_id, count * 8, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r->t_enter, w.r.t_enter, count * 8, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r->t_exit, w.r.t_exit, count * 8, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            tdq_results_free(r);
+            return cuda_error(e, "tdq_search: D2H result copy");
+        }
+    }
+    *out = r;
+    return TDQ_OK;
+}
+
+extern "C" void tdq_results_free(tdq_results *res)
+{
+    if (!res) return;
+    free(res->query_seg_id);
+    free(res->entry_seg_id);
+    free(res->t_enter);
+    free(res->t_exit);
+    free(res);
+}
+
+extern "C" tdq_status tdq_get_stats(const tdq_index *idx, tdq_stats *out)
+{
+    if (!idx || !out) return set_error(TDQ_ERR_INVALID, "tdq_get_stats: NULL argument");
+    *out = idx->last;
+    return TDQ_OK;
+}

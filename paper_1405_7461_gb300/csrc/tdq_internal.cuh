@@ -1,0 +1,162 @@
+// Internal declarations of libtdq (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tdq.h"
+
+namespace tdq {
+
+// ---------------------------------------------------------------------------
+// Time keys.  On GB300 the FP64 pipe issues about two DFMA per clock per SM,
+// sixty times fewer than the integer and FP32 pipes, so every comparison of
+// times (overlap tests, max/min of span ends) is done on 64-bit integer keys
+// whose signed order equals the order of the (finite, non-NaN) doubles.
+// The map is an involution, so the double is recovered exactly.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t key_from_bits(int64_t b)
+{
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ int64_t okey(double x)
+{
+    int64_t b = __double_as_longlong(x);
+    if (b == (int64_t)0x8000000000000000ULL) b = 0;  // -0.0 sorts with +0.0
+    return key_from_bits(b);
+}
+
+__device__ __forceinline__ double key_double(int64_t k)
+{
+    return __longlong_as_double(key_from_bits(k));
+}
+
+// Unsigned radix key with the same order as okey.
+__device__ __forceinline__ uint64_t ukey(double x)
+{
+    return (uint64_t)okey(x) ^ 0x8000000000000000ULL;
+}
+
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
+// Sign tests on the bit pattern (integer pipe).  NaN never reaches them.
+__device__ __forceinline__ bool le0(double x)  // x <= 0
+{
+    return __double_as_longlong(x) <= 0 || __double_as_longlong(x) == (int64_t)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool gt0(double x) { return !le0(x); }  // x > 0
+__device__ __forceinline__ bool lt0(double x)  // x < 0
+{
+    int64_t b = __double_as_longlong(x);
+    return b < 0 && b != (int64_t)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool ge0(double x) { return !lt0(x); }  // x >= 0
+
+// ---------------------------------------------------------------------------
+// Device-side counters of one search, cleared by one memset per search.
+// ---------------------------------------------------------------------------
+struct DevCounters {
+    unsigned long long results;        // appended result items (may exceed capacity)
+    unsigned long long work_next;      // dynamic work-item dispenser of the pair kernel
+    unsigned long long interactions;
+    unsigned long long overlap_pairs;
+    unsigned long long fp64_pairs;
+    unsigned long long valid_queries;  // query segments with a non-empty clipped span
+    unsigned long long work_items;
+    unsigned int error;                // bit 0: invalid query input
+    unsigned int pad;
+};
+
+// Sorted entry segments in device memory (structure of arrays).
+struct EntrySoA {
+    double *px, *py, *pz;  // position at t_start
+    double *vx, *vy, *vz;  // velocity (end - start) / (t_end - t_start)
+    int64_t *ts_key, *te_key;
+    int64_t *seg_id, *traj_id, *orig;
+};
+
+// Sorted, clipped query segments in device memory.
+struct QuerySoA {
+    double *px, *py, *pz;  // position at the clipped start
+    double *vx, *vy, *vz;
+    double *d2;            // squared threshold
+    int64_t *ts_key, *te_key;  // clipped span [max(ts,t0), min(te,t1)]
+    int64_t *qid;          // caller's segment id
+    int64_t *lo, *hi;      // candidate range of sorted entry positions
+};
+
+struct Workspace {
+    uint64_t q_cap = 0;    // queries the buffers below hold
+    void *q_block = nullptr;
+    // host-query staging (8 columns + seg id)
+    double *in_cols[8] = {nullptr};
+    int64_t *in_seg = nullptr;
+    // per-query arrays before sorting
+    double *pre[9] = {nullptr};  // px,py,pz,vx,vy,vz,d2,ts',te'
+    double **pre_dev = nullptr;  // device copy of pre[]
+    uint64_t *keys = nullptr, *keys_alt = nullptr;
+    uint32_t *vals = nullptr, *vals_alt = nullptr;
+    QuerySoA q{};
+    // tiles
+    uint64_t t_cap = 0;
+    void *t_block = nullptr;
+    int64_t *tile_lo = nullptr, *tile_hi = nullptr;
+    unsigned long long *tile_work = nullptr;  // chunks per tile, then exclusive offsets (t_cap+1)
+    // sort scratch
+    uint64_t s_cap = 0;
+    uint32_t *sort_hist = nullptr;
+    // counters + host mirror
+    DevCounters *ctr = nullptr;
+    DevCounters *ctr_host = nullptr;  // pinned
+    // results owned by tdq_search (device)
+    uint64_t r_cap = 0;
+    void *r_block = nullptr;
+    tdq_result_buffer r{};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+}  // namespace tdq
+
+struct tdq_index {
+    int device = 0;
+    int sm_count = 0;
+    uint64_t n = 0;
+    uint32_t m = 0;
+    double t_min = 0.0, t_max = 0.0, width = 0.0;
+    void *e_block = nullptr;
+    tdq::EntrySoA e{};
+    void *b_block = nullptr;
+    int64_t *bin_begin = nullptr;   // m + 1 sorted positions
+    int64_t *bin_end_key = nullptr; // m, largest t_end key (INT64_MIN when empty)
+    int64_t *bin_pmax_key = nullptr;// m, prefix max of bin_end_key
+    tdq::Workspace ws;
+    tdq_stats last{};
+};
+
+namespace tdq {
+
+// Error reporting (api.cu).
+tdq_status set_error(tdq_status st, const char *fmt, ...);
+tdq_status cuda_error(cudaError_t e, const char *what);
+#define TDQ_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return ::tdq::cuda_error(_e, #call); \
+    } while (0)
+
+// Radix sort (sort.cu): stable ascending sort of (keys, vals) of length n.
+// keys_alt/vals_alt are scratch of the same size; hist holds
+// sort_hist_words(n) words.  The sorted data ends in keys/vals.
+uint64_t sort_hist_words(uint64_t n);
+cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
+                             uint32_t *hist, cudaStream_t stream);
+
+// Single-block exclusive scan of n counters in place; total written to *total.
+cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,
+                               cudaStream_t stream);
+
+}  // namespace tdq

@@ -1,0 +1,380 @@
+"""Thin ctypes binding of the libtdq C ABI (include/tdq.h).
+
+Argument marshalling only: every step of the search runs in the CUDA library.
+PyTorch is used for device memory and streams (device-resident inputs and the
+caller's result buffers are torch CUDA tensors); host inputs are numpy arrays.
+Names follow the C functions: build_index, search, search_device,
+search_device_batched, get_stats, index_bins, last_error, version.
+
+The library must be built (``paper_1405_7461_gb300.build.build()``); importing
+this module without it raises, there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .workloads import COLUMNS, Segments
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdq.so")
+
+TDQ_OK = 0
+TDQ_ERR_INVALID = 1
+TDQ_ERR_NOMEM = 2
+TDQ_ERR_CUDA = 3
+TDQ_ERR_TIMEOUT = 4
+TDQ_ERR_OVERFLOW = 5
+STATUS_NAMES = {0: "TDQ_OK", 1: "TDQ_ERR_INVALID", 2: "TDQ_ERR_NOMEM", 3: "TDQ_ERR_CUDA",
+                4: "TDQ_ERR_TIMEOUT", 5: "TDQ_ERR_OVERFLOW"}
+MODE_FP64 = 0
+MODE_FP32_FILTER = 1
+
+c_dbl_p = ctypes.c_void_p
+
+
+class tdq_segments(ctypes.Structure):
+    _fields_ = [(c, ctypes.c_void_p) for c in COLUMNS] + [
+        ("seg_id", ctypes.c_void_p), ("traj_id", ctypes.c_void_p), ("n", ctypes.c_uint64),
+        ("on_device", ctypes.c_int)]
+
+
+class tdq_index_params(ctypes.Structure):
+    _fields_ = [("bin_count", ctypes.c_uint32)]
+
+
+class tdq_search_params(ctypes.Structure):
+    _fields_ = [("query_tile", ctypes.c_uint32), ("entry_chunk", ctypes.c_uint32), ("mode", ctypes.c_int)]
+
+
+class tdq_results(ctypes.Structure):
+    _fields_ = [("query_seg_id", ctypes.c_void_p), ("entry_seg_id", ctypes.c_void_p), ("t_enter", ctypes.c_void_p),
+                ("t_exit", ctypes.c_void_p), ("count", ctypes.c_uint64)]
+
+
+class tdq_result_buffer(ctypes.Structure):
+    _fields_ = [("query_seg_id", ctypes.c_void_p), ("entry_seg_id", ctypes.c_void_p), ("t_enter", ctypes.c_void_p),
+                ("t_exit", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+class tdq_stats(ctypes.Structure):
+    _fields_ = [("query_segments", ctypes.c_uint64), ("interactions", ctypes.c_uint64),
+                ("overlap_pairs", ctypes.c_uint64), ("fp64_pairs", ctypes.c_uint64), ("results", ctypes.c_uint64),
+                ("work_items", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("pair_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Every symbol include/tdq.h declares, with (restype, argtypes).
+P = ctypes.c_void_p
+SIGNATURES = {
+    "tdq_build_index": (ctypes.c_int, [P, P, P, P]),
+    "tdq_index_free": (None, [P]),
+    "tdq_index_size": (ctypes.c_uint64, [P]),
+    "tdq_index_bins": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
+    "tdq_search": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P]),
+    "tdq_results_free": (None, [P]),
+    "tdq_search_device": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P]),
+    "tdq_search_device_batched": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
+    "tdq_get_stats": (ctypes.c_int, [P, P]),
+    "tdq_last_error": (ctypes.c_char_p, []),
+    "tdq_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtdq.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtdq.so not found at {path}: build it with paper_1405_7461_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class TdqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def last_error() -> str:
+    return load().tdq_last_error().decode()
+
+
+def version() -> str:
+    return load().tdq_version().decode()
+
+
+def _check(st):
+    if st != TDQ_OK:
+        raise TdqError(st, last_error())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+# --------------------------------------------------------------------------
+# Segment marshalling
+# --------------------------------------------------------------------------
+
+class HostSegments:
+    """Host (numpy) columns of a segment set, kept alive for the call."""
+
+    def __init__(self, seg: Segments):
+        self.cols = [np.ascontiguousarray(getattr(seg, c), dtype=np.float64) for c in COLUMNS]
+        self.seg_id = np.ascontiguousarray(seg.seg_id, dtype=np.int64)
+        self.traj_id = np.ascontiguousarray(seg.traj_id, dtype=np.int64)
+        self.n = len(self.cols[0])
+
+    def struct(self) -> tdq_segments:
+        s = tdq_segments()
+        for c, a in zip(COLUMNS, self.cols):
+            setattr(s, c, a.ctypes.data)
+        s.seg_id = self.seg_id.ctypes.data
+        s.traj_id = self.traj_id.ctypes.data
+        s.n = self.n
+        s.on_device = 0
+        return s
+
+
+class DeviceSegments:
+    """Device (torch CUDA tensor) columns of a segment set."""
+
+    def __init__(self, seg: Segments | None = None, device="cuda", tensors=None):
+        import torch
+
+        if tensors is not None:
+            self.cols, self.seg_id, self.traj_id = tensors
+        else:
+            self.cols = [torch.from_numpy(np.ascontiguousarray(getattr(seg, c), np.float64)).to(device)
+                         for c in COLUMNS]
+            self.seg_id = torch.from_numpy(np.ascontiguousarray(seg.seg_id, np.int64)).to(device)
+            self.traj_id = torch.from_numpy(np.ascontiguousarray(seg.traj_id, np.int64)).to(device)
+        self.n = int(self.cols[0].shape[0])
+
+    def struct(self) -> tdq_segments:
+        s = tdq_segments()
+        for c, a in zip(COLUMNS, self.cols):
+            assert a.is_cuda and a.is_contiguous()
+            setattr(s, c, a.data_ptr() if self.n else None)
+        s.seg_id = self.seg_id.data_ptr() if self.n else None
+        s.traj_id = self.traj_id.data_ptr() if self.n else None
+        s.n = self.n
+        s.on_device = 1
+        return s
+
+    @property
+    def nbytes(self):
+        return sum(c.numel() * 8 for c in self.cols) + 16 * self.n
+
+
+def _segments(seg):
+    if isinstance(seg, (HostSegments, DeviceSegments)):
+        return seg
+    if isinstance(seg, Segments):
+        return HostSegments(seg)
+    raise TypeError(f"expected Segments, HostSegments or DeviceSegments, got {type(seg)}")
+
+
+def _params(query_tile=0, entry_chunk=0, mode=MODE_FP64):
+    p = tdq_search_params()
+    p.query_tile = query_tile
+    p.entry_chunk = entry_chunk
+    p.mode = mode
+    return p
+
+
+# --------------------------------------------------------------------------
+# Index
+# --------------------------------------------------------------------------
+
+class Index:
+    """Owner of a tdq_index handle."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("index has been freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            load().tdq_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.free()
+
+
+def build_index(entries, bin_count: int = 0, stream=None) -> Index:
+    """tdq_build_index: temporal-bin index over the entry segments."""
+    lib = load()
+    seg = _segments(entries)
+    s = seg.struct()
+    prm = tdq_index_params(bin_count)
+    h = ctypes.c_void_p()
+    _check(lib.tdq_build_index(ctypes.byref(s), ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(h)))
+    return Index(h.value, seg.n)
+
+
+def index_size(idx: Index) -> int:
+    return int(load().tdq_index_size(idx.handle))
+
+
+def index_bins(idx: Index, with_order: bool = False):
+    """tdq_index_bins: the bin table (start, end, first, last) and bin width."""
+    lib = load()
+    m = ctypes.c_uint32()
+    width = ctypes.c_double()
+    tmin = ctypes.c_double()
+    _check(lib.tdq_index_bins(idx.handle, ctypes.byref(m), None, None, None, None, None, None, None))
+    mm = m.value
+    bs = np.empty(mm, np.float64)
+    be = np.empty(mm, np.float64)
+    bf = np.empty(mm, np.int64)
+    bl = np.empty(mm, np.int64)
+    order = np.empty(idx.n, np.int64) if with_order else None
+    _check(lib.tdq_index_bins(idx.handle, ctypes.byref(m), ctypes.byref(width), ctypes.byref(tmin), bs.ctypes.data,
+                              be.ctypes.data, bf.ctypes.data, bl.ctypes.data,
+                              order.ctypes.data if with_order and idx.n else None))
+    out = {"m": mm, "width": width.value, "t_min": tmin.value, "start": bs, "end": be, "first": bf, "last": bl}
+    if with_order:
+        out["order"] = order
+    return out
+
+
+@dataclass
+class Results:
+    query_seg_id: np.ndarray
+    entry_seg_id: np.ndarray
+    t_enter: np.ndarray
+    t_exit: np.ndarray
+
+    def __len__(self):
+        return len(self.query_seg_id)
+
+
+def search(idx: Index, queries, d: float, t0: float = -np.inf, t1: float = np.inf, stream=None,
+           **params) -> Results:
+    """tdq_search: results copied to host memory (the library retries on overflow)."""
+    lib = load()
+    q = _segments(queries)
+    s = q.struct()
+    prm = _params(**params)
+    out = ctypes.POINTER(tdq_results)()
+    _check(lib.tdq_search(idx.handle, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(prm),
+                          _stream_ptr(stream), ctypes.byref(out)))
+    try:
+        r = out.contents
+        n = int(r.count)
+
+        def arr(ptr, dt):
+            if n == 0:
+                return np.empty(0, dt)
+            buf = (ctypes.c_char * (n * 8)).from_address(ptr)
+            return np.frombuffer(buf, dtype=dt).copy()
+
+        res = Results(arr(r.query_seg_id, np.int64), arr(r.entry_seg_id, np.int64), arr(r.t_enter, np.float64),
+                      arr(r.t_exit, np.float64))
+    finally:
+        lib.tdq_results_free(out)
+    return res
+
+
+class DeviceResultBuffer:
+    """Caller-owned device result buffer (torch tensors)."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        import torch
+
+        self.capacity = int(capacity)
+        self.query_seg_id = torch.empty(max(1, capacity), dtype=torch.int64, device=device)
+        self.entry_seg_id = torch.empty(max(1, capacity), dtype=torch.int64, device=device)
+        self.t_enter = torch.empty(max(1, capacity), dtype=torch.float64, device=device)
+        self.t_exit = torch.empty(max(1, capacity), dtype=torch.float64, device=device)
+
+    def struct(self) -> tdq_result_buffer:
+        b = tdq_result_buffer()
+        b.query_seg_id = self.query_seg_id.data_ptr()
+        b.entry_seg_id = self.entry_seg_id.data_ptr()
+        b.t_enter = self.t_enter.data_ptr()
+        b.t_exit = self.t_exit.data_ptr()
+        b.capacity = self.capacity
+        return b
+
+    def to_host(self, count: int) -> Results:
+        count = min(count, self.capacity)
+        return Results(self.query_seg_id[:count].cpu().numpy(), self.entry_seg_id[:count].cpu().numpy(),
+                       self.t_enter[:count].cpu().numpy(), self.t_exit[:count].cpu().numpy())
+
+
+def search_device(idx: Index, queries: DeviceSegments, d: float, t0: float, t1: float,
+                  out: DeviceResultBuffer, stream=None, allow_overflow=False, **params) -> int:
+    """tdq_search_device: returns the result count (raises on overflow unless allowed)."""
+    lib = load()
+    s = queries.struct()
+    prm = _params(**params)
+    b = out.struct()
+    cnt = ctypes.c_uint64()
+    st = lib.tdq_search_device(idx.handle, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(prm),
+                               _stream_ptr(stream), ctypes.byref(b), ctypes.byref(cnt))
+    if st == TDQ_ERR_OVERFLOW and allow_overflow:
+        return int(cnt.value)
+    _check(st)
+    return int(cnt.value)
+
+
+def search_device_batched(idx: Index, queries: DeviceSegments, d_per_query, t0_per_query, t1_per_query,
+                          out: DeviceResultBuffer, stream=None, allow_overflow=False, **params) -> int:
+    """tdq_search_device_batched: per-query-segment d and window (torch CUDA float64 tensors)."""
+    lib = load()
+    s = queries.struct()
+    prm = _params(**params)
+    b = out.struct()
+    cnt = ctypes.c_uint64()
+    for t in (d_per_query, t0_per_query, t1_per_query):
+        assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()
+    st = lib.tdq_search_device_batched(idx.handle, ctypes.byref(s), d_per_query.data_ptr(), t0_per_query.data_ptr(),
+                                       t1_per_query.data_ptr(), ctypes.byref(prm), _stream_ptr(stream),
+                                       ctypes.byref(b), ctypes.byref(cnt))
+    if st == TDQ_ERR_OVERFLOW and allow_overflow:
+        return int(cnt.value)
+    _check(st)
+    return int(cnt.value)
+
+
+def get_stats(idx: Index) -> dict:
+    st = tdq_stats()
+    _check(load().tdq_get_stats(idx.handle, ctypes.byref(st)))
+    return st.as_dict()

@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Pair sets must be identical except for ties (pairs whose distance of closest
+approach is within 1e-9*d of d); matched interval endpoints agree to 1e-9
+relative (or, where a root is ill-conditioned, the reported time is still at
+distance d within the same band)."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1405_7461_gb300 import workloads
+from tests._util import compare_results, read_golden
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def tdq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7461_gb300 import build, tdq as t
+
+    build.build()
+    t.load()
+    return t
+
+
+def _positions(ids, pool):
+    order = np.argsort(pool, kind="stable")
+    pos = np.searchsorted(pool[order], ids)
+    assert np.all(pool[order][pos] == ids)
+    return order[pos]
+
+
+def gpu_as_index(res, entries, queries):
+    return {"qi": _positions(res.query_seg_id, queries.seg_id), "ei": _positions(res.entry_seg_id, entries.seg_id),
+            "t_enter": res.t_enter, "t_exit": res.t_exit}
+
+
+def oracle_as_dict(r):
+    return {"qi": r.query_index, "ei": r.entry_index, "t_enter": r.t_enter, "t_exit": r.t_exit}
+
+
+def check(tdq, entries, queries, d, t0=-np.inf, t1=np.inf, bin_count=0, brute=False, idx=None, **params):
+    own = idx is None
+    if own:
+        idx = tdq.build_index(entries, bin_count=bin_count)
+    try:
+        res = tdq.search(idx, queries, d, t0, t1, **params)
+        stats = tdq.get_stats(idx)
+    finally:
+        if own:
+            idx.free()
+    ref = (oracle.search_bruteforce if brute else oracle.search_sweep)(entries, queries, d, t0, t1)
+    cmp = compare_results(gpu_as_index(res, entries, queries), oracle_as_dict(ref), entries, queries, d, t0, t1,
+                          dmin_fn=lambda ei, qi: oracle.pair_dmin(entries, ei, queries, qi, t0, t1))
+    # the temporal-overlap count is exact integer work: identical
+    assert stats["overlap_pairs"] == ref.overlap_pairs
+    assert stats["interactions"] >= stats["overlap_pairs"] >= stats["results"] == len(res)
+    return res, ref, stats, cmp
+
+
+# --------------------------------------------------------------------------
+# Index (Sec. 4, Fig. 1)
+# --------------------------------------------------------------------------
+
+def test_fig1_bin_table_on_gpu(tdq):
+    g = read_golden("fig1_bins.txt")
+    s = np.array(g["segments"])
+    n = len(s)
+    rng = np.random.default_rng(1)
+    p0 = rng.uniform(0, 1, (n, 3))
+    p1 = rng.uniform(0, 1, (n, 3))
+    # present the segments in a shuffled order: the index must sort them
+    perm = rng.permutation(n)
+    seg = workloads.Segments(p0[perm, 0], p0[perm, 1], p0[perm, 2], s[perm, 1], p1[perm, 0], p1[perm, 1],
+                             p1[perm, 2], s[perm, 2], s[perm, 0].astype(np.int64), np.zeros(n, np.int64))
+    with tdq.build_index(seg, bin_count=4) as idx:
+        bt = tdq.index_bins(idx, with_order=True)
+    assert bt["width"] == 3.0 and bt["t_min"] == 0.0
+    assert np.array_equal(seg.seg_id[bt["order"]], s[:, 0].astype(np.int64))
+    for j, bstart, bend, bfirst, blast in g["bins"]:
+        j = int(j)
+        assert (bt["start"][j], bt["end"][j], bt["first"][j], bt["last"][j]) == (bstart, bend, int(bfirst),
+                                                                                 int(blast))
+
+
+def test_bin_table_matches_oracle_on_random_data(tdq):
+    rng = np.random.default_rng(2)
+    seg = workloads.random_segments(rng, 5000, t_span=50.0, max_dur=4.0)
+    for m in (1, 7, 100, 4096):
+        with tdq.build_index(seg, bin_count=m) as idx:
+            bt = tdq.index_bins(idx, with_order=True)
+        ref = oracle.bin_table(seg.ts, seg.te, m)
+        assert np.array_equal(bt["order"], ref["order"])
+        assert bt["width"] == ref["width"]
+        assert np.array_equal(bt["first"], ref["first"])
+        assert np.array_equal(bt["last"], ref["last"])
+        ne = ref["first"] >= 0
+        assert np.array_equal(bt["start"][ne], ref["start"][ne])
+        assert np.array_equal(bt["end"][ne], ref["end"][ne])
+
+
+# --------------------------------------------------------------------------
+# Parity on the workloads
+# --------------------------------------------------------------------------
+
+def test_tiny_random_walk_parity(tdq):
+    w = workloads.tiny_random_walk()
+    res, ref, stats, cmp = check(tdq, w.entries, w.queries, 5.0, *w.window, brute=True)
+    assert cmp["matched"] == len(ref.query_index) > len(w.queries)
+    assert stats["overlap_pairs"] == 20 * 99 * 200
+
+
+@pytest.mark.parametrize("seed,n,nq,chunk", [(3, 1, 1, 0), (4, 31, 33, 256), (5, 257, 65, 512), (6, 1000, 100, 2048),
+                                              (7, 5000, 97, 1024), (8, 3000, 300, 256)])
+def test_random_sets_ragged(tdq, seed, n, nq, chunk):
+    rng = np.random.default_rng(seed)
+    ent = workloads.random_segments(rng, n, box=8.0, t_span=20.0, max_dur=3.0)
+    qry = workloads.random_segments(rng, nq, box=8.0, t_span=20.0, max_dur=3.0)
+    qry.seg_id += 10 ** 9
+    for d, win in ((1.5, (-np.inf, np.inf)), (0.7, (3.25, 14.5)), (4.0, (0.0, 5.0))):
+        check(tdq, ent, qry, d, *win, bin_count=int(rng.integers(1, 300)), brute=True, entry_chunk=chunk)
+
+
+def test_scale_random_walk_reduced(tdq):
+    w = workloads.scale_random_walk(n_traj=1500, n_queries=25)
+    with tdq.build_index(w.entries) as idx:
+        for d in w.d_values:
+            check(tdq, w.entries, w.queries, d, *w.window, idx=idx)
+
+
+def test_scale_random_walk_full_size(tdq):
+    """The benchmark workload at full size (10,000 walks, 100 queries) in the
+    launch configuration the benchmark times, every d, every pair."""
+    w = workloads.scale_random_walk()
+    with tdq.build_index(w.entries) as idx:
+        for d in w.d_values:
+            res, ref, stats, cmp = check(tdq, w.entries, w.queries, d, *w.window, idx=idx)
+            assert stats["overlap_pairs"] > 1e8
+
+
+def test_galaxy_disk_near_tangent(tdq):
+    w = workloads.galaxy_disk(n_stars=3000, n_queries=30)
+    with tdq.build_index(w.entries) as idx:
+        for d in w.d_values:
+            check(tdq, w.entries, w.queries, d, *w.window, idx=idx)
+
+
+def test_galaxy_disk_full_size_sampled(tdq):
+    """Full-size galaxy database (9.95 M segments); a seeded sample of query
+    trajectories is checked pair by pair against the oracle."""
+    w = workloads.galaxy_disk()
+    rng = np.random.default_rng(5)
+    keep = rng.choice(np.unique(w.queries.traj_id), size=6, replace=False)
+    q = w.queries.take(np.nonzero(np.isin(w.queries.traj_id, keep))[0])
+    with tdq.build_index(w.entries) as idx:
+        for d in w.d_values:
+            check(tdq, w.entries, q, d, *w.window, idx=idx)
+
+
+def test_batched_per_query_threshold_and_window(tdq):
+    w = workloads.batching_walks(n_traj=400, n_queries=60)
+    q = w.queries
+    qdev = tdq.DeviceSegments(q)
+    dd = torch.from_numpy(w.q_d).cuda()
+    t0 = torch.from_numpy(w.q_t0).cuda()
+    t1 = torch.from_numpy(w.q_t1).cuda()
+    buf = tdq.DeviceResultBuffer(1 << 18)
+    with tdq.build_index(w.entries, bin_count=3000) as idx:
+        cnt = tdq.search_device_batched(idx, qdev, dd, t0, t1, buf)
+        res = buf.to_host(cnt)
+    got = gpu_as_index(res, w.entries, q)
+    # oracle: one search per query trajectory with its own d and window
+    parts = {k: [] for k in ("qi", "ei", "t_enter", "t_exit")}
+    for tj in np.unique(q.traj_id):
+        sel = np.nonzero(q.traj_id == tj)[0]
+        r = oracle.search_sweep(w.entries, q.take(sel), w.q_d[sel[0]], w.q_t0[sel[0]], w.q_t1[sel[0]])
+        parts["qi"].append(sel[r.query_index])
+        parts["ei"].append(r.entry_index)
+        parts["t_enter"].append(r.t_enter)
+        parts["t_exit"].append(r.t_exit)
+    ref = {k: np.concatenate(v) for k, v in parts.items()}
+    dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, q, qi, w.q_t0[qi], w.q_t1[qi])  # noqa: E731
+    cmp = compare_results(got, ref, w.entries, q, None, dmin_fn=dmin, d_per_query=w.q_d)
+    assert cmp["matched"] > 0
+
+
+# --------------------------------------------------------------------------
+# Edge cases and the boundary's error behaviour
+# --------------------------------------------------------------------------
+
+def _segs(rows, ids=None):
+    a = np.array(rows, np.float64).reshape(-1, 8)
+    return workloads.Segments.from_columns([a[:, k] for k in range(8)], seg_id=ids)
+
+
+def test_empty_inputs(tdq):
+    rng = np.random.default_rng(9)
+    ent = workloads.random_segments(rng, 100)
+    empty = workloads.random_segments(rng, 0)
+    with tdq.build_index(ent) as idx:
+        assert len(tdq.search(idx, empty, 1.0)) == 0
+    with tdq.build_index(empty) as idx:
+        assert tdq.index_size(idx) == 0
+        assert len(tdq.search(idx, ent, 1.0)) == 0
+
+
+def test_window_outside_data_and_touching_segments(tdq):
+    rng = np.random.default_rng(10)
+    ent = workloads.random_segments(rng, 500, t_span=10.0)
+    with tdq.build_index(ent) as idx:
+        assert len(tdq.search(idx, ent, 100.0, 50.0, 60.0)) == 0
+        assert len(tdq.search(idx, ent, 100.0, 3.0, 3.0)) == 0  # zero-length window
+    # a walk's own consecutive segments touch only at instants
+    e = _segs([[0, 0, 0, 0, 1, 0, 0, 1], [1, 0, 0, 1, 2, 0, 0, 2]])
+    q = _segs([[1, 0, 0, 1, 2, 0, 0, 2]], ids=[77])
+    with tdq.build_index(e) as idx:
+        r = tdq.search(idx, q, 5.0)
+    assert r.entry_seg_id.tolist() == [1] and (r.t_enter[0], r.t_exit[0]) == (1.0, 2.0)
+
+
+def test_zero_threshold_self_match_and_duplicates(tdq):
+    w = workloads.tiny_random_walk(n_traj=30, n_points=20, n_queries=3)
+    e = workloads.Segments.concat([w.entries, w.entries.take(np.arange(len(w.entries)))])
+    e.seg_id = np.arange(len(e), dtype=np.int64)
+    res, ref, stats, cmp = check(tdq, e, w.queries, 0.0, brute=True)
+    # each query segment matches itself and its duplicate, over its whole extent
+    assert len(res) >= 2 * len(w.queries)
+
+
+def test_invalid_inputs_are_rejected(tdq):
+    rng = np.random.default_rng(12)
+    ent = workloads.random_segments(rng, 50)
+    bad = workloads.random_segments(rng, 50)
+    bad.te[7] = bad.ts[7]
+    with pytest.raises(tdq.TdqError) as ei:
+        tdq.build_index(bad)
+    assert ei.value.status == tdq.TDQ_ERR_INVALID
+    nanq = workloads.random_segments(rng, 40)
+    nanq.xs[3] = np.nan
+    with tdq.build_index(ent) as idx:
+        for args in ((nanq, 1.0), (ent, -1.0), (ent, np.nan), (ent, np.inf)):
+            with pytest.raises(tdq.TdqError) as ei:
+                tdq.search(idx, *args)
+            assert ei.value.status == tdq.TDQ_ERR_INVALID
+        with pytest.raises(tdq.TdqError):
+            tdq.search(idx, ent, 1.0, 5.0, 2.0)
+        # the index is still usable after rejected calls
+        assert len(tdq.search(idx, ent, 1.0)) >= len(ent)
+
+
+def test_result_overflow_and_retry(tdq):
+    """A cluster where every pair is in range: the device call reports the
+    needed size, and the host call grows its buffer and re-runs (Sec. 5)."""
+    rng = np.random.default_rng(13)
+    n, nq = 3000, 40
+    ent = workloads.random_segments(rng, n, box=0.1, t_span=0.5, max_dur=20.0, max_speed=0.01)
+    qry = workloads.random_segments(rng, nq, box=0.1, t_span=0.5, max_dur=20.0, max_speed=0.01)
+    qry.seg_id += 10 ** 6
+    need = n * nq
+    with tdq.build_index(ent) as idx:
+        qd = tdq.DeviceSegments(qry)
+        small = tdq.DeviceResultBuffer(1)
+        cnt = tdq.search_device(idx, qd, 5.0, -np.inf, np.inf, small, allow_overflow=True)
+        assert cnt == need
+        with pytest.raises(tdq.TdqError) as ei:
+            tdq.search_device(idx, qd, 5.0, -np.inf, np.inf, small)
+        assert ei.value.status == tdq.TDQ_ERR_OVERFLOW
+        res = tdq.search(idx, qry, 5.0)  # internal buffer starts at 65,536 < 120,000 items
+        assert len(res) == need
+        big = tdq.DeviceResultBuffer(need)
+        cnt = tdq.search_device(idx, qd, 5.0, -np.inf, np.inf, big)
+        r2 = big.to_host(cnt)
+    k1 = np.sort(res.query_seg_id * (1 << 32) + res.entry_seg_id)
+    k2 = np.sort(r2.query_seg_id * (1 << 32) + r2.entry_seg_id)
+    assert np.array_equal(k1, k2)
+
+
+def test_host_and_device_calls_agree(tdq):
+    w = workloads.scale_random_walk(n_traj=800, n_queries=10)
+    with tdq.build_index(tdq.DeviceSegments(w.entries)) as idx:
+        a = tdq.search(idx, w.queries, 15.0, *w.window)
+        buf = tdq.DeviceResultBuffer(len(a) + 10)
+        cnt = tdq.search_device(idx, tdq.DeviceSegments(w.queries), 15.0, *w.window, buf)
+        b = buf.to_host(cnt)
+    oa = np.lexsort((a.entry_seg_id, a.query_seg_id))
+    ob = np.lexsort((b.entry_seg_id, b.query_seg_id))
+    for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit"):
+        assert np.array_equal(getattr(a, f)[oa], getattr(b, f)[ob])
