@@ -46,7 +46,7 @@ from paper_1405_7461_gb300 import workloads  # noqa: E402
 FLOPS_PER_PAIR_FP64 = 32
 # FP64 peak from the unit counts and clocks: 2 DFMA per clock per SM x 2
 # flops x 152 SMs x 2070 MHz (the 1.25 TFLOP/s nominal figure).
-FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070e3
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
 CPU_SAMPLE_QUERIES = 20
 
 

@@ -219,16 +219,16 @@ def _exp_isotropic_steps(rng, n):
     return u * rng.exponential(1.0, size=(n, 1))
 
 
-def batching_walks(seed=DEFAULT_SEED, n_traj=20_000, n_points=300, n_queries=5_000) -> Workload:
+def batching_walks(seed=DEFAULT_SEED, n_traj=20_000, n_points=300, n_queries=5_000, box=1000.0) -> Workload:
     """Entry database: 20,000 walks x 300 points (t=0..299), isotropic step
     direction with exponential length (mean 1), start uniform in [0,1000]^3
     (5.98 M segments).  5,000 fresh query walks: length lognormal(ln 63.2,
     0.94) segments clipped to [10,400], start time uniform integer in
     [0, 300-len], own window [t0,t1] drawn uniformly inside its extent, own d
-    uniform in [0.5,10]."""
+    uniform in [0.5,10].  `box` is the edge of the start cube (1000)."""
     rng = np.random.default_rng(seed)
     counts = np.full(n_traj, n_points, np.int64)
-    starts = rng.uniform(0.0, 1000.0, size=(n_traj, 3))
+    starts = rng.uniform(0.0, box, size=(n_traj, 3))
     pts = _walk_points(starts, counts, _exp_isotropic_steps(rng, int(counts.sum())))
     ent = polylines_to_segments(pts, _unit_times(np.zeros(n_traj), counts), counts, np.arange(n_traj))
 
@@ -236,7 +236,7 @@ def batching_walks(seed=DEFAULT_SEED, n_traj=20_000, n_points=300, n_queries=5_0
                    min(400, n_points - 1)).astype(np.int64)
     qstart = np.floor(rng.uniform(0.0, 1.0, size=n_queries) * (n_points - 1 - nseg + 1)).astype(np.int64)
     qcounts = nseg + 1
-    qpos = rng.uniform(0.0, 1000.0, size=(n_queries, 3))
+    qpos = rng.uniform(0.0, box, size=(n_queries, 3))
     qpts = _walk_points(qpos, qcounts, _exp_isotropic_steps(rng, int(qcounts.sum())))
     qry = polylines_to_segments(qpts, _unit_times(qstart.astype(np.float64), qcounts), qcounts,
                                 np.arange(n_queries) + 10_000_000, first_seg_id=1 << 40)
