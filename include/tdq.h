@@ -188,6 +188,33 @@ tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries
                                      const tdq_search_params *params, void *stream,
                                      const tdq_result_buffer *out, uint64_t *count);
 
+/*
+ * Allocation-free variant of tdq_search_device.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * at search time -- for example a process whose device memory is already
+ * owned by another allocator (a framework's caching pool), or a
+ * latency-critical loop that cannot afford cudaMalloc/cudaFree, which may
+ * synchronize the whole device.  Build the index beforehand; then this call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * It runs the same kernels as tdq_search_device, with the same arguments,
+ * results and errors, but keeps its per-search scratch in one fixed
+ * file-scope device array of about 1.5 MiB that every device loading the
+ * library holds until the process exits.
+ *  - Limit: at most 8192 query segments per call; more is rejected with
+ *    TDQ_ERR_INVALID and a message naming the limit.
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress) for that device; make that first call before
+ *    any stream capture.
+ *  - Every call on a device shares the one array, which keeps the previous
+ *    call's contents (the call clears what must start at zero).  Calls that
+ *    overlap on the GPU race -- including calls on different indexes or
+ *    different streams of the same device; serialize them.
+ *  - Does not update the index's counters (tdq_get_stats).
+ */
+tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segments *queries, double d, double t0, double t1,
+                                     const tdq_search_params *params, void *stream, const tdq_result_buffer *out,
+                                     uint64_t *count);
+
 /* Counters of the last completed search on idx. */
 tdq_status tdq_get_stats(const tdq_index *idx, tdq_stats *out);
 

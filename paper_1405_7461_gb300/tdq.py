@@ -81,6 +81,8 @@ SIGNATURES = {
     "tdq_results_free": (None, [P]),
     "tdq_search_device": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P]),
     "tdq_search_device_batched": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
+    "tdq_search_device_noalloc": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P,
+                                                 P]),
     "tdq_get_stats": (ctypes.c_int, [P, P]),
     "tdq_last_error": (ctypes.c_char_p, []),
     "tdq_version": (ctypes.c_char_p, []),
@@ -368,6 +370,27 @@ def search_device_batched(idx: Index, queries: DeviceSegments, d_per_query, t0_p
     st = lib.tdq_search_device_batched(idx.handle, ctypes.byref(s), d_per_query.data_ptr(), t0_per_query.data_ptr(),
                                        t1_per_query.data_ptr(), ctypes.byref(prm), _stream_ptr(stream),
                                        ctypes.byref(b), ctypes.byref(cnt))
+    if st == TDQ_ERR_OVERFLOW and allow_overflow:
+        return int(cnt.value)
+    _check(st)
+    return int(cnt.value)
+
+
+NOALLOC_MAX_QUERIES = 8192
+
+
+def search_device_noalloc(idx: Index, queries: DeviceSegments, d: float, t0: float, t1: float,
+                          out: DeviceResultBuffer, stream=None, allow_overflow=False, **params) -> int:
+    """tdq_search_device_noalloc: same as search_device, but the library
+    allocates nothing (scratch in a fixed device array; at most
+    NOALLOC_MAX_QUERIES query segments per call; calls must not overlap)."""
+    lib = load()
+    s = queries.struct()
+    prm = _params(**params)
+    b = out.struct()
+    cnt = ctypes.c_uint64()
+    st = lib.tdq_search_device_noalloc(idx.handle, ctypes.byref(s), float(d), float(t0), float(t1),
+                                       ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(b), ctypes.byref(cnt))
     if st == TDQ_ERR_OVERFLOW and allow_overflow:
         return int(cnt.value)
     _check(st)
