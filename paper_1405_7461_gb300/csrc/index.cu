@@ -33,24 +33,36 @@ struct EntryInput {
     const int64_t *seg_id, *traj_id;
 };
 
-// Validate, and emit the sort key and time range of every entry.
+// Validate, and emit the sort key and time range of every entry.  The time
+// range is reduced per warp before one atomic per warp.
 __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *vals, unsigned int *err,
                            unsigned long long *tmin_key, unsigned long long *tmax_key)
 {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    bool ok = true;
+    unsigned long long kmin = ~0ULL, kmax = 0ULL;
+    if (i < n) {
+        bool ok = true;
 #pragma unroll
-    for (int c = 0; c < 8; c++) ok &= finite_bits(in.c[c][i]);
-    int64_t ks = okey(in.c[3][i]);
-    int64_t ke = okey(in.c[7][i]);
-    ok &= ke > ks;
-    if (!ok) atomicOr(err, 1u);
-    keys[i] = (uint64_t)ks ^ 0x8000000000000000ULL;
-    vals[i] = (uint32_t)i;
-    // time extent as unsigned keys (same order as the doubles)
-    atomicMin(tmin_key, (unsigned long long)((uint64_t)ks ^ 0x8000000000000000ULL));
-    atomicMax(tmax_key, (unsigned long long)((uint64_t)ke ^ 0x8000000000000000ULL));
+        for (int c = 0; c < 8; c++) ok &= finite_bits(in.c[c][i]);
+        int64_t ks = okey(in.c[3][i]);
+        int64_t ke = okey(in.c[7][i]);
+        ok &= ke > ks;
+        if (!ok) atomicOr(err, 1u);
+        keys[i] = (uint64_t)ks ^ 0x8000000000000000ULL;
+        vals[i] = (uint32_t)i;
+        // time extent as unsigned keys (same order as the doubles)
+        kmin = (uint64_t)ks ^ 0x8000000000000000ULL;
+        kmax = (uint64_t)ke ^ 0x8000000000000000ULL;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (kmin != ~0ULL) atomicMin(tmin_key, kmin);
+        if (kmax != 0ULL) atomicMax(tmax_key, kmax);
+    }
 }
 
 __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e)
@@ -72,6 +84,9 @@ __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, E
     e.seg_id[k] = in.seg_id[i];
     e.traj_id[k] = in.traj_id ? in.traj_id[i] : 0;
     e.orig[k] = (int64_t)i;
+    // FP32 bounding sphere: midpoint and half length of the segment
+    double hx = 0.5 * (in.c[4][i] - xs), hy = 0.5 * (in.c[5][i] - ys), hz = 0.5 * (in.c[6][i] - zs);
+    e.sph[k] = sphere32(xs + hx, ys + hy, zs + hz, sqrt(hx * hx + hy * hy + hz * hz), 0.0);
 }
 
 __device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
@@ -215,7 +230,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     }
 
     // Resident sorted copy + bin table.
-    uint64_t ebytes = 11 * carve_bytes(n, 8);
+    uint64_t ebytes = 11 * carve_bytes(n, 8) + carve_bytes(n, 16);
     uint64_t bbytes = carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (cudaMalloc(&idx->e_block, ebytes) != cudaSuccess || cudaMalloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -230,6 +245,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         e.vx = carve<double>(p, n); e.vy = carve<double>(p, n); e.vz = carve<double>(p, n);
         e.ts_key = carve<int64_t>(p, n); e.te_key = carve<int64_t>(p, n);
         e.seg_id = carve<int64_t>(p, n); e.traj_id = carve<int64_t>(p, n); e.orig = carve<int64_t>(p, n);
+        e.sph = carve<float4>(p, n);
         char *q = (char *)idx->b_block;
         idx->bin_begin = carve<int64_t>(q, m + 1);
         idx->bin_end_key = carve<int64_t>(q, m);

@@ -59,8 +59,8 @@ __device__ __forceinline__ bool is_nan_bits(double x)
 
 // Validate and clip every query segment.  pre[] columns: px py pz vx vy vz d2
 // ts_key te_key (keys stored bitwise in the double arrays).
-__global__ void query_prep(QueryInput in, uint64_t nq, double *const *pre, uint64_t *keys, uint32_t *vals,
-                           DevCounters *ctr)
+__global__ void query_prep(QueryInput in, uint64_t nq, double *const *pre, float4 *pre_sph, uint64_t *keys,
+                           uint32_t *vals, DevCounters *ctr)
 {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
@@ -98,6 +98,15 @@ __global__ void query_prep(QueryInput in, uint64_t nq, double *const *pre, uint6
         pre[6][i] = d * d;
         pre[7][i] = __longlong_as_double(cs);
         pre[8][i] = __longlong_as_double(ce);
+        // FP32 bounding sphere of the clipped segment, its radius widened by
+        // d (and a relative 2^-30 of d): the pre-test of the filter mode
+        float4 sp = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+        if (valid) {
+            double h = 0.5 * (key_double(ce) - key_double(cs));
+            double vn = sqrt(vx * vx + vy * vy + vz * vz);
+            sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), vn * h, fma(d, 0x1p-30, d));
+        }
+        pre_sph[i] = sp;
         keys[i] = valid ? ((uint64_t)cs ^ 0x8000000000000000ULL) : ~0ULL;
         vals[i] = (uint32_t)i;
     }
@@ -120,8 +129,8 @@ struct BinView {
 };
 
 // Sorted query SoA and the candidate range of each query segment.
-__global__ void query_gather(const double *const *pre, const int64_t *seg_id, const uint32_t *order, uint64_t nq,
-                             const DevCounters *ctr, BinView bins, QuerySoA q)
+__global__ void query_gather(const double *const *pre, const float4 *pre_sph, const int64_t *seg_id,
+                             const uint32_t *order, uint64_t nq, const DevCounters *ctr, BinView bins, QuerySoA q)
 {
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nq || k >= ctr->valid_queries) return;
@@ -134,6 +143,7 @@ __global__ void query_gather(const double *const *pre, const int64_t *seg_id, co
     q.ts_key[k] = cs;
     q.te_key[k] = ce;
     q.qid[k] = seg_id[i];
+    q.sph[k] = pre_sph[i];
     // First bin whose extent reaches past the query start: the prefix maximum
     // of bin ends is non-decreasing, so this is a binary search (Sec. 4 uses
     // an index tree over the bin extents for the same lookup).
@@ -207,9 +217,11 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r)
 struct PairSmem {
     double qp[3][kQT], qv[3][kQT], qd2[kQT];
     int64_t qts[kQT], qte[kQT], qid[kQT];
+    float4 qsph[kQT];
     long long item;
     long long tile;
-    // followed by the entry chunk: 6 double columns + 2 key columns of `chunk` items
+    // followed by the entry chunk: FP64 mode: 6 double columns + 2 key
+    // columns of `chunk` items; filter mode: 2 key columns + 1 float4 column
 };
 
 struct PairArgs {
@@ -259,16 +271,39 @@ __device__ __noinline__ void pair_interval(double A, double Bh, double C, double
     *tout = thi >= L ? b : (le0(thi) ? a : a + thi);
 }
 
+// Conservative FP32 pre-test: false only if the two bounding spheres (the
+// query's radius already widened by d) are certainly apart.  The squared
+// center distance s is computed with at most four roundings, so s <=
+// (1 + 2^-24)^4 * (exact squared distance of the FP32 centers); the bound
+// R = r_e + (r_q + d) and R^2 are rounded up and scaled by (1 + 2^-20).
+__device__ __forceinline__ bool spheres_may_meet(float4 e, float4 q)
+{
+    float dx = e.x - q.x, dy = e.y - q.y, dz = e.z - q.z;
+    float s2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float R = __fadd_ru(e.w, q.w);
+    float thr = __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-20f);
+    return !(s2 > thr);
+}
+
+// GPUTrajDistSearch (Sec. 5, Algorithm 1), tiled: one work item is a tile of
+// 32 sorted query segments against a chunk of the tile's candidate entries.
+// kFilter = false: every temporal-overlap pair is evaluated in FP64.
+// kFilter = true : a pair is evaluated in FP64 only if it overlaps in time
+//                  and passes the FP32 sphere pre-test.
+template <bool kFilter>
 __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairSmem &S = *reinterpret_cast<PairSmem *>(smem_raw);
     const uint32_t EC = args.chunk;
-    double *ecol = reinterpret_cast<double *>(smem_raw + ((sizeof(PairSmem) + 15) & ~(size_t)15));
+    unsigned char *ebase = smem_raw + ((sizeof(PairSmem) + 15) & ~(size_t)15);
+    // entry chunk columns
+    int64_t *ets = reinterpret_cast<int64_t *>(ebase);
+    int64_t *ete = ets + EC;
+    float4 *esph = reinterpret_cast<float4 *>(ete + EC);                  // filter mode
+    double *ecol = reinterpret_cast<double *>(ete + EC);                  // FP64 mode
     double *epx = ecol, *epy = ecol + EC, *epz = ecol + 2 * EC;
     double *evx = ecol + 3 * EC, *evy = ecol + 4 * EC, *evz = ecol + 5 * EC;
-    int64_t *ets = reinterpret_cast<int64_t *>(ecol + 6 * EC);
-    int64_t *ete = ets + EC;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -277,7 +312,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
     const uint64_t nvalid = ctr->valid_queries;
     const uint64_t cap = args.out.capacity;
 
-    unsigned long long n_inter = 0, n_overlap = 0;
+    unsigned long long n_inter = 0, n_overlap = 0, n_fp64 = 0;
 
     for (;;) {
         if (tid == 0) {
@@ -315,22 +350,29 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 S.qts[tid] = args.q.ts_key[k];
                 S.qte[tid] = args.q.te_key[k];
                 S.qid[tid] = args.q.qid[k];
+                if (kFilter) S.qsph[tid] = args.q.sph[k];
             } else {  // padding: a span that overlaps nothing
                 S.qts[tid] = INT64_MAX;
                 S.qte[tid] = INT64_MIN;
+                if (kFilter) S.qsph[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         // stage the chunk's entry segments (coalesced column loads)
         for (int i = tid; i < (int)EC; i += kPairThreads) {
             if (i < ne) {
                 int64_t k = e0 + i;
-                epx[i] = args.e.px[k]; epy[i] = args.e.py[k]; epz[i] = args.e.pz[k];
-                evx[i] = args.e.vx[k]; evy[i] = args.e.vy[k]; evz[i] = args.e.vz[k];
                 ets[i] = args.e.ts_key[k];
                 ete[i] = args.e.te_key[k];
+                if (kFilter) {
+                    esph[i] = args.e.sph[k];
+                } else {
+                    epx[i] = args.e.px[k]; epy[i] = args.e.py[k]; epz[i] = args.e.pz[k];
+                    evx[i] = args.e.vx[k]; evy[i] = args.e.vy[k]; evz[i] = args.e.vz[k];
+                }
             } else {
                 ets[i] = INT64_MAX;
                 ete[i] = INT64_MIN;
+                if (kFilter) esph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         if (tid == 0) n_inter += (unsigned long long)ne * (unsigned long long)nqt;
@@ -339,14 +381,29 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
         for (int g = 0; g < (int)EC; g += kPairThreads) {
             const int el = g + warp * 32 + lane;
             // temporal intersection of this lane's entry with every query of
-            // the tile, as a 32-bit mask (integer keys: strict overlap a < b)
+            // the tile, as a 32-bit mask (integer keys: strict overlap a < b);
+            // in filter mode a second mask keeps the pairs that also pass the
+            // FP32 sphere pre-test
             const int64_t my_ts = ets[el], my_te = ete[el];
-            unsigned mask = 0;
+            unsigned ovmask = 0, mask = 0;
+            if (kFilter) {
+                const float4 my_sph = esph[el];
 #pragma unroll
-            for (int j = 0; j < kQT; j++) {
-                bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
-                mask |= (unsigned)ov << j;
+                for (int j = 0; j < kQT; j++) {
+                    bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
+                    bool near = spheres_may_meet(my_sph, S.qsph[j]);
+                    ovmask |= (unsigned)ov << j;
+                    mask |= (unsigned)(ov & near) << j;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kQT; j++) {
+                    bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
+                    mask |= (unsigned)ov << j;
+                }
+                ovmask = mask;
             }
+            if (kFilter) n_overlap += (unsigned long long)__popc(ovmask);
             const int cnt = __popc(mask);
             int incl = cnt;
 #pragma unroll
@@ -356,9 +413,12 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
             }
             const int excl = incl - cnt;
             const int npairs = __shfl_sync(kFull, incl, 31);
-            if (lane == 0) n_overlap += (unsigned long long)npairs;
+            if (lane == 0) {
+                if (!kFilter) n_overlap += (unsigned long long)npairs;
+                n_fp64 += (unsigned long long)npairs;
+            }
 
-            // evaluate the overlapping pairs 32 at a time, one per lane
+            // evaluate the selected pairs 32 at a time, one per lane
             for (int base = 0; base < npairs; base += 32) {
                 const int kk = base + lane;
                 const bool active = kk < npairs;
@@ -382,8 +442,15 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 const int64_t b_k = min(ete_k, qte_k);
                 const int64_t o_k = e_later ? qts_k : ets_k;
                 const double a = key_double(a_k), b = key_double(b_k), o_ts = key_double(o_k);
-                const double epx_ = epx[ei], epy_ = epy[ei], epz_ = epz[ei];
-                const double evx_ = evx[ei], evy_ = evy[ei], evz_ = evz[ei];
+                double epx_, epy_, epz_, evx_, evy_, evz_;
+                if (kFilter) {  // survivors are rare: read the FP64 entry from global memory
+                    const int64_t k = active ? e0 + ei : e0;
+                    epx_ = args.e.px[k]; epy_ = args.e.py[k]; epz_ = args.e.pz[k];
+                    evx_ = args.e.vx[k]; evy_ = args.e.vy[k]; evz_ = args.e.vz[k];
+                } else {
+                    epx_ = epx[ei]; epy_ = epy[ei]; epz_ = epz[ei];
+                    evx_ = evx[ei]; evy_ = evy[ei]; evz_ = evz[ei];
+                }
                 const double qpx_ = S.qp[0][j], qpy_ = S.qp[1][j], qpz_ = S.qp[2][j];
                 const double qvx_ = S.qv[0][j], qvy_ = S.qv[1][j], qvz_ = S.qv[2][j];
                 const double opx = e_later ? qpx_ : epx_, opy = e_later ? qpy_ : epy_, opz = e_later ? qpz_ : epz_;
@@ -443,19 +510,36 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
     for (int o = 16; o > 0; o >>= 1) {
         n_inter += __shfl_xor_sync(kFull, n_inter, o);
         n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
+        n_fp64 += __shfl_xor_sync(kFull, n_fp64, o);
     }
     if (lane == 0) {
         if (n_inter) atomicAdd(&ctr->interactions, n_inter);
-        if (n_overlap) {
-            atomicAdd(&ctr->overlap_pairs, n_overlap);
-            atomicAdd(&ctr->fp64_pairs, n_overlap);
-        }
+        if (n_overlap) atomicAdd(&ctr->overlap_pairs, n_overlap);
+        if (n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
     }
 }
 
-size_t pair_smem_bytes(uint32_t chunk)
+size_t pair_smem_bytes(uint32_t chunk, bool filter = false)
 {
-    return ((sizeof(PairSmem) + 15) & ~(size_t)15) + (size_t)chunk * 8 * sizeof(double);
+    return ((sizeof(PairSmem) + 15) & ~(size_t)15) + (size_t)chunk * (filter ? 32 : 64);
+}
+
+// Launch the pair kernel of the requested mode as a persistent grid (as many
+// CTAs as fit on every SM at once).
+cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, cudaStream_t stream)
+{
+    auto kern = filter ? traj_dist_search_kernel<true> : traj_dist_search_kernel<false>;
+    const size_t smem = pair_smem_bytes(pa.chunk, filter);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPairThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -477,6 +561,7 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
                      + 9 * cb(cap, 8)                  // pre
                      + 2 * cb(cap, 8) + 2 * cb(cap, 4) // sort
                      + 12 * cb(cap, 8)                 // sorted query SoA
+                     + 2 * cb(cap, 16)                 // query spheres (before / after sorting)
                      + cb(9, sizeof(double *));        // pre pointer table
     uint64_t ntiles = (cap + kQT - 1) / kQT;
     uint64_t tbytes = 2 * cb(ntiles, 8) + cb(ntiles + 1, 8);
@@ -512,6 +597,8 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
     q.d2 = carve<double>(p, cap);
     q.ts_key = carve<int64_t>(p, cap); q.te_key = carve<int64_t>(p, cap);
     q.qid = carve<int64_t>(p, cap); q.lo = carve<int64_t>(p, cap); q.hi = carve<int64_t>(p, cap);
+    w.pre_sph = carve<float4>(p, cap);
+    q.sph = carve<float4>(p, cap);
     w.pre_dev = carve<double *>(p, 9);
     if (cudaMemcpy(w.pre_dev, w.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
         return cuda_error(cudaGetLastError(), "search workspace: pointer table");
@@ -554,6 +641,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
         return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
 
+    const bool filter = params && params->mode == TDQ_MODE_FP32_FILTER;
     tdq_status st = ensure_queries(idx, nq);
     if (st != TDQ_OK) return st;
 
@@ -579,30 +667,19 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     TDQ_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream));
     TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
     double *const *pre = w.pre_dev;
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, pre, w.keys, w.vals, w.ctr);
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, pre, w.pre_sph, w.keys, w.vals, w.ctr);
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream));
         BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
-        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
+        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
         tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, chunk, w.tile_lo, w.tile_hi,
                                                                  w.tile_work);
         TDQ_CUDA(exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream));
         TDQ_CUDA(cudaGetLastError());
-        const size_t smem = pair_smem_bytes(chunk);
-        static int smem_set = 0;
-        if (smem > 48 * 1024 && smem_set < (int)smem) {
-            TDQ_CUDA(cudaFuncSetAttribute(traj_dist_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            smem_set = (int)smem;
-        }
-        int per_sm = 0;
-        TDQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_search_kernel, kPairThreads, smem));
-        if (per_sm < 1) per_sm = 1;
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, chunk};
         TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
-        traj_dist_search_kernel<<<idx->sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
-        TDQ_CUDA(cudaGetLastError());
+        TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, stream));
         TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
     } else {
         TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
@@ -789,6 +866,7 @@ constexpr uint64_t kNoAllocScratchBytes =
     9 * na_bytes(kNoAllocMaxQueries, 8)                                      // pre columns
     + 2 * na_bytes(kNoAllocMaxQueries, 8) + 2 * na_bytes(kNoAllocMaxQueries, 4)  // sort keys / values
     + 12 * na_bytes(kNoAllocMaxQueries, 8)                                   // sorted query SoA
+    + 2 * na_bytes(kNoAllocMaxQueries, 16)                                   // query spheres
     + 2 * na_bytes(kNoAllocTiles, 8) + na_bytes(kNoAllocTiles + 1, 8)        // tile table
     + na_bytes(kNoAllocHistWords, 4)                                         // sort histogram
     + na_bytes(1, sizeof(DevCounters))                                       // counters
@@ -801,6 +879,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 struct NoAllocScratch {
     double *pre[9];
     double **pre_dev;
+    float4 *pre_sph;
     uint64_t *keys, *keys_alt;
     uint32_t *vals, *vals_alt;
     QuerySoA q;
@@ -841,6 +920,8 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         q.ts_key = carve<int64_t>(p, kNoAllocMaxQueries); q.te_key = carve<int64_t>(p, kNoAllocMaxQueries);
         q.qid = carve<int64_t>(p, kNoAllocMaxQueries); q.lo = carve<int64_t>(p, kNoAllocMaxQueries);
         q.hi = carve<int64_t>(p, kNoAllocMaxQueries);
+        s.pre_sph = carve<float4>(p, kNoAllocMaxQueries);
+        q.sph = carve<float4>(p, kNoAllocMaxQueries);
         s.tile_lo = carve<int64_t>(p, kNoAllocTiles);
         s.tile_hi = carve<int64_t>(p, kNoAllocTiles);
         s.tile_work = carve<unsigned long long>(p, kNoAllocTiles + 1);
@@ -908,24 +989,18 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     in.t1 = t1;
     // the array keeps the previous call's contents: clear the counters
     TDQ_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), stream));
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, s->pre_dev, s->keys, s->vals, s->ctr);
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr);
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream));
         BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
-        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(s->pre_dev, in.seg_id, s->vals, nq, s->ctr, bins, s->q);
+        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(s->pre_dev, s->pre_sph, in.seg_id, s->vals, nq, s->ctr,
+                                                          bins, s->q);
         tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(s->q, ntiles, s->ctr, chunk, s->tile_lo, s->tile_hi,
                                                                  s->tile_work);
         TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
-        const size_t smem = pair_smem_bytes(chunk);
-        if (smem > 48 * 1024)
-            TDQ_CUDA(cudaFuncSetAttribute(traj_dist_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        int per_sm = 0;
-        TDQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_search_kernel, kPairThreads, smem));
-        if (per_sm < 1) per_sm = 1;
         PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk};
-        traj_dist_search_kernel<<<idx->sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
+        TDQ_CUDA(launch_pair_kernel(pa, params && params->mode == TDQ_MODE_FP32_FILTER, idx->sm_count, stream));
     }
     TDQ_CUDA(cudaGetLastError());
     DevCounters h{};

@@ -57,6 +57,24 @@ __device__ __forceinline__ bool lt0(double x)  // x < 0
 __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }  // x >= 0
 
 // ---------------------------------------------------------------------------
+// Conservative FP32 bounding sphere of a segment piece whose FP64 center is
+// (cx,cy,cz) and radius r: the center rounded to nearest, the radius rounded
+// up after widening it by 2^-22 * max|c| (more than the sqrt(3) * 2^-24 *
+// max|c| the center's rounding can move it, and more than any FP64 rounding
+// of the positions the FP64 path evaluates) and by r * 2^-40.  Every point
+// the FP64 path can place on the piece lies inside the FP32 sphere.
+// Magnitudes beyond 2^60 get an infinite radius (never rejected).
+__device__ __forceinline__ float4 sphere32(double cx, double cy, double cz, double r, double extra)
+{
+    double m = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
+    float fr;
+    if (m < 0x1p60 && r < 0x1p60 && extra < 0x1p60)
+        fr = __double2float_ru(fma(r, 0x1p-40, r) + fma(m, 0x1p-22, extra));
+    else
+        fr = __int_as_float(0x7f800000);
+    return make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz), fr);
+}
+
 // Device-side counters of one search, cleared by one memset per search.
 // ---------------------------------------------------------------------------
 struct DevCounters {
@@ -77,6 +95,7 @@ struct EntrySoA {
     double *vx, *vy, *vz;  // velocity (end - start) / (t_end - t_start)
     int64_t *ts_key, *te_key;
     int64_t *seg_id, *traj_id, *orig;
+    float4 *sph;           // FP32 bounding sphere of the segment (center, radius rounded up)
 };
 
 // Sorted, clipped query segments in device memory.
@@ -87,6 +106,7 @@ struct QuerySoA {
     int64_t *ts_key, *te_key;  // clipped span [max(ts,t0), min(te,t1)]
     int64_t *qid;          // caller's segment id
     int64_t *lo, *hi;      // candidate range of sorted entry positions
+    float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
 };
 
 struct Workspace {
@@ -98,6 +118,7 @@ struct Workspace {
     // per-query arrays before sorting
     double *pre[9] = {nullptr};  // px,py,pz,vx,vy,vz,d2,ts',te'
     double **pre_dev = nullptr;  // device copy of pre[]
+    float4 *pre_sph = nullptr;   // per-query sphere before sorting
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;
     QuerySoA q{};

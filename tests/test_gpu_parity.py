@@ -290,3 +290,79 @@ def test_host_and_device_calls_agree(tdq):
     ob = np.lexsort((b.entry_seg_id, b.query_seg_id))
     for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit"):
         assert np.array_equal(getattr(a, f)[oa], getattr(b, f)[ob])
+
+
+# --------------------------------------------------------------------------
+# FP32 conservative pre-test + FP64 refinement (filter mode)
+# --------------------------------------------------------------------------
+
+def _sorted_arrays(r):
+    o = np.lexsort((r.entry_seg_id, r.query_seg_id))
+    return r.query_seg_id[o], r.entry_seg_id[o], r.t_enter[o], r.t_exit[o]
+
+
+def _filter_vs_fp64(tdq, idx, queries, d, window):
+    r64 = tdq.search(idx, queries, d, *window, mode=tdq.MODE_FP64)
+    s64 = tdq.get_stats(idx)
+    r32 = tdq.search(idx, queries, d, *window, mode=tdq.MODE_FP32_FILTER)
+    s32 = tdq.get_stats(idx)
+    # the filter drops only pairs the FP64 test rejects, and survivors run the
+    # same FP64 code: the results are bitwise identical
+    for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
+        assert np.array_equal(a, b)
+    assert s32["overlap_pairs"] == s64["overlap_pairs"] == s64["fp64_pairs"]
+    assert s32["results"] <= s32["fp64_pairs"] <= s32["overlap_pairs"]
+    return s64, s32
+
+
+@pytest.mark.parametrize("name", ["tiny", "scale", "galaxy", "batching"])
+def test_filter_mode_equals_plain_fp64(tdq, name):
+    if name == "tiny":
+        w = workloads.tiny_random_walk()
+    elif name == "scale":
+        w = workloads.scale_random_walk(n_traj=2000, n_queries=20)
+    elif name == "galaxy":
+        w = workloads.galaxy_disk(n_stars=4000, n_queries=25)
+    else:
+        w = workloads.batching_walks(n_traj=500, n_queries=40, box=60.0)
+        w.d_values = (0.5, 4.0, 10.0)
+    with tdq.build_index(w.entries) as idx:
+        for d in w.d_values:
+            s64, s32 = _filter_vs_fp64(tdq, idx, w.queries, d, w.window)
+        # and against the oracle, through the filter path
+        check(tdq, w.entries, w.queries, w.d_values[-1], *w.window, idx=idx, mode=tdq.MODE_FP32_FILTER)
+
+
+def test_filter_mode_full_size_scale_walk(tdq):
+    w = workloads.scale_random_walk()
+    with tdq.build_index(w.entries) as idx:
+        for d in w.d_values:
+            s64, s32 = _filter_vs_fp64(tdq, idx, w.queries, d, w.window)
+            assert s32["fp64_pairs"] < 0.01 * s32["overlap_pairs"]
+
+
+@pytest.mark.parametrize("offset", [0.0, 1e3, 1e5, 3e6])
+def test_filter_is_conservative_at_the_threshold(tdq, offset):
+    """Pairs whose closest distance is d(1 - 1e-7) .. d(1 + 1e-7), far from
+    the origin where FP32 rounding is coarse: the filter must keep every
+    pair the FP64 test accepts (the two modes agree pair for pair)."""
+    rng = np.random.default_rng(int(offset) + 17)
+    n = 4000
+    d = 0.75
+    rel = rng.uniform(-1e-7, 1e-7, n)
+    # query: a point moving along x through the origin region (plus offset)
+    q = np.array([[offset - 5.0, offset, offset, 0.0, offset + 5.0, offset, offset, 10.0]])
+    # entries: stationary points at distance d(1+rel) from the query's line,
+    # each over a span that contains its closest-approach time
+    u = rng.normal(size=(n, 2))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    x = offset + rng.uniform(-4.0, 4.0, n)
+    y = offset + u[:, 0] * d * (1 + rel)
+    z = offset + u[:, 1] * d * (1 + rel)
+    t0 = rng.uniform(0.0, 1.0, n)  # spans hold the closest approach (t in [1, 9])
+    t1 = rng.uniform(9.0, 10.0, n)
+    ent = workloads.Segments.from_columns([x, y, z, t0, x, y, z, t1])
+    qry = workloads.Segments.from_columns([q[:, k] for k in range(8)], seg_id=[10 ** 9])
+    with tdq.build_index(ent) as idx:
+        s64, s32 = _filter_vs_fp64(tdq, idx, qry, d, (-np.inf, np.inf))
+    assert s64["results"] > 0.3 * n
