@@ -7,12 +7,15 @@ trajectories taken from it.  One step = one search per threshold d in
 {1, 5, 15} over the full window.
 
 value     temporal-overlap pair tests per second (pairs whose common span has
-          positive length; the index-independent work of the search), with
-          queries and results in device memory, device-timed with CUDA events
-          on the stream the library launches on;
+          positive length; the index-independent work of the search) of the
+          headline mode (default: FP32 conservative pre-test + FP64 refine),
+          with queries and results in device memory, device-timed with CUDA
+          events on the stream the library launches on; the plain FP64 mode
+          is measured the same way and reported beside it;
 e2e       the same metric through the C ABI with host query arrays and host
           results (host<->device copies inside the timed region);
-roofline  the pair kernel (the dominant kernel) against the FP64 issue peak;
+roofline  the dominant pair kernel of each mode against its pipe's peak
+          (FP64 for the plain mode, FP32 for the filter mode);
 cpu_baseline / --impl reference
           the CPU FP64 oracle (time sweep, all host cores) on a bounded sample.
 
@@ -44,9 +47,14 @@ from paper_1405_7461_gb300 import workloads  # noqa: E402
 # the span start 6, relative position 3, relative velocity 3, A 5, B/2 5,
 # C 6, discriminant 3.
 FLOPS_PER_PAIR_FP64 = 32
-# FP64 peak from the unit counts and clocks: 2 DFMA per clock per SM x 2
-# flops x 152 SMs x 2070 MHz (the 1.25 TFLOP/s nominal figure).
+# Algorithmic FP32 flops per candidate pair in the filter kernel's sphere
+# pre-test: center difference 3, squared distance minus bound 6 (3 FMA),
+# bound (w_e + w_q)^2 as w_e (w_e + 2 w_q) + w_q^2: 3.
+FLOPS_PER_CANDIDATE_FP32 = 12
+# Peaks from unit counts and clocks (152 SMs, 2070 MHz): FP64 2 DFMA/clk/SM
+# (the 1.25 TFLOP/s nominal figure), FP32 128 FFMA/clk/SM.
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
+FP32_PEAK_GFLOPS = 2 * 128 * 152 * 2.070
 CPU_SAMPLE_QUERIES = 20
 
 
@@ -56,7 +64,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32filter"])
+    ap.add_argument("--mode", default="fp32filter", choices=["fp64", "fp32filter"],
+                    help="headline search mode (the other mode is measured beside it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
@@ -141,19 +150,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_record():
-    """ncu DRAM bytes per pair-kernel launch, if taken on the current kernel source."""
+def traffic_record(mode):
+    """ncu DRAM bytes per pair-kernel launch of `mode`, if they were taken on
+    the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     src = os.path.join(ROOT, "paper_1405_7461_gb300", "csrc", "search.cu")
-    if not os.path.exists(path):
-        return None
     try:
-        rec = json.load(open(path))
+        rec = json.load(open(path)).get(mode)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("search_cu_sha256_16") != h or rec.get("mode") is None:
+        if not rec or rec.get("search_cu_sha256_16") != h:
             return None
-        return rec
-    except (OSError, ValueError):
+        return rec.get("bytes_per_launch")
+    except (OSError, ValueError, AttributeError):
         return None
 
 
@@ -213,6 +221,26 @@ def run_reference(args):
     return 0
 
 
+def roofline(mode, tot, n_launch):
+    """Roofline of the dominant kernel over the timed launches: algorithmic
+    work per launch / the kernel's average CUDA-event duration."""
+    kern_ms = tot["kernel_ms"] / n_launch
+    if mode == "fp64":
+        work = FLOPS_PER_PAIR_FP64 * tot["fp64_pairs"] / n_launch
+        peak, kernel = FP64_PEAK_GFLOPS, "traj_dist_search_kernel"
+        src = "derived: 2 DFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal FP64)"
+        per = f"{FLOPS_PER_PAIR_FP64} FP64 flops per temporal-overlap pair"
+    else:
+        work = FLOPS_PER_CANDIDATE_FP32 * tot["interactions"] / n_launch
+        peak, kernel = FP32_PEAK_GFLOPS, "traj_dist_filter_kernel"
+        src = "derived: 128 FFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz"
+        per = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per candidate pair (sphere pre-test)"
+    achieved = work / (kern_ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_record(mode), "kernel": kernel, "kernel_ms_avg": kern_ms, "work_unit": per,
+            "peak_source": src}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -233,7 +261,7 @@ def main():
     dev = torch.cuda.current_device()
     build.build()
     tdq.load()
-    mode = tdq.MODE_FP64 if args.mode == "fp64" else tdq.MODE_FP32_FILTER
+    modes = {"fp64": tdq.MODE_FP64, "fp32filter": tdq.MODE_FP32_FILTER}
 
     def barrier():
         if world > 1:
@@ -243,79 +271,78 @@ def main():
     stream = torch.cuda.current_stream()
     ent_dev = tdq.DeviceSegments(w.entries)
     idx = tdq.build_index(ent_dev, stream=stream)
+    torch.cuda.synchronize()
     t_build = time.perf_counter()
     tdq.build_index(ent_dev, stream=stream).free()
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t_build
     del ent_dev
     qdev = tdq.DeviceSegments(w.queries)
-    cap = 1 << 22
-    buf = tdq.DeviceResultBuffer(cap)
+    buf = tdq.DeviceResultBuffer(1 << 22)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step():
-        pairs = inter = res = launches = 0
-        kms = 0.0
+    def step(mode):
+        t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0}
         for d in w.d_values:
-            cnt = tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=mode)
+            cnt = tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=modes[mode])
             s = tdq.get_stats(idx)
-            pairs += s["overlap_pairs"]
-            inter += s["interactions"]
-            res += cnt
-            launches += s["kernel_launches"]
-            kms += s["pair_kernel_ms"]
-        return pairs, inter, res, launches, kms
+            t["pairs"] += s["overlap_pairs"]
+            t["interactions"] += s["interactions"]
+            t["fp64_pairs"] += s["fp64_pairs"]
+            t["results"] += cnt
+            t["launches"] += s["kernel_launches"]
+            t["kernel_ms"] += s["pair_kernel_ms"]
+        return t
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier()
+    def timed(mode):
+        for _ in range(args.warmup):
+            step(mode)
+        torch.cuda.synchronize()
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ms, tot = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            out = step(mode)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            tot = out if tot is None else {k: tot[k] + out[k] for k in tot}
+        torch.cuda.synchronize()
+        barrier()
+        total_ms = sum(ms)
+        pairs = float(tot["pairs"])
+        if world > 1:
+            tt = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(tt.item())
+            pp = torch.tensor([pairs], device="cuda")
+            torch.distributed.all_reduce(pp)
+            pairs = float(pp.item())
+        n_launch = args.steps * len(w.d_values)
+        return {"value": pairs / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / (total_ms / 1e3),
+                "interactions_per_s": world * tot["interactions"] / (total_ms / 1e3),
+                "fp64_pairs_per_step": tot["fp64_pairs"] / args.steps,
+                "results_per_step": tot["results"] / args.steps, "gpu_launches": int(tot["launches"]),
+                "roofline": roofline(mode, tot, n_launch)}
+
+    head_mode = args.mode
+    other_mode = "fp64" if head_mode == "fp32filter" else "fp32filter"
     clocks = ClockSampler(dev)
     clocks.start()
     time.sleep(0.3)
-    torch.cuda.synchronize()
-    barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    step_ms, tot = [], [0, 0, 0, 0, 0.0]
-    for _ in range(args.steps):
-        flush.zero_()
-        ev0.record(stream)
-        out = step()
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        for k in range(5):
-            tot[k] += out[k]
-    torch.cuda.synchronize()
-    barrier()
+    head = timed(head_mode)
+    other = timed(other_mode)
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        p = torch.tensor([float(tot[0])], device="cuda")
-        torch.distributed.all_reduce(p)
-        all_pairs = float(p.item())
-    else:
-        all_pairs = float(tot[0])
-    value = all_pairs / (total_ms / 1e3)
-    queries_per_s = world * args.steps * len(w.d_values) * args.n_queries / (total_ms / 1e3)
-    n_pair_launches = args.steps * len(w.d_values)
-    kern_ms = tot[4] / n_pair_launches
-    flops_per_launch = FLOPS_PER_PAIR_FP64 * tot[0] / n_pair_launches
-    achieved = flops_per_launch / (kern_ms / 1e3) / 1e9
-    trec = traffic_record()
-    traffic = None
-    if trec and trec.get("mode") == args.mode:
-        traffic = trec.get("bytes_per_launch")
 
     # end to end through the C ABI: host queries in, host results out
     e2e = None
     if not args.no_e2e:
         qhost = tdq.HostSegments(w.queries)
-        tdq.search(idx, qhost, w.d_values[0], *w.window, stream=stream, mode=mode)
+        tdq.search(idx, qhost, w.d_values[0], *w.window, stream=stream, mode=modes[head_mode])
         barrier()
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -323,7 +350,7 @@ def main():
         d2h = 0
         for _ in range(args.steps):
             for d in w.d_values:
-                r = tdq.search(idx, qhost, d, *w.window, stream=stream, mode=mode)
+                r = tdq.search(idx, qhost, d, *w.window, stream=stream, mode=modes[head_mode])
                 e_pairs += tdq.get_stats(idx)["overlap_pairs"]
                 d2h += 32 * len(r) + 64
         torch.cuda.synchronize()
@@ -342,25 +369,28 @@ def main():
         cpu = cpu_baseline(w, w.d_values, CPU_SAMPLE_QUERIES)
 
     if rank == 0:
+        names = {"fp64": "plain FP64", "fp32filter": "FP32 conservative pre-test + FP64 refine"}
         line = {
-            "metric": "segment-pair tests/s (temporal-overlap pairs), plain FP64 search" if args.mode == "fp64"
-            else "segment-pair tests/s (temporal-overlap pairs), FP32 filter + FP64 refine",
-            "value": value, "unit": "pair tests/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": "segment-pair tests/s (temporal-overlap pairs) & queries/s, %s search" % names[head_mode],
+            "value": head["value"], "unit": "pair tests/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, w, {"parallelism": "replicas" if world > 1 else "single GPU",
                                             "index_build_s": build_s}),
-            "queries_per_s": queries_per_s,
-            "interactions_per_s": world * tot[1] / (total_ms / 1e3),
-            "results_per_step": tot[2] / args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                         "kernel": "traj_dist_search_kernel", "kernel_ms_avg": kern_ms,
-                         "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal FP64)"},
+            "queries_per_s": head["queries_per_s"],
+            "interactions_per_s": head["interactions_per_s"],
+            "fp64_pairs_per_step": head["fp64_pairs_per_step"],
+            "results_per_step": head["results_per_step"],
+            "roofline": head["roofline"],
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
-            "gpu_launches": int(tot[3]),
+            "gpu_launches": head["gpu_launches"],
+            ("plain_fp64" if other_mode == "fp64" else "fp32filter"): {
+                "value": other["value"], "unit": "pair tests/s", "ms_per_step": other["ms_per_step"],
+                "queries_per_s": other["queries_per_s"], "roofline": other["roofline"],
+                "gpu_launches": other["gpu_launches"]},
+            "speedup_vs_plain_fp64": (head["value"] / other["value"]) if other_mode == "fp64" else None,
         }
         print(json.dumps(line), flush=True)
     idx.free()

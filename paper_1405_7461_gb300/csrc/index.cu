@@ -89,6 +89,22 @@ __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, E
     e.sph[k] = sphere32(xs + hx, ys + hy, zs + hz, sqrt(hx * hx + hy * hy + hz * hz), 0.0);
 }
 
+// Unsigned radix keys of the sorted entries' t_end (values unused).
+__global__ void te_keys(const int64_t *te_key, uint64_t n, uint64_t *keys, uint32_t *vals)
+{
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    keys[k] = (uint64_t)te_key[k] ^ 0x8000000000000000ULL;
+    vals[k] = 0;
+}
+
+__global__ void te_store(const uint64_t *keys, uint64_t n, int64_t *te_sorted)
+{
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    te_sorted[k] = (int64_t)(keys[k] ^ 0x8000000000000000ULL);
+}
+
 __device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
 {
     double f = floor((t - t_min) / width);
@@ -230,7 +246,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     }
 
     // Resident sorted copy + bin table.
-    uint64_t ebytes = 11 * carve_bytes(n, 8) + carve_bytes(n, 16);
+    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 16) + 256;
     uint64_t bbytes = carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (cudaMalloc(&idx->e_block, ebytes) != cudaSuccess || cudaMalloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -245,7 +261,8 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         e.vx = carve<double>(p, n); e.vy = carve<double>(p, n); e.vz = carve<double>(p, n);
         e.ts_key = carve<int64_t>(p, n); e.te_key = carve<int64_t>(p, n);
         e.seg_id = carve<int64_t>(p, n); e.traj_id = carve<int64_t>(p, n); e.orig = carve<int64_t>(p, n);
-        e.sph = carve<float4>(p, n);
+        e.te_sorted = carve<int64_t>(p, n);
+        e.sph = carve<float4>(p, n);  // last: the filter kernel may read one item past n
         char *q = (char *)idx->b_block;
         idx->bin_begin = carve<int64_t>(q, m + 1);
         idx->bin_end_key = carve<int64_t>(q, m);
@@ -345,6 +362,13 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         bin_assign<<<grid_for(n), kBlock, 0, stream>>>(idx->e.ts_key, idx->e.te_key, n, idx->t_min, idx->width, m,
                                                        idx->bin_begin, idx->bin_end_key);
         bin_prefix_max<<<1, 1024, 0, stream>>>(idx->bin_end_key, m, idx->bin_pmax_key);
+        // t_end keys in ascending order: #overlaps(q) = #{ts < q.te} - #{te <= q.ts}
+        te_keys<<<grid_for(n), kBlock, 0, stream>>>(idx->e.te_key, n, keys, vals);
+        if (radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, hist, stream) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "tdq_build_index: t_end sort");
+            break;
+        }
+        te_store<<<grid_for(n), kBlock, 0, stream>>>(keys, n, idx->e.te_sorted);
         if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: index kernels");
             break;

@@ -143,7 +143,9 @@ __global__ void query_gather(const double *const *pre, const float4 *pre_sph, co
     q.ts_key[k] = cs;
     q.te_key[k] = ce;
     q.qid[k] = seg_id[i];
-    q.sph[k] = pre_sph[i];
+    const float4 sp = pre_sph[i];
+    q.sph[k] = sp;
+    q.sph2[k] = make_float4(2.0f * sp.w, __fmul_ru(sp.w, sp.w), 0.f, 0.f);
     // First bin whose extent reaches past the query start: the prefix maximum
     // of bin ends is non-decreasing, so this is a binary search (Sec. 4 uses
     // an index tree over the bin extents for the same lookup).
@@ -217,7 +219,6 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r)
 struct PairSmem {
     double qp[3][kQT], qv[3][kQT], qd2[kQT];
     int64_t qts[kQT], qte[kQT], qid[kQT];
-    float4 qsph[kQT];
     long long item;
     long long tile;
     // followed by the entry chunk: FP64 mode: 6 double columns + 2 key
@@ -271,26 +272,318 @@ __device__ __noinline__ void pair_interval(double A, double Bh, double C, double
     *tout = thi >= L ? b : (le0(thi) ? a : a + thi);
 }
 
-// Conservative FP32 pre-test: false only if the two bounding spheres (the
-// query's radius already widened by d) are certainly apart.  The squared
-// center distance s is computed with at most four roundings, so s <=
-// (1 + 2^-24)^4 * (exact squared distance of the FP32 centers); the bound
-// R = r_e + (r_q + d) and R^2 are rounded up and scaled by (1 + 2^-20).
-__device__ __forceinline__ bool spheres_may_meet(float4 e, float4 q)
+// ---------------------------------------------------------------------------
+// FP64 evaluation of one pair, shared by both pair kernels so that a pair
+// gets bitwise the same decision and interval in either mode.
+//
+// temporalIntersection: common span [a, b] from the integer time keys; S is
+// the segment that starts at a, O the other one.  calcTimeInterval: with
+// tau = t - a, |dp + dv tau|^2 - d^2 = A tau^2 + 2 Bh tau + C, dp = O - S at
+// a, dv = v_O - v_S.  The minimum over [0, L] is <= 0 without dividing:
+// C <= 0 (in range at a), or approaching (Bh < 0) with a real root pair
+// (disc >= 0) whose closest point lies inside the span or whose value at L
+// is <= 0.  All lanes of the warp must call it (warp vote inside).
+// ---------------------------------------------------------------------------
+struct PairEval {
+    double A, Bh, C, disc, a, b;
+    bool hit;
+};
+
+__device__ __forceinline__ PairEval eval_pair_fp64(bool active, int64_t ets_k, int64_t ete_k, int64_t qts_k,
+                                                   int64_t qte_k, double epx_, double epy_, double epz_,
+                                                   double evx_, double evy_, double evz_, double qpx_, double qpy_,
+                                                   double qpz_, double qvx_, double qvy_, double qvz_, double d2)
 {
-    float dx = e.x - q.x, dy = e.y - q.y, dz = e.z - q.z;
-    float s2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    float R = __fadd_ru(e.w, q.w);
-    float thr = __fmul_ru(__fmul_ru(R, R), 1.0f + 0x1p-20f);
-    return !(s2 > thr);
+    PairEval r;
+    const bool e_later = ets_k >= qts_k;
+    const int64_t a_k = e_later ? ets_k : qts_k;
+    const int64_t b_k = min(ete_k, qte_k);
+    const int64_t o_k = e_later ? qts_k : ets_k;
+    r.a = key_double(a_k);
+    r.b = key_double(b_k);
+    const double o_ts = key_double(o_k);
+    const double opx = e_later ? qpx_ : epx_, opy = e_later ? qpy_ : epy_, opz = e_later ? qpz_ : epz_;
+    const double ovx = e_later ? qvx_ : evx_, ovy = e_later ? qvy_ : evy_, ovz = e_later ? qvz_ : evz_;
+    const double spx = e_later ? epx_ : qpx_, spy = e_later ? epy_ : qpy_, spz = e_later ? epz_ : qpz_;
+    const double svx = e_later ? evx_ : qvx_, svy = e_later ? evy_ : qvy_, svz = e_later ? evz_ : qvz_;
+    const double dt = r.a - o_ts;
+    const double dpx = fma(ovx, dt, opx) - spx;
+    const double dpy = fma(ovy, dt, opy) - spy;
+    const double dpz = fma(ovz, dt, opz) - spz;
+    const double dvx = ovx - svx, dvy = ovy - svy, dvz = ovz - svz;
+    r.A = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
+    r.Bh = fma(dpz, dvz, fma(dpy, dvy, dpx * dvx));
+    r.C = fma(dpz, dpz, fma(dpy, dpy, fma(dpx, dpx, -d2)));
+    r.disc = fma(r.Bh, r.Bh, -(r.A * r.C));
+    bool hit = le0(r.C);
+    const bool need_L = !hit && lt0(r.Bh) && ge0(r.disc);
+    if (__any_sync(kFull, active && need_L)) {
+        const double L = r.b - r.a;
+        const double gL = fma(r.A, L, r.Bh);
+        const double fL = fma(gL + r.Bh, L, r.C);
+        hit = hit || (need_L && (gt0(gL) || le0(fL)));
+    }
+    r.hit = hit && active;
+    return r;
+}
+
+// Append the hits of a warp: one atomic per warp, writes past the capacity
+// skipped while the count keeps counting.
+__device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr, const tdq_result_buffer &out,
+                                            uint64_t cap, int64_t qid, int64_t eid, int lane, unsigned lt_mask)
+{
+    const unsigned hm = __ballot_sync(kFull, r.hit);
+    if (!hm) return;
+    unsigned long long rbase = 0;
+    const int leader = __ffs(hm) - 1;
+    if (lane == leader) rbase = atomicAdd(&ctr->results, (unsigned long long)__popc(hm));
+    rbase = __shfl_sync(kFull, rbase, leader);
+    if (r.hit) {
+        double tin, tout;
+        pair_interval(r.A, r.Bh, r.C, r.disc, r.a, r.b, &tin, &tout);
+        const unsigned long long pos = rbase + __popc(hm & lt_mask);
+        if (pos < cap) {
+            out.query_seg_id[pos] = qid;
+            out.entry_seg_id[pos] = eid;
+            out.t_enter[pos] = tin;
+            out.t_exit[pos] = tout;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Filter mode: conservative FP32 pre-test, FP64 for the survivors.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct FilterDesc {
+    long long item;  // < 0: none
+    long long e0;    // first sorted entry of the chunk
+    long long q0;    // first sorted query segment of the tile
+    int ne, nqt;
+};
+
+struct FilterSmem {
+    float4 qa[2][kQT];  // (cx, cy, cz, w) of the tile's query segments, w = radius + d
+    float4 qb[2][kQT];  // (2w, w^2, -, -)
+    FilterDesc desc[2];
+    // followed by the entry chunks: float4 spheres, [2][chunk]
+};
+
+size_t filter_smem_bytes(uint32_t chunk)
+{
+    return ((sizeof(FilterSmem) + 15) & ~(size_t)15) + (size_t)2 * chunk * sizeof(float4);
+}
+
+// Work items are split into contiguous ranges, one per CTA; a CTA walks the
+// tile table forward.  Entry spheres and query spheres of the next item are
+// copied into the other half of a double buffer with cp.async while the
+// current item is tested.  Per candidate pair the test is 8 FP32 operations
+// and one funnel shift that moves the sign of
+//   |c_e - c_q|^2 - (w_e + w_q)^2   (rounded so that it is negative whenever
+//                                     the exact spheres meet)
+// into the lane's 32-bit mask.  Exact temporal overlap is checked only for
+// survivors (the count of all overlapping pairs comes from count_overlaps).
+__global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(PairArgs args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FilterSmem &S = *reinterpret_cast<FilterSmem *>(smem_raw);
+    const uint32_t EC = args.chunk;
+    float4 *es = reinterpret_cast<float4 *>(smem_raw + ((sizeof(FilterSmem) + 15) & ~(size_t)15));
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    DevCounters *ctr = args.ctr;
+    const unsigned long long total = args.tile_work[args.ntiles];
+    const uint64_t nvalid = ctr->valid_queries;
+    const uint64_t cap = args.out.capacity;
+    const unsigned long long per = (total + gridDim.x - 1) / gridDim.x;
+    const unsigned long long ibeg = min((unsigned long long)blockIdx.x * per, total);
+    const unsigned long long iend = min(ibeg + per, total);
+    unsigned long long n_inter = 0, n_fp64 = 0;
+
+    // thread 0's position in the tile table
+    uint64_t t_walk = 0;
+    unsigned long long w_base = 0, w_next = 0;
+    int64_t t_lo = 0, t_hi = 0;
+    auto describe = [&](unsigned long long item, FilterDesc &d) {
+        bool moved = false;
+        while (w_next <= item) {
+            t_walk++;
+            w_base = w_next;
+            w_next = args.tile_work[t_walk + 1];
+            moved = true;
+        }
+        if (moved) {
+            t_lo = args.tile_lo[t_walk];
+            t_hi = args.tile_hi[t_walk];
+        }
+        d.item = (long long)item;
+        d.e0 = t_lo + (long long)(item - w_base) * EC;
+        d.ne = (int)(min(d.e0 + (long long)EC, (long long)t_hi) - d.e0);
+        d.q0 = (long long)t_walk * kQT;
+        d.nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)d.q0);
+    };
+    auto issue = [&](int slot, const FilterDesc &d) {
+        float4 *dst = es + (size_t)slot * EC;
+        const float4 *src = args.e.sph + d.e0;
+        for (int i = tid; i < d.ne; i += kPairThreads) cp_async16(dst + i, src + i);
+        if (tid < d.nqt) {
+            cp_async16(&S.qa[slot][tid], args.q.sph + d.q0 + tid);
+            cp_async16(&S.qb[slot][tid], args.q.sph2 + d.q0 + tid);
+        }
+    };
+
+    if (tid == 0) {
+        S.desc[0].item = -1;
+        S.desc[1].item = -1;
+        if (ibeg < iend) {
+            uint64_t lo = 0, hi = args.ntiles;  // last tile whose first item is <= ibeg
+            while (hi - lo > 1) {
+                uint64_t mid = (lo + hi) >> 1;
+                if (args.tile_work[mid] <= ibeg) lo = mid; else hi = mid;
+            }
+            t_walk = lo;
+            w_base = args.tile_work[lo];
+            w_next = args.tile_work[lo + 1];
+            t_lo = args.tile_lo[lo];
+            t_hi = args.tile_hi[lo];
+            describe(ibeg, S.desc[0]);
+            if (ibeg + 1 < iend) describe(ibeg + 1, S.desc[1]);
+        }
+    }
+    __syncthreads();
+    if (S.desc[0].item >= 0) {
+        issue(0, S.desc[0]);
+        cp_async_commit();
+        int slot = 0;
+        for (unsigned long long it = ibeg; it < iend; it++) {
+            const FilterDesc cur = S.desc[slot];
+            const FilterDesc nxt = S.desc[slot ^ 1];
+            if (nxt.item >= 0) issue(slot ^ 1, nxt);
+            cp_async_commit();
+            cp_async_wait_prior();  // this item's copies have landed
+            __syncthreads();
+
+            const int ne = cur.ne;
+            const unsigned qvalid = 0xffffffffu << (kQT - cur.nqt);  // bit 31-j <-> query j
+            if (tid == 0) n_inter += (unsigned long long)ne * (unsigned long long)cur.nqt;
+            const float4 *esl = es + (size_t)slot * EC;
+            for (int g = 0; g < (int)EC; g += kPairThreads) {
+                if (g + warp * 32 >= ne) break;  // warp-uniform: nothing left for this warp
+                const int el = g + warp * 32 + lane;
+                unsigned mask = 0;
+                {
+                    const float4 e = esl[el];
+#pragma unroll
+                    for (int j = 0; j < kQT; j++) {
+                        const float4 qa = S.qa[slot][j];
+                        const float4 qb = S.qb[slot][j];
+                        const float dx = e.x - qa.x, dy = e.y - qa.y, dz = e.z - qa.z;
+                        const float thr = __fmaf_ru(e.w, __fadd_ru(e.w, qb.x), qb.y);
+                        const float v = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -thr)));
+                        mask = __funnelshift_l(__float_as_uint(v), mask, 1);
+                    }
+                }
+                mask &= qvalid;
+                if (el >= ne) mask = 0;
+                const int cnt = __popc(mask);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int npairs = __shfl_sync(kFull, incl, 31);
+                if (npairs == 0) continue;
+                const int excl = incl - cnt;
+                for (int base = 0; base < npairs; base += 32) {
+                    const int kk = base + lane;
+                    const bool valid = kk < npairs;
+                    int owner = 0;
+#pragma unroll
+                    for (int s = 16; s >= 1; s >>= 1) {
+                        int v = __shfl_sync(kFull, incl, owner + s - 1);
+                        if (v <= kk) owner += s;
+                    }
+                    const unsigned mo = __shfl_sync(kFull, mask, owner);
+                    const int eo = __shfl_sync(kFull, excl, owner);
+                    const int j = valid ? (31 - nth_set_bit(mo, kk - eo)) : 0;
+                    const int64_t ek = cur.e0 + (valid ? g + warp * 32 + owner : 0);
+                    const int64_t qk = cur.q0 + j;
+                    // exact temporal overlap of the survivor
+                    const int64_t ets_k = args.e.ts_key[ek], ete_k = args.e.te_key[ek];
+                    const int64_t qts_k = args.q.ts_key[qk], qte_k = args.q.te_key[qk];
+                    const bool active = valid && (ets_k < qte_k) && (ete_k > qts_k);
+                    const unsigned am = __ballot_sync(kFull, active);
+                    if (lane == 0) n_fp64 += (unsigned long long)__popc(am);
+                    if (!am) continue;
+                    const PairEval r = eval_pair_fp64(
+                        active, ets_k, ete_k, qts_k, qte_k, args.e.px[ek], args.e.py[ek], args.e.pz[ek],
+                        args.e.vx[ek], args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk], args.q.pz[qk],
+                        args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
+                    append_hits(r, ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+                }
+            }
+            if (tid == 0) {
+                if (it + 2 < iend) describe(it + 2, S.desc[slot]);
+                else S.desc[slot].item = -1;
+            }
+            __syncthreads();  // this slot is refilled next iteration
+            slot ^= 1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_inter += __shfl_xor_sync(kFull, n_inter, o);
+        n_fp64 += __shfl_xor_sync(kFull, n_fp64, o);
+    }
+    if (lane == 0) {
+        if (n_inter) atomicAdd(&ctr->interactions, n_inter);
+        if (n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
+    }
+}
+
+// Exact number of temporal-overlap pairs of each query segment: entries
+// with t_start < q.t_end minus entries with t_end <= q.t_start (the second
+// set lies inside the first because t_end > t_start), by binary searches in
+// the sorted t_start keys and the sorted t_end keys.
+__global__ void count_overlaps(const QuerySoA q, const int64_t *ts_sorted, const int64_t *te_sorted, uint64_t n,
+                               DevCounters *ctr)
+{
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = 0;
+    if (k < ctr->valid_queries) {
+        const int64_t cs = q.ts_key[k], ce = q.te_key[k];
+        uint64_t lo = 0, hi = n;  // first t_start >= ce
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (ts_sorted[mid] < ce) lo = mid + 1; else hi = mid;
+        }
+        const uint64_t n1 = lo;
+        lo = 0;
+        hi = n;  // first t_end > cs
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (te_sorted[mid] <= cs) lo = mid + 1; else hi = mid;
+        }
+        c = (unsigned long long)(n1 - lo);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->overlap_pairs, c);
 }
 
 // GPUTrajDistSearch (Sec. 5, Algorithm 1), tiled: one work item is a tile of
 // 32 sorted query segments against a chunk of the tile's candidate entries.
-// kFilter = false: every temporal-overlap pair is evaluated in FP64.
-// kFilter = true : a pair is evaluated in FP64 only if it overlaps in time
-//                  and passes the FP32 sphere pre-test.
-template <bool kFilter>
+// Every temporal-overlap pair is evaluated in FP64 (the plain method).
 __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -300,8 +593,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
     // entry chunk columns
     int64_t *ets = reinterpret_cast<int64_t *>(ebase);
     int64_t *ete = ets + EC;
-    float4 *esph = reinterpret_cast<float4 *>(ete + EC);                  // filter mode
-    double *ecol = reinterpret_cast<double *>(ete + EC);                  // FP64 mode
+    double *ecol = reinterpret_cast<double *>(ete + EC);
     double *epx = ecol, *epy = ecol + EC, *epz = ecol + 2 * EC;
     double *evx = ecol + 3 * EC, *evy = ecol + 4 * EC, *evz = ecol + 5 * EC;
 
@@ -312,7 +604,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
     const uint64_t nvalid = ctr->valid_queries;
     const uint64_t cap = args.out.capacity;
 
-    unsigned long long n_inter = 0, n_overlap = 0, n_fp64 = 0;
+    unsigned long long n_inter = 0, n_overlap = 0;
 
     for (;;) {
         if (tid == 0) {
@@ -350,11 +642,9 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 S.qts[tid] = args.q.ts_key[k];
                 S.qte[tid] = args.q.te_key[k];
                 S.qid[tid] = args.q.qid[k];
-                if (kFilter) S.qsph[tid] = args.q.sph[k];
             } else {  // padding: a span that overlaps nothing
                 S.qts[tid] = INT64_MAX;
                 S.qte[tid] = INT64_MIN;
-                if (kFilter) S.qsph[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         // stage the chunk's entry segments (coalesced column loads)
@@ -363,16 +653,11 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 int64_t k = e0 + i;
                 ets[i] = args.e.ts_key[k];
                 ete[i] = args.e.te_key[k];
-                if (kFilter) {
-                    esph[i] = args.e.sph[k];
-                } else {
-                    epx[i] = args.e.px[k]; epy[i] = args.e.py[k]; epz[i] = args.e.pz[k];
-                    evx[i] = args.e.vx[k]; evy[i] = args.e.vy[k]; evz[i] = args.e.vz[k];
-                }
+                epx[i] = args.e.px[k]; epy[i] = args.e.py[k]; epz[i] = args.e.pz[k];
+                evx[i] = args.e.vx[k]; evy[i] = args.e.vy[k]; evz[i] = args.e.vz[k];
             } else {
                 ets[i] = INT64_MAX;
                 ete[i] = INT64_MIN;
-                if (kFilter) esph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         if (tid == 0) n_inter += (unsigned long long)ne * (unsigned long long)nqt;
@@ -381,29 +666,14 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
         for (int g = 0; g < (int)EC; g += kPairThreads) {
             const int el = g + warp * 32 + lane;
             // temporal intersection of this lane's entry with every query of
-            // the tile, as a 32-bit mask (integer keys: strict overlap a < b);
-            // in filter mode a second mask keeps the pairs that also pass the
-            // FP32 sphere pre-test
+            // the tile, as a 32-bit mask (integer keys: strict overlap a < b)
             const int64_t my_ts = ets[el], my_te = ete[el];
-            unsigned ovmask = 0, mask = 0;
-            if (kFilter) {
-                const float4 my_sph = esph[el];
+            unsigned mask = 0;
 #pragma unroll
-                for (int j = 0; j < kQT; j++) {
-                    bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
-                    bool near = spheres_may_meet(my_sph, S.qsph[j]);
-                    ovmask |= (unsigned)ov << j;
-                    mask |= (unsigned)(ov & near) << j;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kQT; j++) {
-                    bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
-                    mask |= (unsigned)ov << j;
-                }
-                ovmask = mask;
+            for (int j = 0; j < kQT; j++) {
+                bool ov = (my_ts < S.qte[j]) & (my_te > S.qts[j]);
+                mask |= (unsigned)ov << j;
             }
-            if (kFilter) n_overlap += (unsigned long long)__popc(ovmask);
             const int cnt = __popc(mask);
             int incl = cnt;
 #pragma unroll
@@ -413,10 +683,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
             }
             const int excl = incl - cnt;
             const int npairs = __shfl_sync(kFull, incl, 31);
-            if (lane == 0) {
-                if (!kFilter) n_overlap += (unsigned long long)npairs;
-                n_fp64 += (unsigned long long)npairs;
-            }
+            if (lane == 0) n_overlap += (unsigned long long)npairs;
 
             // evaluate the selected pairs 32 at a time, one per lane
             for (int base = 0; base < npairs; base += 32) {
@@ -433,74 +700,10 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 const int j = active ? nth_set_bit(mo, kk - eo) : 0;
                 const int ei = active ? (g + warp * 32 + owner) : el;
 
-                // temporalIntersection: common span [a, b]; S = the segment
-                // that starts at a, O = the other one
-                const int64_t ets_k = ets[ei], ete_k = ete[ei];
-                const int64_t qts_k = S.qts[j], qte_k = S.qte[j];
-                const bool e_later = ets_k >= qts_k;
-                const int64_t a_k = e_later ? ets_k : qts_k;
-                const int64_t b_k = min(ete_k, qte_k);
-                const int64_t o_k = e_later ? qts_k : ets_k;
-                const double a = key_double(a_k), b = key_double(b_k), o_ts = key_double(o_k);
-                double epx_, epy_, epz_, evx_, evy_, evz_;
-                if (kFilter) {  // survivors are rare: read the FP64 entry from global memory
-                    const int64_t k = active ? e0 + ei : e0;
-                    epx_ = args.e.px[k]; epy_ = args.e.py[k]; epz_ = args.e.pz[k];
-                    evx_ = args.e.vx[k]; evy_ = args.e.vy[k]; evz_ = args.e.vz[k];
-                } else {
-                    epx_ = epx[ei]; epy_ = epy[ei]; epz_ = epz[ei];
-                    evx_ = evx[ei]; evy_ = evy[ei]; evz_ = evz[ei];
-                }
-                const double qpx_ = S.qp[0][j], qpy_ = S.qp[1][j], qpz_ = S.qp[2][j];
-                const double qvx_ = S.qv[0][j], qvy_ = S.qv[1][j], qvz_ = S.qv[2][j];
-                const double opx = e_later ? qpx_ : epx_, opy = e_later ? qpy_ : epy_, opz = e_later ? qpz_ : epz_;
-                const double ovx = e_later ? qvx_ : evx_, ovy = e_later ? qvy_ : evy_, ovz = e_later ? qvz_ : evz_;
-                const double spx = e_later ? epx_ : qpx_, spy = e_later ? epy_ : qpy_, spz = e_later ? epz_ : qpz_;
-                const double svx = e_later ? evx_ : qvx_, svy = e_later ? evy_ : qvy_, svz = e_later ? evz_ : qvz_;
-
-                // relative position O - S at a, and relative velocity
-                const double dt = a - o_ts;
-                const double dpx = fma(ovx, dt, opx) - spx;
-                const double dpy = fma(ovy, dt, opy) - spy;
-                const double dpz = fma(ovz, dt, opz) - spz;
-                const double dvx = ovx - svx, dvy = ovy - svy, dvz = ovz - svz;
-                // calcTimeInterval: |dp + dv tau|^2 - d^2 = A tau^2 + 2 Bh tau + C
-                const double A = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
-                const double Bh = fma(dpz, dvz, fma(dpy, dvy, dpx * dvx));
-                const double C = fma(dpz, dpz, fma(dpy, dpy, fma(dpx, dpx, -S.qd2[j])));
-                const double disc = fma(Bh, Bh, -(A * C));
-                // Minimum over [0, L] <= 0 without dividing: C <= 0 (in range
-                // at a), or approaching (Bh < 0) with a real root pair
-                // (disc >= 0) whose closest point lies inside the span or
-                // whose value at L is <= 0.
-                bool hit = le0(C);
-                const bool need_L = !hit && lt0(Bh) && ge0(disc);
-                if (__any_sync(kFull, active && need_L)) {
-                    const double L = b - a;
-                    const double gL = fma(A, L, Bh);
-                    const double fL = fma(gL + Bh, L, C);
-                    hit = hit || (need_L && (gt0(gL) || le0(fL)));
-                }
-                hit = hit && active;
-
-                const unsigned hm = __ballot_sync(kFull, hit);
-                if (hm) {
-                    unsigned long long rbase = 0;
-                    const int leader = __ffs(hm) - 1;
-                    if (lane == leader) rbase = atomicAdd(&ctr->results, (unsigned long long)__popc(hm));
-                    rbase = __shfl_sync(kFull, rbase, leader);
-                    if (hit) {
-                        double tin, tout;
-                        pair_interval(A, Bh, C, disc, a, b, &tin, &tout);
-                        const unsigned long long pos = rbase + __popc(hm & lt_mask);
-                        if (pos < cap) {
-                            args.out.query_seg_id[pos] = S.qid[j];
-                            args.out.entry_seg_id[pos] = args.e.seg_id[e0 + ei];
-                            args.out.t_enter[pos] = tin;
-                            args.out.t_exit[pos] = tout;
-                        }
-                    }
-                }
+                const PairEval r = eval_pair_fp64(active, ets[ei], ete[ei], S.qts[j], S.qte[j], epx[ei], epy[ei],
+                                                  epz[ei], evx[ei], evy[ei], evz[ei], S.qp[0][j], S.qp[1][j],
+                                                  S.qp[2][j], S.qv[0][j], S.qv[1][j], S.qv[2][j], S.qd2[j]);
+                append_hits(r, ctr, args.out, cap, S.qid[j], active ? args.e.seg_id[e0 + ei] : 0, lane, lt_mask);
             }
         }
         __syncthreads();  // the chunk is about to be restaged
@@ -510,26 +713,28 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
     for (int o = 16; o > 0; o >>= 1) {
         n_inter += __shfl_xor_sync(kFull, n_inter, o);
         n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
-        n_fp64 += __shfl_xor_sync(kFull, n_fp64, o);
     }
     if (lane == 0) {
         if (n_inter) atomicAdd(&ctr->interactions, n_inter);
-        if (n_overlap) atomicAdd(&ctr->overlap_pairs, n_overlap);
-        if (n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
+        if (n_overlap) {
+            atomicAdd(&ctr->overlap_pairs, n_overlap);
+            atomicAdd(&ctr->fp64_pairs, n_overlap);
+        }
     }
 }
 
-size_t pair_smem_bytes(uint32_t chunk, bool filter = false)
+size_t pair_smem_bytes(uint32_t chunk)
 {
-    return ((sizeof(PairSmem) + 15) & ~(size_t)15) + (size_t)chunk * (filter ? 32 : 64);
+    return ((sizeof(PairSmem) + 15) & ~(size_t)15) + (size_t)chunk * 64;
 }
 
 // Launch the pair kernel of the requested mode as a persistent grid (as many
-// CTAs as fit on every SM at once).
+// CTAs as fit on every SM at once).  The filter mode's pair kernel does not
+// count the overlapping pairs: launch_overlap_count does.
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, cudaStream_t stream)
 {
-    auto kern = filter ? traj_dist_search_kernel<true> : traj_dist_search_kernel<false>;
-    const size_t smem = pair_smem_bytes(pa.chunk, filter);
+    auto kern = filter ? traj_dist_filter_kernel : traj_dist_search_kernel;
+    const size_t smem = filter ? filter_smem_bytes(pa.chunk) : pair_smem_bytes(pa.chunk);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -539,6 +744,12 @@ cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, cu
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     kern<<<sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_count(const PairArgs &pa, uint64_t nq, uint64_t n, cudaStream_t stream)
+{
+    count_overlaps<<<grid_for(nq), kBlock, 0, stream>>>(pa.q, pa.e.ts_key, pa.e.te_sorted, n, pa.ctr);
     return cudaGetLastError();
 }
 
@@ -561,7 +772,7 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
                      + 9 * cb(cap, 8)                  // pre
                      + 2 * cb(cap, 8) + 2 * cb(cap, 4) // sort
                      + 12 * cb(cap, 8)                 // sorted query SoA
-                     + 2 * cb(cap, 16)                 // query spheres (before / after sorting)
+                     + 3 * cb(cap, 16)                 // query spheres (before / after sorting)
                      + cb(9, sizeof(double *));        // pre pointer table
     uint64_t ntiles = (cap + kQT - 1) / kQT;
     uint64_t tbytes = 2 * cb(ntiles, 8) + cb(ntiles + 1, 8);
@@ -599,6 +810,7 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
     q.qid = carve<int64_t>(p, cap); q.lo = carve<int64_t>(p, cap); q.hi = carve<int64_t>(p, cap);
     w.pre_sph = carve<float4>(p, cap);
     q.sph = carve<float4>(p, cap);
+    q.sph2 = carve<float4>(p, cap);
     w.pre_dev = carve<double *>(p, 9);
     if (cudaMemcpy(w.pre_dev, w.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
         return cuda_error(cudaGetLastError(), "search workspace: pointer table");
@@ -681,6 +893,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
         TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
         TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, stream));
         TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
+        if (filter) TDQ_CUDA(launch_overlap_count(pa, nq, idx->n, stream));
     } else {
         TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
         TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
@@ -702,7 +915,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     s.work_items = h.work_items;
     // query_prep; with entries: 8 sort passes x 3 kernels, query_gather,
     // tile_plan, scan, pair kernel
-    s.kernel_launches = idx->n > 0 ? 1 + 24 + 4 : 1;
+    s.kernel_launches = idx->n > 0 ? 1 + 24 + 4 + (filter ? 1 : 0) : 1;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s.pair_kernel_ms = ms;
     if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s.total_ms = ms;
@@ -866,7 +1079,7 @@ constexpr uint64_t kNoAllocScratchBytes =
     9 * na_bytes(kNoAllocMaxQueries, 8)                                      // pre columns
     + 2 * na_bytes(kNoAllocMaxQueries, 8) + 2 * na_bytes(kNoAllocMaxQueries, 4)  // sort keys / values
     + 12 * na_bytes(kNoAllocMaxQueries, 8)                                   // sorted query SoA
-    + 2 * na_bytes(kNoAllocMaxQueries, 16)                                   // query spheres
+    + 3 * na_bytes(kNoAllocMaxQueries, 16)                                   // query spheres
     + 2 * na_bytes(kNoAllocTiles, 8) + na_bytes(kNoAllocTiles + 1, 8)        // tile table
     + na_bytes(kNoAllocHistWords, 4)                                         // sort histogram
     + na_bytes(1, sizeof(DevCounters))                                       // counters
@@ -922,6 +1135,7 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         q.hi = carve<int64_t>(p, kNoAllocMaxQueries);
         s.pre_sph = carve<float4>(p, kNoAllocMaxQueries);
         q.sph = carve<float4>(p, kNoAllocMaxQueries);
+        q.sph2 = carve<float4>(p, kNoAllocMaxQueries);
         s.tile_lo = carve<int64_t>(p, kNoAllocTiles);
         s.tile_hi = carve<int64_t>(p, kNoAllocTiles);
         s.tile_work = carve<unsigned long long>(p, kNoAllocTiles + 1);
@@ -1000,7 +1214,9 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
                                                                  s->tile_work);
         TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
         PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk};
-        TDQ_CUDA(launch_pair_kernel(pa, params && params->mode == TDQ_MODE_FP32_FILTER, idx->sm_count, stream));
+        const bool filter = params && params->mode == TDQ_MODE_FP32_FILTER;
+        TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, stream));
+        if (filter) TDQ_CUDA(launch_overlap_count(pa, nq, idx->n, stream));
     }
     TDQ_CUDA(cudaGetLastError());
     DevCounters h{};

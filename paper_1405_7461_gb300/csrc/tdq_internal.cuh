@@ -58,20 +58,25 @@ __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }  // x >= 0
 
 // ---------------------------------------------------------------------------
 // Conservative FP32 bounding sphere of a segment piece whose FP64 center is
-// (cx,cy,cz) and radius r: the center rounded to nearest, the radius rounded
-// up after widening it by 2^-22 * max|c| (more than the sqrt(3) * 2^-24 *
-// max|c| the center's rounding can move it, and more than any FP64 rounding
-// of the positions the FP64 path evaluates) and by r * 2^-40.  Every point
-// the FP64 path can place on the piece lies inside the FP32 sphere.
-// Magnitudes beyond 2^60 get an infinite radius (never rejected).
+// (cx,cy,cz) and radius r, for the filter mode's pre-test.  The center is
+// rounded to nearest.  The radius w is widened by 2^-22 * max|c| (more than
+// the sqrt(3) * 2^-24 * max|c| the center's rounding can move it, and more
+// than any FP64 rounding of the positions the FP64 path evaluates), by
+// r * 2^-40, by `extra` (the threshold d, for a query) and by 2^-60 (so that
+// w > 0 and w^2 stays a normal number), then scaled by (1 + 2^-20) and
+// rounded up.  The scaling pays for the FP32 roundings of the pair test (see
+// spheres_may_meet).  Magnitudes beyond 2^60 get an infinite radius, which
+// never rejects.
 __device__ __forceinline__ float4 sphere32(double cx, double cy, double cz, double r, double extra)
 {
     double m = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
     float fr;
-    if (m < 0x1p60 && r < 0x1p60 && extra < 0x1p60)
-        fr = __double2float_ru(fma(r, 0x1p-40, r) + fma(m, 0x1p-22, extra));
-    else
+    if (m < 0x1p60 && r < 0x1p60 && extra < 0x1p60) {
+        double w = fma(r, 0x1p-40, r) + fma(m, 0x1p-22, extra) + 0x1p-60;
+        fr = __double2float_ru(fma(w, 0x1p-20, w));
+    } else {
         fr = __int_as_float(0x7f800000);
+    }
     return make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz), fr);
 }
 
@@ -96,6 +101,7 @@ struct EntrySoA {
     int64_t *ts_key, *te_key;
     int64_t *seg_id, *traj_id, *orig;
     float4 *sph;           // FP32 bounding sphere of the segment (center, radius rounded up)
+    int64_t *te_sorted;    // t_end keys in ascending order (for exact overlap counts)
 };
 
 // Sorted, clipped query segments in device memory.
@@ -107,6 +113,7 @@ struct QuerySoA {
     int64_t *qid;          // caller's segment id
     int64_t *lo, *hi;      // candidate range of sorted entry positions
     float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
+    float4 *sph2;          // (2 w, w^2 rounded up, 0, 0) for the pair pre-test
 };
 
 struct Workspace {
