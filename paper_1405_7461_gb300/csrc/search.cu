@@ -57,10 +57,24 @@ __device__ __forceinline__ bool is_nan_bits(double x)
     return b > 0x7ff0000000000000LL;
 }
 
+__device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
+{
+    double f = floor((t - t_min) / width);
+    if (!(f < (double)(m - 1))) return (int64_t)m - 1;
+    if (f < 0.0) return 0;
+    return (int64_t)f;
+}
+
+struct BinView {
+    const int64_t *bin_begin, *bin_pmax_key;
+    double t_min, width;
+    uint32_t m;
+};
+
 // Validate and clip every query segment.  pre[] columns: px py pz vx vy vz d2
 // ts_key te_key (keys stored bitwise in the double arrays).
-__global__ void query_prep(QueryInput in, uint64_t nq, double *const *pre, float4 *pre_sph, uint64_t *keys,
-                           uint32_t *vals, DevCounters *ctr)
+__global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *const *pre, float4 *pre_sph,
+                           uint64_t *keys, uint32_t *vals, DevCounters *ctr)
 {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
@@ -107,26 +121,14 @@ __global__ void query_prep(QueryInput in, uint64_t nq, double *const *pre, float
             sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), vn * h, fma(d, 0x1p-30, d));
         }
         pre_sph[i] = sp;
-        keys[i] = valid ? ((uint64_t)cs ^ 0x8000000000000000ULL) : ~0ULL;
+        // sort key: the temporal bin of the clipped start (tiles of 32 sorted
+        // query segments then span few bins); invalid segments sort last
+        keys[i] = valid ? (uint64_t)bin_of(key_double(cs), bins.t_min, bins.width, bins.m) : (uint64_t)bins.m;
         vals[i] = (uint32_t)i;
     }
     unsigned vm = __ballot_sync(kFull, valid);
     if ((threadIdx.x & 31) == 0 && vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
 }
-
-__device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
-{
-    double f = floor((t - t_min) / width);
-    if (!(f < (double)(m - 1))) return (int64_t)m - 1;
-    if (f < 0.0) return 0;
-    return (int64_t)f;
-}
-
-struct BinView {
-    const int64_t *bin_begin, *bin_pmax_key;
-    double t_min, width;
-    uint32_t m;
-};
 
 // Sorted query SoA and the candidate range of each query segment.
 __global__ void query_gather(const double *const *pre, const float4 *pre_sph, const int64_t *seg_id,
@@ -143,9 +145,7 @@ __global__ void query_gather(const double *const *pre, const float4 *pre_sph, co
     q.ts_key[k] = cs;
     q.te_key[k] = ce;
     q.qid[k] = seg_id[i];
-    const float4 sp = pre_sph[i];
-    q.sph[k] = sp;
-    q.sph2[k] = make_float4(2.0f * sp.w, __fmul_ru(sp.w, sp.w), 0.f, 0.f);
+    q.sph[k] = pre_sph[i];
     // First bin whose extent reaches past the query start: the prefix maximum
     // of bin ends is non-decreasing, so this is a binary search (Sec. 4 uses
     // an index tree over the bin extents for the same lookup).
@@ -372,7 +372,6 @@ struct FilterDesc {
 
 struct FilterSmem {
     float4 qa[2][kQT];  // (cx, cy, cz, w) of the tile's query segments, w = radius + d
-    float4 qb[2][kQT];  // (2w, w^2, -, -)
     FilterDesc desc[2];
     // followed by the entry chunks: float4 spheres, [2][chunk]
 };
@@ -387,9 +386,12 @@ size_t filter_smem_bytes(uint32_t chunk)
 // copied into the other half of a double buffer with cp.async while the
 // current item is tested.  Per candidate pair the test is 8 FP32 operations
 // and one funnel shift that moves the sign of
-//   |c_e - c_q|^2 - (w_e + w_q)^2   (rounded so that it is negative whenever
-//                                     the exact spheres meet)
-// into the lane's 32-bit mask.  Exact temporal overlap is checked only for
+//   v = |c_e - c_q|^2 - R^2,  R = w_e + w_q rounded up, R^2 rounded up,
+// into the lane's 32-bit mask.  v is negative whenever the exact spheres
+// meet: with u = 2^-24, the center differences and the three fused steps
+// add at most ~5u (|c_e - c_q|^2 + R^2) of rounding, while the radii carry
+// a factor (1 + 2^-20) >= (1 + 16u) (so R^2 exceeds the exact bound by at
+// least 32u of itself); R >= 2^-60 keeps every quantity normal.  Exact temporal overlap is checked only for
 // survivors (the count of all overlapping pairs comes from count_overlaps).
 __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(PairArgs args)
 {
@@ -435,10 +437,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(PairArgs
         float4 *dst = es + (size_t)slot * EC;
         const float4 *src = args.e.sph + d.e0;
         for (int i = tid; i < d.ne; i += kPairThreads) cp_async16(dst + i, src + i);
-        if (tid < d.nqt) {
-            cp_async16(&S.qa[slot][tid], args.q.sph + d.q0 + tid);
-            cp_async16(&S.qb[slot][tid], args.q.sph2 + d.q0 + tid);
-        }
+        if (tid < d.nqt) cp_async16(&S.qa[slot][tid], args.q.sph + d.q0 + tid);
     };
 
     if (tid == 0) {
@@ -476,60 +475,71 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(PairArgs
             const unsigned qvalid = 0xffffffffu << (kQT - cur.nqt);  // bit 31-j <-> query j
             if (tid == 0) n_inter += (unsigned long long)ne * (unsigned long long)cur.nqt;
             const float4 *esl = es + (size_t)slot * EC;
-            for (int g = 0; g < (int)EC; g += kPairThreads) {
+            const float4 *qsl = S.qa[slot];
+            // each lane tests two entries (el and el + 256) per query load
+            for (int g = 0; g < (int)EC; g += 2 * kPairThreads) {
                 if (g + warp * 32 >= ne) break;  // warp-uniform: nothing left for this warp
-                const int el = g + warp * 32 + lane;
-                unsigned mask = 0;
+                const int el0 = g + warp * 32 + lane;
+                const int el1 = el0 + kPairThreads;
+                unsigned m0 = 0, m1 = 0;
                 {
-                    const float4 e = esl[el];
+                    const float4 e0 = esl[el0];
+                    const float4 e1 = esl[el1 < (int)EC ? el1 : el0];
 #pragma unroll
                     for (int j = 0; j < kQT; j++) {
-                        const float4 qa = S.qa[slot][j];
-                        const float4 qb = S.qb[slot][j];
-                        const float dx = e.x - qa.x, dy = e.y - qa.y, dz = e.z - qa.z;
-                        const float thr = __fmaf_ru(e.w, __fadd_ru(e.w, qb.x), qb.y);
-                        const float v = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -thr)));
-                        mask = __funnelshift_l(__float_as_uint(v), mask, 1);
+                        const float4 q = qsl[j];
+                        const float dx0 = e0.x - q.x, dy0 = e0.y - q.y, dz0 = e0.z - q.z;
+                        const float R0 = __fadd_ru(e0.w, q.w);
+                        const float v0 = fmaf(dz0, dz0, fmaf(dy0, dy0, fmaf(dx0, dx0, -__fmul_ru(R0, R0))));
+                        m0 = __funnelshift_l(__float_as_uint(v0), m0, 1);
+                        const float dx1 = e1.x - q.x, dy1 = e1.y - q.y, dz1 = e1.z - q.z;
+                        const float R1 = __fadd_ru(e1.w, q.w);
+                        const float v1 = fmaf(dz1, dz1, fmaf(dy1, dy1, fmaf(dx1, dx1, -__fmul_ru(R1, R1))));
+                        m1 = __funnelshift_l(__float_as_uint(v1), m1, 1);
                     }
                 }
-                mask &= qvalid;
-                if (el >= ne) mask = 0;
-                const int cnt = __popc(mask);
-                int incl = cnt;
+                m0 = el0 < ne ? (m0 & qvalid) : 0u;
+                m1 = el1 < ne ? (m1 & qvalid) : 0u;
+                if (!__any_sync(kFull, (m0 | m1) != 0u)) continue;
+                for (int half = 0; half < 2; half++) {
+                    const unsigned mask = half ? m1 : m0;
+                    const int gbase = g + half * kPairThreads + warp * 32;
+                    const int cnt = __popc(mask);
+                    int incl = cnt;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int npairs = __shfl_sync(kFull, incl, 31);
-                if (npairs == 0) continue;
-                const int excl = incl - cnt;
-                for (int base = 0; base < npairs; base += 32) {
-                    const int kk = base + lane;
-                    const bool valid = kk < npairs;
-                    int owner = 0;
-#pragma unroll
-                    for (int s = 16; s >= 1; s >>= 1) {
-                        int v = __shfl_sync(kFull, incl, owner + s - 1);
-                        if (v <= kk) owner += s;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
                     }
-                    const unsigned mo = __shfl_sync(kFull, mask, owner);
-                    const int eo = __shfl_sync(kFull, excl, owner);
-                    const int j = valid ? (31 - nth_set_bit(mo, kk - eo)) : 0;
-                    const int64_t ek = cur.e0 + (valid ? g + warp * 32 + owner : 0);
-                    const int64_t qk = cur.q0 + j;
-                    // exact temporal overlap of the survivor
-                    const int64_t ets_k = args.e.ts_key[ek], ete_k = args.e.te_key[ek];
-                    const int64_t qts_k = args.q.ts_key[qk], qte_k = args.q.te_key[qk];
-                    const bool active = valid && (ets_k < qte_k) && (ete_k > qts_k);
-                    const unsigned am = __ballot_sync(kFull, active);
-                    if (lane == 0) n_fp64 += (unsigned long long)__popc(am);
-                    if (!am) continue;
-                    const PairEval r = eval_pair_fp64(
-                        active, ets_k, ete_k, qts_k, qte_k, args.e.px[ek], args.e.py[ek], args.e.pz[ek],
-                        args.e.vx[ek], args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk], args.q.pz[qk],
-                        args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
-                    append_hits(r, ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+                    const int npairs = __shfl_sync(kFull, incl, 31);
+                    const int excl = incl - cnt;
+                    for (int base = 0; base < npairs; base += 32) {
+                        const int kk = base + lane;
+                        const bool valid = kk < npairs;
+                        int owner = 0;
+#pragma unroll
+                        for (int s = 16; s >= 1; s >>= 1) {
+                            int v = __shfl_sync(kFull, incl, owner + s - 1);
+                            if (v <= kk) owner += s;
+                        }
+                        const unsigned mo = __shfl_sync(kFull, mask, owner);
+                        const int eo = __shfl_sync(kFull, excl, owner);
+                        const int j = valid ? (31 - nth_set_bit(mo, kk - eo)) : 0;
+                        const int64_t ek = cur.e0 + (valid ? gbase + owner : 0);
+                        const int64_t qk = cur.q0 + j;
+                        // exact temporal overlap of the survivor
+                        const int64_t ets_k = args.e.ts_key[ek], ete_k = args.e.te_key[ek];
+                        const int64_t qts_k = args.q.ts_key[qk], qte_k = args.q.te_key[qk];
+                        const bool active = valid && (ets_k < qte_k) && (ete_k > qts_k);
+                        const unsigned am = __ballot_sync(kFull, active);
+                        if (lane == 0) n_fp64 += (unsigned long long)__popc(am);
+                        if (!am) continue;
+                        const PairEval r = eval_pair_fp64(
+                            active, ets_k, ete_k, qts_k, qte_k, args.e.px[ek], args.e.py[ek], args.e.pz[ek],
+                            args.e.vx[ek], args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk],
+                            args.q.pz[qk], args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
+                        append_hits(r, ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+                    }
                 }
             }
             if (tid == 0) {
@@ -772,7 +782,7 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
                      + 9 * cb(cap, 8)                  // pre
                      + 2 * cb(cap, 8) + 2 * cb(cap, 4) // sort
                      + 12 * cb(cap, 8)                 // sorted query SoA
-                     + 3 * cb(cap, 16)                 // query spheres (before / after sorting)
+                     + 2 * cb(cap, 16)                 // query spheres (before / after sorting)
                      + cb(9, sizeof(double *));        // pre pointer table
     uint64_t ntiles = (cap + kQT - 1) / kQT;
     uint64_t tbytes = 2 * cb(ntiles, 8) + cb(ntiles + 1, 8);
@@ -810,7 +820,6 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
     q.qid = carve<int64_t>(p, cap); q.lo = carve<int64_t>(p, cap); q.hi = carve<int64_t>(p, cap);
     w.pre_sph = carve<float4>(p, cap);
     q.sph = carve<float4>(p, cap);
-    q.sph2 = carve<float4>(p, cap);
     w.pre_dev = carve<double *>(p, 9);
     if (cudaMemcpy(w.pre_dev, w.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
         return cuda_error(cudaGetLastError(), "search workspace: pointer table");
@@ -845,7 +854,8 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
         if (!cols[c]) return set_error(TDQ_ERR_INVALID, "tdq_search: query column %d is NULL", c);
     if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_search: query seg_id is NULL");
 
-    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
+    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk
+                     : ((params && params->mode == TDQ_MODE_FP32_FILTER) ? 1024u : 512u);
     if (chunk % kPairThreads != 0 || chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
     if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
@@ -879,11 +889,12 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     TDQ_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream));
     TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
     double *const *pre = w.pre_dev;
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, pre, w.pre_sph, w.keys, w.vals, w.ctr);
+    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
-        TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream));
-        BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+        TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
+                                  bin_key_bits(idx->m)));
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
         tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, chunk, w.tile_lo, w.tile_hi,
                                                                  w.tile_work);
@@ -915,7 +926,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     s.work_items = h.work_items;
     // query_prep; with entries: 8 sort passes x 3 kernels, query_gather,
     // tile_plan, scan, pair kernel
-    s.kernel_launches = idx->n > 0 ? 1 + 24 + 4 + (filter ? 1 : 0) : 1;
+    s.kernel_launches = idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 4 + (filter ? 1 : 0) : 1;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s.pair_kernel_ms = ms;
     if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s.total_ms = ms;
@@ -1079,7 +1090,7 @@ constexpr uint64_t kNoAllocScratchBytes =
     9 * na_bytes(kNoAllocMaxQueries, 8)                                      // pre columns
     + 2 * na_bytes(kNoAllocMaxQueries, 8) + 2 * na_bytes(kNoAllocMaxQueries, 4)  // sort keys / values
     + 12 * na_bytes(kNoAllocMaxQueries, 8)                                   // sorted query SoA
-    + 3 * na_bytes(kNoAllocMaxQueries, 16)                                   // query spheres
+    + 2 * na_bytes(kNoAllocMaxQueries, 16)                                   // query spheres
     + 2 * na_bytes(kNoAllocTiles, 8) + na_bytes(kNoAllocTiles + 1, 8)        // tile table
     + na_bytes(kNoAllocHistWords, 4)                                         // sort histogram
     + na_bytes(1, sizeof(DevCounters))                                       // counters
@@ -1135,7 +1146,6 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         q.hi = carve<int64_t>(p, kNoAllocMaxQueries);
         s.pre_sph = carve<float4>(p, kNoAllocMaxQueries);
         q.sph = carve<float4>(p, kNoAllocMaxQueries);
-        q.sph2 = carve<float4>(p, kNoAllocMaxQueries);
         s.tile_lo = carve<int64_t>(p, kNoAllocTiles);
         s.tile_hi = carve<int64_t>(p, kNoAllocTiles);
         s.tile_work = carve<unsigned long long>(p, kNoAllocTiles + 1);
@@ -1174,7 +1184,8 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search_device_noalloc: %llu query segments exceed the fixed maximum of %llu",
                          (unsigned long long)nq, (unsigned long long)kNoAllocMaxQueries);
-    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
+    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk
+                     : ((params && params->mode == TDQ_MODE_FP32_FILTER) ? 1024u : 512u);
     if (chunk % kPairThreads != 0 || chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search_device_noalloc: entry_chunk must be a multiple of 256, <= 2048");
     if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
@@ -1203,11 +1214,12 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     in.t1 = t1;
     // the array keeps the previous call's contents: clear the counters
     TDQ_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), stream));
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr);
+    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr);
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
-        TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream));
-        BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+        TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream,
+                                  bin_key_bits(idx->m)));
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(s->pre_dev, s->pre_sph, in.seg_id, s->vals, nq, s->ctr,
                                                           bins, s->q);
         tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(s->q, ntiles, s->ctr, chunk, s->tile_lo, s->tile_hi,

@@ -141,21 +141,22 @@ uint64_t sort_hist_words(uint64_t n)
 }
 
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
-                             uint32_t *hist, cudaStream_t stream)
+                             uint32_t *hist, cudaStream_t stream, int key_bits)
 {
     if (n <= 1) return cudaSuccess;
     if (n > 0xffffffffULL) return cudaErrorInvalidValue;  // 32-bit offsets
     uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     uint64_t *src_k = keys, *dst_k = keys_alt;
     uint32_t *src_v = vals, *dst_v = vals_alt;
-    for (int shift = 0; shift < 64; shift += 8) {
+    const int passes = sort_passes(key_bits < 64 ? key_bits : 64);
+    for (int shift = 0; shift < 8 * passes; shift += 8) {
         radix_hist<<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
         scan_exclusive_block<uint32_t><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
         radix_scatter<<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
         uint64_t *tk = src_k; src_k = dst_k; dst_k = tk;
         uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
     }
-    // eight passes: the data is back in keys/vals
+    // an even number of passes: the data is back in keys/vals
     return cudaGetLastError();
 }
 

@@ -113,7 +113,6 @@ struct QuerySoA {
     int64_t *qid;          // caller's segment id
     int64_t *lo, *hi;      // candidate range of sorted entry positions
     float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
-    float4 *sph2;          // (2 w, w^2 rounded up, 0, 0) for the pair pre-test
 };
 
 struct Workspace {
@@ -179,9 +178,18 @@ tdq_status cuda_error(cudaError_t e, const char *what);
 // Radix sort (sort.cu): stable ascending sort of (keys, vals) of length n.
 // keys_alt/vals_alt are scratch of the same size; hist holds
 // sort_hist_words(n) words.  The sorted data ends in keys/vals.
+// Only the low key_bits bits are sorted on (an even number of 8-bit passes).
 uint64_t sort_hist_words(uint64_t n);
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
-                             uint32_t *hist, cudaStream_t stream);
+                             uint32_t *hist, cudaStream_t stream, int key_bits = 64);
+inline int sort_passes(int key_bits) { return 2 * ((key_bits + 15) / 16); }
+// Bits of a query sort key: bin indices 0..m-1 and m for invalid segments.
+inline int bin_key_bits(uint32_t m)
+{
+    int b = 1;
+    while (b < 32 && ((uint64_t)1 << b) <= (uint64_t)m) b++;
+    return b;
+}
 
 // Single-block exclusive scan of n counters in place; total written to *total.
 cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,
