@@ -81,7 +81,7 @@ enum {
 typedef struct {
     uint32_t query_tile;  /* query segments per tile (multiple of 32, <= 32; default 32) */
     uint32_t entry_chunk; /* entry segments per work item (multiple of 256, <= 2048; default 512 in
-                             FP64 mode, 1024 in filter mode) */
+                             FP64 mode, 256 in filter mode) */
     int mode;             /* TDQ_MODE_* (default TDQ_MODE_FP64) */
 } tdq_search_params;
 

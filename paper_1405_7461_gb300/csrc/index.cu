@@ -105,6 +105,23 @@ __global__ void te_store(const uint64_t *keys, uint64_t n, int64_t *te_sorted)
     te_sorted[k] = (int64_t)(keys[k] ^ 0x8000000000000000ULL);
 }
 
+// Largest sphere radius of each aligned block of 64 sorted entries (one
+// warp per block).
+__global__ void block_wmax(const float4 *sph, uint64_t n, float *out)
+{
+    const uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b * 64 >= n) return;
+    float w = 0.f;
+    for (int k = lane; k < 64; k += 32) {
+        const uint64_t i = b * 64 + k;
+        if (i < n) w = fmaxf(w, sph[i].w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if (lane == 0) out[b] = w;
+}
+
 __device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
 {
     double f = floor((t - t_min) / width);
@@ -246,7 +263,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     }
 
     // Resident sorted copy + bin table.
-    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 16) + 256;
+    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n / 64 + 1, 4) + carve_bytes(n, 16);
     uint64_t bbytes = carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (cudaMalloc(&idx->e_block, ebytes) != cudaSuccess || cudaMalloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -262,7 +279,8 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         e.ts_key = carve<int64_t>(p, n); e.te_key = carve<int64_t>(p, n);
         e.seg_id = carve<int64_t>(p, n); e.traj_id = carve<int64_t>(p, n); e.orig = carve<int64_t>(p, n);
         e.te_sorted = carve<int64_t>(p, n);
-        e.sph = carve<float4>(p, n);  // last: the filter kernel may read one item past n
+        e.blk_wmax = carve<float>(p, n / 64 + 1);
+        e.sph = carve<float4>(p, n);
         char *q = (char *)idx->b_block;
         idx->bin_begin = carve<int64_t>(q, m + 1);
         idx->bin_end_key = carve<int64_t>(q, m);
@@ -369,6 +387,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             break;
         }
         te_store<<<grid_for(n), kBlock, 0, stream>>>(keys, n, idx->e.te_sorted);
+        block_wmax<<<grid_for((n + 63) / 64 * 32), kBlock, 0, stream>>>(idx->e.sph, n, idx->e.blk_wmax);
         if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: index kernels");
             break;
@@ -432,6 +451,7 @@ extern "C" void tdq_index_free(tdq_index *idx)
     cudaFree(w.t_block);
     cudaFree(w.sort_hist);
     cudaFree(w.r_block);
+    cudaFree(w.s_block);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < 4; k++)

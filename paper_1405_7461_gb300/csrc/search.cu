@@ -355,210 +355,188 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // Filter mode: conservative FP32 pre-test, FP64 for the survivors.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-struct FilterDesc {
-    long long item;  // < 0: none
-    long long e0;    // first sorted entry of the chunk
-    long long q0;    // first sorted query segment of the tile
-    int ne, nqt;
-};
-
-struct FilterSmem {
-    float4 qa[2][kQT];  // (cx, cy, cz, w) of the tile's query segments, w = radius + d
-    FilterDesc desc[2];
-    // followed by the entry chunks: float4 spheres, [2][chunk]
-};
-
-size_t filter_smem_bytes(uint32_t chunk)
-{
-    return ((sizeof(FilterSmem) + 15) & ~(size_t)15) + (size_t)2 * chunk * sizeof(float4);
-}
-
-// Work items are split into contiguous ranges, one per CTA; a CTA walks the
-// tile table forward.  Entry spheres and query spheres of the next item are
-// copied into the other half of a double buffer with cp.async while the
-// current item is tested.  Per candidate pair the test is 8 FP32 operations
-// and one funnel shift that moves the sign of
-//   v = |c_e - c_q|^2 - R^2,  R = w_e + w_q rounded up, R^2 rounded up,
+// Work items of the filter kernel are (tile, chunk) pairs as for the plain
+// kernel, but each is processed by one warp: the warps of the grid split the
+// items into contiguous ranges; a warp walks the tile table forward, keeps
+// the tile's 32 query spheres in its own slice of shared memory (reloaded
+// only when the tile changes), and reads its entry spheres straight into
+// registers, two per lane per pass over the queries, the next pair loaded
+// while the current one is tested.  No CTA-wide barrier is involved.
+//
+// A pass covers 64 consecutive entries.  For the pass, lane j computes the
+// bound R_j^2 = (w_max + w_j)^2 (rounded up) where w_max is the largest
+// radius of the aligned 64-entry blocks the pass touches; then per candidate
+// pair the test is 6 FP32 operations and one funnel shift that moves the
+// sign of
+//   v = |c_e - c_q|^2 - R_j^2
 // into the lane's 32-bit mask.  v is negative whenever the exact spheres
 // meet: with u = 2^-24, the center differences and the three fused steps
-// add at most ~5u (|c_e - c_q|^2 + R^2) of rounding, while the radii carry
-// a factor (1 + 2^-20) >= (1 + 16u) (so R^2 exceeds the exact bound by at
-// least 32u of itself); R >= 2^-60 keeps every quantity normal.  Exact temporal overlap is checked only for
-// survivors (the count of all overlapping pairs comes from count_overlaps).
-__global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(PairArgs args)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FilterSmem &S = *reinterpret_cast<FilterSmem *>(smem_raw);
-    const uint32_t EC = args.chunk;
-    float4 *es = reinterpret_cast<float4 *>(smem_raw + ((sizeof(FilterSmem) + 15) & ~(size_t)15));
+// add at most ~5u (|c_e - c_q|^2 + R^2) of rounding, while the radii carry a
+// factor (1 + 2^-20) >= (1 + 16u) (so R^2 exceeds the exact bound by at
+// least 32u of itself); R >= 2^-60 keeps every quantity normal.  The
+// survivors (entry, query) are appended to a list with one atomic per warp;
+// traj_dist_refine_kernel then evaluates them in FP64.
+constexpr int kFilterWarps = kPairThreads / 32;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
+__device__ __forceinline__ float sphere_gap2(float4 e, float4 q)
+{
+    const float dx = e.x - q.x, dy = e.y - q.y, dz = e.z - q.z;
+    return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -q.w)));
+}
+
+struct FilterArgs {
+    PairArgs p;
+    uint2 *surv;            // survivor list: (sorted entry position, sorted query position)
+    uint64_t surv_cap;
+};
+
+__global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterArgs fa)
+{
+    const PairArgs &args = fa.p;
+    __shared__ float4 qs_all[kFilterWarps][kQT];  // the tile's query spheres (cx, cy, cz, w)
+    __shared__ float4 qr_all[kFilterWarps][kQT];  // per pass: (cx, cy, cz, R_j^2)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *qs = qs_all[warp];
+    float4 *qr = qr_all[warp];
     DevCounters *ctr = args.ctr;
+    const uint32_t EC = args.chunk;
     const unsigned long long total = args.tile_work[args.ntiles];
     const uint64_t nvalid = ctr->valid_queries;
-    const uint64_t cap = args.out.capacity;
-    const unsigned long long per = (total + gridDim.x - 1) / gridDim.x;
-    const unsigned long long ibeg = min((unsigned long long)blockIdx.x * per, total);
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * kFilterWarps;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * kFilterWarps + warp;
+    const unsigned long long per = (total + nwarps - 1) / nwarps;
+    const unsigned long long ibeg = min(gw * per, total);
     const unsigned long long iend = min(ibeg + per, total);
-    unsigned long long n_inter = 0, n_fp64 = 0;
+    unsigned long long n_inter = 0;
 
-    // thread 0's position in the tile table
-    uint64_t t_walk = 0;
-    unsigned long long w_base = 0, w_next = 0;
-    int64_t t_lo = 0, t_hi = 0;
-    auto describe = [&](unsigned long long item, FilterDesc &d) {
-        bool moved = false;
-        while (w_next <= item) {
-            t_walk++;
-            w_base = w_next;
-            w_next = args.tile_work[t_walk + 1];
-            moved = true;
-        }
-        if (moved) {
-            t_lo = args.tile_lo[t_walk];
-            t_hi = args.tile_hi[t_walk];
-        }
-        d.item = (long long)item;
-        d.e0 = t_lo + (long long)(item - w_base) * EC;
-        d.ne = (int)(min(d.e0 + (long long)EC, (long long)t_hi) - d.e0);
-        d.q0 = (long long)t_walk * kQT;
-        d.nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)d.q0);
-    };
-    auto issue = [&](int slot, const FilterDesc &d) {
-        float4 *dst = es + (size_t)slot * EC;
-        const float4 *src = args.e.sph + d.e0;
-        for (int i = tid; i < d.ne; i += kPairThreads) cp_async16(dst + i, src + i);
-        if (tid < d.nqt) cp_async16(&S.qa[slot][tid], args.q.sph + d.q0 + tid);
-    };
-
-    if (tid == 0) {
-        S.desc[0].item = -1;
-        S.desc[1].item = -1;
-        if (ibeg < iend) {
+    if (ibeg < iend) {
+        // position in the tile table (the same on every lane)
+        uint64_t t = 0;
+        {
             uint64_t lo = 0, hi = args.ntiles;  // last tile whose first item is <= ibeg
             while (hi - lo > 1) {
                 uint64_t mid = (lo + hi) >> 1;
                 if (args.tile_work[mid] <= ibeg) lo = mid; else hi = mid;
             }
-            t_walk = lo;
-            w_base = args.tile_work[lo];
-            w_next = args.tile_work[lo + 1];
-            t_lo = args.tile_lo[lo];
-            t_hi = args.tile_hi[lo];
-            describe(ibeg, S.desc[0]);
-            if (ibeg + 1 < iend) describe(ibeg + 1, S.desc[1]);
+            t = lo;
         }
-    }
-    __syncthreads();
-    if (S.desc[0].item >= 0) {
-        issue(0, S.desc[0]);
-        cp_async_commit();
-        int slot = 0;
-        for (unsigned long long it = ibeg; it < iend; it++) {
-            const FilterDesc cur = S.desc[slot];
-            const FilterDesc nxt = S.desc[slot ^ 1];
-            if (nxt.item >= 0) issue(slot ^ 1, nxt);
-            cp_async_commit();
-            cp_async_wait_prior();  // this item's copies have landed
-            __syncthreads();
+        unsigned long long w_base = args.tile_work[t], w_next = args.tile_work[t + 1];
+        int64_t t_lo = args.tile_lo[t], t_hi = args.tile_hi[t];
+        int64_t q0 = (int64_t)t * kQT;
+        int nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)q0);
+        float4 my_q = lane < nqt ? args.q.sph[q0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
 
-            const int ne = cur.ne;
-            const unsigned qvalid = 0xffffffffu << (kQT - cur.nqt);  // bit 31-j <-> query j
-            if (tid == 0) n_inter += (unsigned long long)ne * (unsigned long long)cur.nqt;
-            const float4 *esl = es + (size_t)slot * EC;
-            const float4 *qsl = S.qa[slot];
-            // each lane tests two entries (el and el + 256) per query load
-            for (int g = 0; g < (int)EC; g += 2 * kPairThreads) {
-                if (g + warp * 32 >= ne) break;  // warp-uniform: nothing left for this warp
-                const int el0 = g + warp * 32 + lane;
-                const int el1 = el0 + kPairThreads;
-                unsigned m0 = 0, m1 = 0;
-                {
-                    const float4 e0 = esl[el0];
-                    const float4 e1 = esl[el1 < (int)EC ? el1 : el0];
-#pragma unroll
-                    for (int j = 0; j < kQT; j++) {
-                        const float4 q = qsl[j];
-                        const float dx0 = e0.x - q.x, dy0 = e0.y - q.y, dz0 = e0.z - q.z;
-                        const float R0 = __fadd_ru(e0.w, q.w);
-                        const float v0 = fmaf(dz0, dz0, fmaf(dy0, dy0, fmaf(dx0, dx0, -__fmul_ru(R0, R0))));
-                        m0 = __funnelshift_l(__float_as_uint(v0), m0, 1);
-                        const float dx1 = e1.x - q.x, dy1 = e1.y - q.y, dz1 = e1.z - q.z;
-                        const float R1 = __fadd_ru(e1.w, q.w);
-                        const float v1 = fmaf(dz1, dz1, fmaf(dy1, dy1, fmaf(dx1, dx1, -__fmul_ru(R1, R1))));
-                        m1 = __funnelshift_l(__float_as_uint(v1), m1, 1);
-                    }
+        for (unsigned long long it = ibeg; it < iend; it++) {
+            if (w_next <= it) {  // next tile (possibly skipping tiles without work)
+                do {
+                    t++;
+                    w_base = w_next;
+                    w_next = args.tile_work[t + 1];
+                } while (w_next <= it);
+                t_lo = args.tile_lo[t];
+                t_hi = args.tile_hi[t];
+                q0 = (int64_t)t * kQT;
+                nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)q0);
+                my_q = lane < nqt ? args.q.sph[q0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const int64_t e0 = t_lo + (int64_t)(it - w_base) * EC;
+            const int ne = (int)(min(e0 + (int64_t)EC, t_hi) - e0);
+            const unsigned qvalid = 0xffffffffu << (kQT - nqt);  // bit 31-j <-> query j
+            if (lane == 0) n_inter += (unsigned long long)ne * (unsigned long long)nqt;
+            // entry pairs (el, el + 32), el = 64 p + lane; prefetched one pass ahead
+            const int npass = (ne + 63) / 64;
+            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+            if (lane < ne) na = args.e.sph[e0 + lane];
+            if (lane + 32 < ne) nb = args.e.sph[e0 + lane + 32];
+            for (int p = 0; p < npass; p++) {
+                const float4 ea = na, eb = nb;
+                const int ela = 64 * p + lane, elb = ela + 32;
+                const int64_t pe = e0 + 64 * p;  // first entry of the pass
+                if (p + 1 < npass) {
+                    if (ela + 64 < ne) na = args.e.sph[e0 + ela + 64];
+                    if (elb + 64 < ne) nb = args.e.sph[e0 + elb + 64];
                 }
-                m0 = el0 < ne ? (m0 & qvalid) : 0u;
-                m1 = el1 < ne ? (m1 & qvalid) : 0u;
-                if (!__any_sync(kFull, (m0 | m1) != 0u)) continue;
-                for (int half = 0; half < 2; half++) {
-                    const unsigned mask = half ? m1 : m0;
-                    const int gbase = g + half * kPairThreads + warp * 32;
-                    const int cnt = __popc(mask);
-                    int incl = cnt;
+                // per-pass bound of query j = lane
+                const int64_t plast = pe + min(63, ne - 1 - 64 * p);
+                const float wmax = fmaxf(args.e.blk_wmax[pe >> 6], args.e.blk_wmax[plast >> 6]);
+                const float Rj = __fadd_ru(wmax, my_q.w);
+                __syncwarp();
+                qr[lane] = make_float4(my_q.x, my_q.y, my_q.z, __fmul_ru(Rj, Rj));
+                __syncwarp();
+                unsigned ma = 0, mb = 0;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        int y = __shfl_up_sync(kFull, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const int npairs = __shfl_sync(kFull, incl, 31);
-                    const int excl = incl - cnt;
-                    for (int base = 0; base < npairs; base += 32) {
-                        const int kk = base + lane;
-                        const bool valid = kk < npairs;
-                        int owner = 0;
+                for (int j = 0; j < kQT; j++) {
+                    const float4 q = qr[j];
+                    ma = __funnelshift_l(__float_as_uint(sphere_gap2(ea, q)), ma, 1);
+                    mb = __funnelshift_l(__float_as_uint(sphere_gap2(eb, q)), mb, 1);
+                }
+                ma = ela < ne ? (ma & qvalid) : 0u;
+                mb = elb < ne ? (mb & qvalid) : 0u;
+                if (!__any_sync(kFull, (ma | mb) != 0u)) continue;
+                // append this lane's survivors: one atomic per warp
+                const int cnt = __popc(ma) + __popc(mb);
+                int incl = cnt;
 #pragma unroll
-                        for (int s = 16; s >= 1; s >>= 1) {
-                            int v = __shfl_sync(kFull, incl, owner + s - 1);
-                            if (v <= kk) owner += s;
-                        }
-                        const unsigned mo = __shfl_sync(kFull, mask, owner);
-                        const int eo = __shfl_sync(kFull, excl, owner);
-                        const int j = valid ? (31 - nth_set_bit(mo, kk - eo)) : 0;
-                        const int64_t ek = cur.e0 + (valid ? gbase + owner : 0);
-                        const int64_t qk = cur.q0 + j;
-                        // exact temporal overlap of the survivor
-                        const int64_t ets_k = args.e.ts_key[ek], ete_k = args.e.te_key[ek];
-                        const int64_t qts_k = args.q.ts_key[qk], qte_k = args.q.te_key[qk];
-                        const bool active = valid && (ets_k < qte_k) && (ete_k > qts_k);
-                        const unsigned am = __ballot_sync(kFull, active);
-                        if (lane == 0) n_fp64 += (unsigned long long)__popc(am);
-                        if (!am) continue;
-                        const PairEval r = eval_pair_fp64(
-                            active, ets_k, ete_k, qts_k, qte_k, args.e.px[ek], args.e.py[ek], args.e.pz[ek],
-                            args.e.vx[ek], args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk],
-                            args.q.pz[qk], args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
-                        append_hits(r, ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int wtot = __shfl_sync(kFull, incl, 31);
+                unsigned long long sbase = 0;
+                if (lane == 31) sbase = atomicAdd(&ctr->survivors, (unsigned long long)wtot);
+                sbase = __shfl_sync(kFull, sbase, 31);
+                unsigned long long pos = sbase + (incl - cnt);
+                for (int h = 0; h < 2; h++) {
+                    unsigned m = h ? mb : ma;
+                    const uint32_t ek = (uint32_t)(e0 + (h ? elb : ela));
+                    while (m) {
+                        const int bit = 31 - __clz(m);
+                        m &= ~(1u << bit);
+                        if (pos < fa.surv_cap) fa.surv[pos] = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
+                        pos++;
                     }
                 }
             }
-            if (tid == 0) {
-                if (it + 2 < iend) describe(it + 2, S.desc[slot]);
-                else S.desc[slot].item = -1;
-            }
-            __syncthreads();  // this slot is refilled next iteration
-            slot ^= 1;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n_inter += __shfl_xor_sync(kFull, n_inter, o);
-        n_fp64 += __shfl_xor_sync(kFull, n_fp64, o);
+    for (int o = 16; o > 0; o >>= 1) n_inter += __shfl_xor_sync(kFull, n_inter, o);
+    if (lane == 0 && n_inter) atomicAdd(&ctr->interactions, n_inter);
+}
+
+// FP64 evaluation of the filter's survivors, one per lane: exact temporal
+// overlap first (the pre-test ignores time), then the same FP64 code as the
+// plain kernel, then the warp-aggregated append.
+__global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterArgs fa)
+{
+    const PairArgs &args = fa.p;
+    DevCounters *ctr = args.ctr;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t cap = args.out.capacity;
+    const unsigned long long ns = min(ctr->survivors, (unsigned long long)fa.surv_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long n_fp64 = 0;
+    // warp-uniform trip count (eval_pair_fp64 and append_hits vote over the warp)
+    const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (unsigned long long wb = first; wb < ns; wb += stride) {
+        const unsigned long long k = wb + lane;
+        const bool valid = k < ns;
+        const uint2 sv = valid ? fa.surv[k] : make_uint2(0u, 0u);
+        const int64_t ek = sv.x, qk = sv.y;
+        const int64_t ets_k = args.e.ts_key[ek], ete_k = args.e.te_key[ek];
+        const int64_t qts_k = args.q.ts_key[qk], qte_k = args.q.te_key[qk];
+        const bool active = valid && (ets_k < qte_k) && (ete_k > qts_k);
+        const unsigned am = __ballot_sync(kFull, active);
+        if (lane == 0) n_fp64 += (unsigned long long)__popc(am);
+        if (!am) continue;
+        const PairEval r = eval_pair_fp64(active, ets_k, ete_k, qts_k, qte_k, args.e.px[ek], args.e.py[ek],
+                                          args.e.pz[ek], args.e.vx[ek], args.e.vy[ek], args.e.vz[ek], args.q.px[qk],
+                                          args.q.py[qk], args.q.pz[qk], args.q.vx[qk], args.q.vy[qk], args.q.vz[qk],
+                                          args.q.d2[qk]);
+        append_hits(r, ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
     }
-    if (lane == 0) {
-        if (n_inter) atomicAdd(&ctr->interactions, n_inter);
-        if (n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
-    }
+    if (lane == 0 && n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
 }
 
 // Exact number of temporal-overlap pairs of each query segment: entries
@@ -739,21 +717,36 @@ size_t pair_smem_bytes(uint32_t chunk)
 }
 
 // Launch the pair kernel of the requested mode as a persistent grid (as many
-// CTAs as fit on every SM at once).  The filter mode's pair kernel does not
-// count the overlapping pairs: launch_overlap_count does.
-cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, cudaStream_t stream)
+// CTAs as fit on every SM at once).  Filter mode: the FP32 pre-test kernel,
+// then the FP64 refine kernel over its survivors.  Neither counts the
+// overlapping pairs: launch_overlap_count does.
+cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
+                               cudaStream_t stream)
 {
-    auto kern = filter ? traj_dist_filter_kernel : traj_dist_search_kernel;
-    const size_t smem = filter ? filter_smem_bytes(pa.chunk) : pair_smem_bytes(pa.chunk);
+    if (filter) {
+        FilterArgs fa{pa, surv, surv_cap};
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_filter_kernel, kPairThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        traj_dist_filter_kernel<<<sm_count * per_sm, kPairThreads, 0, stream>>>(fa);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_refine_kernel, kPairThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        traj_dist_refine_kernel<<<sm_count * per_sm, kPairThreads, 0, stream>>>(fa);
+        return cudaGetLastError();
+    }
+    const size_t smem = pair_smem_bytes(pa.chunk);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(traj_dist_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPairThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_search_kernel, kPairThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    kern<<<sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
+    traj_dist_search_kernel<<<sm_count * per_sm, kPairThreads, smem, stream>>>(pa);
     return cudaGetLastError();
 }
 
@@ -833,6 +826,23 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
     return TDQ_OK;
 }
 
+tdq_status ensure_survivors(tdq_index *idx, uint64_t cap)
+{
+    Workspace &w = idx->ws;
+    if (cap <= w.s_cap_pairs && w.s_block) return TDQ_OK;
+    cudaFree(w.s_block);
+    w.s_block = nullptr;
+    w.surv = nullptr;
+    w.s_cap_pairs = 0;
+    if (cudaMalloc(&w.s_block, cap * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(TDQ_ERR_NOMEM, "tdq_search: survivor list of %llu pairs", (unsigned long long)cap);
+    }
+    w.surv = (uint2 *)w.s_block;
+    w.s_cap_pairs = cap;
+    return TDQ_OK;
+}
+
 struct SearchSpec {
     double d, t0, t1;
     const double *d_arr, *t0_arr, *t1_arr;
@@ -855,7 +865,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_search: query seg_id is NULL");
 
     uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk
-                     : ((params && params->mode == TDQ_MODE_FP32_FILTER) ? 1024u : 512u);
+                     : ((params && params->mode == TDQ_MODE_FP32_FILTER) ? 256u : 512u);
     if (chunk % kPairThreads != 0 || chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
     if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
@@ -886,37 +896,51 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     in.t0_arr = spec.t0_arr;
     in.t1_arr = spec.t1_arr;
 
-    TDQ_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream));
-    TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
-    double *const *pre = w.pre_dev;
-    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
-    const uint64_t ntiles = (nq + kQT - 1) / kQT;
-    if (idx->n > 0) {
-        TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
-                                  bin_key_bits(idx->m)));
-        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
-        tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, chunk, w.tile_lo, w.tile_hi,
-                                                                 w.tile_work);
-        TDQ_CUDA(exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream));
-        TDQ_CUDA(cudaGetLastError());
-        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, chunk};
-        TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
-        TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, stream));
-        TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
-        if (filter) TDQ_CUDA(launch_overlap_count(pa, nq, idx->n, stream));
-    } else {
-        TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
-        TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
+    if (filter && idx->n > 0) {
+        st = ensure_survivors(idx, w.s_cap_pairs ? w.s_cap_pairs : (nq * 64 > (1u << 20) ? nq * 64 : (1u << 20)));
+        if (st != TDQ_OK) return st;
     }
-    TDQ_CUDA(cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream));
-    TDQ_CUDA(cudaEventRecord(w.ev[3], stream));
-    TDQ_CUDA(cudaStreamSynchronize(stream));
+    // The survivor list of the filter mode is sized from the last search; if
+    // it overflows, it is grown and the search re-run (like the results).
+    for (int attempt = 0;; attempt++) {
+        TDQ_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream));
+        TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
+        double *const *pre = w.pre_dev;
+        BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+        query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
+        const uint64_t ntiles = (nq + kQT - 1) / kQT;
+        if (idx->n > 0) {
+            TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
+                                      bin_key_bits(idx->m)));
+            query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins,
+                                                              w.q);
+            tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, chunk, w.tile_lo, w.tile_hi,
+                                                                     w.tile_work);
+            TDQ_CUDA(exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream));
+            TDQ_CUDA(cudaGetLastError());
+            PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, chunk};
+            TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
+            TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, w.surv, w.s_cap_pairs, stream));
+            TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
+            if (filter) TDQ_CUDA(launch_overlap_count(pa, nq, idx->n, stream));
+        } else {
+            TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
+            TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
+        }
+        TDQ_CUDA(cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream));
+        TDQ_CUDA(cudaEventRecord(w.ev[3], stream));
+        TDQ_CUDA(cudaStreamSynchronize(stream));
+        if (w.ctr_host->error & 1u)
+            return set_error(TDQ_ERR_INVALID,
+                             "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
+                             "NaN window or t0 > t1)");
+        if (!filter || w.ctr_host->survivors <= w.s_cap_pairs) break;
+        if (attempt >= 2) return set_error(TDQ_ERR_NOMEM, "tdq_search: survivor list kept overflowing");
+        const uint64_t need = w.ctr_host->survivors;
+        st = ensure_survivors(idx, need + need / 4 + 1024);
+        if (st != TDQ_OK) return st;
+    }
     const DevCounters &h = *w.ctr_host;
-    if (h.error & 1u)
-        return set_error(TDQ_ERR_INVALID,
-                         "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
-                         "NaN window or t0 > t1)");
     tdq_stats &s = idx->last;
     s.query_segments = h.valid_queries;
     s.interactions = h.interactions;
@@ -924,9 +948,9 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     s.fp64_pairs = h.fp64_pairs;
     s.results = h.results;
     s.work_items = h.work_items;
-    // query_prep; with entries: 8 sort passes x 3 kernels, query_gather,
-    // tile_plan, scan, pair kernel
-    s.kernel_launches = idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 4 + (filter ? 1 : 0) : 1;
+    // query_prep; with entries: sort passes x 3 kernels, query_gather,
+    // tile_plan, scan, pair kernel (filter mode: filter, refine, overlap count)
+    s.kernel_launches = idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 3 + (filter ? 3 : 1) : 1;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s.pair_kernel_ms = ms;
     if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s.total_ms = ms;
@@ -1184,8 +1208,10 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search_device_noalloc: %llu query segments exceed the fixed maximum of %llu",
                          (unsigned long long)nq, (unsigned long long)kNoAllocMaxQueries);
-    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk
-                     : ((params && params->mode == TDQ_MODE_FP32_FILTER) ? 1024u : 512u);
+    if (params && params->mode == TDQ_MODE_FP32_FILTER)
+        return set_error(TDQ_ERR_INVALID,
+                         "tdq_search_device_noalloc: the filter mode needs a survivor list; use TDQ_MODE_FP64");
+    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
     if (chunk % kPairThreads != 0 || chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search_device_noalloc: entry_chunk must be a multiple of 256, <= 2048");
     if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
@@ -1226,9 +1252,7 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
                                                                  s->tile_work);
         TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
         PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk};
-        const bool filter = params && params->mode == TDQ_MODE_FP32_FILTER;
-        TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, stream));
-        if (filter) TDQ_CUDA(launch_overlap_count(pa, nq, idx->n, stream));
+        TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream));
     }
     TDQ_CUDA(cudaGetLastError());
     DevCounters h{};

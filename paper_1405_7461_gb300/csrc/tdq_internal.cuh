@@ -90,6 +90,7 @@ struct DevCounters {
     unsigned long long fp64_pairs;
     unsigned long long valid_queries;  // query segments with a non-empty clipped span
     unsigned long long work_items;
+    unsigned long long survivors;      // filter mode: pairs that passed the FP32 pre-test
     unsigned int error;                // bit 0: invalid query input
     unsigned int pad;
 };
@@ -102,6 +103,7 @@ struct EntrySoA {
     int64_t *seg_id, *traj_id, *orig;
     float4 *sph;           // FP32 bounding sphere of the segment (center, radius rounded up)
     int64_t *te_sorted;    // t_end keys in ascending order (for exact overlap counts)
+    float *blk_wmax;       // largest sphere radius of each aligned block of 64 sorted entries
 };
 
 // Sorted, clipped query segments in device memory.
@@ -143,6 +145,10 @@ struct Workspace {
     uint64_t r_cap = 0;
     void *r_block = nullptr;
     tdq_result_buffer r{};
+    // filter mode: survivors of the FP32 pre-test (entry, query) positions
+    uint64_t s_cap_pairs = 0;
+    void *s_block = nullptr;
+    uint2 *surv = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 

@@ -366,3 +366,16 @@ def test_filter_is_conservative_at_the_threshold(tdq, offset):
     with tdq.build_index(ent) as idx:
         s64, s32 = _filter_vs_fp64(tdq, idx, qry, d, (-np.inf, np.inf))
     assert s64["results"] > 0.3 * n
+
+
+def test_filter_survivor_list_overflow_is_regrown(tdq):
+    """A cluster where every pair survives the pre-test: 1.3 M survivors
+    overflow the initial survivor list (2^20 pairs), which is grown and the
+    search re-run; the results equal the plain FP64 mode's."""
+    rng = np.random.default_rng(21)
+    ent = workloads.random_segments(rng, 20_000, box=0.2, t_span=0.5, max_dur=20.0, max_speed=0.01)
+    qry = workloads.random_segments(rng, 64, box=0.2, t_span=0.5, max_dur=20.0, max_speed=0.01)
+    qry.seg_id += 10 ** 7
+    with tdq.build_index(ent) as idx:
+        s64, s32 = _filter_vs_fp64(tdq, idx, qry, 3.0, (-np.inf, np.inf))
+    assert s32["results"] == 20_000 * 64
