@@ -216,6 +216,89 @@ tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segments *queries
                                      const tdq_search_params *params, void *stream, const tdq_result_buffer *out,
                                      uint64_t *count);
 
+/*
+ * Batched search plan.  The paper splits a query into batches of query
+ * segments processed in sequence, one kernel invocation each (Sec. 4, 6.1).
+ * A plan runs one batch -- query segments of uneven trajectories, each with
+ * its own threshold d and window [t0, t1] -- as one CUDA graph launch: the
+ * whole search (counter reset, query preparation and sort, candidate ranges,
+ * tiles, pair kernels, overlap count, counter read-back) is captured once per
+ * power-of-two size class of the batch and replayed.  The plan owns its
+ * workspace, staging buffers and a device result buffer; it keeps a pointer
+ * to the index (free the plan before the index).  One search at a time per
+ * plan; distinct plans on one index may run concurrently on distinct
+ * streams.
+ */
+typedef struct tdq_plan tdq_plan;
+
+typedef struct {
+    uint64_t max_query_segments; /* largest batch (required, < 2^31) */
+    uint64_t result_capacity;    /* initial device result capacity in items (0: max(|D|, 65536)); grown and the
+                                    batch re-run when a batch overflows it (Sec. 5) */
+    uint32_t entry_chunk;        /* as in tdq_search_params (0: mode default) */
+    int mode;                    /* TDQ_MODE_* */
+    int no_graph;                /* 1: launch the kernels one by one instead of replaying a CUDA graph */
+} tdq_plan_params;
+
+tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *params, tdq_plan **out);
+void tdq_plan_free(tdq_plan *plan);
+
+/*
+ * Search one batch.  queries->n <= max_query_segments; d_per_query,
+ * t0_per_query and t1_per_query hold one value per query segment, in the
+ * same memory (host or device) as the query columns.  The inputs are copied
+ * into the plan before the graph launch; the call blocks until the batch is
+ * done and returns the number of results in *count.  Errors as tdq_search.
+ */
+tdq_status tdq_plan_search(tdq_plan *plan, const tdq_segments *queries, const double *d_per_query,
+                           const double *t0_per_query, const double *t1_per_query, void *stream, uint64_t *count);
+
+/* Device view of the plan's results (valid until the next search on the
+ * plan or its release): the first *count items of the four arrays. */
+tdq_status tdq_plan_results(const tdq_plan *plan, tdq_result_buffer *view, uint64_t *count);
+
+/* Copy the first n results of the plan's last search into caller arrays:
+ * host memory (to_device = 0) or device memory (to_device = 1).  Blocks. */
+tdq_status tdq_plan_copy_results(const tdq_plan *plan, int64_t *query_seg_id, int64_t *entry_seg_id,
+                                 double *t_enter, double *t_exit, uint64_t n, int to_device, void *stream);
+
+/* Counters of the plan's last search (total_ms: device time of the graph). */
+tdq_status tdq_plan_get_stats(const tdq_plan *plan, tdq_stats *out);
+
+/*
+ * Autotuner: measures, on a sample of query segments (with their own d and
+ * windows), the bin count m of the index (Sec. 4), the entry chunk of the
+ * pair kernels, and the batch size of a plan, and suggests a per-batch
+ * result capacity.  Candidates default to m in {1000, 10000, 100000},
+ * chunks {256, 512, 1024}, batches {1024, 4096, 16384, 65536, 262144, the
+ * whole sample}; the chosen batch is the smallest whose throughput is within
+ * batch_tolerance of the best.  Builds temporary indexes; blocks.
+ */
+typedef struct {
+    const uint32_t *bin_counts;
+    int n_bin_counts;
+    const uint32_t *entry_chunks;
+    int n_entry_chunks;
+    const uint64_t *batch_sizes;
+    int n_batch_sizes;
+    int mode;               /* TDQ_MODE_* to tune for */
+    int repeats;            /* timed repetitions per candidate (0: 3, at most 16) */
+    double batch_tolerance; /* 0: 0.05 */
+} tdq_autotune_params;
+
+typedef struct {
+    uint32_t bin_count;
+    uint32_t entry_chunk;
+    uint64_t batch_query_segments;
+    uint64_t result_capacity;          /* suggested for batches of batch_query_segments */
+    double ms_per_query_segment;       /* measured at the chosen setting */
+    double results_per_query_segment;  /* measured on the sample */
+} tdq_tuning;
+
+tdq_status tdq_autotune(const tdq_segments *entries, const tdq_segments *sample, const double *d_per_query,
+                        const double *t0_per_query, const double *t1_per_query, const tdq_autotune_params *params,
+                        void *stream, tdq_tuning *out);
+
 /* Counters of the last completed search on idx. */
 tdq_status tdq_get_stats(const tdq_index *idx, tdq_stats *out);
 

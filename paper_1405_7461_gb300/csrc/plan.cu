@@ -1,0 +1,532 @@
+// Batched searches under a CUDA graph, and the autotuner.
+//
+// A plan owns a search workspace, staging buffers for one batch of query
+// segments (each with its own threshold and window), and a result buffer.
+// tdq_plan_search stages the batch, then replays the whole search -- counter
+// reset, query preparation and sort, candidate ranges, tiles, pair kernels,
+// overlap count, counter read-back -- as one CUDA graph launch.  Graphs are
+// captured once per power-of-two size class of the batch (the slots past the
+// batch's real size are empty padding, told apart by a device-side count),
+// so batches of uneven size reuse a few graphs.  The paper processes a query
+// in batches of s query segments, one kernel invocation and host round trip
+// per batch (Sec. 6.1); here a batch is one graph launch and the batch size
+// is chosen by measurement (tdq_autotune).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "tdq_internal.cuh"
+
+namespace {
+
+constexpr int kMaxGraphs = 24;
+constexpr uint64_t kMinClass = 1024;
+
+uint64_t size_class(uint64_t n)
+{
+    uint64_t c = kMinClass;
+    while (c < n) c <<= 1;
+    return c;
+}
+
+}  // namespace
+
+struct tdq_plan {
+    tdq_index *idx = nullptr;
+    uint64_t max_q = 0;      // largest batch
+    uint64_t cap_q = 0;      // size class of the largest batch (buffer capacity)
+    tdq::LaunchCfg cfg{};
+    bool use_graph = true;
+    tdq::Workspace ws;
+    void *stage_block = nullptr;
+    double *d_arr = nullptr, *t0_arr = nullptr, *t1_arr = nullptr;
+    unsigned long long *n_dev = nullptr;
+    unsigned long long *n_host = nullptr;  // pinned
+    void *r_block = nullptr;
+    tdq_result_buffer res{};
+    cudaStream_t cap_stream = nullptr;
+    struct Graph {
+        uint64_t cls;
+        cudaGraphExec_t exec;
+    } graphs[kMaxGraphs];
+    int ngraphs = 0;
+    uint64_t last_count = 0;
+    tdq_stats last{};
+};
+
+namespace {
+
+using namespace tdq;
+
+void drop_graphs(tdq_plan *p)
+{
+    for (int k = 0; k < p->ngraphs; k++) cudaGraphExecDestroy(p->graphs[k].exec);
+    p->ngraphs = 0;
+}
+
+tdq_status plan_results(tdq_plan *p, uint64_t cap)
+{
+    if (cap <= p->res.capacity && p->r_block) return TDQ_OK;
+    drop_graphs(p);  // captured graphs hold the old pointers
+    cudaFree(p->r_block);
+    p->r_block = nullptr;
+    p->res = tdq_result_buffer{};
+    const uint64_t b = (cap * 8 + 255) & ~(uint64_t)255;
+    if (cudaMalloc(&p->r_block, 4 * b) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(TDQ_ERR_NOMEM, "tdq_plan: result buffer of %llu items", (unsigned long long)cap);
+    }
+    char *c = (char *)p->r_block;
+    p->res.query_seg_id = (int64_t *)c;
+    p->res.entry_seg_id = (int64_t *)(c + b);
+    p->res.t_enter = (double *)(c + 2 * b);
+    p->res.t_exit = (double *)(c + 3 * b);
+    p->res.capacity = cap;
+    return TDQ_OK;
+}
+
+tdq_status plan_survivors(tdq_plan *p, uint64_t cap)
+{
+    if (cap <= p->ws.s_cap_pairs && p->ws.s_block) return TDQ_OK;
+    drop_graphs(p);
+    return ensure_survivors(p->ws, cap);
+}
+
+cudaGraphExec_t find_graph(tdq_plan *p, uint64_t cls)
+{
+    for (int k = 0; k < p->ngraphs; k++)
+        if (p->graphs[k].cls == cls) return p->graphs[k].exec;
+    return nullptr;
+}
+
+QueryInput staged_input(const tdq_plan *p)
+{
+    QueryInput in{};
+    for (int c = 0; c < 8; c++) in.c[c] = p->ws.in_cols[c];
+    in.seg_id = p->ws.in_seg;
+    in.d_arr = p->d_arr;
+    in.t0_arr = p->t0_arr;
+    in.t1_arr = p->t1_arr;
+    in.n_dev = p->n_dev;
+    return in;
+}
+
+tdq_status capture(tdq_plan *p, uint64_t cls, cudaGraphExec_t *out)
+{
+    if (p->ngraphs == kMaxGraphs) drop_graphs(p);
+    const QueryInput in = staged_input(p);
+    TDQ_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_search(p->idx, p->ws, in, cls, p->cfg, p->res, p->cap_stream, false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_error(e != cudaSuccess ? e : e2, "tdq_plan: graph capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(e, "tdq_plan: graph instantiation");
+    p->graphs[p->ngraphs].cls = cls;
+    p->graphs[p->ngraphs].exec = exec;
+    p->ngraphs++;
+    *out = exec;
+    return TDQ_OK;
+}
+
+void plan_release(tdq_plan *p)
+{
+    drop_graphs(p);
+    Workspace &w = p->ws;
+    cudaFree(w.q_block);
+    cudaFree(w.t_block);
+    cudaFree(w.sort_hist);
+    cudaFree(w.s_block);
+    cudaFree(w.ctr);
+    if (w.ctr_host) cudaFreeHost(w.ctr_host);
+    for (int k = 0; k < 4; k++)
+        if (w.ev[k]) cudaEventDestroy(w.ev[k]);
+    cudaFree(p->stage_block);
+    if (p->n_host) cudaFreeHost(p->n_host);
+    cudaFree(p->r_block);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+}
+
+}  // namespace
+
+extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *params, tdq_plan **out)
+{
+    if (!out) return set_error(TDQ_ERR_INVALID, "tdq_plan_create: out is NULL");
+    *out = nullptr;
+    if (!idx || !params) return set_error(TDQ_ERR_INVALID, "tdq_plan_create: NULL argument");
+    if (params->max_query_segments == 0 || params->max_query_segments > 0x7fffffffULL)
+        return set_error(TDQ_ERR_INVALID, "tdq_plan_create: max_query_segments must be in [1, 2^31)");
+    tdq_search_params sp{};
+    sp.entry_chunk = params->entry_chunk;
+    sp.mode = params->mode;
+    LaunchCfg cfg;
+    tdq_status st = parse_params(&sp, &cfg);
+    if (st != TDQ_OK) return st;
+    tdq_plan *p = new (std::nothrow) tdq_plan();
+    if (!p) return set_error(TDQ_ERR_NOMEM, "tdq_plan_create: host allocation failed");
+    p->idx = idx;
+    p->max_q = params->max_query_segments;
+    p->cap_q = size_class(p->max_q);
+    p->cfg = cfg;
+    p->use_graph = !params->no_graph;
+    do {
+        Workspace &w = p->ws;
+        bool ok = cudaMalloc(&w.ctr, sizeof(DevCounters)) == cudaSuccess &&
+                  cudaMallocHost(&w.ctr_host, sizeof(DevCounters)) == cudaSuccess &&
+                  cudaMallocHost(&p->n_host, sizeof(unsigned long long)) == cudaSuccess &&
+                  cudaMalloc(&p->stage_block, (3 * p->cap_q + 1) * 8) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            st = set_error(TDQ_ERR_NOMEM, "tdq_plan_create: allocation failed");
+            break;
+        }
+        for (int k = 0; k < 4 && st == TDQ_OK; k++)
+            if (cudaEventCreate(&w.ev[k]) != cudaSuccess) st = set_error(TDQ_ERR_CUDA, "tdq_plan_create: events");
+        if (st != TDQ_OK) break;
+        if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            st = set_error(TDQ_ERR_CUDA, "tdq_plan_create: stream");
+            break;
+        }
+        p->d_arr = (double *)p->stage_block;
+        p->t0_arr = p->d_arr + p->cap_q;
+        p->t1_arr = p->t0_arr + p->cap_q;
+        p->n_dev = (unsigned long long *)(p->t1_arr + p->cap_q);
+        st = ensure_queries(w, p->cap_q);
+        if (st != TDQ_OK) break;
+        const uint64_t rc = params->result_capacity ? params->result_capacity : (idx->n > 65536 ? idx->n : 65536);
+        st = plan_results(p, rc);
+        if (st != TDQ_OK) break;
+        if (cfg.filter && idx->n > 0) {
+            st = plan_survivors(p, p->cap_q * 64 > (1u << 20) ? p->cap_q * 64 : (1u << 20));
+            if (st != TDQ_OK) break;
+        }
+    } while (0);
+    if (st != TDQ_OK) {
+        plan_release(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return TDQ_OK;
+}
+
+extern "C" void tdq_plan_free(tdq_plan *p)
+{
+    if (!p) return;
+    plan_release(p);
+    delete p;
+}
+
+extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, const double *d_per_query,
+                                      const double *t0_per_query, const double *t1_per_query, void *stream_,
+                                      uint64_t *count)
+{
+    if (!p || !queries || !count || !d_per_query || !t0_per_query || !t1_per_query)
+        return set_error(TDQ_ERR_INVALID, "tdq_plan_search: NULL argument");
+    *count = 0;
+    p->last = tdq_stats{};
+    p->last_count = 0;
+    const uint64_t nq = queries->n;
+    if (nq > p->max_q)
+        return set_error(TDQ_ERR_INVALID, "tdq_plan_search: %llu query segments exceed the plan's %llu",
+                         (unsigned long long)nq, (unsigned long long)p->max_q);
+    if (nq == 0) return TDQ_OK;
+    const double *cols[8] = {queries->xs, queries->ys, queries->zs, queries->ts,
+                             queries->xe, queries->ye, queries->ze, queries->te};
+    for (int c = 0; c < 8; c++)
+        if (!cols[c]) return set_error(TDQ_ERR_INVALID, "tdq_plan_search: query column %d is NULL", c);
+    if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_plan_search: query seg_id is NULL");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    Workspace &w = p->ws;
+    const cudaMemcpyKind kind = queries->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int c = 0; c < 8; c++) TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(p->d_arr, d_per_query, nq * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(p->t0_arr, t0_per_query, nq * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(p->t1_arr, t1_per_query, nq * 8, kind, stream));
+    *p->n_host = nq;
+    TDQ_CUDA(cudaMemcpyAsync(p->n_dev, p->n_host, sizeof(unsigned long long), cudaMemcpyHostToDevice, stream));
+    const uint64_t cls = size_class(nq);
+    for (int attempt = 0;; attempt++) {
+        if (p->use_graph) {
+            cudaGraphExec_t exec = find_graph(p, cls);
+            if (!exec) {
+                tdq_status st = capture(p, cls, &exec);
+                if (st != TDQ_OK) return st;
+            }
+            TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
+            TDQ_CUDA(cudaGraphLaunch(exec, stream));
+            TDQ_CUDA(cudaEventRecord(w.ev[3], stream));
+        } else {
+            TDQ_CUDA(enqueue_search(p->idx, w, staged_input(p), cls, p->cfg, p->res, stream, true));
+        }
+        TDQ_CUDA(cudaStreamSynchronize(stream));
+        bool grow_surv = false;
+        uint64_t cnt = 0;
+        tdq_status st = finish_search(p->idx, w, p->cfg, p->res.capacity, !p->use_graph, &p->last, &cnt, &grow_surv);
+        if (p->use_graph) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) p->last.total_ms = ms;
+            p->last.kernel_launches = (uint64_t)search_kernel_launches(p->idx, p->cfg);
+        }
+        if (st == TDQ_OK && !grow_surv) {
+            *count = cnt;
+            p->last_count = cnt;
+            return TDQ_OK;
+        }
+        if (attempt >= 3) return st != TDQ_OK ? st : set_error(TDQ_ERR_NOMEM, "tdq_plan_search: kept overflowing");
+        if (grow_surv) {
+            const uint64_t need = w.ctr_host->survivors;
+            st = plan_survivors(p, need + need / 4 + 1024);
+        } else if (st == TDQ_ERR_OVERFLOW) {  // the statically sized result buffer was too small (Sec. 5)
+            st = plan_results(p, cnt + cnt / 8 + 1024);
+        }
+        if (st != TDQ_OK) return st;
+    }
+}
+
+extern "C" tdq_status tdq_plan_results(const tdq_plan *p, tdq_result_buffer *view, uint64_t *count)
+{
+    if (!p || !view || !count) return set_error(TDQ_ERR_INVALID, "tdq_plan_results: NULL argument");
+    *view = p->res;
+    *count = p->last_count;
+    return TDQ_OK;
+}
+
+extern "C" tdq_status tdq_plan_copy_results(const tdq_plan *p, int64_t *query_seg_id, int64_t *entry_seg_id,
+                                            double *t_enter, double *t_exit, uint64_t n, int to_device,
+                                            void *stream_)
+{
+    if (!p) return set_error(TDQ_ERR_INVALID, "tdq_plan_copy_results: NULL plan");
+    if (n > p->last_count || n > p->res.capacity)
+        return set_error(TDQ_ERR_INVALID, "tdq_plan_copy_results: %llu items requested, %llu available",
+                         (unsigned long long)n, (unsigned long long)p->last_count);
+    if (n == 0) return TDQ_OK;
+    if (!query_seg_id || !entry_seg_id || !t_enter || !t_exit)
+        return set_error(TDQ_ERR_INVALID, "tdq_plan_copy_results: NULL array");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    TDQ_CUDA(cudaMemcpyAsync(query_seg_id, p->res.query_seg_id, n * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(entry_seg_id, p->res.entry_seg_id, n * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(t_enter, p->res.t_enter, n * 8, kind, stream));
+    TDQ_CUDA(cudaMemcpyAsync(t_exit, p->res.t_exit, n * 8, kind, stream));
+    TDQ_CUDA(cudaStreamSynchronize(stream));
+    return TDQ_OK;
+}
+
+extern "C" tdq_status tdq_plan_get_stats(const tdq_plan *p, tdq_stats *out)
+{
+    if (!p || !out) return set_error(TDQ_ERR_INVALID, "tdq_plan_get_stats: NULL argument");
+    *out = p->last;
+    return TDQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct DeviceSample {
+    tdq_segments q{};
+    const double *d = nullptr, *t0 = nullptr, *t1 = nullptr;
+    void *block = nullptr;
+};
+
+// The sample in device memory (copied if it is on the host), so that the
+// timings see device-resident inputs.
+tdq_status device_sample(const tdq_segments *q, const double *d, const double *t0, const double *t1,
+                         DeviceSample *s)
+{
+    s->q = *q;
+    s->d = d;
+    s->t0 = t0;
+    s->t1 = t1;
+    if (q->on_device) return TDQ_OK;
+    const uint64_t n = q->n;
+    if (cudaMalloc(&s->block, n * 8 * 12) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(TDQ_ERR_NOMEM, "tdq_autotune: sample staging");
+    }
+    double *b = (double *)s->block;
+    const double *src[8] = {q->xs, q->ys, q->zs, q->ts, q->xe, q->ye, q->ze, q->te};
+    double *dst[8];
+    for (int c = 0; c < 8; c++) {
+        dst[c] = b + c * n;
+        TDQ_CUDA(cudaMemcpy(dst[c], src[c], n * 8, cudaMemcpyHostToDevice));
+    }
+    int64_t *sid = (int64_t *)(b + 8 * n);
+    TDQ_CUDA(cudaMemcpy(sid, q->seg_id, n * 8, cudaMemcpyHostToDevice));
+    double *dd = b + 9 * n, *tt0 = b + 10 * n, *tt1 = b + 11 * n;
+    TDQ_CUDA(cudaMemcpy(dd, d, n * 8, cudaMemcpyHostToDevice));
+    TDQ_CUDA(cudaMemcpy(tt0, t0, n * 8, cudaMemcpyHostToDevice));
+    TDQ_CUDA(cudaMemcpy(tt1, t1, n * 8, cudaMemcpyHostToDevice));
+    s->q.xs = dst[0]; s->q.ys = dst[1]; s->q.zs = dst[2]; s->q.ts = dst[3];
+    s->q.xe = dst[4]; s->q.ye = dst[5]; s->q.ze = dst[6]; s->q.te = dst[7];
+    s->q.seg_id = sid;
+    s->q.traj_id = nullptr;
+    s->q.on_device = 1;
+    s->d = dd;
+    s->t0 = tt0;
+    s->t1 = tt1;
+    return TDQ_OK;
+}
+
+tdq_segments slice(const tdq_segments &q, uint64_t off, uint64_t n)
+{
+    tdq_segments s = q;
+    s.xs += off; s.ys += off; s.zs += off; s.ts += off;
+    s.xe += off; s.ye += off; s.ze += off; s.te += off;
+    s.seg_id += off;
+    if (s.traj_id) s.traj_id += off;
+    s.n = n;
+    return s;
+}
+
+// Time (ms) of searching the whole sample in batches of `batch` query
+// segments with a plan: median over `reps` after one warm-up pass.
+tdq_status time_batches(tdq_index *idx, const DeviceSample &s, uint64_t batch, uint32_t chunk, int mode, int reps,
+                        cudaStream_t stream, double *ms_out, uint64_t *results_out)
+{
+    tdq_plan_params pp{};
+    pp.max_query_segments = batch;
+    pp.entry_chunk = chunk;
+    pp.mode = mode;
+    tdq_plan *p = nullptr;
+    tdq_status st = tdq_plan_create(idx, &pp, &p);
+    if (st != TDQ_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double times[16];
+    if (reps > 16) reps = 16;
+    uint64_t results = 0;
+    for (int r = -1; r < reps && st == TDQ_OK; r++) {
+        cudaEventRecord(e0, stream);
+        uint64_t tot = 0;
+        for (uint64_t off = 0; off < s.q.n && st == TDQ_OK; off += batch) {
+            const uint64_t n = s.q.n - off < batch ? s.q.n - off : batch;
+            tdq_segments q = slice(s.q, off, n);
+            uint64_t cnt = 0;
+            st = tdq_plan_search(p, &q, s.d + off, s.t0 + off, s.t1 + off, stream, &cnt);
+            tot += cnt;
+        }
+        cudaEventRecord(e1, stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r >= 0) times[r] = ms;
+        results = tot;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tdq_plan_free(p);
+    if (st != TDQ_OK) return st;
+    // median
+    for (int i = 1; i < reps; i++)
+        for (int j = i; j > 0 && times[j] < times[j - 1]; j--) {
+            double t = times[j];
+            times[j] = times[j - 1];
+            times[j - 1] = t;
+        }
+    *ms_out = times[reps / 2];
+    *results_out = results;
+    return TDQ_OK;
+}
+
+}  // namespace
+
+extern "C" tdq_status tdq_autotune(const tdq_segments *entries, const tdq_segments *sample, const double *d,
+                                   const double *t0, const double *t1, const tdq_autotune_params *ap, void *stream_,
+                                   tdq_tuning *out)
+{
+    if (!entries || !sample || !d || !t0 || !t1 || !out)
+        return set_error(TDQ_ERR_INVALID, "tdq_autotune: NULL argument");
+    if (sample->n == 0) return set_error(TDQ_ERR_INVALID, "tdq_autotune: empty sample");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    static const uint32_t kBins[] = {1000, 10000, 100000};
+    static const uint32_t kChunks[] = {256, 512, 1024};
+    const int mode = ap ? ap->mode : TDQ_MODE_FP64;
+    const uint32_t *bins = (ap && ap->bin_counts) ? ap->bin_counts : kBins;
+    const int nb = (ap && ap->bin_counts) ? ap->n_bin_counts : 3;
+    const uint32_t *chunks = (ap && ap->entry_chunks) ? ap->entry_chunks : kChunks;
+    const int nc = (ap && ap->entry_chunks) ? ap->n_entry_chunks : 3;
+    const int reps = (ap && ap->repeats > 0) ? ap->repeats : 3;
+    const double tol = (ap && ap->batch_tolerance > 0) ? ap->batch_tolerance : 0.05;
+    if (nb <= 0 || nc <= 0) return set_error(TDQ_ERR_INVALID, "tdq_autotune: empty candidate list");
+
+    DeviceSample s;
+    tdq_status st = device_sample(sample, d, t0, t1, &s);
+    if (st != TDQ_OK) return st;
+    const uint64_t n = s.q.n;
+    double best_ms = INFINITY;
+    uint32_t best_bins = bins[0], best_chunk = chunks[0];
+    uint64_t results = 0;
+    // 1. bin count x entry chunk, one batch holding the whole sample
+    for (int i = 0; i < nb && st == TDQ_OK; i++) {
+        tdq_index_params ip{bins[i]};
+        tdq_index *idx = nullptr;
+        st = tdq_build_index(entries, &ip, stream, &idx);
+        for (int j = 0; j < nc && st == TDQ_OK; j++) {
+            double ms = 0;
+            uint64_t r = 0;
+            st = time_batches(idx, s, n, chunks[j], mode, reps, stream, &ms, &r);
+            if (st == TDQ_OK && ms < best_ms) {
+                best_ms = ms;
+                best_bins = bins[i];
+                best_chunk = chunks[j];
+                results = r;
+            }
+        }
+        tdq_index_free(idx);
+    }
+    // 2. batch size: the smallest whose throughput is within tol of the best
+    uint64_t best_batch = n;
+    double batch_ms = best_ms;
+    if (st == TDQ_OK) {
+        static const uint64_t kBatches[] = {1024, 4096, 16384, 65536, 262144};
+        const uint64_t *bs = (ap && ap->batch_sizes) ? ap->batch_sizes : kBatches;
+        const int nbs = (ap && ap->batch_sizes) ? ap->n_batch_sizes : 5;
+        tdq_index_params ip{best_bins};
+        tdq_index *idx = nullptr;
+        st = tdq_build_index(entries, &ip, stream, &idx);
+        double tms[32];
+        uint64_t cand[32];
+        int nt = 0;
+        for (int k = 0; k < nbs && k < 31 && st == TDQ_OK; k++) {
+            if (bs[k] == 0 || bs[k] >= n) continue;
+            double ms = 0;
+            uint64_t r = 0;
+            st = time_batches(idx, s, bs[k], best_chunk, mode, reps, stream, &ms, &r);
+            cand[nt] = bs[k];
+            tms[nt++] = ms;
+        }
+        cand[nt] = n;
+        tms[nt++] = best_ms;
+        double fastest = INFINITY;
+        for (int k = 0; k < nt; k++) fastest = fmin(fastest, tms[k]);
+        for (int k = 0; k < nt; k++)
+            if (tms[k] <= fastest * (1.0 + tol) && cand[k] <= best_batch) {
+                best_batch = cand[k];
+                batch_ms = tms[k];
+            }
+        tdq_index_free(idx);
+    }
+    cudaFree(s.block);
+    if (st != TDQ_OK) return st;
+    out->bin_count = best_bins;
+    out->entry_chunk = best_chunk;
+    out->batch_query_segments = best_batch;
+    out->results_per_query_segment = (double)results / (double)n;
+    const double est = ceil(out->results_per_query_segment * (double)best_batch);
+    out->result_capacity = (uint64_t)(2.0 * est) + 1024;
+    out->ms_per_query_segment = batch_ms / (double)n;
+    return TDQ_OK;
+}

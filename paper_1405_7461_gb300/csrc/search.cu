@@ -44,13 +44,6 @@ inline unsigned grid_for(uint64_t n, int block = kBlock)
     return (unsigned)(g > 0 ? g : 1);
 }
 
-struct QueryInput {
-    const double *c[8];  // xs ys zs ts xe ye ze te
-    const int64_t *seg_id;
-    double d, t0, t1;                            // one threshold and window ...
-    const double *d_arr, *t0_arr, *t1_arr;       // ... or one per query segment
-};
-
 __device__ __forceinline__ bool is_nan_bits(double x)
 {
     int64_t b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
@@ -78,7 +71,15 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
 {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
-    if (i < nq) {
+    // slots at or beyond the device-side count are padding: empty, not errors
+    const uint64_t nreal = in.n_dev ? (uint64_t)*in.n_dev : nq;
+    if (i < nq && i >= nreal) {
+        pre[7][i] = __longlong_as_double(INT64_MAX);
+        pre[8][i] = __longlong_as_double(INT64_MIN);
+        pre_sph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        keys[i] = (uint64_t)bins.m;
+        vals[i] = (uint32_t)i;
+    } else if (i < nq) {
         bool ok = true;
         double c[8];
 #pragma unroll
@@ -765,9 +766,10 @@ T *carve(char *&p, uint64_t count)
 }
 inline uint64_t cb(uint64_t count, uint64_t size) { return (count * size + 255) & ~(uint64_t)255; }
 
-tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
+}  // namespace
+
+tdq_status ensure_queries(Workspace &w, uint64_t nq)
 {
-    Workspace &w = idx->ws;
     if (nq <= w.q_cap && w.q_block) return TDQ_OK;
     uint64_t cap = nq > 2 * w.q_cap ? nq : 2 * w.q_cap;
     if (cap < 1024) cap = 1024;
@@ -826,9 +828,8 @@ tdq_status ensure_queries(tdq_index *idx, uint64_t nq)
     return TDQ_OK;
 }
 
-tdq_status ensure_survivors(tdq_index *idx, uint64_t cap)
+tdq_status ensure_survivors(Workspace &w, uint64_t cap)
 {
-    Workspace &w = idx->ws;
     if (cap <= w.s_cap_pairs && w.s_block) return TDQ_OK;
     cudaFree(w.s_block);
     w.s_block = nullptr;
@@ -842,6 +843,92 @@ tdq_status ensure_survivors(tdq_index *idx, uint64_t cap)
     w.s_cap_pairs = cap;
     return TDQ_OK;
 }
+
+tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
+{
+    if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
+    cfg->filter = params && params->mode == TDQ_MODE_FP32_FILTER;
+    cfg->chunk = (params && params->entry_chunk) ? params->entry_chunk : (cfg->filter ? 256u : 512u);
+    if (cfg->chunk % kPairThreads != 0 || cfg->chunk > 2048)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
+    if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: query_tile must be 32");
+    return TDQ_OK;
+}
+
+int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg)
+{
+    // query_prep; with entries: sort passes x 3 kernels, query_gather,
+    // tile_plan, scan, pair kernel (filter mode: filter, refine, overlap count)
+    return idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 3 + (cfg.filter ? 3 : 1) : 1;
+}
+
+cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq, const LaunchCfg &cfg,
+                           const tdq_result_buffer &out, cudaStream_t stream, bool events)
+{
+    cudaError_t e = cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream);
+    if (e != cudaSuccess) return e;
+    if (events && (e = cudaEventRecord(w.ev[0], stream)) != cudaSuccess) return e;
+    double *const *pre = w.pre_dev;
+    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
+    const uint64_t ntiles = (nq + kQT - 1) / kQT;
+    if (idx->n > 0) {
+        if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
+                                  bin_key_bits(idx->m))) != cudaSuccess)
+            return e;
+        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
+        tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, cfg.chunk, w.tile_lo, w.tile_hi,
+                                                                 w.tile_work);
+        if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
+        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk};
+        if (events && (e = cudaEventRecord(w.ev[1], stream)) != cudaSuccess) return e;
+        if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream)) != cudaSuccess)
+            return e;
+        if (events && (e = cudaEventRecord(w.ev[2], stream)) != cudaSuccess) return e;
+        if (cfg.filter && (e = launch_overlap_count(pa, nq, idx->n, stream)) != cudaSuccess) return e;
+    } else if (events) {
+        if ((e = cudaEventRecord(w.ev[1], stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(w.ev[2], stream)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return e;
+    if (events && (e = cudaEventRecord(w.ev[3], stream)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t capacity,
+                         bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow)
+{
+    const DevCounters &h = *w.ctr_host;
+    *surv_overflow = false;
+    if (h.error & 1u)
+        return set_error(TDQ_ERR_INVALID,
+                         "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
+                         "NaN window or t0 > t1)");
+    if (cfg.filter && idx->n > 0 && h.survivors > w.s_cap_pairs) {
+        *surv_overflow = true;
+        return TDQ_OK;
+    }
+    *s = tdq_stats{};
+    s->query_segments = h.valid_queries;
+    s->interactions = h.interactions;
+    s->overlap_pairs = h.overlap_pairs;
+    s->fp64_pairs = h.fp64_pairs;
+    s->results = h.results;
+    s->work_items = h.work_items;
+    s->kernel_launches = (uint64_t)search_kernel_launches(idx, cfg);
+    if (events) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s->pair_kernel_ms = ms;
+        if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s->total_ms = ms;
+    }
+    *count = h.results;
+    return h.results > capacity ? TDQ_ERR_OVERFLOW : TDQ_OK;
+}
+
+namespace {
 
 struct SearchSpec {
     double d, t0, t1;
@@ -863,18 +950,10 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     for (int c = 0; c < 8; c++)
         if (!cols[c]) return set_error(TDQ_ERR_INVALID, "tdq_search: query column %d is NULL", c);
     if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_search: query seg_id is NULL");
-
-    uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk
-                     : ((params && params->mode == TDQ_MODE_FP32_FILTER) ? 256u : 512u);
-    if (chunk % kPairThreads != 0 || chunk > 2048)
-        return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
-    if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
-        return set_error(TDQ_ERR_INVALID, "tdq_search: query_tile must be 32");
-    if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
-        return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
-
-    const bool filter = params && params->mode == TDQ_MODE_FP32_FILTER;
-    tdq_status st = ensure_queries(idx, nq);
+    LaunchCfg cfg;
+    tdq_status st = parse_params(params, &cfg);
+    if (st != TDQ_OK) return st;
+    st = ensure_queries(w, nq);
     if (st != TDQ_OK) return st;
 
     QueryInput in{};
@@ -895,67 +974,25 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     in.d_arr = spec.d_arr;
     in.t0_arr = spec.t0_arr;
     in.t1_arr = spec.t1_arr;
+    in.n_dev = nullptr;
 
-    if (filter && idx->n > 0) {
-        st = ensure_survivors(idx, w.s_cap_pairs ? w.s_cap_pairs : (nq * 64 > (1u << 20) ? nq * 64 : (1u << 20)));
+    if (cfg.filter && idx->n > 0) {
+        st = ensure_survivors(w, w.s_cap_pairs ? w.s_cap_pairs : (nq * 64 > (1u << 20) ? nq * 64 : (1u << 20)));
         if (st != TDQ_OK) return st;
     }
     // The survivor list of the filter mode is sized from the last search; if
     // it overflows, it is grown and the search re-run (like the results).
     for (int attempt = 0;; attempt++) {
-        TDQ_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream));
-        TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
-        double *const *pre = w.pre_dev;
-        BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
-        query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
-        const uint64_t ntiles = (nq + kQT - 1) / kQT;
-        if (idx->n > 0) {
-            TDQ_CUDA(radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
-                                      bin_key_bits(idx->m)));
-            query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins,
-                                                              w.q);
-            tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, chunk, w.tile_lo, w.tile_hi,
-                                                                     w.tile_work);
-            TDQ_CUDA(exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream));
-            TDQ_CUDA(cudaGetLastError());
-            PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, chunk};
-            TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
-            TDQ_CUDA(launch_pair_kernel(pa, filter, idx->sm_count, w.surv, w.s_cap_pairs, stream));
-            TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
-            if (filter) TDQ_CUDA(launch_overlap_count(pa, nq, idx->n, stream));
-        } else {
-            TDQ_CUDA(cudaEventRecord(w.ev[1], stream));
-            TDQ_CUDA(cudaEventRecord(w.ev[2], stream));
-        }
-        TDQ_CUDA(cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream));
-        TDQ_CUDA(cudaEventRecord(w.ev[3], stream));
+        TDQ_CUDA(enqueue_search(idx, w, in, nq, cfg, out, stream, true));
         TDQ_CUDA(cudaStreamSynchronize(stream));
-        if (w.ctr_host->error & 1u)
-            return set_error(TDQ_ERR_INVALID,
-                             "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
-                             "NaN window or t0 > t1)");
-        if (!filter || w.ctr_host->survivors <= w.s_cap_pairs) break;
+        bool grow = false;
+        st = finish_search(idx, w, cfg, out.capacity, true, &idx->last, count, &grow);
+        if (!grow) return st;
         if (attempt >= 2) return set_error(TDQ_ERR_NOMEM, "tdq_search: survivor list kept overflowing");
         const uint64_t need = w.ctr_host->survivors;
-        st = ensure_survivors(idx, need + need / 4 + 1024);
+        st = ensure_survivors(w, need + need / 4 + 1024);
         if (st != TDQ_OK) return st;
     }
-    const DevCounters &h = *w.ctr_host;
-    tdq_stats &s = idx->last;
-    s.query_segments = h.valid_queries;
-    s.interactions = h.interactions;
-    s.overlap_pairs = h.overlap_pairs;
-    s.fp64_pairs = h.fp64_pairs;
-    s.results = h.results;
-    s.work_items = h.work_items;
-    // query_prep; with entries: sort passes x 3 kernels, query_gather,
-    // tile_plan, scan, pair kernel (filter mode: filter, refine, overlap count)
-    s.kernel_launches = idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 3 + (filter ? 3 : 1) : 1;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s.pair_kernel_ms = ms;
-    if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s.total_ms = ms;
-    *count = h.results;
-    return h.results > out.capacity ? TDQ_ERR_OVERFLOW : TDQ_OK;
 }
 
 tdq_status check_scalars(double d, double t0, double t1)

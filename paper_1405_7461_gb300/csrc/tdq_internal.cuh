@@ -172,6 +172,35 @@ struct tdq_index {
 
 namespace tdq {
 
+// Query input of one search: device columns and either one threshold and
+// window or one per query segment.  n_dev (optional): device-side number of
+// real query segments; slots at or beyond it are empty padding (used by
+// captured searches whose launch shapes are fixed).
+struct QueryInput {
+    const double *c[8];  // xs ys zs ts xe ye ze te
+    const int64_t *seg_id;
+    double d, t0, t1;
+    const double *d_arr, *t0_arr, *t1_arr;
+    const unsigned long long *n_dev;
+};
+
+struct LaunchCfg {
+    uint32_t chunk;
+    bool filter;
+};
+
+// search.cu: workspace sizing, parameters, and one search split into a part
+// that only enqueues device work (capturable in a CUDA graph) and a part that
+// reads the counters once the stream has reached the end of it.
+tdq_status ensure_queries(Workspace &w, uint64_t nq);
+tdq_status ensure_survivors(Workspace &w, uint64_t cap);
+tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg);
+int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg);
+cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq, const LaunchCfg &cfg,
+                           const tdq_result_buffer &out, cudaStream_t stream, bool events);
+tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t capacity,
+                         bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
+
 // Error reporting (api.cu).
 tdq_status set_error(tdq_status st, const char *fmt, ...);
 tdq_status cuda_error(cudaError_t e, const char *what);

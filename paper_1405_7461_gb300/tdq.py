@@ -70,6 +70,26 @@ class tdq_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class tdq_plan_params(ctypes.Structure):
+    _fields_ = [("max_query_segments", ctypes.c_uint64), ("result_capacity", ctypes.c_uint64),
+                ("entry_chunk", ctypes.c_uint32), ("mode", ctypes.c_int), ("no_graph", ctypes.c_int)]
+
+
+class tdq_autotune_params(ctypes.Structure):
+    _fields_ = [("bin_counts", ctypes.c_void_p), ("n_bin_counts", ctypes.c_int), ("entry_chunks", ctypes.c_void_p),
+                ("n_entry_chunks", ctypes.c_int), ("batch_sizes", ctypes.c_void_p), ("n_batch_sizes", ctypes.c_int),
+                ("mode", ctypes.c_int), ("repeats", ctypes.c_int), ("batch_tolerance", ctypes.c_double)]
+
+
+class tdq_tuning(ctypes.Structure):
+    _fields_ = [("bin_count", ctypes.c_uint32), ("entry_chunk", ctypes.c_uint32),
+                ("batch_query_segments", ctypes.c_uint64), ("result_capacity", ctypes.c_uint64),
+                ("ms_per_query_segment", ctypes.c_double), ("results_per_query_segment", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # Every symbol include/tdq.h declares, with (restype, argtypes).
 P = ctypes.c_void_p
 SIGNATURES = {
@@ -84,6 +104,13 @@ SIGNATURES = {
     "tdq_search_device_noalloc": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P,
                                                  P]),
     "tdq_get_stats": (ctypes.c_int, [P, P]),
+    "tdq_plan_create": (ctypes.c_int, [P, P, P]),
+    "tdq_plan_free": (None, [P]),
+    "tdq_plan_search": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "tdq_plan_results": (ctypes.c_int, [P, P, P]),
+    "tdq_plan_get_stats": (ctypes.c_int, [P, P]),
+    "tdq_plan_copy_results": (ctypes.c_int, [P, P, P, P, P, ctypes.c_uint64, ctypes.c_int, P]),
+    "tdq_autotune": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
     "tdq_last_error": (ctypes.c_char_p, []),
     "tdq_version": (ctypes.c_char_p, []),
 }
@@ -401,3 +428,111 @@ def get_stats(idx: Index) -> dict:
     st = tdq_stats()
     _check(load().tdq_get_stats(idx.handle, ctypes.byref(st)))
     return st.as_dict()
+
+
+# --------------------------------------------------------------------------
+# Batched plans (CUDA graph) and the autotuner
+# --------------------------------------------------------------------------
+
+def _per_query_ptrs(queries, d, t0, t1):
+    """Pointers of the per-query d / t0 / t1 arrays, in the queries' memory."""
+    if isinstance(queries, DeviceSegments):
+        import torch
+
+        keep = [torch.as_tensor(np.asarray(a, np.float64) if not hasattr(a, "is_cuda") else a,
+                                dtype=torch.float64).to(queries.cols[0].device).contiguous() for a in (d, t0, t1)]
+        return keep, [k.data_ptr() for k in keep]
+    keep = [np.ascontiguousarray(a, np.float64) for a in (d, t0, t1)]
+    return keep, [k.ctypes.data for k in keep]
+
+
+class Plan:
+    """Owner of a tdq_plan: batches of query segments with their own d and
+    window, each batch one CUDA graph launch."""
+
+    def __init__(self, idx: Index, max_query_segments: int, mode=MODE_FP64, entry_chunk=0, result_capacity=0,
+                 use_graph=True):
+        self.idx = idx
+        prm = tdq_plan_params(int(max_query_segments), int(result_capacity), int(entry_chunk), int(mode),
+                              0 if use_graph else 1)
+        h = ctypes.c_void_p()
+        _check(load().tdq_plan_create(idx.handle, ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h.value
+
+    def free(self):
+        if self._h:
+            load().tdq_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.free()
+
+    def search(self, queries, d, t0, t1, stream=None) -> int:
+        """tdq_plan_search: d, t0, t1 per query segment; returns the result count."""
+        q = _segments(queries)
+        s = q.struct()
+        keep, ptrs = _per_query_ptrs(q, d, t0, t1)
+        cnt = ctypes.c_uint64()
+        _check(load().tdq_plan_search(self._h, ctypes.byref(s), *ptrs, _stream_ptr(stream), ctypes.byref(cnt)))
+        del keep
+        return int(cnt.value)
+
+    def results(self) -> Results:
+        """tdq_plan_copy_results: the last batch's results, copied to host."""
+        view = tdq_result_buffer()
+        cnt = ctypes.c_uint64()
+        _check(load().tdq_plan_results(self._h, ctypes.byref(view), ctypes.byref(cnt)))
+        n = int(cnt.value)
+        qi = np.empty(n, np.int64)
+        ei = np.empty(n, np.int64)
+        tin = np.empty(n, np.float64)
+        tout = np.empty(n, np.float64)
+        if n:
+            _check(load().tdq_plan_copy_results(self._h, qi.ctypes.data, ei.ctypes.data, tin.ctypes.data,
+                                                tout.ctypes.data, n, 0, None))
+        return Results(qi, ei, tin, tout)
+
+    def stats(self) -> dict:
+        st = tdq_stats()
+        _check(load().tdq_plan_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+
+def autotune(entries, sample, d, t0, t1, mode=MODE_FP64, bin_counts=None, entry_chunks=None, batch_sizes=None,
+             repeats=3, batch_tolerance=0.05, stream=None) -> dict:
+    """tdq_autotune: measured bin count, entry chunk and batch size."""
+    e = _segments(entries)
+    q = _segments(sample)
+    es, qs = e.struct(), q.struct()
+    keep, ptrs = _per_query_ptrs(q, d, t0, t1)
+    ap = tdq_autotune_params()
+    arrs = []
+    if bin_counts is not None:
+        a = np.ascontiguousarray(bin_counts, np.uint32)
+        arrs.append(a)
+        ap.bin_counts, ap.n_bin_counts = a.ctypes.data, len(a)
+    if entry_chunks is not None:
+        a = np.ascontiguousarray(entry_chunks, np.uint32)
+        arrs.append(a)
+        ap.entry_chunks, ap.n_entry_chunks = a.ctypes.data, len(a)
+    if batch_sizes is not None:
+        a = np.ascontiguousarray(batch_sizes, np.uint64)
+        arrs.append(a)
+        ap.batch_sizes, ap.n_batch_sizes = a.ctypes.data, len(a)
+    ap.mode = mode
+    ap.repeats = repeats
+    ap.batch_tolerance = batch_tolerance
+    out = tdq_tuning()
+    _check(load().tdq_autotune(ctypes.byref(es), ctypes.byref(qs), *ptrs, ctypes.byref(ap), _stream_ptr(stream),
+                               ctypes.byref(out)))
+    del keep, arrs
+    return out.as_dict()

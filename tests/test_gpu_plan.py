@@ -1,0 +1,157 @@
+"""Batched plans (one CUDA graph launch per batch) and the autotuner, against
+the oracle and against the unbatched device search."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1405_7461_gb300 import workloads
+from tests._util import compare_results
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def tdq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7461_gb300 import build, tdq as t
+
+    build.build()
+    t.load()
+    return t
+
+
+def _positions(ids, pool):
+    order = np.argsort(pool, kind="stable")
+    pos = np.searchsorted(pool[order], ids)
+    assert np.all(pool[order][pos] == ids)
+    return order[pos]
+
+
+def _key_sorted(r):
+    o = np.lexsort((r.entry_seg_id, r.query_seg_id))
+    return r.query_seg_id[o], r.entry_seg_id[o], r.t_enter[o], r.t_exit[o]
+
+
+def _same(a, b):
+    for x, y in zip(_key_sorted(a), _key_sorted(b)):
+        assert np.array_equal(x, y)
+
+
+def _oracle_per_trajectory(w, q, qd, q0, q1):
+    parts = {k: [] for k in ("qi", "ei", "t_enter", "t_exit")}
+    for tj in np.unique(q.traj_id):
+        sel = np.nonzero(q.traj_id == tj)[0]
+        r = oracle.search_sweep(w.entries, q.take(sel), qd[sel[0]], q0[sel[0]], q1[sel[0]])
+        parts["qi"].append(sel[r.query_index])
+        parts["ei"].append(r.entry_index)
+        parts["t_enter"].append(r.t_enter)
+        parts["t_exit"].append(r.t_exit)
+    return {k: np.concatenate(v) for k, v in parts.items()}
+
+
+@pytest.mark.parametrize("mode_name", ["fp64", "filter"])
+def test_plan_batches_match_oracle_and_unbatched_search(tdq, mode_name):
+    mode = tdq.MODE_FP64 if mode_name == "fp64" else tdq.MODE_FP32_FILTER
+    w = workloads.batching_walks(n_traj=500, n_queries=80, box=50.0)
+    q = w.queries
+    n = len(q)
+    with tdq.build_index(w.entries, bin_count=3000) as idx:
+        # reference: the unbatched device search with per-query parameters
+        buf = tdq.DeviceResultBuffer(1 << 18)
+        cnt = tdq.search_device_batched(idx, tdq.DeviceSegments(q), torch.from_numpy(w.q_d).cuda(),
+                                        torch.from_numpy(w.q_t0).cuda(), torch.from_numpy(w.q_t1).cuda(), buf,
+                                        mode=mode)
+        ref = buf.to_host(cnt)
+        # the same queries as uneven batches through one plan (graph replay,
+        # several size classes); host and device inputs
+        cuts = [0, 7, 1500, 1501, 4000, n]
+        with tdq.Plan(idx, max_query_segments=4000, mode=mode) as plan:
+            got = []
+            for k, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+                if b <= a:
+                    continue
+                sub = q.take(np.arange(a, b))
+                src = tdq.DeviceSegments(sub) if k % 2 else sub
+                c = plan.search(src, w.q_d[a:b], w.q_t0[a:b], w.q_t1[a:b])
+                r = plan.results()
+                assert len(r) == c == plan.stats()["results"]
+                got.append(r)
+        merged = tdq.Results(*[np.concatenate([getattr(r, f) for r in got])
+                               for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit")])
+    _same(merged, ref)
+    # against the oracle, trajectory by trajectory (own d and window each)
+    ora = _oracle_per_trajectory(w, q, w.q_d, w.q_t0, w.q_t1)
+    gi = {"qi": _positions(merged.query_seg_id, q.seg_id), "ei": _positions(merged.entry_seg_id, w.entries.seg_id),
+          "t_enter": merged.t_enter, "t_exit": merged.t_exit}
+    dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, q, qi, w.q_t0[qi], w.q_t1[qi])  # noqa: E731
+    cmp = compare_results(gi, ora, w.entries, q, None, dmin_fn=dmin, d_per_query=w.q_d)
+    assert cmp["matched"] > 1000
+
+
+def test_plan_graph_equals_direct_launches_and_regrows(tdq):
+    """Graph replay and direct launches give identical results; a result
+    buffer that is too small is grown and the batch re-run."""
+    w = workloads.scale_random_walk(n_traj=1500, n_queries=12)
+    q = w.queries
+    n = len(q)
+    d = np.full(n, 15.0)
+    t0 = np.full(n, w.window[0])
+    t1 = np.full(n, w.window[1])
+    with tdq.build_index(w.entries) as idx:
+        with tdq.Plan(idx, n, result_capacity=16) as g, tdq.Plan(idx, n, use_graph=False) as nog:
+            c1 = g.search(q, d, t0, t1)
+            c2 = nog.search(q, d, t0, t1)
+            assert c1 == c2 > 16
+            _same(g.results(), nog.results())
+            # replay the captured graph a few times: same answer
+            for _ in range(3):
+                assert g.search(q, d, t0, t1) == c1
+            rg = g.results()
+            _same(rg, nog.results())
+        ref = tdq.search(idx, q, 15.0, *w.window)
+    _same(rg, ref)
+
+
+def test_plan_rejects_oversized_batches(tdq):
+    rng = np.random.default_rng(5)
+    ent = workloads.random_segments(rng, 100)
+    q = workloads.random_segments(rng, 50)
+    with tdq.build_index(ent) as idx, tdq.Plan(idx, 20) as plan:
+        with pytest.raises(tdq.TdqError) as ei:
+            plan.search(q, np.ones(50), np.zeros(50), np.full(50, 10.0))
+        assert ei.value.status == tdq.TDQ_ERR_INVALID
+        bad = q.take(np.arange(10))
+        with pytest.raises(tdq.TdqError):
+            plan.search(bad, np.full(10, -1.0), np.zeros(10), np.full(10, 10.0))
+        assert plan.search(bad, np.ones(10), np.zeros(10), np.full(10, 10.0)) >= 0
+
+
+def test_autotune_picks_measured_candidates(tdq):
+    w = workloads.batching_walks(n_traj=800, n_queries=60, box=200.0)
+    q = w.queries
+    tun = tdq.autotune(w.entries, q, w.q_d, w.q_t0, w.q_t1, mode=tdq.MODE_FP32_FILTER, bin_counts=[500, 5000],
+                       entry_chunks=[256, 512], batch_sizes=[1024, 2048], repeats=2)
+    assert tun["bin_count"] in (500, 5000)
+    assert tun["entry_chunk"] in (256, 512)
+    assert tun["batch_query_segments"] in (1024, 2048, len(q))
+    assert tun["ms_per_query_segment"] > 0
+    # a plan with the tuned parameters returns the same results as an untuned one
+    with tdq.build_index(w.entries, bin_count=tun["bin_count"]) as idx:
+        b = int(tun["batch_query_segments"])
+        with tdq.Plan(idx, b, mode=tdq.MODE_FP32_FILTER, entry_chunk=tun["entry_chunk"],
+                      result_capacity=tun["result_capacity"]) as plan:
+            parts = []
+            for a in range(0, len(q), b):
+                sl = np.arange(a, min(a + b, len(q)))
+                plan.search(q.take(sl), w.q_d[sl], w.q_t0[sl], w.q_t1[sl])
+                parts.append(plan.results())
+        buf = tdq.DeviceResultBuffer(1 << 18)
+        cnt = tdq.search_device_batched(idx, tdq.DeviceSegments(q), torch.from_numpy(w.q_d).cuda(),
+                                        torch.from_numpy(w.q_t0).cuda(), torch.from_numpy(w.q_t1).cuda(), buf)
+        ref = buf.to_host(cnt)
+    merged = tdq.Results(*[np.concatenate([getattr(r, f) for r in parts])
+                           for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit")])
+    _same(merged, ref)
