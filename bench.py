@@ -64,8 +64,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp32filter", choices=["fp64", "fp32filter"],
-                    help="headline search mode (the other mode is measured beside it)")
+    ap.add_argument("--mode", default="fp32filter", choices=["fp32filter"],
+                    help="the headline is the batched filter path; unbatched filter and plain FP64 are measured "
+                         "beside it")
+    ap.add_argument("--no-batching", action="store_true", help="skip the batching-workload section")
+    ap.add_argument("--batch-n-traj", type=int, default=20_000)
+    ap.add_argument("--batch-n-queries", type=int, default=5_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
@@ -241,6 +245,75 @@ def roofline(mode, tot, n_launch):
             "peak_source": src}
 
 
+def concat_thresholds(w):
+    """The step's searches (one per threshold d) as one batch: the query set
+    repeated once per d, each copy with its own segment ids and threshold."""
+    k = len(w.d_values)
+    q = workloads.Segments.concat([w.queries] * k)
+    n = len(w.queries)
+    q.seg_id = q.seg_id + np.repeat(np.arange(k, dtype=np.int64) << 40, n)
+    d = np.repeat(np.asarray(w.d_values, np.float64), n)
+    t0 = np.full(k * n, w.window[0])
+    t1 = np.full(k * n, w.window[1])
+    return q, d, t0, t1
+
+
+def batching_section(args, tdq, torch, stream):
+    """F2 on the batching workload: 20,000 walks x 300 points (5.98 M entries),
+    5,000 fresh query trajectories of lognormal length with their own d and
+    window; autotuned bin count, chunk and batch size; batches replayed as
+    CUDA graphs."""
+    w = workloads.batching_walks(n_traj=args.batch_n_traj, n_queries=args.batch_n_queries)
+    q = w.queries
+    n = len(q)
+    rng = np.random.default_rng(7)
+    sample_traj = rng.choice(args.batch_n_queries, size=max(1, args.batch_n_queries // 10), replace=False)
+    sel = np.nonzero(np.isin(q.traj_id - 10_000_000, sample_traj))[0]
+    t_tune = time.perf_counter()
+    tun = tdq.autotune(w.entries, q.take(sel), w.q_d[sel], w.q_t0[sel], w.q_t1[sel], mode=tdq.MODE_FP32_FILTER,
+                       stream=stream)
+    tune_s = time.perf_counter() - t_tune
+    idx = tdq.build_index(tdq.DeviceSegments(w.entries), bin_count=tun["bin_count"], stream=stream)
+    qdev = tdq.DeviceSegments(q)
+    dd, t0, t1 = (torch.from_numpy(a).cuda() for a in (w.q_d, w.q_t0, w.q_t1))
+    b = int(tun["batch_query_segments"])
+    plan = tdq.Plan(idx, b, mode=tdq.MODE_FP32_FILTER, entry_chunk=tun["entry_chunk"],
+                    result_capacity=tun["result_capacity"])
+    batches = [(a, min(a + b, n)) for a in range(0, n, b)]
+    subs = [tdq.DeviceSegments(tensors=([c[a:e] for c in qdev.cols], qdev.seg_id[a:e], qdev.traj_id[a:e]))
+            for a, e in batches]
+
+    def run():
+        pairs = kms = 0.0
+        for (a, e), sq in zip(batches, subs):
+            plan.search(sq, dd[a:e], t0[a:e], t1[a:e], stream=stream)
+            st = plan.stats()
+            pairs += st["overlap_pairs"]
+            kms += st["pair_kernel_ms"]
+        return pairs, kms
+
+    run()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms, pairs = [], 0.0
+    for _ in range(max(1, args.steps // 2)):
+        ev0.record(stream)
+        p, _ = run()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        pairs += p
+    plan.free()
+    idx.free()
+    tot = sum(ms) / 1e3
+    return {"workload": "batching_walks: %d walks x 300 points (%d entries), %d query trajectories (%d segments), "
+                        "own d and window each" % (args.batch_n_traj, len(w.entries), args.batch_n_queries, n),
+            "tuning": tun, "autotune_s": tune_s, "batches_per_step": len(batches),
+            "pair_tests_per_s": pairs / tot, "queries_per_s": len(ms) * args.batch_n_queries / tot,
+            "ms_per_step": 1e3 * tot / len(ms)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -280,16 +353,27 @@ def main():
     qdev = tdq.DeviceSegments(w.queries)
     buf = tdq.DeviceResultBuffer(1 << 22)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # the batched form of a step: all thresholds in one batch (one graph launch)
+    q3, d3, t03, t13 = concat_thresholds(w)
+    q3dev = tdq.DeviceSegments(q3)
+    d3dev, t03dev, t13dev = (torch.from_numpy(a).cuda() for a in (d3, t03, t13))
+    plan = tdq.Plan(idx, len(q3), mode=tdq.MODE_FP32_FILTER, result_capacity=1 << 22)
 
     def step(mode):
         t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0}
-        for d in w.d_values:
-            cnt = tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=modes[mode])
-            s = tdq.get_stats(idx)
+        if mode == "batched":
+            cnt = plan.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
+            stats = [plan.stats()]
+            t["results"] = cnt
+        else:
+            stats = []
+            for d in w.d_values:
+                t["results"] += tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=modes[mode])
+                stats.append(tdq.get_stats(idx))
+        for s in stats:
             t["pairs"] += s["overlap_pairs"]
             t["interactions"] += s["interactions"]
             t["fp64_pairs"] += s["fp64_pairs"]
-            t["results"] += cnt
             t["launches"] += s["kernel_launches"]
             t["kernel_ms"] += s["pair_kernel_ms"]
         return t
@@ -321,38 +405,37 @@ def main():
             pp = torch.tensor([pairs], device="cuda")
             torch.distributed.all_reduce(pp)
             pairs = float(pp.item())
-        n_launch = args.steps * len(w.d_values)
+        n_launch = args.steps * (1 if mode == "batched" else len(w.d_values))
         return {"value": pairs / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                 "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / (total_ms / 1e3),
                 "interactions_per_s": world * tot["interactions"] / (total_ms / 1e3),
                 "fp64_pairs_per_step": tot["fp64_pairs"] / args.steps,
                 "results_per_step": tot["results"] / args.steps, "gpu_launches": int(tot["launches"]),
-                "roofline": roofline(mode, tot, n_launch)}
+                "roofline": roofline("fp64" if mode == "fp64" else "fp32filter", tot, n_launch)}
 
-    head_mode = args.mode
-    other_mode = "fp64" if head_mode == "fp32filter" else "fp32filter"
     clocks = ClockSampler(dev)
     clocks.start()
     time.sleep(0.3)
-    head = timed(head_mode)
-    other = timed(other_mode)
+    head = timed("batched")
+    unb = timed("fp32filter")
+    plain = timed("fp64")
     clk = clocks.stop()
 
     # end to end through the C ABI: host queries in, host results out
     e2e = None
     if not args.no_e2e:
-        qhost = tdq.HostSegments(w.queries)
-        tdq.search(idx, qhost, w.d_values[0], *w.window, stream=stream, mode=modes[head_mode])
+        plan.search(q3, d3, t03, t13, stream=stream)
+        plan.results()
         barrier()
         torch.cuda.synchronize()
         t = time.perf_counter()
         e_pairs = 0
         d2h = 0
         for _ in range(args.steps):
-            for d in w.d_values:
-                r = tdq.search(idx, qhost, d, *w.window, stream=stream, mode=modes[head_mode])
-                e_pairs += tdq.get_stats(idx)["overlap_pairs"]
-                d2h += 32 * len(r) + 64
+            plan.search(q3, d3, t03, t13, stream=stream)
+            r = plan.results()
+            e_pairs += plan.stats()["overlap_pairs"]
+            d2h += 32 * len(r) + 64
         torch.cuda.synchronize()
         e_dt = time.perf_counter() - t
         if world > 1:
@@ -360,23 +443,26 @@ def main():
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             e_dt = float(tt.item())
         e2e = {"value": world * e_pairs / e_dt, "unit": "pair tests/s",
-               "h2d_bytes_per_step": len(w.d_values) * len(w.queries) * 72,
-               "d2h_bytes_per_step": d2h // args.steps,
+               "h2d_bytes_per_step": len(q3) * 96, "d2h_bytes_per_step": d2h // args.steps,
                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / e_dt}
+
+    batching = None
+    if rank == 0 and world == 1 and not args.no_batching:
+        batching = batching_section(args, tdq, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, w.d_values, CPU_SAMPLE_QUERIES)
 
     if rank == 0:
-        names = {"fp64": "plain FP64", "fp32filter": "FP32 conservative pre-test + FP64 refine"}
         line = {
-            "metric": "segment-pair tests/s (temporal-overlap pairs) & queries/s, %s search" % names[head_mode],
+            "metric": "segment-pair tests/s (temporal-overlap pairs) & queries/s; FP32 conservative pre-test + "
+                      "FP64 refine, thresholds batched in one CUDA-graph launch",
             "value": head["value"], "unit": "pair tests/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, w, {"parallelism": "replicas" if world > 1 else "single GPU",
-                                            "index_build_s": build_s}),
+                                            "index_build_s": build_s, "path": "batched plan, filter mode"}),
             "queries_per_s": head["queries_per_s"],
             "interactions_per_s": head["interactions_per_s"],
             "fp64_pairs_per_step": head["fp64_pairs_per_step"],
@@ -386,13 +472,16 @@ def main():
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": head["gpu_launches"],
-            ("plain_fp64" if other_mode == "fp64" else "fp32filter"): {
-                "value": other["value"], "unit": "pair tests/s", "ms_per_step": other["ms_per_step"],
-                "queries_per_s": other["queries_per_s"], "roofline": other["roofline"],
-                "gpu_launches": other["gpu_launches"]},
-            "speedup_vs_plain_fp64": (head["value"] / other["value"]) if other_mode == "fp64" else None,
+            "unbatched_fp32filter": {k: unb[k] for k in ("value", "ms_per_step", "queries_per_s", "roofline",
+                                                         "gpu_launches")},
+            "plain_fp64": {k: plain[k] for k in ("value", "ms_per_step", "queries_per_s", "roofline",
+                                                 "gpu_launches")},
+            "speedup_vs_plain_fp64": {"pair_tests": head["value"] / plain["value"],
+                                      "queries": head["queries_per_s"] / plain["queries_per_s"]},
+            "batching_workload": batching,
         }
         print(json.dumps(line), flush=True)
+    plan.free()
     idx.free()
     if world > 1:
         torch.distributed.destroy_process_group()

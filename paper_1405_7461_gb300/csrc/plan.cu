@@ -118,7 +118,8 @@ tdq_status capture(tdq_plan *p, uint64_t cls, cudaGraphExec_t *out)
     if (p->ngraphs == kMaxGraphs) drop_graphs(p);
     const QueryInput in = staged_input(p);
     TDQ_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_search(p->idx, p->ws, in, cls, p->cfg, p->res, p->cap_stream, false);
+    // the events become event-record nodes: the pair kernels stay timed
+    cudaError_t e = enqueue_search(p->idx, p->ws, in, cls, p->cfg, p->res, p->cap_stream, true);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -261,21 +262,15 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
                 tdq_status st = capture(p, cls, &exec);
                 if (st != TDQ_OK) return st;
             }
-            TDQ_CUDA(cudaEventRecord(w.ev[0], stream));
             TDQ_CUDA(cudaGraphLaunch(exec, stream));
-            TDQ_CUDA(cudaEventRecord(w.ev[3], stream));
         } else {
             TDQ_CUDA(enqueue_search(p->idx, w, staged_input(p), cls, p->cfg, p->res, stream, true));
         }
         TDQ_CUDA(cudaStreamSynchronize(stream));
         bool grow_surv = false;
         uint64_t cnt = 0;
-        tdq_status st = finish_search(p->idx, w, p->cfg, p->res.capacity, !p->use_graph, &p->last, &cnt, &grow_surv);
-        if (p->use_graph) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) p->last.total_ms = ms;
-            p->last.kernel_launches = (uint64_t)search_kernel_launches(p->idx, p->cfg);
-        }
+        tdq_status st = finish_search(p->idx, w, p->cfg, p->res.capacity, true, &p->last, &cnt, &grow_surv);
+        cudaGetLastError();
         if (st == TDQ_OK && !grow_surv) {
             *count = cnt;
             p->last_count = cnt;
