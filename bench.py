@@ -239,6 +239,8 @@ def roofline(mode, tot, n_launch):
         peak, kernel = FP32_PEAK_GFLOPS, "traj_dist_filter_kernel"
         src = "derived: 128 FFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz"
         per = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per candidate pair (sphere pre-test)"
+    if kern_ms <= 0:
+        return None
     achieved = work / (kern_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
             "traffic": traffic_record(mode), "kernel": kernel, "kernel_ms_avg": kern_ms, "work_unit": per,

@@ -864,12 +864,14 @@ int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg)
     return idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 3 + (cfg.filter ? 3 : 1) : 1;
 }
 
+// Events are recorded as external event-record nodes when the stream is being
+// captured, so the timings stay valid inside a replayed CUDA graph.
 cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq, const LaunchCfg &cfg,
                            const tdq_result_buffer &out, cudaStream_t stream, bool events)
 {
     cudaError_t e = cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream);
     if (e != cudaSuccess) return e;
-    if (events && (e = cudaEventRecord(w.ev[0], stream)) != cudaSuccess) return e;
+    if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
     BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
@@ -883,18 +885,18 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                                                  w.tile_work);
         if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk};
-        if (events && (e = cudaEventRecord(w.ev[1], stream)) != cudaSuccess) return e;
+        if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream)) != cudaSuccess)
             return e;
-        if (events && (e = cudaEventRecord(w.ev[2], stream)) != cudaSuccess) return e;
+        if (events && (e = cudaEventRecordWithFlags(w.ev[2], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
         if (cfg.filter && (e = launch_overlap_count(pa, nq, idx->n, stream)) != cudaSuccess) return e;
     } else if (events) {
-        if ((e = cudaEventRecord(w.ev[1], stream)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(w.ev[2], stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecordWithFlags(w.ev[1], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = cudaEventRecordWithFlags(w.ev[2], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return e;
-    if (events && (e = cudaEventRecord(w.ev[3], stream)) != cudaSuccess) return e;
+    if (events && (e = cudaEventRecordWithFlags(w.ev[3], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
