@@ -869,9 +869,13 @@ int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg)
 cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq, const LaunchCfg &cfg,
                            const tdq_result_buffer &out, cudaStream_t stream, bool events)
 {
-    cudaError_t e = cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
     if (e != cudaSuccess) return e;
-    if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+    const unsigned evflags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    e = cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream);
+    if (e != cudaSuccess) return e;
+    if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, evflags)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
     BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
@@ -885,18 +889,18 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                                                  w.tile_work);
         if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk};
-        if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream)) != cudaSuccess)
             return e;
-        if (events && (e = cudaEventRecordWithFlags(w.ev[2], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if (events && (e = cudaEventRecordWithFlags(w.ev[2], stream, evflags)) != cudaSuccess) return e;
         if (cfg.filter && (e = launch_overlap_count(pa, nq, idx->n, stream)) != cudaSuccess) return e;
     } else if (events) {
-        if ((e = cudaEventRecordWithFlags(w.ev[1], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-        if ((e = cudaEventRecordWithFlags(w.ev[2], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+        if ((e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
+        if ((e = cudaEventRecordWithFlags(w.ev[2], stream, evflags)) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return e;
-    if (events && (e = cudaEventRecordWithFlags(w.ev[3], stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if (events && (e = cudaEventRecordWithFlags(w.ev[3], stream, evflags)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
