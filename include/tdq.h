@@ -299,6 +299,73 @@ tdq_status tdq_autotune(const tdq_segments *entries, const tdq_segments *sample,
                         const double *t0_per_query, const double *t1_per_query, const tdq_autotune_params *params,
                         void *stream, tdq_tuning *out);
 
+/*
+ * Serving loop with continuous batching.  The paper's setting is online: one
+ * database resident on the GPU, many queries, response time as the
+ * objective, batches because result memory is reserved up front, and several
+ * users competing for that memory (Sec. 3).  A server keeps the index
+ * resident and runs `lanes` worker threads, each with its own CUDA stream and
+ * batched plan.  Submitted requests (one query trajectory's segments with its
+ * own d and window) wait in a FIFO queue; a free lane admits requests from
+ * its head while the batch stays within max_batch_query_segments and the
+ * estimated result-buffer bytes of all admitted, unfinished requests stay
+ * within memory_cap_bytes (at least one request is admitted when nothing is
+ * in flight), then searches the batch.  Requests that arrive while batches
+ * are running are admitted by free lanes as slots and memory free up, so
+ * batches overlap on the device.  A request's results do not depend on the
+ * batch it ran in.  The server keeps a pointer to the index; free the
+ * server first.
+ */
+typedef struct tdq_server tdq_server;
+
+typedef struct {
+    uint64_t max_batch_query_segments; /* per batch, and the largest request (0: 65536) */
+    uint64_t memory_cap_bytes;         /* admission cap on estimated result-buffer bytes (0: 16 GiB) */
+    int lanes;                         /* concurrent batches (0: 2, at most 16) */
+    int mode;                          /* TDQ_MODE_* */
+    uint32_t entry_chunk;              /* 0: mode default */
+    double results_per_query_segment;  /* estimate used for admission (0: 4); tdq_autotune measures it */
+} tdq_server_params;
+
+typedef struct {
+    double queue_ms;    /* submit -> admitted to a batch */
+    double run_ms;      /* admitted -> results ready */
+    double latency_ms;  /* submit -> results ready */
+    uint64_t batch;     /* id of the batch the request ran in */
+    uint64_t batch_query_segments;
+} tdq_request_info;
+
+typedef struct {
+    uint64_t requests_submitted;
+    uint64_t requests_completed;
+    uint64_t batches;
+    uint64_t failed_batches;
+    uint64_t query_segments;
+    uint64_t max_concurrent_batches; /* most batches running at once */
+    double peak_bytes_in_flight;     /* largest estimated bytes admitted at once */
+    uint64_t queued;                 /* requests waiting now */
+} tdq_server_stats;
+
+tdq_status tdq_server_create(tdq_index *idx, const tdq_server_params *params, tdq_server **out);
+
+/* Queue one request (host memory; copied).  Validated here: TDQ_ERR_INVALID
+ * for bad segments, d < 0 or NaN, NaN or reversed window, or more segments
+ * than max_batch_query_segments.  *ticket identifies it for tdq_server_wait. */
+tdq_status tdq_server_submit(tdq_server *srv, const tdq_segments *queries, double d, double t0, double t1,
+                             uint64_t *ticket);
+
+/* Wait for a request (timeout_ms < 0: no limit) and take its results (host,
+ * library-owned, release with tdq_results_free) and timings.
+ * TDQ_ERR_TIMEOUT if not done in time (the request stays queued/running and
+ * can be waited for again). */
+tdq_status tdq_server_wait(tdq_server *srv, uint64_t ticket, int64_t timeout_ms, tdq_results **out,
+                           tdq_request_info *info);
+
+tdq_status tdq_server_get_stats(tdq_server *srv, tdq_server_stats *out);
+
+/* Finish the queued requests, stop the lanes and release the server. */
+void tdq_server_free(tdq_server *srv);
+
 /* Counters of the last completed search on idx. */
 tdq_status tdq_get_stats(const tdq_index *idx, tdq_stats *out);
 

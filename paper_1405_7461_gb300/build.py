@@ -47,8 +47,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                     "--expt-relaxed-constexpr"] + list(extra_flags)
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I",
+                     INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"] + list(extra_flags)
     if verbose:
         common += ["-Xptxas", "-v"]
 
@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for _, err in outs:
             sys.stderr.write(err)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in outs] + ARCH + ["-lcudart"]
+    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in outs] + ARCH + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -90,6 +90,30 @@ class tdq_tuning(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class tdq_server_params(ctypes.Structure):
+    _fields_ = [("max_batch_query_segments", ctypes.c_uint64), ("memory_cap_bytes", ctypes.c_uint64),
+                ("lanes", ctypes.c_int), ("mode", ctypes.c_int), ("entry_chunk", ctypes.c_uint32),
+                ("results_per_query_segment", ctypes.c_double)]
+
+
+class tdq_request_info(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("batch", ctypes.c_uint64), ("batch_query_segments", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class tdq_server_stats(ctypes.Structure):
+    _fields_ = [("requests_submitted", ctypes.c_uint64), ("requests_completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("failed_batches", ctypes.c_uint64),
+                ("query_segments", ctypes.c_uint64), ("max_concurrent_batches", ctypes.c_uint64),
+                ("peak_bytes_in_flight", ctypes.c_double), ("queued", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # Every symbol include/tdq.h declares, with (restype, argtypes).
 P = ctypes.c_void_p
 SIGNATURES = {
@@ -111,6 +135,11 @@ SIGNATURES = {
     "tdq_plan_get_stats": (ctypes.c_int, [P, P]),
     "tdq_plan_copy_results": (ctypes.c_int, [P, P, P, P, P, ctypes.c_uint64, ctypes.c_int, P]),
     "tdq_autotune": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
+    "tdq_server_create": (ctypes.c_int, [P, P, P]),
+    "tdq_server_submit": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]),
+    "tdq_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_int64, P, P]),
+    "tdq_server_get_stats": (ctypes.c_int, [P, P]),
+    "tdq_server_free": (None, [P]),
     "tdq_last_error": (ctypes.c_char_p, []),
     "tdq_version": (ctypes.c_char_p, []),
 }
@@ -536,3 +565,74 @@ def autotune(entries, sample, d, t0, t1, mode=MODE_FP64, bin_counts=None, entry_
                                ctypes.byref(out)))
     del keep, arrs
     return out.as_dict()
+
+
+# --------------------------------------------------------------------------
+# Serving loop
+# --------------------------------------------------------------------------
+
+def _take_results(ptr) -> Results:
+    lib = load()
+    try:
+        r = ptr.contents
+        n = int(r.count)
+
+        def arr(p, dt):
+            if n == 0:
+                return np.empty(0, dt)
+            return np.frombuffer((ctypes.c_char * (n * 8)).from_address(p), dtype=dt).copy()
+
+        return Results(arr(r.query_seg_id, np.int64), arr(r.entry_seg_id, np.int64), arr(r.t_enter, np.float64),
+                       arr(r.t_exit, np.float64))
+    finally:
+        lib.tdq_results_free(ptr)
+
+
+class Server:
+    """Owner of a tdq_server: continuous batching over a resident index."""
+
+    def __init__(self, idx: Index, max_batch_query_segments=65536, memory_cap_bytes=16 << 30, lanes=2,
+                 mode=MODE_FP32_FILTER, entry_chunk=0, results_per_query_segment=0.0):
+        self.idx = idx
+        prm = tdq_server_params(int(max_batch_query_segments), int(memory_cap_bytes), int(lanes), int(mode),
+                                int(entry_chunk), float(results_per_query_segment))
+        h = ctypes.c_void_p()
+        _check(load().tdq_server_create(idx.handle, ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h.value
+
+    def submit(self, query: Segments, d: float, t0: float, t1: float) -> int:
+        q = HostSegments(query)
+        s = q.struct()
+        t = ctypes.c_uint64()
+        _check(load().tdq_server_submit(self._h, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Results and timing info of a request (raises TdqError with
+        TDQ_ERR_TIMEOUT if it is not done within timeout_ms)."""
+        out = ctypes.POINTER(tdq_results)()
+        info = tdq_request_info()
+        _check(load().tdq_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(out), ctypes.byref(info)))
+        return _take_results(out), info.as_dict()
+
+    def stats(self) -> dict:
+        st = tdq_server_stats()
+        _check(load().tdq_server_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def free(self):
+        if self._h:
+            load().tdq_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.free()

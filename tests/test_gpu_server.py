@@ -1,0 +1,138 @@
+"""Serving loop: continuous batching gives every request the same results
+alone and in the mix, matches the oracle, honours the memory cap, and
+reports timeouts and invalid requests on the host."""
+import threading
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1405_7461_gb300 import workloads
+from tests._util import compare_results
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def tdq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7461_gb300 import build, tdq as t
+
+    build.build()
+    t.load()
+    return t
+
+
+@pytest.fixture(scope="module")
+def db():
+    return workloads.serving_database(n_traj=3000, n_points=120)
+
+
+@pytest.fixture(scope="module")
+def requests():
+    return workloads.serving_requests(n_requests=48, rate_per_s=2000.0, n_points=120, min_seg=5, max_seg=110)
+
+
+def _sorted(r):
+    o = np.lexsort((r.entry_seg_id, r.query_seg_id))
+    return r.query_seg_id[o], r.entry_seg_id[o], r.t_enter[o], r.t_exit[o]
+
+
+def _same(a, b):
+    for x, y in zip(_sorted(a), _sorted(b)):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("mode_name", ["filter", "fp64"])
+def test_results_same_alone_and_in_the_mix(tdq, db, requests, mode_name):
+    mode = tdq.MODE_FP32_FILTER if mode_name == "filter" else tdq.MODE_FP64
+    with tdq.build_index(db) as idx:
+        with tdq.Server(idx, max_batch_query_segments=2048, lanes=3, mode=mode) as srv:
+            alone = []
+            for rq in requests:
+                res, info = srv.wait(srv.submit(rq.query, rq.d, rq.t0, rq.t1))
+                alone.append(res)
+                assert info["latency_ms"] >= info["run_ms"] >= 0
+            st_alone = srv.stats()
+            assert st_alone["batches"] == len(requests)
+            # the mix: all requests submitted from two threads at once
+            tickets = [None] * len(requests)
+
+            def submitter(ks):
+                for k in ks:
+                    rq = requests[k]
+                    tickets[k] = srv.submit(rq.query, rq.d, rq.t0, rq.t1)
+
+            ths = [threading.Thread(target=submitter, args=(range(i, len(requests), 2),)) for i in range(2)]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+            mixed = [srv.wait(t)[0] for t in tickets]
+            st = srv.stats()
+        assert st["requests_completed"] == 2 * len(requests)
+        assert st["batches"] - st_alone["batches"] < len(requests)  # requests shared batches
+        for a, m in zip(alone, mixed):
+            _same(a, m)
+        # each request against a direct search with its own d and window
+        for rq, a in zip(requests[:8], alone[:8]):
+            ref = tdq.search(idx, rq.query, rq.d, rq.t0, rq.t1)
+            _same(a, ref)
+    assert sum(len(a) for a in alone) > 0
+
+
+def test_request_results_match_the_oracle(tdq, db, requests):
+    with tdq.build_index(db) as idx, tdq.Server(idx, lanes=2) as srv:
+        tickets = [srv.submit(rq.query, rq.d, rq.t0, rq.t1) for rq in requests[:12]]
+        got = [srv.wait(t)[0] for t in tickets]
+    matched = 0
+    for rq, g in zip(requests[:12], got):
+        ref = oracle.search_sweep(db, rq.query, rq.d, rq.t0, rq.t1)
+        qpos = {int(s): i for i, s in enumerate(rq.query.seg_id)}
+        gi = {"qi": np.array([qpos[int(s)] for s in g.query_seg_id], np.int64), "ei": g.entry_seg_id.copy(),
+              "t_enter": g.t_enter, "t_exit": g.t_exit}
+        cmp = compare_results(gi, {"qi": ref.query_index, "ei": ref.entry_index, "t_enter": ref.t_enter,
+                                   "t_exit": ref.t_exit}, db, rq.query, rq.d, rq.t0, rq.t1,
+                              dmin_fn=lambda ei, qi: oracle.pair_dmin(db, ei, rq.query, qi, rq.t0, rq.t1))
+        matched += cmp["matched"]
+    assert matched > 0
+
+
+def test_memory_cap_admits_one_request_at_a_time(tdq, db, requests):
+    with tdq.build_index(db) as idx:
+        with tdq.Server(idx, lanes=3, memory_cap_bytes=1) as srv:
+            tickets = [srv.submit(rq.query, rq.d, rq.t0, rq.t1) for rq in requests[:20]]
+            got = [srv.wait(t)[0] for t in tickets]
+            st = srv.stats()
+        assert st["batches"] == 20 and st["max_concurrent_batches"] == 1
+        for rq, g in zip(requests[:20], got):
+            _same(g, tdq.search(idx, rq.query, rq.d, rq.t0, rq.t1))
+
+
+def test_timeouts_and_invalid_requests_are_reported_on_the_host(tdq, db, requests):
+    with tdq.build_index(db) as idx, tdq.Server(idx, lanes=1, max_batch_query_segments=512) as srv:
+        rq = requests[0]
+        with pytest.raises(tdq.TdqError) as ei:
+            srv.submit(rq.query, -1.0, rq.t0, rq.t1)
+        assert ei.value.status == tdq.TDQ_ERR_INVALID
+        with pytest.raises(tdq.TdqError) as ei:
+            srv.submit(rq.query, rq.d, 5.0, 1.0)
+        assert ei.value.status == tdq.TDQ_ERR_INVALID
+        big = workloads.Segments.concat([requests[k].query for k in range(12)])
+        if len(big) > 512:
+            with pytest.raises(tdq.TdqError):
+                srv.submit(big, 1.0, -np.inf, np.inf)
+        with pytest.raises(tdq.TdqError) as ei:
+            srv.wait(987654321, 0)
+        assert ei.value.status == tdq.TDQ_ERR_INVALID
+        # a wait that runs out of time leaves the request waitable
+        tickets = [srv.submit(r.query, r.d, r.t0, r.t1) for r in requests[:10]]
+        try:
+            srv.wait(tickets[-1], 0)
+        except tdq.TdqError as e:
+            assert e.status == tdq.TDQ_ERR_TIMEOUT
+        for t in tickets:
+            srv.wait(t)
