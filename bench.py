@@ -70,6 +70,11 @@ def parse():
     ap.add_argument("--no-batching", action="store_true", help="skip the batching-workload section")
     ap.add_argument("--batch-n-traj", type=int, default=20_000)
     ap.add_argument("--batch-n-queries", type=int, default=5_000)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-workload section")
+    ap.add_argument("--serve-n-traj", type=int, default=40_000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-plain-requests", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
@@ -316,6 +321,82 @@ def batching_section(args, tdq, torch, stream):
             "ms_per_step": 1e3 * tot / len(ms)}
 
 
+def serving_section(args, tdq, torch):
+    """F3: 40,000 walks x 500 points resident (19.96 M entries); Poisson
+    arrivals at 2,000/s for 10 s, each a fresh walk of 5..499 segments with
+    its own d and window; p50/p99 latency and queries/s of the serving loop,
+    its saturation throughput, and the plain FP64 search issued one query at
+    a time for comparison."""
+    import threading
+
+    db = workloads.serving_database(n_traj=args.serve_n_traj, n_points=500)
+    reqs = workloads.serving_requests(n_requests=int(args.serve_rate * args.serve_seconds),
+                                      rate_per_s=args.serve_rate, n_points=500)
+    idx = tdq.build_index(tdq.DeviceSegments(db))
+    del db
+    srv = tdq.Server(idx, max_batch_query_segments=65536, memory_cap_bytes=16 << 30, lanes=3,
+                     mode=tdq.MODE_FP32_FILTER, results_per_query_segment=1.0)
+    for rq in reqs[:50]:  # warm up (graph capture per size class)
+        srv.wait(srv.submit(rq.query, rq.d, rq.t0, rq.t1))
+    tickets = [None] * len(reqs)
+    lat = np.zeros(len(reqs))
+
+    def submitter():
+        t_start = time.perf_counter()
+        for k, rq in enumerate(reqs):
+            delay = rq.arrival_s - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(rq.query, rq.d, rq.t0, rq.t1)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    n_results = 0
+    for k in range(len(reqs)):
+        while tickets[k] is None:
+            time.sleep(0.0002)
+        res, info = srv.wait(tickets[k])
+        lat[k] = info["latency_ms"]
+        n_results += len(res)
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    # saturation: a burst of all requests at once
+    t1 = time.perf_counter()
+    burst = [srv.submit(rq.query, rq.d, rq.t0, rq.t1) for rq in reqs]
+    for t in burst:
+        srv.wait(t)
+    burst_s = time.perf_counter() - t1
+    srv.free()
+    # plain FP64 search, one query at a time (host API, blocking)
+    n_plain = min(len(reqs), args.serve_plain_requests)
+    plat = np.zeros(n_plain)
+    for rq in reqs[:5]:
+        tdq.search(idx, rq.query, rq.d, rq.t0, rq.t1, mode=tdq.MODE_FP64)
+    tp = time.perf_counter()
+    for k, rq in enumerate(reqs[:n_plain]):
+        a = time.perf_counter()
+        tdq.search(idx, rq.query, rq.d, rq.t0, rq.t1, mode=tdq.MODE_FP64)
+        plat[k] = 1e3 * (time.perf_counter() - a)
+    plain_s = time.perf_counter() - tp
+    idx.free()
+    return {"workload": "serving_walks: %d walks x 500 points resident (%d entries); Poisson arrivals %.0f/s for "
+                        "%.0f s (%d requests of 5..499 segments, own d in [1,20] and window)"
+                        % (args.serve_n_traj, args.serve_n_traj * 499, args.serve_rate, args.serve_seconds,
+                           len(reqs)),
+            "open_loop": {"queries_per_s": len(reqs) / wall, "p50_latency_ms": float(np.percentile(lat, 50)),
+                          "p99_latency_ms": float(np.percentile(lat, 99)), "max_latency_ms": float(lat.max()),
+                          "batches": st["batches"], "max_concurrent_batches": st["max_concurrent_batches"],
+                          "results": n_results},
+            "saturation_queries_per_s": len(reqs) / burst_s,
+            "plain_fp64_one_at_a_time": {"queries_per_s": n_plain / plain_s,
+                                         "p50_latency_ms": float(np.percentile(plat, 50)),
+                                         "p99_latency_ms": float(np.percentile(plat, 99)),
+                                         "sample_requests": n_plain},
+            "lanes": 3, "memory_cap_bytes": 16 << 30}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -451,6 +532,9 @@ def main():
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
         batching = batching_section(args, tdq, torch, stream)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_section(args, tdq, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -481,6 +565,7 @@ def main():
             "speedup_vs_plain_fp64": {"pair_tests": head["value"] / plain["value"],
                                       "queries": head["queries_per_s"] / plain["queries_per_s"]},
             "batching_workload": batching,
+            "serving_workload": serving,
         }
         print(json.dumps(line), flush=True)
     plan.free()
