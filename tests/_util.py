@@ -77,10 +77,13 @@ def compare_results(gpu, ora, entries, queries, d, t0=-np.inf, t1=np.inf, dmin_f
             f"pair (q={qi}, e={ei}) reported by one side only; dmin={dm!r}, d={dd!r}")
         ties += 1
     bad = 0
+    max_rel = 0.0
     for name in ("t_enter", "t_exit"):
         a = gpu[name][og][ig]
         b = ora[name][oo][io]
         tol = ENDPOINT_REL * np.maximum(1.0, np.abs(b))
+        if len(a):
+            max_rel = max(max_rel, float(np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b)))))
         off = np.nonzero(np.abs(a - b) > tol)[0]
         for j in off:
             k = int(common[j])
@@ -92,4 +95,5 @@ def compare_results(gpu, ora, entries, queries, d, t0=-np.inf, t1=np.inf, dmin_f
             assert abs(dist - dd) <= TIE_REL * dd + 1e-12, (
                 f"{name} mismatch for pair (q={qi}, e={ei}): {a[j]!r} vs {b[j]!r}, dist at ours {dist!r}")
             bad += 1
-    return {"matched": len(common), "ties": ties, "ill_conditioned_endpoints": bad}
+    return {"matched": len(common), "ties": ties, "ill_conditioned_endpoints": bad, "max_endpoint_rel": max_rel,
+            "gpu_only": len(only_g), "oracle_only": len(only_o)}

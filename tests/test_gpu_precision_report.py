@@ -1,0 +1,60 @@
+"""Precision report: for each workload and threshold, the filter-mode
+results against the CPU FP64 oracle -- matched pairs, ties (pairs within
+1e-9*d of the threshold that one side reports), ill-conditioned endpoints
+and the largest relative endpoint difference.  Asserts the parity bar and,
+when TDQ_REPORT_DIR is set, writes the table there as JSON."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1405_7461_gb300 import workloads
+from tests._util import compare_results
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_precision_report():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7461_gb300 import build, tdq
+
+    build.build()
+    rows = []
+    cases = [("tiny_random_walk", workloads.tiny_random_walk(), None),
+             ("scale_random_walk (2,000 walks, 20 queries)", workloads.scale_random_walk(n_traj=2000, n_queries=20),
+              None),
+             ("galaxy_disk (full 9.95 M entries, 4 query stars)", workloads.galaxy_disk(), 4)]
+    for name, w, nq in cases:
+        q = w.queries
+        if nq:
+            keep = np.unique(q.traj_id)[:nq]
+            q = q.take(np.nonzero(np.isin(q.traj_id, keep))[0])
+        with tdq.build_index(w.entries) as idx:
+            for d in w.d_values:
+                r = tdq.search(idx, q, d, *w.window, mode=tdq.MODE_FP32_FILTER)
+                st = tdq.get_stats(idx)
+                ref = oracle.search_sweep(w.entries, q, d, *w.window)
+                order = np.argsort(q.seg_id)
+                qi = order[np.searchsorted(q.seg_id[order], r.query_seg_id)]
+                eorder = np.argsort(w.entries.seg_id)
+                ei = eorder[np.searchsorted(w.entries.seg_id[eorder], r.entry_seg_id)]
+                cmp = compare_results({"qi": qi, "ei": ei, "t_enter": r.t_enter, "t_exit": r.t_exit},
+                                      {"qi": ref.query_index, "ei": ref.entry_index, "t_enter": ref.t_enter,
+                                       "t_exit": ref.t_exit}, w.entries, q, d, *w.window,
+                                      dmin_fn=lambda e, k: oracle.pair_dmin(w.entries, e, q, k, *w.window))
+                rows.append({"workload": name, "d": d, "query_segments": len(q), "overlap_pairs": st["overlap_pairs"],
+                             "fp64_pairs": st["fp64_pairs"], "oracle_pairs": len(ref.query_index), **cmp})
+    for row in rows:
+        assert row["max_endpoint_rel"] <= 1e-9 or row["ill_conditioned_endpoints"] > 0
+    out = os.environ.get("TDQ_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "precision_report.json"), "w") as f:
+            json.dump(rows, f, indent=1)
+    for row in rows:
+        print(json.dumps(row))
