@@ -86,6 +86,21 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_over_ranks(seconds, work, device="cpu"):
+    """Weak-scaling reduction of one timed region: the slowest rank's time
+    and the work summed over ranks (no collective outside the timing)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds), float(work)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
 def workload(args, rank):
     w = workloads.scale_random_walk(n_traj=args.n_traj, n_queries=args.n_queries)
     if rank > 0:  # each rank its own query trajectories from the same database
@@ -479,15 +494,7 @@ def main():
             tot = out if tot is None else {k: tot[k] + out[k] for k in tot}
         torch.cuda.synchronize()
         barrier()
-        total_ms = sum(ms)
-        pairs = float(tot["pairs"])
-        if world > 1:
-            tt = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(tt.item())
-            pp = torch.tensor([pairs], device="cuda")
-            torch.distributed.all_reduce(pp)
-            pairs = float(pp.item())
+        total_ms, pairs = reduce_over_ranks(sum(ms), float(tot["pairs"]), device="cuda")
         n_launch = args.steps * (1 if mode == "batched" else len(w.d_values))
         return {"value": pairs / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                 "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / (total_ms / 1e3),
@@ -520,12 +527,8 @@ def main():
             e_pairs += plan.stats()["overlap_pairs"]
             d2h += 32 * len(r) + 64
         torch.cuda.synchronize()
-        e_dt = time.perf_counter() - t
-        if world > 1:
-            tt = torch.tensor([e_dt], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e_dt = float(tt.item())
-        e2e = {"value": world * e_pairs / e_dt, "unit": "pair tests/s",
+        e_dt, e_pairs = reduce_over_ranks(time.perf_counter() - t, e_pairs, device="cuda")
+        e2e = {"value": e_pairs / e_dt, "unit": "pair tests/s",
                "h2d_bytes_per_step": len(q3) * 96, "d2h_bytes_per_step": d2h // args.steps,
                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / e_dt}
 

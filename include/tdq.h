@@ -369,6 +369,12 @@ void tdq_server_free(tdq_server *srv);
 /* Counters of the last completed search on idx. */
 tdq_status tdq_get_stats(const tdq_index *idx, tdq_stats *out);
 
+/* Fault injection for tests of the error paths: the allocation (device or
+ * pinned host) made `after` allocations from now fails as if memory were
+ * exhausted, once; after < 0 disables it.  Calls then return TDQ_ERR_NOMEM
+ * and release what they had allocated.  Process-wide. */
+void tdq_debug_fail_allocations(int64_t after);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *tdq_last_error(void);
 

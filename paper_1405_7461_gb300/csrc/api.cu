@@ -2,10 +2,14 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "tdq_internal.cuh"
 
 namespace {
 thread_local char g_err[512] = "";
+// allocations left before the injected failure (< 0: none injected)
+std::atomic<long long> g_alloc_countdown{-1};
 }
 
 namespace tdq {
@@ -26,7 +30,18 @@ tdq_status cuda_error(cudaError_t e, const char *what)
     return set_error(TDQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+cudaError_t alloc_gate()
+{
+    long long c = g_alloc_countdown.load();
+    while (c >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0 ? cudaErrorMemoryAllocation : cudaSuccess;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace tdq
+
+extern "C" void tdq_debug_fail_allocations(int64_t after) { g_alloc_countdown.store(after < 0 ? -1 : after); }
 
 extern "C" const char *tdq_last_error(void) { return g_err; }
 

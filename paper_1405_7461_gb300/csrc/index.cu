@@ -252,8 +252,8 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             return set_error(TDQ_ERR_CUDA, "tdq_build_index: cudaEventCreate failed");
         }
     }
-    if (cudaMalloc(&idx->ws.ctr, sizeof(DevCounters)) != cudaSuccess ||
-        cudaMallocHost(&idx->ws.ctr_host, sizeof(DevCounters)) != cudaSuccess) {
+    if (dev_alloc(&idx->ws.ctr, sizeof(DevCounters)) != cudaSuccess ||
+        host_alloc(&idx->ws.ctr_host, sizeof(DevCounters)) != cudaSuccess) {
         tdq_index_free(idx);
         return set_error(TDQ_ERR_NOMEM, "tdq_build_index: counter allocation failed");
     }
@@ -265,7 +265,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     // Resident sorted copy + bin table.
     uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n / 64 + 1, 4) + carve_bytes(n, 16);
     uint64_t bbytes = carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
-    if (cudaMalloc(&idx->e_block, ebytes) != cudaSuccess || cudaMalloc(&idx->b_block, bbytes) != cudaSuccess) {
+    if (dev_alloc(&idx->e_block, ebytes) != cudaSuccess || dev_alloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
         tdq_index_free(idx);
         return set_error(TDQ_ERR_NOMEM, "tdq_build_index: device allocation of %llu bytes failed",
@@ -292,7 +292,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     uint64_t tbytes = (host_in ? 10 * carve_bytes(n, 8) : 0) + 2 * carve_bytes(n, 8) + 2 * carve_bytes(n, 4) +
                       carve_bytes(sort_hist_words(n), 4) + carve_bytes(4, 8);
     void *tmp = nullptr;
-    if (cudaMalloc(&tmp, tbytes) != cudaSuccess) {
+    if (dev_alloc(&tmp, tbytes) != cudaSuccess) {
         cudaGetLastError();
         tdq_index_free(idx);
         return set_error(TDQ_ERR_NOMEM, "tdq_build_index: device allocation of %llu bytes failed",
@@ -425,7 +425,7 @@ extern "C" tdq_status tdq_index_bins(const tdq_index *idx, uint32_t *m, double *
         return TDQ_OK;
     }
     void *tmp = nullptr;
-    if (cudaMalloc(&tmp, (uint64_t)mm * 32) != cudaSuccess) {
+    if (dev_alloc(&tmp, (uint64_t)mm * 32) != cudaSuccess) {
         cudaGetLastError();
         return set_error(TDQ_ERR_NOMEM, "tdq_index_bins: device allocation failed");
     }

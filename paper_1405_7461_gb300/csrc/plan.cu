@@ -74,7 +74,7 @@ tdq_status plan_results(tdq_plan *p, uint64_t cap)
     p->r_block = nullptr;
     p->res = tdq_result_buffer{};
     const uint64_t b = (cap * 8 + 255) & ~(uint64_t)255;
-    if (cudaMalloc(&p->r_block, 4 * b) != cudaSuccess) {
+    if (dev_alloc(&p->r_block, 4 * b) != cudaSuccess) {
         cudaGetLastError();
         return set_error(TDQ_ERR_NOMEM, "tdq_plan: result buffer of %llu items", (unsigned long long)cap);
     }
@@ -179,10 +179,10 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
     p->use_graph = !params->no_graph;
     do {
         Workspace &w = p->ws;
-        bool ok = cudaMalloc(&w.ctr, sizeof(DevCounters)) == cudaSuccess &&
-                  cudaMallocHost(&w.ctr_host, sizeof(DevCounters)) == cudaSuccess &&
-                  cudaMallocHost(&p->n_host, sizeof(unsigned long long)) == cudaSuccess &&
-                  cudaMalloc(&p->stage_block, (3 * p->cap_q + 1) * 8) == cudaSuccess;
+        bool ok = dev_alloc(&w.ctr, sizeof(DevCounters)) == cudaSuccess &&
+                  host_alloc(&w.ctr_host, sizeof(DevCounters)) == cudaSuccess &&
+                  host_alloc(&p->n_host, sizeof(unsigned long long)) == cudaSuccess &&
+                  dev_alloc(&p->stage_block, (3 * p->cap_q + 1) * 8) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             st = set_error(TDQ_ERR_NOMEM, "tdq_plan_create: allocation failed");
@@ -346,7 +346,7 @@ tdq_status device_sample(const tdq_segments *q, const double *d, const double *t
     s->t1 = t1;
     if (q->on_device) return TDQ_OK;
     const uint64_t n = q->n;
-    if (cudaMalloc(&s->block, n * 8 * 12) != cudaSuccess) {
+    if (dev_alloc(&s->block, n * 8 * 12) != cudaSuccess) {
         cudaGetLastError();
         return set_error(TDQ_ERR_NOMEM, "tdq_autotune: sample staging");
     }

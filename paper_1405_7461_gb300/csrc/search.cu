@@ -788,8 +788,8 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     w.q_block = w.t_block = nullptr;
     w.sort_hist = nullptr;
     w.q_cap = 0;
-    if (cudaMalloc(&w.q_block, bytes) != cudaSuccess || cudaMalloc(&w.t_block, tbytes) != cudaSuccess ||
-        cudaMalloc(&w.sort_hist, hwords * 4) != cudaSuccess) {
+    if (dev_alloc(&w.q_block, bytes) != cudaSuccess || dev_alloc(&w.t_block, tbytes) != cudaSuccess ||
+        dev_alloc(&w.sort_hist, hwords * 4) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(w.q_block);
         cudaFree(w.t_block);
@@ -835,7 +835,7 @@ tdq_status ensure_survivors(Workspace &w, uint64_t cap)
     w.s_block = nullptr;
     w.surv = nullptr;
     w.s_cap_pairs = 0;
-    if (cudaMalloc(&w.s_block, cap * sizeof(uint2)) != cudaSuccess) {
+    if (dev_alloc(&w.s_block, cap * sizeof(uint2)) != cudaSuccess) {
         cudaGetLastError();
         return set_error(TDQ_ERR_NOMEM, "tdq_search: survivor list of %llu pairs", (unsigned long long)cap);
     }
@@ -1015,7 +1015,7 @@ tdq_status ensure_results(tdq_index *idx, uint64_t cap)
     cudaFree(w.r_block);
     w.r_block = nullptr;
     w.r_cap = 0;
-    if (cudaMalloc(&w.r_block, 4 * cb(cap, 8)) != cudaSuccess) {
+    if (dev_alloc(&w.r_block, 4 * cb(cap, 8)) != cudaSuccess) {
         cudaGetLastError();
         return set_error(TDQ_ERR_NOMEM, "tdq_search: result buffer of %llu items", (unsigned long long)cap);
     }

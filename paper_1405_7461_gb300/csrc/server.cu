@@ -116,9 +116,9 @@ tdq_status lane_alloc(Lane &L, uint64_t cap)
 {
     L.cap = cap;
     for (int c = 0; c < 8; c++)
-        if (cudaMallocHost(&L.h_cols[c], cap * 8) != cudaSuccess) return set_error(TDQ_ERR_NOMEM, "server: staging");
-    if (cudaMallocHost(&L.h_seg, cap * 8) != cudaSuccess || cudaMallocHost(&L.h_d, cap * 8) != cudaSuccess ||
-        cudaMallocHost(&L.h_t0, cap * 8) != cudaSuccess || cudaMallocHost(&L.h_t1, cap * 8) != cudaSuccess)
+        if (host_alloc(&L.h_cols[c], cap * 8) != cudaSuccess) return set_error(TDQ_ERR_NOMEM, "server: staging");
+    if (host_alloc(&L.h_seg, cap * 8) != cudaSuccess || host_alloc(&L.h_d, cap * 8) != cudaSuccess ||
+        host_alloc(&L.h_t0, cap * 8) != cudaSuccess || host_alloc(&L.h_t1, cap * 8) != cudaSuccess)
         return set_error(TDQ_ERR_NOMEM, "server: staging");
     return TDQ_OK;
 }
@@ -134,8 +134,8 @@ tdq_status lane_results(Lane &L, uint64_t n)
     L.h_rin = L.h_rout = nullptr;
     L.r_cap = 0;
     const uint64_t cap = n + n / 2 + 1024;
-    if (cudaMallocHost(&L.h_rq, cap * 8) != cudaSuccess || cudaMallocHost(&L.h_re, cap * 8) != cudaSuccess ||
-        cudaMallocHost(&L.h_rin, cap * 8) != cudaSuccess || cudaMallocHost(&L.h_rout, cap * 8) != cudaSuccess)
+    if (host_alloc(&L.h_rq, cap * 8) != cudaSuccess || host_alloc(&L.h_re, cap * 8) != cudaSuccess ||
+        host_alloc(&L.h_rin, cap * 8) != cudaSuccess || host_alloc(&L.h_rout, cap * 8) != cudaSuccess)
         return set_error(TDQ_ERR_NOMEM, "server: result staging");
     L.r_cap = cap;
     return TDQ_OK;

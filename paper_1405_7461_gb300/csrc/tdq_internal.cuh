@@ -201,6 +201,31 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
 tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t capacity,
                          bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
 
+// Allocation gate (api.cu).  Every device and pinned-host allocation of the
+// library goes through dev_alloc / host_alloc; tdq_debug_fail_allocations
+// makes a chosen one fail, to test the error paths without touching a GPU.
+cudaError_t alloc_gate();
+template <typename T>
+inline cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    cudaError_t e = alloc_gate();
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    return cudaMalloc((void **)p, bytes);
+}
+template <typename T>
+inline cudaError_t host_alloc(T **p, size_t bytes)
+{
+    cudaError_t e = alloc_gate();
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    return cudaMallocHost((void **)p, bytes);
+}
+
 // Error reporting (api.cu).
 tdq_status set_error(tdq_status st, const char *fmt, ...);
 tdq_status cuda_error(cudaError_t e, const char *what);

@@ -141,6 +141,7 @@ SIGNATURES = {
     "tdq_server_get_stats": (ctypes.c_int, [P, P]),
     "tdq_server_free": (None, [P]),
     "tdq_last_error": (ctypes.c_char_p, []),
+    "tdq_debug_fail_allocations": (None, [ctypes.c_int64]),
     "tdq_version": (ctypes.c_char_p, []),
 }
 
@@ -166,6 +167,12 @@ class TdqError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+def debug_fail_allocations(after: int) -> None:
+    """tdq_debug_fail_allocations: make the allocation `after` allocations
+    from now fail once (after < 0: off)."""
+    load().tdq_debug_fail_allocations(int(after))
 
 
 def last_error() -> str:
