@@ -36,10 +36,33 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def build_mutant(k: int, out_dir: str) -> str:
+    """Compile the oracle with deliberate mistake number k planted (the
+    test-suite checks that its pins catch every one)."""
+    path = os.path.join(out_dir, "liboracle_mutant%d.so" % k)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+                           "-DORACLE_MUTANT=%d" % k, "-o", path, _SRC, "-lm"])
+    return path
+
+
+def use_library(path):
+    """Make the module call the oracle library at `path` (None: the normal
+    build).  Returns the previous library handle."""
+    global _lib
+    prev = _lib
+    _lib = _configure(ctypes.CDLL(path)) if path else None
+    return prev
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        _lib = _configure(ctypes.CDLL(build()))
+    return _lib
+
+
+def _configure(lib):
+    if True:
         P = ctypes.c_void_p
         i64 = ctypes.c_int64
         dbl = ctypes.c_double
@@ -64,8 +87,7 @@ def _load():
         lib.oracle_bin_table.argtypes = [P, P, i64, i64, P, P, P, P, P]
         lib.oracle_batch_interactions.restype = i64
         lib.oracle_batch_interactions.argtypes = [P, P, P, P, i64, P, P, P, i64]
-        _lib = lib
-    return _lib
+    return lib
 
 
 def _ptr(a: np.ndarray) -> int:

@@ -40,7 +40,13 @@
  *
  * Compiled with -O2 -ffp-contract=off so that no multiply-add is fused and the
  * arithmetic is the same on every host.
+ *
+ * ORACLE_MUTANT (undefined in every normal build) plants one deliberate
+ * mistake, so that the test-suite can show that its pins catch it.
  */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -69,6 +75,7 @@ static oseg load_seg(const double *const *a, int64_t i)
 static void position_at(const oseg *s, double t, double p[3])
 {
     double f = (t - s->t0) / (s->t1 - s->t0);
+    if (ORACLE_MUTANT == 3) f = (s->t1 - t) / (s->t1 - s->t0);
     p[0] = s->x0 + (s->x1 - s->x0) * f;
     p[1] = s->y0 + (s->y1 - s->y0) * f;
     p[2] = s->z0 + (s->z1 - s->z0) * f;
@@ -105,7 +112,11 @@ int oracle_pair(const double e8[8], const double q8[8], double d, double wt0, do
     /* temporalIntersection: the common span [a, b]. */
     double a = dmax3(e.t0, q.t0, wt0);
     double b = dmin3(e.t1, q.t1, wt1);
-    if (!(a < b))
+    if (ORACLE_MUTANT == 8) {
+        a = dmax3(e.t0, q.t0, -INFINITY);
+        b = dmin3(e.t1, q.t1, INFINITY);
+    }
+    if (ORACLE_MUTANT == 4 ? !(a <= b) : !(a < b))
         return -1;
 
     /* Both segments clipped to [a, b]: their endpoints at a and at b. */
@@ -124,10 +135,12 @@ int oracle_pair(const double e8[8], const double q8[8], double d, double wt0, do
     for (int k = 0; k < 3; k++) {
         r0[k] = qa[k] - ea[k];
         w[k] = (qb[k] - eb[k]) - r0[k];
+        if (ORACLE_MUTANT == 1) w[k] = 0.0;
     }
     double A = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     double r0w = r0[0] * w[0] + r0[1] * w[1] + r0[2] * w[2];
     double B = 2.0 * r0w;
+    if (ORACLE_MUTANT == 2) B = -B;
     double C = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2] - d * d;
 
     /* Closest approach inside the span: the vertex of f clamped to [0,1]. */
@@ -142,7 +155,7 @@ int oracle_pair(const double e8[8], const double q8[8], double d, double wt0, do
         rc[k] = r0[k] + w[k] * sstar;
     double dm = sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
     if (dmin) *dmin = dm;
-    if (!(dm <= d))
+    if (ORACLE_MUTANT == 5 ? !(dm < d) : !(dm <= d))
         return 0;
 
     /* Non-empty: the roots of f, clipped to [0,1]. */
@@ -158,6 +171,7 @@ int oracle_pair(const double e8[8], const double q8[8], double d, double wt0, do
         double qq = -0.5 * (B + (B >= 0.0 ? sq : -sq));
         double r1 = qq / A;
         double r2 = (qq != 0.0) ? C / qq : r1;
+        if (ORACLE_MUTANT == 6 && C != 0.0) r2 = qq / C;
         double lo = r1 < r2 ? r1 : r2;
         double hi = r1 < r2 ? r2 : r1;
         slo = lo > 0.0 ? lo : 0.0;
@@ -428,6 +442,7 @@ double oracle_bin_table(const double *ts, const double *te, int64_t n, int64_t m
     for (int64_t k = 0; k < n; k++) {
         int64_t i = order[k];
         int64_t j = (int64_t)floor((ts[i] - tmin) / b);
+        if (ORACLE_MUTANT == 7) j = (int64_t)floor(ts[i] / b);
         if (j >= m) j = m - 1;
         if (j < 0) j = 0;
         if (bin_first[j] < 0) {

@@ -321,6 +321,20 @@ def test_fig1_bin_table():
         assert bt["last"][j] == int(blast)
 
 
+def test_fig1_bin_table_time_shifted():
+    """Fig. 1 with every time shifted by 1000: the same bins (the extent now
+    starts at 1000), the same index ranges, extents shifted by 1000."""
+    g = read_golden("fig1_bins.txt")
+    segs = np.array(g["segments"])
+    bt = oracle.bin_table(1000.0 + segs[:, 1], 1000.0 + segs[:, 2], 4)
+    assert bt["width"] == 3.0
+    for j, bstart, bend, bfirst, blast in g["bins"]:
+        j = int(j)
+        assert bt["start"][j] == 1000.0 + bstart
+        assert bt["end"][j] == 1000.0 + bend
+        assert (bt["first"][j], bt["last"][j]) == (int(bfirst), int(blast))
+
+
 def test_fig2_batch_interactions_documented_mismatch():
     """Fig. 2's printed totals cannot all be reproduced under one reading of the
     bin extent: the text defines B_start = j*b, the figure prints the smallest
