@@ -65,7 +65,7 @@ __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *
     }
 }
 
-__global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e)
+__global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e, float *radius)
 {
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -84,9 +84,19 @@ __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, E
     e.seg_id[k] = in.seg_id[i];
     e.traj_id[k] = in.traj_id ? in.traj_id[i] : 0;
     e.orig[k] = (int64_t)i;
-    // FP32 bounding sphere: midpoint and half length of the segment
+    // FP32 bounding sphere: midpoint and half length of the segment.  The
+    // pre-test record keeps the rounded center and E' = |center|^2 scaled by
+    // (1 - 2^-20), rounded down (the squares of floats are exact in FP64);
+    // the radius goes to the per-block maxima.
     double hx = 0.5 * (in.c[4][i] - xs), hy = 0.5 * (in.c[5][i] - ys), hz = 0.5 * (in.c[6][i] - zs);
-    e.sph[k] = sphere32(xs + hx, ys + hy, zs + hz, sqrt(hx * hx + hy * hy + hz * hz), 0.0);
+    const float4 sp = sphere32(xs + hx, ys + hy, zs + hz, sqrt(hx * hx + hy * hy + hz * hz), 0.0);
+    radius[k] = sp.w;
+    if (isinf(sp.w)) {
+        e.sph[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(0xff800000));  // -inf: never rejected
+    } else {
+        const double c2 = (double)sp.x * sp.x + (double)sp.y * sp.y + (double)sp.z * sp.z;
+        e.sph[k] = make_float4(sp.x, sp.y, sp.z, __double2float_rd(c2 * (1.0 - 0x1p-20 - 0x1p-50)));
+    }
 }
 
 // Unsigned radix keys of the sorted entries' t_end (values unused).
@@ -107,7 +117,7 @@ __global__ void te_store(const uint64_t *keys, uint64_t n, int64_t *te_sorted)
 
 // Largest sphere radius of each aligned block of 64 sorted entries (one
 // warp per block).
-__global__ void block_wmax(const float4 *sph, uint64_t n, float *out)
+__global__ void block_wmax(const float *radius, uint64_t n, float *out)
 {
     const uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -115,7 +125,7 @@ __global__ void block_wmax(const float4 *sph, uint64_t n, float *out)
     float w = 0.f;
     for (int k = lane; k < 64; k += 32) {
         const uint64_t i = b * 64 + k;
-        if (i < n) w = fmaxf(w, sph[i].w);
+        if (i < n) w = fmaxf(w, radius[i]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
@@ -289,7 +299,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
 
     // Temporary build memory: staged input (host case), sort buffers, scratch.
     const bool host_in = !entries->on_device;
-    uint64_t tbytes = (host_in ? 10 * carve_bytes(n, 8) : 0) + 2 * carve_bytes(n, 8) + 2 * carve_bytes(n, 4) +
+    uint64_t tbytes = (host_in ? 10 * carve_bytes(n, 8) : 0) + 2 * carve_bytes(n, 8) + 3 * carve_bytes(n, 4) +
                       carve_bytes(sort_hist_words(n), 4) + carve_bytes(4, 8);
     void *tmp = nullptr;
     if (dev_alloc(&tmp, tbytes) != cudaSuccess) {
@@ -339,6 +349,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         uint32_t *vals = carve<uint32_t>(p, n);
         uint32_t *vals_alt = carve<uint32_t>(p, n);
         uint32_t *hist = carve<uint32_t>(p, sort_hist_words(n));
+        float *radius = carve<float>(p, n);
         unsigned long long *small = carve<unsigned long long>(p, 4);  // err, tmin, tmax
 
         unsigned long long init[3] = {0ULL, ~0ULL, 0ULL};
@@ -375,7 +386,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             st = cuda_error(cudaGetLastError(), "tdq_build_index: sort");
             break;
         }
-        entry_gather<<<grid_for(n), kBlock, 0, stream>>>(in, n, vals, idx->e);
+        entry_gather<<<grid_for(n), kBlock, 0, stream>>>(in, n, vals, idx->e, radius);
         bin_init<<<grid_for(m), kBlock, 0, stream>>>(idx->bin_end_key, m);
         bin_assign<<<grid_for(n), kBlock, 0, stream>>>(idx->e.ts_key, idx->e.te_key, n, idx->t_min, idx->width, m,
                                                        idx->bin_begin, idx->bin_end_key);
@@ -387,7 +398,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             break;
         }
         te_store<<<grid_for(n), kBlock, 0, stream>>>(keys, n, idx->e.te_sorted);
-        block_wmax<<<grid_for((n + 63) / 64 * 32), kBlock, 0, stream>>>(idx->e.sph, n, idx->e.blk_wmax);
+        block_wmax<<<grid_for((n + 63) / 64 * 32), kBlock, 0, stream>>>(radius, n, idx->e.blk_wmax);
         if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: index kernels");
             break;
@@ -452,6 +463,7 @@ extern "C" void tdq_index_free(tdq_index *idx)
     cudaFree(w.sort_hist);
     cudaFree(w.r_block);
     cudaFree(w.s_block);
+    workspace_streams_free(w);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < 4; k++)

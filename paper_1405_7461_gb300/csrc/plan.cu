@@ -6,8 +6,10 @@
 // reset, query preparation and sort, candidate ranges, tiles, pair kernels,
 // overlap count, counter read-back -- as one CUDA graph launch.  Graphs are
 // captured once per power-of-two size class of the batch (the slots past the
-// batch's real size are empty padding, told apart by a device-side count),
-// so batches of uneven size reuse a few graphs.  The paper processes a query
+// batch's real size are empty padding), so batches of uneven size reuse a
+// few graphs.  Per batch, the two kernels that read the input are re-pointed
+// at it (device inputs in place, host inputs through staging buffers) and
+// told the batch's real size, without re-capturing.  The paper processes a query
 // in batches of s query segments, one kernel invocation and host round trip
 // per batch (Sec. 6.1); here a batch is one graph launch and the batch size
 // is chosen by measurement (tdq_autotune).
@@ -42,14 +44,14 @@ struct tdq_plan {
     tdq::Workspace ws;
     void *stage_block = nullptr;
     double *d_arr = nullptr, *t0_arr = nullptr, *t1_arr = nullptr;
-    unsigned long long *n_dev = nullptr;
-    unsigned long long *n_host = nullptr;  // pinned
     void *r_block = nullptr;
     tdq_result_buffer res{};
     cudaStream_t cap_stream = nullptr;
     struct Graph {
         uint64_t cls;
+        cudaGraph_t graph;
         cudaGraphExec_t exec;
+        tdq::GraphInputNodes nodes;
     } graphs[kMaxGraphs];
     int ngraphs = 0;
     uint64_t last_count = 0;
@@ -62,7 +64,10 @@ using namespace tdq;
 
 void drop_graphs(tdq_plan *p)
 {
-    for (int k = 0; k < p->ngraphs; k++) cudaGraphExecDestroy(p->graphs[k].exec);
+    for (int k = 0; k < p->ngraphs; k++) {
+        cudaGraphExecDestroy(p->graphs[k].exec);
+        cudaGraphDestroy(p->graphs[k].graph);
+    }
     p->ngraphs = 0;
 }
 
@@ -94,10 +99,10 @@ tdq_status plan_survivors(tdq_plan *p, uint64_t cap)
     return ensure_survivors(p->ws, cap);
 }
 
-cudaGraphExec_t find_graph(tdq_plan *p, uint64_t cls)
+tdq_plan::Graph *find_graph(tdq_plan *p, uint64_t cls)
 {
     for (int k = 0; k < p->ngraphs; k++)
-        if (p->graphs[k].cls == cls) return p->graphs[k].exec;
+        if (p->graphs[k].cls == cls) return &p->graphs[k];
     return nullptr;
 }
 
@@ -109,11 +114,10 @@ QueryInput staged_input(const tdq_plan *p)
     in.d_arr = p->d_arr;
     in.t0_arr = p->t0_arr;
     in.t1_arr = p->t1_arr;
-    in.n_dev = p->n_dev;
     return in;
 }
 
-tdq_status capture(tdq_plan *p, uint64_t cls, cudaGraphExec_t *out)
+tdq_status capture(tdq_plan *p, uint64_t cls, tdq_plan::Graph **out)
 {
     if (p->ngraphs == kMaxGraphs) drop_graphs(p);
     const QueryInput in = staged_input(p);
@@ -126,14 +130,16 @@ tdq_status capture(tdq_plan *p, uint64_t cls, cudaGraphExec_t *out)
         if (g) cudaGraphDestroy(g);
         return cuda_error(e != cudaSuccess ? e : e2, "tdq_plan: graph capture");
     }
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_error(e, "tdq_plan: graph instantiation");
-    p->graphs[p->ngraphs].cls = cls;
-    p->graphs[p->ngraphs].exec = exec;
+    tdq_plan::Graph G{cls, g, nullptr, GraphInputNodes{}};
+    e = find_input_nodes(g, &G.nodes);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_error(e, "tdq_plan: graph instantiation");
+    }
+    p->graphs[p->ngraphs] = G;
+    *out = &p->graphs[p->ngraphs];
     p->ngraphs++;
-    *out = exec;
     return TDQ_OK;
 }
 
@@ -149,8 +155,8 @@ void plan_release(tdq_plan *p)
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < 4; k++)
         if (w.ev[k]) cudaEventDestroy(w.ev[k]);
+    workspace_streams_free(w);
     cudaFree(p->stage_block);
-    if (p->n_host) cudaFreeHost(p->n_host);
     cudaFree(p->r_block);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
 }
@@ -181,8 +187,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
         Workspace &w = p->ws;
         bool ok = dev_alloc(&w.ctr, sizeof(DevCounters)) == cudaSuccess &&
                   host_alloc(&w.ctr_host, sizeof(DevCounters)) == cudaSuccess &&
-                  host_alloc(&p->n_host, sizeof(unsigned long long)) == cudaSuccess &&
-                  dev_alloc(&p->stage_block, (3 * p->cap_q + 1) * 8) == cudaSuccess;
+                  dev_alloc(&p->stage_block, 3 * p->cap_q * 8) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             st = set_error(TDQ_ERR_NOMEM, "tdq_plan_create: allocation failed");
@@ -198,7 +203,8 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
         p->d_arr = (double *)p->stage_block;
         p->t0_arr = p->d_arr + p->cap_q;
         p->t1_arr = p->t0_arr + p->cap_q;
-        p->n_dev = (unsigned long long *)(p->t1_arr + p->cap_q);
+        st = workspace_streams(w);
+        if (st != TDQ_OK) break;
         st = ensure_queries(w, p->cap_q);
         if (st != TDQ_OK) break;
         const uint64_t rc = params->result_capacity ? params->result_capacity : (idx->n > 65536 ? idx->n : 65536);
@@ -246,25 +252,39 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
     if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_plan_search: query seg_id is NULL");
     cudaStream_t stream = (cudaStream_t)stream_;
     Workspace &w = p->ws;
-    const cudaMemcpyKind kind = queries->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    for (int c = 0; c < 8; c++) TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, kind, stream));
-    TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, kind, stream));
-    TDQ_CUDA(cudaMemcpyAsync(p->d_arr, d_per_query, nq * 8, kind, stream));
-    TDQ_CUDA(cudaMemcpyAsync(p->t0_arr, t0_per_query, nq * 8, kind, stream));
-    TDQ_CUDA(cudaMemcpyAsync(p->t1_arr, t1_per_query, nq * 8, kind, stream));
-    *p->n_host = nq;
-    TDQ_CUDA(cudaMemcpyAsync(p->n_dev, p->n_host, sizeof(unsigned long long), cudaMemcpyHostToDevice, stream));
+    // the batch's input: the caller's device arrays in place, or host arrays
+    // staged into the plan's buffers
+    QueryInput in{};
+    if (queries->on_device) {
+        for (int c = 0; c < 8; c++) in.c[c] = cols[c];
+        in.seg_id = queries->seg_id;
+        in.d_arr = d_per_query;
+        in.t0_arr = t0_per_query;
+        in.t1_arr = t1_per_query;
+    } else {
+        for (int c = 0; c < 8; c++)
+            TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, cudaMemcpyHostToDevice, stream));
+        TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, cudaMemcpyHostToDevice, stream));
+        TDQ_CUDA(cudaMemcpyAsync(p->d_arr, d_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
+        TDQ_CUDA(cudaMemcpyAsync(p->t0_arr, t0_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
+        TDQ_CUDA(cudaMemcpyAsync(p->t1_arr, t1_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
+        in = staged_input(p);
+    }
     const uint64_t cls = size_class(nq);
+    in.n_real = nq;
     for (int attempt = 0;; attempt++) {
         if (p->use_graph) {
-            cudaGraphExec_t exec = find_graph(p, cls);
-            if (!exec) {
-                tdq_status st = capture(p, cls, &exec);
+            tdq_plan::Graph *G = find_graph(p, cls);
+            if (!G) {
+                tdq_status st = capture(p, cls, &G);
                 if (st != TDQ_OK) return st;
             }
-            TDQ_CUDA(cudaGraphLaunch(exec, stream));
+            TDQ_CUDA(bind_inputs(G->exec, G->nodes, p->idx, w, in, cls));
+            TDQ_CUDA(cudaGraphLaunch(G->exec, stream));
         } else {
-            TDQ_CUDA(enqueue_search(p->idx, w, staged_input(p), cls, p->cfg, p->res, stream, true));
+            QueryInput direct = in;
+            direct.n_real = 0;
+            TDQ_CUDA(enqueue_search(p->idx, w, direct, nq, p->cfg, p->res, stream, true));
         }
         TDQ_CUDA(cudaStreamSynchronize(stream));
         bool grow_surv = false;

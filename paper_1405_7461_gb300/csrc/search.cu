@@ -72,7 +72,7 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
     // slots at or beyond the device-side count are padding: empty, not errors
-    const uint64_t nreal = in.n_dev ? (uint64_t)*in.n_dev : nq;
+    const uint64_t nreal = in.n_real ? in.n_real : nq;
     if (i < nq && i >= nreal) {
         pre[7][i] = __longlong_as_double(INT64_MAX);
         pre[8][i] = __longlong_as_double(INT64_MIN);
@@ -99,8 +99,9 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
         if (!ok) atomicOr(&ctr->error, 1u);
         int64_t cs = max(ks, k0), ce = min(ke, k1);
         valid = ok && cs < ce;
-        double dt = c[7] - c[3];
-        double vx = (c[4] - c[0]) / dt, vy = (c[5] - c[1]) / dt, vz = (c[6] - c[2]) / dt;
+        // one FP64 division per segment (the FP64 pipe is narrow)
+        const double inv = 1.0 / (c[7] - c[3]);
+        double vx = (c[4] - c[0]) * inv, vy = (c[5] - c[1]) * inv, vz = (c[6] - c[2]) * inv;
         double px = c[0], py = c[1], pz = c[2];
         if (valid && cs != ks) {  // the window cuts the start: position at the clipped start
             double shift = key_double(cs) - c[3];
@@ -360,29 +361,34 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // kernel, but each is processed by one warp: the warps of the grid split the
 // items into contiguous ranges; a warp walks the tile table forward, keeps
 // the tile's 32 query spheres in its own slice of shared memory (reloaded
-// only when the tile changes), and reads its entry spheres straight into
-// registers, two per lane per pass over the queries, the next pair loaded
-// while the current one is tested.  No CTA-wide barrier is involved.
+// only when the tile changes), and reads its entry records straight into
+// registers, four per lane per pass over the queries, the next pass's
+// loaded while the current one is tested.  No CTA-wide barrier is involved.
 //
-// A pass covers 64 consecutive entries.  For the pass, lane j computes the
-// bound R_j^2 = (w_max + w_j)^2 (rounded up) where w_max is the largest
-// radius of the aligned 64-entry blocks the pass touches; then per candidate
-// pair the test is 6 FP32 operations and one funnel shift that moves the
+// A pass covers 128 consecutive entries (four per lane).  For the pass, lane
+// j computes R_j = w_max + w_j (rounded up), w_max the largest radius of the
+// aligned 64-entry blocks the pass touches, and
+//   K'_j = |c_j|^2 (1 - g) - R_j^2   (rounded down, g = 2^-20);
+// each entry carries E'_e = |c_e|^2 (1 - g) rounded down.  Per candidate
+// pair the test is one add, three FMAs and one funnel shift that moves the
 // sign of
-//   v = |c_e - c_q|^2 - R_j^2
+//   v = E'_e + K'_j - 2 c_j . c_e  =  |c_e - c_j|^2 - R_j^2 - g (|c_e|^2 + |c_j|^2)
 // into the lane's 32-bit mask.  v is negative whenever the exact spheres
-// meet: with u = 2^-24, the center differences and the three fused steps
-// add at most ~5u (|c_e - c_q|^2 + R^2) of rounding, while the radii carry a
-// factor (1 + 2^-20) >= (1 + 16u) (so R^2 exceeds the exact bound by at
-// least 32u of itself); R >= 2^-60 keeps every quantity normal.  The
-// survivors (entry, query) are appended to a list with one atomic per warp;
-// traj_dist_refine_kernel then evaluates them in FP64.
+// meet: with u = 2^-24 the four roundings of v add at most
+// u (7 (|c_e|^2 + |c_j|^2) + 4 R^2), less than the g (|c_e|^2 + |c_j|^2) = 16u (...)
+// subtracted and the 32u R^2 by which R_j^2 exceeds the exact bound (the
+// radii carry a factor 1 + 2^-20); R >= 2^-60 keeps every quantity normal.
+// Segments beyond 2^60 in magnitude carry E' = -inf or K' = -inf and are
+// never rejected.  The survivors (entry, query) are appended to a list with
+// one atomic per warp; traj_dist_refine_kernel then evaluates them in FP64.
 constexpr int kFilterWarps = kPairThreads / 32;
+constexpr int kPer = 4;            // entries per lane per pass
+constexpr int kPass = 32 * kPer;   // entries per pass
 
+// v = E'_e + K'_j - 2 c_q . c_e with q = (-2 c_q, K'_j): one add, three FMAs.
 __device__ __forceinline__ float sphere_gap2(float4 e, float4 q)
 {
-    const float dx = e.x - q.x, dy = e.y - q.y, dz = e.z - q.z;
-    return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -q.w)));
+    return fmaf(q.z, e.z, fmaf(q.y, e.y, fmaf(q.x, e.x, e.w + q.w)));
 }
 
 struct FilterArgs {
@@ -444,38 +450,57 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
             const int ne = (int)(min(e0 + (int64_t)EC, t_hi) - e0);
             const unsigned qvalid = 0xffffffffu << (kQT - nqt);  // bit 31-j <-> query j
             if (lane == 0) n_inter += (unsigned long long)ne * (unsigned long long)nqt;
-            // entry pairs (el, el + 32), el = 64 p + lane; prefetched one pass ahead
-            const int npass = (ne + 63) / 64;
-            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
-            if (lane < ne) na = args.e.sph[e0 + lane];
-            if (lane + 32 < ne) nb = args.e.sph[e0 + lane + 32];
+            // entries el + 32 k (k < kPer), el = kPass p + lane; the next
+            // pass's entries are loaded while this pass is tested
+            const int npass = (ne + kPass - 1) / kPass;
+            float4 nx[kPer];
+#pragma unroll
+            for (int k = 0; k < kPer; k++)
+                nx[k] = lane + 32 * k < ne ? args.e.sph[e0 + lane + 32 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int p = 0; p < npass; p++) {
-                const float4 ea = na, eb = nb;
-                const int ela = 64 * p + lane, elb = ela + 32;
-                const int64_t pe = e0 + 64 * p;  // first entry of the pass
+                float4 ex[kPer];
+#pragma unroll
+                for (int k = 0; k < kPer; k++) ex[k] = nx[k];
+                const int el0 = kPass * p + lane;
+                const int64_t pe = e0 + kPass * p;  // first entry of the pass
                 if (p + 1 < npass) {
-                    if (ela + 64 < ne) na = args.e.sph[e0 + ela + 64];
-                    if (elb + 64 < ne) nb = args.e.sph[e0 + elb + 64];
+#pragma unroll
+                    for (int k = 0; k < kPer; k++)
+                        if (el0 + kPass + 32 * k < ne) nx[k] = args.e.sph[e0 + el0 + kPass + 32 * k];
                 }
-                // per-pass bound of query j = lane
-                const int64_t plast = pe + min(63, ne - 1 - 64 * p);
-                const float wmax = fmaxf(args.e.blk_wmax[pe >> 6], args.e.blk_wmax[plast >> 6]);
+                // per-pass bound of query j = lane: the largest entry radius of
+                // the aligned 64-entry blocks the pass touches
+                const int64_t plast = pe + min(kPass - 1, ne - 1 - kPass * p);
+                float wmax = 0.f;
+                for (int64_t blk = pe >> 6; blk <= (plast >> 6); blk++) wmax = fmaxf(wmax, args.e.blk_wmax[blk]);
                 const float Rj = __fadd_ru(wmax, my_q.w);
+                const float cq2 = __fmaf_rd(my_q.z, my_q.z, __fmaf_rd(my_q.y, my_q.y, __fmul_rd(my_q.x, my_q.x)));
+                const float Kj = __fsub_rd(__fmul_rd(cq2, 1.0f - 0x1p-20f), __fmul_ru(Rj, Rj));
                 __syncwarp();
-                qr[lane] = make_float4(my_q.x, my_q.y, my_q.z, __fmul_ru(Rj, Rj));
+                qr[lane] = isinf(my_q.w) ? make_float4(0.f, 0.f, 0.f, -INFINITY)  // never rejected
+                                         : make_float4(-2.0f * my_q.x, -2.0f * my_q.y, -2.0f * my_q.z, Kj);
                 __syncwarp();
-                unsigned ma = 0, mb = 0;
+                unsigned m[kPer];
+#pragma unroll
+                for (int k = 0; k < kPer; k++) m[k] = 0u;
 #pragma unroll
                 for (int j = 0; j < kQT; j++) {
                     const float4 q = qr[j];
-                    ma = __funnelshift_l(__float_as_uint(sphere_gap2(ea, q)), ma, 1);
-                    mb = __funnelshift_l(__float_as_uint(sphere_gap2(eb, q)), mb, 1);
+#pragma unroll
+                    for (int k = 0; k < kPer; k++)
+                        m[k] = __funnelshift_l(__float_as_uint(sphere_gap2(ex[k], q)), m[k], 1);
                 }
-                ma = ela < ne ? (ma & qvalid) : 0u;
-                mb = elb < ne ? (mb & qvalid) : 0u;
-                if (!__any_sync(kFull, (ma | mb) != 0u)) continue;
+                unsigned any = 0u;
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    m[k] = el0 + 32 * k < ne ? (m[k] & qvalid) : 0u;
+                    any |= m[k];
+                }
+                if (!__any_sync(kFull, any != 0u)) continue;
                 // append this lane's survivors: one atomic per warp
-                const int cnt = __popc(ma) + __popc(mb);
+                int cnt = 0;
+#pragma unroll
+                for (int k = 0; k < kPer; k++) cnt += __popc(m[k]);
                 int incl = cnt;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -487,12 +512,13 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                 if (lane == 31) sbase = atomicAdd(&ctr->survivors, (unsigned long long)wtot);
                 sbase = __shfl_sync(kFull, sbase, 31);
                 unsigned long long pos = sbase + (incl - cnt);
-                for (int h = 0; h < 2; h++) {
-                    unsigned m = h ? mb : ma;
-                    const uint32_t ek = (uint32_t)(e0 + (h ? elb : ela));
-                    while (m) {
-                        const int bit = 31 - __clz(m);
-                        m &= ~(1u << bit);
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    unsigned mk = m[k];
+                    const uint32_t ek = (uint32_t)(e0 + el0 + 32 * k);
+                    while (mk) {
+                        const int bit = 31 - __clz(mk);
+                        mk &= ~(1u << bit);
                         if (pos < fa.surv_cap) fa.surv[pos] = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
                         pos++;
                     }
@@ -889,11 +915,19 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                                                  w.tile_work);
         if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk};
+        if (cfg.filter) {
+            // fork: the overlap count needs only the sorted queries, so it
+            // runs beside the pair kernels on the side stream
+            if ((e = cudaEventRecord(w.fork, stream)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(w.side, w.fork, 0)) != cudaSuccess) return e;
+            if ((e = launch_overlap_count(pa, nq, idx->n, w.side)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(w.join, w.side)) != cudaSuccess) return e;
+        }
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream)) != cudaSuccess)
             return e;
         if (events && (e = cudaEventRecordWithFlags(w.ev[2], stream, evflags)) != cudaSuccess) return e;
-        if (cfg.filter && (e = launch_overlap_count(pa, nq, idx->n, stream)) != cudaSuccess) return e;
+        if (cfg.filter && (e = cudaStreamWaitEvent(stream, w.join, 0)) != cudaSuccess) return e;
     } else if (events) {
         if ((e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if ((e = cudaEventRecordWithFlags(w.ev[2], stream, evflags)) != cudaSuccess) return e;
@@ -932,6 +966,93 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
     }
     *count = h.results;
     return h.results > capacity ? TDQ_ERR_OVERFLOW : TDQ_OK;
+}
+
+tdq_status workspace_streams(Workspace &w)
+{
+    if (w.side) return TDQ_OK;
+    if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming) != cudaSuccess) {
+        workspace_streams_free(w);
+        return cuda_error(cudaGetLastError(), "search workspace: streams");
+    }
+    return TDQ_OK;
+}
+
+void workspace_streams_free(Workspace &w)
+{
+    if (w.side) cudaStreamDestroy(w.side);
+    if (w.fork) cudaEventDestroy(w.fork);
+    if (w.join) cudaEventDestroy(w.join);
+    w.side = nullptr;
+    w.fork = w.join = nullptr;
+}
+
+cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
+{
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t *nodes = (cudaGraphNode_t *)malloc((n ? n : 1) * sizeof(cudaGraphNode_t));
+    if (!nodes) return cudaErrorMemoryAllocation;
+    e = cudaGraphGetNodes(g, nodes, &n);
+    *out = GraphInputNodes{};
+    for (size_t k = 0; k < n && e == cudaSuccess; k++) {
+        cudaGraphNodeType t;
+        if ((e = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if ((e = cudaGraphKernelNodeGetParams(nodes[k], &kp)) != cudaSuccess) break;
+        if (kp.func == (void *)query_prep) out->prep = nodes[k];
+        if (kp.func == (void *)query_gather) out->gather = nodes[k];
+    }
+    free(nodes);
+    if (e == cudaSuccess && (!out->prep || !out->gather)) e = cudaErrorInvalidValue;
+    return e;
+}
+
+cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
+                        const QueryInput &in, uint64_t nq)
+{
+    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    double *const *pre = w.pre_dev;
+    {
+        QueryInput a0 = in;
+        uint64_t a1 = nq;
+        BinView a2 = bins;
+        double *const *a3 = pre;
+        float4 *a4 = w.pre_sph;
+        uint64_t *a5 = w.keys;
+        uint32_t *a6 = w.vals;
+        DevCounters *a7 = w.ctr;
+        void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)query_prep;
+        kp.gridDim = dim3(grid_for(nq));
+        kp.blockDim = dim3(kBlock);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaError_t e = cudaGraphExecKernelNodeSetParams(exec, nodes.prep, &kp);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        double *const *a0 = pre;
+        const float4 *a1 = w.pre_sph;
+        const int64_t *a2 = in.seg_id;
+        const uint32_t *a3 = w.vals;
+        uint64_t a4 = nq;
+        const DevCounters *a5 = w.ctr;
+        BinView a6 = bins;
+        QuerySoA a7 = w.q;
+        void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)query_gather;
+        kp.gridDim = dim3(grid_for(nq));
+        kp.blockDim = dim3(kBlock);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        return cudaGraphExecKernelNodeSetParams(exec, nodes.gather, &kp);
+    }
 }
 
 namespace {
@@ -980,7 +1101,9 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     in.d_arr = spec.d_arr;
     in.t0_arr = spec.t0_arr;
     in.t1_arr = spec.t1_arr;
-    in.n_dev = nullptr;
+    in.n_real = 0;
+    st = workspace_streams(w);
+    if (st != TDQ_OK) return st;
 
     if (cfg.filter && idx->n > 0) {
         st = ensure_survivors(w, w.s_cap_pairs ? w.s_cap_pairs : (nq * 64 > (1u << 20) ? nq * 64 : (1u << 20)));
@@ -1151,7 +1274,7 @@ namespace {
 
 constexpr uint64_t kNoAllocMaxQueries = 8192;
 constexpr uint64_t kNoAllocTiles = kNoAllocMaxQueries / kQT;
-constexpr uint64_t kNoAllocHistWords = (kNoAllocMaxQueries + 4095) / 4096 * 256 + 1;
+constexpr uint64_t kNoAllocHistWords = (kNoAllocMaxQueries + 1023) / 1024 * 256 + 1;  // 1024-key sort tiles
 constexpr uint64_t na_bytes(uint64_t count, uint64_t size) { return (count * size + 255) & ~(uint64_t)255; }
 constexpr uint64_t kNoAllocScratchBytes =
     9 * na_bytes(kNoAllocMaxQueries, 8)                                      // pre columns
@@ -1219,7 +1342,7 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         s.hist = carve<uint32_t>(p, kNoAllocHistWords);
         s.ctr = carve<DevCounters>(p, 1);
         s.pre_dev = carve<double *>(p, 9);
-        if ((uint64_t)(p - (char *)base) > kNoAllocScratchBytes)
+        if ((uint64_t)(p - (char *)base) > kNoAllocScratchBytes || sort_hist_words(kNoAllocMaxQueries) > kNoAllocHistWords)
             return set_error(TDQ_ERR_CUDA, "tdq_search_device_noalloc: scratch layout exceeds the array");
         e = cudaMemcpy(s.pre_dev, s.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_error(e, "tdq_search_device_noalloc: pointer table");

@@ -13,14 +13,18 @@ namespace tdq {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;  // 4096 keys per tile
 constexpr int kRadix = 256;
 constexpr int kWarps = kThreads / 32;
+// Keys per thread of a tile: 16 for large inputs (4096-key tiles); 4 for
+// inputs up to 2^20 keys, so that small sorts still spread over the SMs.
+constexpr uint64_t kSmallSort = 1u << 20;
+inline int items_for(uint64_t n) { return n <= kSmallSort ? 4 : 16; }
 
+template <int kItems>
 __global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restrict__ keys, uint64_t n, int shift,
                                                        uint32_t *__restrict__ hist, uint32_t ntiles)
 {
+    constexpr int kTile = kThreads * kItems;
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -34,12 +38,14 @@ __global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restric
     hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+template <int kItems>
 __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__restrict__ keys,
                                                           const uint32_t *__restrict__ vals, uint64_t n, int shift,
                                                           const uint32_t *__restrict__ offsets, uint32_t ntiles,
                                                           uint64_t *__restrict__ keys_out,
                                                           uint32_t *__restrict__ vals_out)
 {
+    constexpr int kTile = kThreads * kItems;
     __shared__ uint32_t off[kRadix];
     __shared__ uint32_t run[kRadix];
     __shared__ uint32_t wcnt[kWarps][kRadix];
@@ -134,10 +140,14 @@ __global__ void __launch_bounds__(1024) scan_exclusive_block(T *data, uint64_t n
 
 }  // namespace
 
+// Histogram words for sorting any count up to n (small counts use smaller
+// tiles, hence more of them).
 uint64_t sort_hist_words(uint64_t n)
 {
-    uint64_t ntiles = (n + kTile - 1) / kTile;
-    return ntiles * kRadix + 1;
+    const uint64_t small = n < kSmallSort ? n : kSmallSort;
+    const uint64_t t4 = (small + kThreads * 4 - 1) / (kThreads * 4);
+    const uint64_t t16 = (n + kThreads * 16 - 1) / (kThreads * 16);
+    return (t4 > t16 ? t4 : t16) * kRadix + 1;
 }
 
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
@@ -145,14 +155,22 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
 {
     if (n <= 1) return cudaSuccess;
     if (n > 0xffffffffULL) return cudaErrorInvalidValue;  // 32-bit offsets
-    uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
+    const int items = items_for(n);
+    const uint64_t tile = (uint64_t)kThreads * items;
+    uint32_t ntiles = (uint32_t)((n + tile - 1) / tile);
     uint64_t *src_k = keys, *dst_k = keys_alt;
     uint32_t *src_v = vals, *dst_v = vals_alt;
     const int passes = sort_passes(key_bits < 64 ? key_bits : 64);
     for (int shift = 0; shift < 8 * passes; shift += 8) {
-        radix_hist<<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+        if (items == 4)
+            radix_hist<4><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+        else
+            radix_hist<16><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
         scan_exclusive_block<uint32_t><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
-        radix_scatter<<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
+        if (items == 4)
+            radix_scatter<4><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
+        else
+            radix_scatter<16><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
         uint64_t *tk = src_k; src_k = dst_k; dst_k = tk;
         uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
     }

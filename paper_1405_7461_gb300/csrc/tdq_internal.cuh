@@ -101,9 +101,10 @@ struct EntrySoA {
     double *vx, *vy, *vz;  // velocity (end - start) / (t_end - t_start)
     int64_t *ts_key, *te_key;
     int64_t *seg_id, *traj_id, *orig;
-    float4 *sph;           // FP32 bounding sphere of the segment (center, radius rounded up)
+    float4 *sph;           // FP32 pre-test record: center (rounded to nearest) and E' = |center|^2 (1 - 2^-20)
+                           // rounded down (see entry_prepass); (0, 0, 0, -inf) for huge magnitudes
     int64_t *te_sorted;    // t_end keys in ascending order (for exact overlap counts)
-    float *blk_wmax;       // largest sphere radius of each aligned block of 64 sorted entries
+    float *blk_wmax;       // largest bounding-sphere radius of each aligned block of 64 sorted entries
 };
 
 // Sorted, clipped query segments in device memory.
@@ -145,6 +146,10 @@ struct Workspace {
     uint64_t r_cap = 0;
     void *r_block = nullptr;
     tdq_result_buffer r{};
+    // second stream and events for the overlap count, forked off the main
+    // stream and joined before the counters are read
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // filter mode: survivors of the FP32 pre-test (entry, query) positions
     uint64_t s_cap_pairs = 0;
     void *s_block = nullptr;
@@ -173,15 +178,15 @@ struct tdq_index {
 namespace tdq {
 
 // Query input of one search: device columns and either one threshold and
-// window or one per query segment.  n_dev (optional): device-side number of
-// real query segments; slots at or beyond it are empty padding (used by
-// captured searches whose launch shapes are fixed).
+// window or one per query segment.  n_real: number of real query segments
+// when the launch covers more slots (captured searches have fixed launch
+// shapes); slots at or beyond it are empty padding.  0: all slots are real.
 struct QueryInput {
     const double *c[8];  // xs ys zs ts xe ye ze te
     const int64_t *seg_id;
     double d, t0, t1;
     const double *d_arr, *t0_arr, *t1_arr;
-    const unsigned long long *n_dev;
+    uint64_t n_real;
 };
 
 struct LaunchCfg {
@@ -200,6 +205,17 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                            const tdq_result_buffer &out, cudaStream_t stream, bool events);
 tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t capacity,
                          bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
+// Side stream and fork/join events of a workspace (created once).
+tdq_status workspace_streams(Workspace &w);
+void workspace_streams_free(Workspace &w);
+// The two kernels of a captured search that read the caller's input (query
+// preparation and gather); re-pointed per batch without re-capturing.
+struct GraphInputNodes {
+    cudaGraphNode_t prep = nullptr, gather = nullptr;
+};
+cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out);
+cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
+                        const QueryInput &in, uint64_t nq);
 
 // Allocation gate (api.cu).  Every device and pinned-host allocation of the
 // library goes through dev_alloc / host_alloc; tdq_debug_fail_allocations
