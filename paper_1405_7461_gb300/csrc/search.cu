@@ -379,8 +379,9 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // subtracted and the 32u R^2 by which R_j^2 exceeds the exact bound (the
 // radii carry a factor 1 + 2^-20); R >= 2^-60 keeps every quantity normal.
 // Segments beyond 2^60 in magnitude carry E' = -inf or K' = -inf and are
-// never rejected.  The survivors (entry, query) are appended to a list with
-// one atomic per warp; traj_dist_refine_kernel then evaluates them in FP64.
+// never rejected.  The survivors (entry, query) are appended to a list (one
+// atomic per lane that has any); traj_dist_refine_kernel then evaluates
+// them in FP64.
 constexpr int kFilterWarps = kPairThreads / 32;
 constexpr int kPer = 4;            // entries per lane per pass
 constexpr int kPass = 32 * kPer;   // entries per pass
@@ -496,22 +497,13 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                     m[k] = el0 + 32 * k < ne ? (m[k] & qvalid) : 0u;
                     any |= m[k];
                 }
-                if (!__any_sync(kFull, any != 0u)) continue;
-                // append this lane's survivors: one atomic per warp
+                if (any == 0u) continue;
+                // append this lane's survivors (few lanes ever have any: one
+                // atomic per such lane, no warp-wide step)
                 int cnt = 0;
 #pragma unroll
                 for (int k = 0; k < kPer; k++) cnt += __popc(m[k]);
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int wtot = __shfl_sync(kFull, incl, 31);
-                unsigned long long sbase = 0;
-                if (lane == 31) sbase = atomicAdd(&ctr->survivors, (unsigned long long)wtot);
-                sbase = __shfl_sync(kFull, sbase, 31);
-                unsigned long long pos = sbase + (incl - cnt);
+                unsigned long long pos = atomicAdd(&ctr->survivors, (unsigned long long)cnt);
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
                     unsigned mk = m[k];

@@ -86,27 +86,37 @@ __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__rest
     }
 }
 
-// Exclusive scan of 32-bit counts (digit-major histogram) in one block.
-template <typename T>
+// Exclusive scan of n counters in one block of 1024 threads.  Each
+// iteration stages 1024 * kPer counters in shared memory with coalesced
+// loads (one padding word per 32 against bank conflicts), scans kPer
+// consecutive counters per thread, scans the thread sums across the block,
+// writes the prefixes back and stores them coalesced; a carry links the
+// iterations.
+template <typename T, int kPer>
 __global__ void __launch_bounds__(1024) scan_exclusive_block(T *data, uint64_t n, T *total)
 {
+    constexpr int kChunk = 1024 * kPer;
+    __shared__ T buf[kChunk + kChunk / 32];
     __shared__ T warp_sums[32];
     __shared__ T carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto pad = [](int i) { return i + (i >> 5); };
     if (tid == 0) carry = 0;
-    __syncthreads();
-    constexpr int kPer = 4;
-    for (uint64_t start = 0; start < n; start += 1024 * kPer) {
+    for (uint64_t start = 0; start < n; start += kChunk) {
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const int i = j * 1024 + tid;
+            buf[pad(i)] = start + i < n ? data[start + i] : (T)0;
+        }
+        __syncthreads();
         T v[kPer];
         T s = 0;
 #pragma unroll
         for (int j = 0; j < kPer; j++) {
-            uint64_t idx = start + (uint64_t)tid * kPer + j;
-            v[j] = idx < n ? data[idx] : 0;
+            v[j] = buf[pad(tid * kPer + j)];
             s += v[j];
         }
-        // inclusive warp scan of per-thread sums
-        T x = s;
+        T x = s;  // inclusive scan of the thread sums
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             T y = __shfl_up_sync(0xffffffffu, x, o);
@@ -127,11 +137,15 @@ __global__ void __launch_bounds__(1024) scan_exclusive_block(T *data, uint64_t n
         T before = carry + (warp > 0 ? warp_sums[warp - 1] : 0) + (x - s);
 #pragma unroll
         for (int j = 0; j < kPer; j++) {
-            uint64_t idx = start + (uint64_t)tid * kPer + j;
-            if (idx < n) data[idx] = before;
+            buf[pad(tid * kPer + j)] = before;
             before += v[j];
         }
         __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const int i = j * 1024 + tid;
+            if (start + i < n) data[start + i] = buf[pad(i)];
+        }
         if (tid == 0) carry += warp_sums[31];
         __syncthreads();
     }
@@ -166,7 +180,7 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
             radix_hist<4><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
         else
             radix_hist<16><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
-        scan_exclusive_block<uint32_t><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
+        scan_exclusive_block<uint32_t, 8><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
         if (items == 4)
             radix_scatter<4><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
         else
@@ -181,7 +195,7 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
 cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,
                                cudaStream_t stream)
 {
-    scan_exclusive_block<unsigned long long><<<1, 1024, 0, stream>>>(data, n, total);
+    scan_exclusive_block<unsigned long long, 4><<<1, 1024, 0, stream>>>(data, n, total);
     return cudaGetLastError();
 }
 
