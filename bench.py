@@ -48,9 +48,10 @@ from paper_1405_7461_gb300 import workloads  # noqa: E402
 # C 6, discriminant 3.
 FLOPS_PER_PAIR_FP64 = 32
 # Algorithmic FP32 flops per candidate pair in the filter kernel's sphere
-# pre-test: center difference 3, squared distance minus the per-pass bound
-# R_j^2 6 (3 FMA); R_j^2 is computed once per (64-entry pass, query).
-FLOPS_PER_CANDIDATE_FP32 = 9
+# pre-test, written as v = E'_e + K'_j - 2 c_j . c_e: one add and three FMAs
+# (7 flops); K'_j (with the per-pass bound R_j^2) is formed once per
+# (64-entry pass, query), E'_e once per entry when the index is built.
+FLOPS_PER_CANDIDATE_FP32 = 7
 # Peaks from unit counts and clocks (152 SMs, 2070 MHz): FP64 2 DFMA/clk/SM
 # (the 1.25 TFLOP/s nominal figure), FP32 128 FFMA/clk/SM.
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070

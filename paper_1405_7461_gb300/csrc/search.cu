@@ -362,15 +362,16 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // items into contiguous ranges; a warp walks the tile table forward, keeps
 // the tile's 32 query spheres in its own slice of shared memory (reloaded
 // only when the tile changes), and reads its entry records straight into
-// registers, four per lane per pass over the queries, the next pass's
+// registers, two per lane per pass over the queries, the next pass's
 // loaded while the current one is tested.  No CTA-wide barrier is involved.
 //
-// A pass covers 128 consecutive entries (four per lane).  For the pass, lane
+// A pass covers 64 consecutive entries (two per lane).  For the pass, lane
 // j computes R_j = w_max + w_j (rounded up), w_max the largest radius of the
 // aligned 64-entry blocks the pass touches, and
 //   K'_j = |c_j|^2 (1 - g) - R_j^2   (rounded down, g = 2^-20);
 // each entry carries E'_e = |c_e|^2 (1 - g) rounded down.  Per candidate
-// pair the test is one add, three FMAs and one funnel shift that moves the
+// pair the test is one add, three FMAs (issued as paired FP32 instructions
+// that evaluate two queries at once) and one funnel shift that moves the
 // sign of
 //   v = E'_e + K'_j - 2 c_j . c_e  =  |c_e - c_j|^2 - R_j^2 - g (|c_e|^2 + |c_j|^2)
 // into the lane's 32-bit mask.  v is negative whenever the exact spheres
@@ -383,13 +384,28 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // atomic per lane that has any); traj_dist_refine_kernel then evaluates
 // them in FP64.
 constexpr int kFilterWarps = kPairThreads / 32;
-constexpr int kPer = 4;            // entries per lane per pass
+constexpr int kPer = 2;            // entries per lane per pass
 constexpr int kPass = 32 * kPer;   // entries per pass
 
-// v = E'_e + K'_j - 2 c_q . c_e with q = (-2 c_q, K'_j): one add, three FMAs.
-__device__ __forceinline__ float sphere_gap2(float4 e, float4 q)
+// Entry components duplicated into both halves of paired FP32 operands.
+struct EntryDup {
+    float2 x, y, z, w;
+};
+
+__device__ __forceinline__ EntryDup dup(float4 e)
 {
-    return fmaf(q.z, e.z, fmaf(q.y, e.y, fmaf(q.x, e.x, e.w + q.w)));
+    return EntryDup{make_float2(e.x, e.x), make_float2(e.y, e.y), make_float2(e.z, e.z), make_float2(e.w, e.w)};
+}
+
+// v = E'_e + K'_j - 2 c_j . c_e for the two queries j, j+1 of a pair at once
+// (paired FP32: one add and three FMAs for two candidates); qa = (-2x_j,
+// -2x_j+1, -2y_j, -2y_j+1), qb = (-2z_j, -2z_j+1, K'_j, K'_j+1).
+__device__ __forceinline__ float2 sphere_gap_pair(const EntryDup &e, float4 qa, float4 qb)
+{
+    float2 v = __fadd2_rn(e.w, make_float2(qb.z, qb.w));
+    v = __ffma2_rn(make_float2(qa.x, qa.y), e.x, v);
+    v = __ffma2_rn(make_float2(qa.z, qa.w), e.y, v);
+    return __ffma2_rn(make_float2(qb.x, qb.y), e.z, v);
 }
 
 struct FilterArgs {
@@ -401,11 +417,12 @@ struct FilterArgs {
 __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterArgs fa)
 {
     const PairArgs &args = fa.p;
-    __shared__ float4 qs_all[kFilterWarps][kQT];  // the tile's query spheres (cx, cy, cz, w)
-    __shared__ float4 qr_all[kFilterWarps][kQT];  // per pass: (cx, cy, cz, R_j^2)
+    // per pass: the tile's queries as interleaved pairs, qr[2i] = (-2x, -2y of
+    // queries 2i, 2i+1), qr[2i+1] = (-2z, K' of queries 2i, 2i+1)
+    __shared__ float4 qr_all[kFilterWarps][kQT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float4 *qs = qs_all[warp];
     float4 *qr = qr_all[warp];
+    float *qrf = reinterpret_cast<float *>(qr);
     DevCounters *ctr = args.ctr;
     const uint32_t EC = args.chunk;
     const unsigned long long total = args.tile_work[args.ntiles];
@@ -477,19 +494,29 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                 const float Rj = __fadd_ru(wmax, my_q.w);
                 const float cq2 = __fmaf_rd(my_q.z, my_q.z, __fmaf_rd(my_q.y, my_q.y, __fmul_rd(my_q.x, my_q.x)));
                 const float Kj = __fsub_rd(__fmul_rd(cq2, 1.0f - 0x1p-20f), __fmul_ru(Rj, Rj));
+                const bool huge = isinf(my_q.w);  // never rejected
+                const int pb = (lane >> 1) * 8 + (lane & 1);  // this query's slot in its pair
                 __syncwarp();
-                qr[lane] = isinf(my_q.w) ? make_float4(0.f, 0.f, 0.f, -INFINITY)  // never rejected
-                                         : make_float4(-2.0f * my_q.x, -2.0f * my_q.y, -2.0f * my_q.z, Kj);
+                qrf[pb + 0] = huge ? 0.f : -2.0f * my_q.x;
+                qrf[pb + 2] = huge ? 0.f : -2.0f * my_q.y;
+                qrf[pb + 4] = huge ? 0.f : -2.0f * my_q.z;
+                qrf[pb + 6] = huge ? -INFINITY : Kj;
                 __syncwarp();
+                EntryDup ed[kPer];
+#pragma unroll
+                for (int k = 0; k < kPer; k++) ed[k] = dup(ex[k]);
                 unsigned m[kPer];
 #pragma unroll
                 for (int k = 0; k < kPer; k++) m[k] = 0u;
 #pragma unroll
-                for (int j = 0; j < kQT; j++) {
-                    const float4 q = qr[j];
+                for (int j = 0; j < kQT; j += 2) {
+                    const float4 qa = qr[j], qb = qr[j + 1];
 #pragma unroll
-                    for (int k = 0; k < kPer; k++)
-                        m[k] = __funnelshift_l(__float_as_uint(sphere_gap2(ex[k], q)), m[k], 1);
+                    for (int k = 0; k < kPer; k++) {
+                        const float2 v = sphere_gap_pair(ed[k], qa, qb);
+                        m[k] = __funnelshift_l(__float_as_uint(v.x), m[k], 1);
+                        m[k] = __funnelshift_l(__float_as_uint(v.y), m[k], 1);
+                    }
                 }
                 unsigned any = 0u;
 #pragma unroll
