@@ -48,10 +48,10 @@ from paper_1405_7461_gb300 import workloads  # noqa: E402
 # C 6, discriminant 3.
 FLOPS_PER_PAIR_FP64 = 32
 # Algorithmic FP32 flops per candidate pair in the filter kernel's sphere
-# pre-test, written as v = E'_e + K'_j - 2 c_j . c_e: one add and three FMAs
-# (7 flops); K'_j (with the per-pass bound R_j^2) is formed once per
-# (64-entry pass, query), E'_e once per entry when the index is built.
-FLOPS_PER_CANDIDATE_FP32 = 7
+# pre-test, written as v = E_e + K_j - 2 (c_e . c_j + w_e w_j): one add and
+# four FMAs (9 flops); K_j is formed once per (query tile, query), E_e once
+# per entry when the index is built.
+FLOPS_PER_CANDIDATE_FP32 = 9
 # Peaks from unit counts and clocks (152 SMs, 2070 MHz): FP64 2 DFMA/clk/SM
 # (the 1.25 TFLOP/s nominal figure), FP32 128 FFMA/clk/SM.
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
@@ -459,7 +459,8 @@ def main():
     plan = tdq.Plan(idx, len(q3), mode=tdq.MODE_FP32_FILTER, result_capacity=1 << 22)
 
     def step(mode):
-        t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0}
+        t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0,
+             "survivors": 0}
         if mode == "batched":
             cnt = plan.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
             stats = [plan.stats()]
@@ -473,6 +474,7 @@ def main():
             t["pairs"] += s["overlap_pairs"]
             t["interactions"] += s["interactions"]
             t["fp64_pairs"] += s["fp64_pairs"]
+            t["survivors"] += s["filter_survivors"]
             t["launches"] += s["kernel_launches"]
             t["kernel_ms"] += s["pair_kernel_ms"]
         return t
@@ -501,6 +503,7 @@ def main():
                 "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / (total_ms / 1e3),
                 "interactions_per_s": world * tot["interactions"] / (total_ms / 1e3),
                 "fp64_pairs_per_step": tot["fp64_pairs"] / args.steps,
+                "filter_survivors_per_step": tot["survivors"] / args.steps,
                 "results_per_step": tot["results"] / args.steps, "gpu_launches": int(tot["launches"]),
                 "roofline": roofline("fp64" if mode == "fp64" else "fp32filter", tot, n_launch)}
 
@@ -556,6 +559,7 @@ def main():
             "queries_per_s": head["queries_per_s"],
             "interactions_per_s": head["interactions_per_s"],
             "fp64_pairs_per_step": head["fp64_pairs_per_step"],
+            "filter_survivors_per_step": head["filter_survivors_per_step"],
             "results_per_step": head["results_per_step"],
             "roofline": head["roofline"],
             "cpu_baseline": cpu,

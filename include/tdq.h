@@ -119,6 +119,7 @@ typedef struct {
     uint64_t kernel_launches;   /* CUDA kernels the library launched for the search */
     double pair_kernel_ms;      /* device time of the pair kernel (CUDA events) */
     double total_ms;            /* device time of the whole search on its stream */
+    uint64_t filter_survivors;  /* filter mode: pairs that passed the FP32 pre-test (0 in FP64 mode) */
 } tdq_stats;
 
 /*

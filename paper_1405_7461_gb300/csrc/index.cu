@@ -65,7 +65,7 @@ __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *
     }
 }
 
-__global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e, float *radius)
+__global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e)
 {
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -84,18 +84,18 @@ __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, E
     e.seg_id[k] = in.seg_id[i];
     e.traj_id[k] = in.traj_id ? in.traj_id[i] : 0;
     e.orig[k] = (int64_t)i;
-    // FP32 bounding sphere: midpoint and half length of the segment.  The
-    // pre-test record keeps the rounded center and E' = |center|^2 scaled by
-    // (1 - 2^-20), rounded down (the squares of floats are exact in FP64);
-    // the radius goes to the per-block maxima.
+    // FP32 bounding sphere: midpoint and half length of the segment, and the
+    // pre-test's per-entry term E = |c|^2 (1 - 2^-20), rounded down (the
+    // squares of floats are exact in FP64).
     double hx = 0.5 * (in.c[4][i] - xs), hy = 0.5 * (in.c[5][i] - ys), hz = 0.5 * (in.c[6][i] - zs);
     const float4 sp = sphere32(xs + hx, ys + hy, zs + hz, sqrt(hx * hx + hy * hy + hz * hz), 0.0);
-    radius[k] = sp.w;
     if (isinf(sp.w)) {
-        e.sph[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(0xff800000));  // -inf: never rejected
+        e.sph[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        e.sph_e[k] = __int_as_float(0xff800000);  // -inf: never rejected
     } else {
-        const double c2 = (double)sp.x * sp.x + (double)sp.y * sp.y + (double)sp.z * sp.z;
-        e.sph[k] = make_float4(sp.x, sp.y, sp.z, __double2float_rd(c2 * (1.0 - 0x1p-20 - 0x1p-50)));
+        const double c2 = __fma_rd(sp.z, sp.z, __fma_rd(sp.y, sp.y, __dmul_rd(sp.x, sp.x)));
+        e.sph[k] = sp;
+        e.sph_e[k] = __double2float_rd(__dmul_rd(c2, 1.0 - 0x1p-20));
     }
 }
 
@@ -113,23 +113,6 @@ __global__ void te_store(const uint64_t *keys, uint64_t n, int64_t *te_sorted)
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     te_sorted[k] = (int64_t)(keys[k] ^ 0x8000000000000000ULL);
-}
-
-// Largest sphere radius of each aligned block of 64 sorted entries (one
-// warp per block).
-__global__ void block_wmax(const float *radius, uint64_t n, float *out)
-{
-    const uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b * 64 >= n) return;
-    float w = 0.f;
-    for (int k = lane; k < 64; k += 32) {
-        const uint64_t i = b * 64 + k;
-        if (i < n) w = fmaxf(w, radius[i]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
-    if (lane == 0) out[b] = w;
 }
 
 __device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
@@ -273,7 +256,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     }
 
     // Resident sorted copy + bin table.
-    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n / 64 + 1, 4) + carve_bytes(n, 16);
+    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 4) + carve_bytes(n, 16);
     uint64_t bbytes = carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (dev_alloc(&idx->e_block, ebytes) != cudaSuccess || dev_alloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -289,7 +272,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         e.ts_key = carve<int64_t>(p, n); e.te_key = carve<int64_t>(p, n);
         e.seg_id = carve<int64_t>(p, n); e.traj_id = carve<int64_t>(p, n); e.orig = carve<int64_t>(p, n);
         e.te_sorted = carve<int64_t>(p, n);
-        e.blk_wmax = carve<float>(p, n / 64 + 1);
+        e.sph_e = carve<float>(p, n);
         e.sph = carve<float4>(p, n);
         char *q = (char *)idx->b_block;
         idx->bin_begin = carve<int64_t>(q, m + 1);
@@ -299,7 +282,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
 
     // Temporary build memory: staged input (host case), sort buffers, scratch.
     const bool host_in = !entries->on_device;
-    uint64_t tbytes = (host_in ? 10 * carve_bytes(n, 8) : 0) + 2 * carve_bytes(n, 8) + 3 * carve_bytes(n, 4) +
+    uint64_t tbytes = (host_in ? 10 * carve_bytes(n, 8) : 0) + 2 * carve_bytes(n, 8) + 2 * carve_bytes(n, 4) +
                       carve_bytes(sort_hist_words(n), 4) + carve_bytes(4, 8);
     void *tmp = nullptr;
     if (dev_alloc(&tmp, tbytes) != cudaSuccess) {
@@ -349,7 +332,6 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         uint32_t *vals = carve<uint32_t>(p, n);
         uint32_t *vals_alt = carve<uint32_t>(p, n);
         uint32_t *hist = carve<uint32_t>(p, sort_hist_words(n));
-        float *radius = carve<float>(p, n);
         unsigned long long *small = carve<unsigned long long>(p, 4);  // err, tmin, tmax
 
         unsigned long long init[3] = {0ULL, ~0ULL, 0ULL};
@@ -386,7 +368,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             st = cuda_error(cudaGetLastError(), "tdq_build_index: sort");
             break;
         }
-        entry_gather<<<grid_for(n), kBlock, 0, stream>>>(in, n, vals, idx->e, radius);
+        entry_gather<<<grid_for(n), kBlock, 0, stream>>>(in, n, vals, idx->e);
         bin_init<<<grid_for(m), kBlock, 0, stream>>>(idx->bin_end_key, m);
         bin_assign<<<grid_for(n), kBlock, 0, stream>>>(idx->e.ts_key, idx->e.te_key, n, idx->t_min, idx->width, m,
                                                        idx->bin_begin, idx->bin_end_key);
@@ -398,7 +380,6 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             break;
         }
         te_store<<<grid_for(n), kBlock, 0, stream>>>(keys, n, idx->e.te_sorted);
-        block_wmax<<<grid_for((n + 63) / 64 * 32), kBlock, 0, stream>>>(radius, n, idx->e.blk_wmax);
         if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: index kernels");
             break;

@@ -359,53 +359,91 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 
 // Work items of the filter kernel are (tile, chunk) pairs as for the plain
 // kernel, but each is processed by one warp: the warps of the grid split the
-// items into contiguous ranges; a warp walks the tile table forward, keeps
-// the tile's 32 query spheres in its own slice of shared memory (reloaded
-// only when the tile changes), and reads its entry records straight into
-// registers, two per lane per pass over the queries, the next pass's
-// loaded while the current one is tested.  No CTA-wide barrier is involved.
+// items into contiguous ranges, and a warp treats its items of one tile as
+// one run of consecutive sorted entries.  It walks those runs tile by tile,
+// keeps the tile's 32 query segments in its own slice of shared memory, and
+// streams the entries through registers, two per lane per pass over the
+// queries (64 per pass); the next pass's records -- in the same run or at
+// the start of the next one -- are loaded while the current pass is tested.
+// No CTA-wide barrier is involved.
 //
-// A pass covers 64 consecutive entries (two per lane).  For the pass, lane
-// j computes R_j = w_max + w_j (rounded up), w_max the largest radius of the
-// aligned 64-entry blocks the pass touches, and
-//   K'_j = |c_j|^2 (1 - g) - R_j^2   (rounded down, g = 2^-20);
-// each entry carries E'_e = |c_e|^2 (1 - g) rounded down.  Per candidate
-// pair the test is one add, three FMAs (issued as paired FP32 instructions
-// that evaluate two queries at once) and one funnel shift that moves the
+// For a pass, lane j forms the bound R_j = w_max + w_j (rounded up), w_max
+// the largest entry radius of the pass (one warp max-reduction over the
+// records already in registers), and
+//   K_j = |c_j|^2 (1 - g) - R_j^2   (rounded down, g = 2^-20);
+// each entry carries E_e = |c_e|^2 (1 - g) rounded down.  Per candidate pair
+// the test is one add and three FMAs -- issued as paired FP32 instructions
+// that evaluate two queries at once -- and one funnel shift that moves the
 // sign of
-//   v = E'_e + K'_j - 2 c_j . c_e  =  |c_e - c_j|^2 - R_j^2 - g (|c_e|^2 + |c_j|^2)
+//   v = E_e + K_j - 2 c_j . c_e  =  |c_e - c_j|^2 - R_j^2 - g (|c_e|^2 + |c_j|^2)
 // into the lane's 32-bit mask.  v is negative whenever the exact spheres
 // meet: with u = 2^-24 the four roundings of v add at most
-// u (7 (|c_e|^2 + |c_j|^2) + 4 R^2), less than the g (|c_e|^2 + |c_j|^2) = 16u (...)
+// u (8 (|c_e|^2 + |c_j|^2) + 4 R^2), less than the g (|c_e|^2 + |c_j|^2) = 16u (...)
 // subtracted and the 32u R^2 by which R_j^2 exceeds the exact bound (the
 // radii carry a factor 1 + 2^-20); R >= 2^-60 keeps every quantity normal.
-// Segments beyond 2^60 in magnitude carry E' = -inf or K' = -inf and are
-// never rejected.  The survivors (entry, query) are appended to a list (one
-// atomic per lane that has any); traj_dist_refine_kernel then evaluates
-// them in FP64.
+// Segments beyond 2^60 in magnitude carry a zero sphere and E = -inf, or an
+// infinite radius and K = -inf, and are never rejected.  The survivors
+// (entry, query) are appended to a list (one atomic per lane that has any);
+// traj_dist_refine_kernel then evaluates them in FP64.
 constexpr int kFilterWarps = kPairThreads / 32;
 constexpr int kPer = 2;            // entries per lane per pass
 constexpr int kPass = 32 * kPer;   // entries per pass
 
-// Entry components duplicated into both halves of paired FP32 operands.
+// One entry's pre-test terms, each duplicated into both halves of a paired
+// FP32 operand.
 struct EntryDup {
-    float2 x, y, z, w;
+    float2 x, y, z, e;
 };
 
-__device__ __forceinline__ EntryDup dup(float4 e)
+__device__ __forceinline__ EntryDup dup(float4 s, float e)
 {
-    return EntryDup{make_float2(e.x, e.x), make_float2(e.y, e.y), make_float2(e.z, e.z), make_float2(e.w, e.w)};
+    return EntryDup{make_float2(s.x, s.x), make_float2(s.y, s.y), make_float2(s.z, s.z), make_float2(e, e)};
 }
 
-// v = E'_e + K'_j - 2 c_j . c_e for the two queries j, j+1 of a pair at once
-// (paired FP32: one add and three FMAs for two candidates); qa = (-2x_j,
-// -2x_j+1, -2y_j, -2y_j+1), qb = (-2z_j, -2z_j+1, K'_j, K'_j+1).
+// v for the two queries j, j+1 of a pair at once; qa = (-2x_j, -2x_j+1,
+// -2y_j, -2y_j+1), qb = (-2z_j, -2z_j+1, K_j, K_j+1).
 __device__ __forceinline__ float2 sphere_gap_pair(const EntryDup &e, float4 qa, float4 qb)
 {
-    float2 v = __fadd2_rn(e.w, make_float2(qb.z, qb.w));
+    float2 v = __fadd2_rn(e.e, make_float2(qb.z, qb.w));
     v = __ffma2_rn(make_float2(qa.x, qa.y), e.x, v);
     v = __ffma2_rn(make_float2(qa.z, qa.w), e.y, v);
     return __ffma2_rn(make_float2(qb.x, qb.y), e.z, v);
+}
+
+// The warp's run of entries in tile t: its items there are
+// [max(ibeg, tile_work[t]), min(iend, tile_work[t+1])), chunk_len entries each.
+__device__ __forceinline__ void filter_run(const PairArgs &args, uint64_t t, unsigned long long ibeg,
+                                           unsigned long long iend, int64_t &eb, int64_t &ee)
+{
+    const unsigned long long wb = args.tile_work[t], wn = args.tile_work[t + 1];
+    const int64_t lo = args.tile_lo[t], hi = args.tile_hi[t];
+    eb = lo + (int64_t)(max(ibeg, wb) - wb) * args.chunk;
+    ee = min(lo + (int64_t)(min(iend, wn) - wb) * args.chunk, hi);
+}
+
+// Query terms of lane j for its tile: -2 c_j into the warp's table (pairs of
+// queries interleaved: qr[2i] = (-2x, -2y of queries 2i, 2i+1), qr[2i+1].xy =
+// -2z of both; qr[2i+1].zw receives K of both every pass), and |c_j|^2 (1 - g)
+// and w_j kept in registers.  Lanes past the tile's last query hold zeros.
+__device__ __forceinline__ void stage_queries(float4 s, bool real, int lane, float4 *qr, float &c2g, float &w)
+{
+    if (!real) s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float X = -2.0f * s.x, Y = -2.0f * s.y, Z = -2.0f * s.z;
+    w = s.w;
+    if (isinf(s.w)) {  // huge magnitudes: K = -inf, never rejected
+        X = Y = Z = 0.f;
+        c2g = 0.f;
+    } else {
+        c2g = __fmul_rd(__fmaf_rd(s.z, s.z, __fmaf_rd(s.y, s.y, __fmul_rd(s.x, s.x))), 1.0f - 0x1p-20f);
+    }
+    const bool odd = lane & 1;
+    const float r1 = __shfl_xor_sync(kFull, odd ? X : Z, 1);
+    const float r2 = __shfl_xor_sync(kFull, Y, 1);
+    __syncwarp();  // the previous tile's table is no longer read
+    if (odd)
+        *reinterpret_cast<float2 *>(&qr[lane]) = make_float2(r1, Z);
+    else
+        qr[lane] = make_float4(X, r1, Y, r2);
 }
 
 struct FilterArgs {
@@ -417,14 +455,12 @@ struct FilterArgs {
 __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterArgs fa)
 {
     const PairArgs &args = fa.p;
-    // per pass: the tile's queries as interleaved pairs, qr[2i] = (-2x, -2y of
-    // queries 2i, 2i+1), qr[2i+1] = (-2z, K' of queries 2i, 2i+1)
     __shared__ float4 qr_all[kFilterWarps][kQT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *qr = qr_all[warp];
     float *qrf = reinterpret_cast<float *>(qr);
+    const int k_slot = (lane >> 1) * 8 + 6 + (lane & 1);  // this lane's K in qr[2i+1].zw
     DevCounters *ctr = args.ctr;
-    const uint32_t EC = args.chunk;
     const unsigned long long total = args.tile_work[args.ntiles];
     const uint64_t nvalid = ctr->valid_queries;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * kFilterWarps;
@@ -432,10 +468,11 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
     const unsigned long long per = (total + nwarps - 1) / nwarps;
     const unsigned long long ibeg = min(gw * per, total);
     const unsigned long long iend = min(ibeg + per, total);
+    const float4 *esph = args.e.sph;
+    const float *esphe = args.e.sph_e;
     unsigned long long n_inter = 0;
 
     if (ibeg < iend) {
-        // position in the tile table (the same on every lane)
         uint64_t t = 0;
         {
             uint64_t lo = 0, hi = args.ntiles;  // last tile whose first item is <= ibeg
@@ -445,66 +482,63 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
             }
             t = lo;
         }
-        unsigned long long w_base = args.tile_work[t], w_next = args.tile_work[t + 1];
-        int64_t t_lo = args.tile_lo[t], t_hi = args.tile_hi[t];
-        int64_t q0 = (int64_t)t * kQT;
-        int nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)q0);
-        float4 my_q = lane < nqt ? args.q.sph[q0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-
-        for (unsigned long long it = ibeg; it < iend; it++) {
-            if (w_next <= it) {  // next tile (possibly skipping tiles without work)
-                do {
-                    t++;
-                    w_base = w_next;
-                    w_next = args.tile_work[t + 1];
-                } while (w_next <= it);
-                t_lo = args.tile_lo[t];
-                t_hi = args.tile_hi[t];
-                q0 = (int64_t)t * kQT;
-                nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)q0);
-                my_q = lane < nqt ? args.q.sph[q0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t eb, ee;
+        filter_run(args, t, ibeg, iend, eb, ee);
+        int nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)t * kQT);
+        float my_c2g, my_w;
+        stage_queries(args.q.sph[(int64_t)t * kQT + min(lane, nqt - 1)], lane < nqt, lane, qr, my_c2g, my_w);
+        float4 ns[kPer];
+        float nse[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const int64_t e = eb + lane + 32 * k;
+            ns[k] = e < ee ? esph[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            nse[k] = e < ee ? esphe[e] : 0.f;
+        }
+        for (;;) {
+            // the next run of this warp (a later tile with items in range),
+            // located and its queries fetched while this run is tested
+            uint64_t tn = t + 1;
+            const bool has_next = args.tile_work[tn] < iend;
+            int64_t ebn = 0, een = 0;
+            int nqn = 0;
+            float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (has_next) {
+                while (args.tile_work[tn + 1] == args.tile_work[tn]) tn++;
+                filter_run(args, tn, ibeg, iend, ebn, een);
+                nqn = (int)min((uint64_t)kQT, nvalid - tn * kQT);
+                qn = args.q.sph[(int64_t)tn * kQT + min(lane, nqn - 1)];
             }
-            const int64_t e0 = t_lo + (int64_t)(it - w_base) * EC;
-            const int ne = (int)(min(e0 + (int64_t)EC, t_hi) - e0);
+            const int64_t q0 = (int64_t)t * kQT;
             const unsigned qvalid = 0xffffffffu << (kQT - nqt);  // bit 31-j <-> query j
-            if (lane == 0) n_inter += (unsigned long long)ne * (unsigned long long)nqt;
-            // entries el + 32 k (k < kPer), el = kPass p + lane; the next
-            // pass's entries are loaded while this pass is tested
-            const int npass = (ne + kPass - 1) / kPass;
-            float4 nx[kPer];
-#pragma unroll
-            for (int k = 0; k < kPer; k++)
-                nx[k] = lane + 32 * k < ne ? args.e.sph[e0 + lane + 32 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int p = 0; p < npass; p++) {
-                float4 ex[kPer];
-#pragma unroll
-                for (int k = 0; k < kPer; k++) ex[k] = nx[k];
-                const int el0 = kPass * p + lane;
-                const int64_t pe = e0 + kPass * p;  // first entry of the pass
-                if (p + 1 < npass) {
-#pragma unroll
-                    for (int k = 0; k < kPer; k++)
-                        if (el0 + kPass + 32 * k < ne) nx[k] = args.e.sph[e0 + el0 + kPass + 32 * k];
-                }
-                // per-pass bound of query j = lane: the largest entry radius of
-                // the aligned 64-entry blocks the pass touches
-                const int64_t plast = pe + min(kPass - 1, ne - 1 - kPass * p);
-                float wmax = 0.f;
-                for (int64_t blk = pe >> 6; blk <= (plast >> 6); blk++) wmax = fmaxf(wmax, args.e.blk_wmax[blk]);
-                const float Rj = __fadd_ru(wmax, my_q.w);
-                const float cq2 = __fmaf_rd(my_q.z, my_q.z, __fmaf_rd(my_q.y, my_q.y, __fmul_rd(my_q.x, my_q.x)));
-                const float Kj = __fsub_rd(__fmul_rd(cq2, 1.0f - 0x1p-20f), __fmul_ru(Rj, Rj));
-                const bool huge = isinf(my_q.w);  // never rejected
-                const int pb = (lane >> 1) * 8 + (lane & 1);  // this query's slot in its pair
-                __syncwarp();
-                qrf[pb + 0] = huge ? 0.f : -2.0f * my_q.x;
-                qrf[pb + 2] = huge ? 0.f : -2.0f * my_q.y;
-                qrf[pb + 4] = huge ? 0.f : -2.0f * my_q.z;
-                qrf[pb + 6] = huge ? -INFINITY : Kj;
-                __syncwarp();
+            if (lane == 0) n_inter += (unsigned long long)(ee - eb) * (unsigned long long)nqt;
+            for (int64_t pe = eb; pe < ee; pe += kPass) {
                 EntryDup ed[kPer];
+                float wl = 0.f;
 #pragma unroll
-                for (int k = 0; k < kPer; k++) ed[k] = dup(ex[k]);
+                for (int k = 0; k < kPer; k++) {
+                    ed[k] = dup(ns[k], nse[k]);
+                    wl = fmaxf(wl, ns[k].w);
+                }
+                // the next pass's records: this run, else the next run's first pass
+                {
+                    const bool same = pe + kPass < ee;
+                    const int64_t nb = same ? pe + kPass : ebn, ne_ = same ? ee : een;
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) {
+                        const int64_t e = nb + lane + 32 * k;
+                        const bool in = e < ne_;
+                        ns[k] = in ? esph[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        nse[k] = in ? esphe[e] : 0.f;
+                    }
+                }
+                // radii are non-negative: their bit patterns order like the values
+                const float wmax = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(wl)));
+                const float Rj = __fadd_ru(wmax, my_w);
+                const float Kj = __fsub_rd(my_c2g, __fmul_ru(Rj, Rj));
+                __syncwarp();  // the previous pass's K are no longer read
+                qrf[k_slot] = Kj;
+                __syncwarp();
                 unsigned m[kPer];
 #pragma unroll
                 for (int k = 0; k < kPer; k++) m[k] = 0u;
@@ -521,12 +555,11 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                 unsigned any = 0u;
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
-                    m[k] = el0 + 32 * k < ne ? (m[k] & qvalid) : 0u;
+                    m[k] = pe + lane + 32 * k < ee ? (m[k] & qvalid) : 0u;
                     any |= m[k];
                 }
                 if (any == 0u) continue;
-                // append this lane's survivors (few lanes ever have any: one
-                // atomic per such lane, no warp-wide step)
+                // append this lane's survivors (one atomic per lane that has any)
                 int cnt = 0;
 #pragma unroll
                 for (int k = 0; k < kPer; k++) cnt += __popc(m[k]);
@@ -534,7 +567,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
                     unsigned mk = m[k];
-                    const uint32_t ek = (uint32_t)(e0 + el0 + 32 * k);
+                    const uint32_t ek = (uint32_t)(pe + lane + 32 * k);
                     while (mk) {
                         const int bit = 31 - __clz(mk);
                         mk &= ~(1u << bit);
@@ -543,6 +576,12 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                     }
                 }
             }
+            if (!has_next) break;
+            t = tn;
+            eb = ebn;
+            ee = een;
+            nqt = nqn;
+            stage_queries(qn, lane < nqt, lane, qr, my_c2g, my_w);
         }
     }
 #pragma unroll
@@ -977,6 +1016,7 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
     s->fp64_pairs = h.fp64_pairs;
     s->results = h.results;
     s->work_items = h.work_items;
+    s->filter_survivors = cfg.filter ? h.survivors : 0;
     s->kernel_launches = (uint64_t)search_kernel_launches(idx, cfg);
     if (events) {
         float ms = 0.f;

@@ -64,9 +64,8 @@ __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }  // x >= 0
 // than any FP64 rounding of the positions the FP64 path evaluates), by
 // r * 2^-40, by `extra` (the threshold d, for a query) and by 2^-60 (so that
 // w > 0 and w^2 stays a normal number), then scaled by (1 + 2^-20) and
-// rounded up.  The scaling pays for the FP32 roundings of the pair test (see
-// spheres_may_meet).  Magnitudes beyond 2^60 get an infinite radius, which
-// never rejects.
+// rounded up.  Magnitudes beyond 2^60 get an infinite radius, which never
+// rejects.
 __device__ __forceinline__ float4 sphere32(double cx, double cy, double cz, double r, double extra)
 {
     double m = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
@@ -101,10 +100,11 @@ struct EntrySoA {
     double *vx, *vy, *vz;  // velocity (end - start) / (t_end - t_start)
     int64_t *ts_key, *te_key;
     int64_t *seg_id, *traj_id, *orig;
-    float4 *sph;           // FP32 pre-test record: center (rounded to nearest) and E' = |center|^2 (1 - 2^-20)
-                           // rounded down (see entry_prepass); (0, 0, 0, -inf) for huge magnitudes
+    float4 *sph;           // FP32 bounding sphere: center (rounded to nearest) and radius w (rounded up);
+                           // (0, 0, 0, 0) for huge magnitudes
+    float *sph_e;          // E = |center|^2 (1 - 2^-20), rounded down; -inf for huge magnitudes (the
+                           // pair is then never rejected)
     int64_t *te_sorted;    // t_end keys in ascending order (for exact overlap counts)
-    float *blk_wmax;       // largest bounding-sphere radius of each aligned block of 64 sorted entries
 };
 
 // Sorted, clipped query segments in device memory.

@@ -64,7 +64,8 @@ class tdq_stats(ctypes.Structure):
     _fields_ = [("query_segments", ctypes.c_uint64), ("interactions", ctypes.c_uint64),
                 ("overlap_pairs", ctypes.c_uint64), ("fp64_pairs", ctypes.c_uint64), ("results", ctypes.c_uint64),
                 ("work_items", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("pair_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("pair_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("filter_survivors", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
