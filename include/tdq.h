@@ -80,8 +80,7 @@ enum {
 /* Search tuning.  Zero fields select defaults. */
 typedef struct {
     uint32_t query_tile;  /* query segments per tile (multiple of 32, <= 32; default 32) */
-    uint32_t entry_chunk; /* entry segments per work item (multiple of 256, <= 2048; default 512 in
-                             FP64 mode, 256 in filter mode) */
+    uint32_t entry_chunk; /* entry segments per work item (multiple of 256, <= 2048; default 512) */
     int mode;             /* TDQ_MODE_* (default TDQ_MODE_FP64) */
 } tdq_search_params;
 

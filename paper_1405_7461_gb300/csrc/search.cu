@@ -362,8 +362,8 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // items into contiguous ranges, and a warp treats its items of one tile as
 // one run of consecutive sorted entries.  It walks those runs tile by tile,
 // keeps the tile's 32 query segments in its own slice of shared memory, and
-// streams the entries through registers, two per lane per pass over the
-// queries (64 per pass); the next pass's records -- in the same run or at
+// streams the entries through registers, four per lane per pass over the
+// queries (128 per pass); the next pass's records -- in the same run or at
 // the start of the next one -- are loaded while the current pass is tested.
 // No CTA-wide barrier is involved.
 //
@@ -386,7 +386,7 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // (entry, query) are appended to a list (one atomic per lane that has any);
 // traj_dist_refine_kernel then evaluates them in FP64.
 constexpr int kFilterWarps = kPairThreads / 32;
-constexpr int kPer = 2;            // entries per lane per pass
+constexpr int kPer = 4;            // entries per lane per pass
 constexpr int kPass = 32 * kPer;   // entries per pass
 
 // One entry's pre-test terms, each duplicated into both halves of a paired
@@ -589,37 +589,64 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
     if (lane == 0 && n_inter) atomicAdd(&ctr->interactions, n_inter);
 }
 
-// FP64 evaluation of the filter's survivors, one per lane: exact temporal
-// overlap first (the pre-test ignores time), then the same FP64 code as the
-// plain kernel, then the warp-aggregated append.
+// FP64 evaluation of the filter's survivors.  The pre-test ignores time, so
+// most survivors do not overlap in time; a warp checks the exact span keys
+// of 32 survivors at a time, queues the overlapping ones in its slice of
+// shared memory, and runs the FP64 code of the plain kernel (then the
+// warp-aggregated append) on full batches of 32 queued pairs: the FP64 pipe
+// is busy for a warp instruction whatever the number of active lanes.
+constexpr int kRefineWarps = kPairThreads / 32;
+
+__device__ __forceinline__ void refine_batch(const PairArgs &args, uint2 sv, bool active, uint64_t cap, int lane,
+                                             unsigned lt_mask)
+{
+    const int64_t ek = sv.x, qk = sv.y;
+    const PairEval r = eval_pair_fp64(active, args.e.ts_key[ek], args.e.te_key[ek], args.q.ts_key[qk],
+                                      args.q.te_key[qk], args.e.px[ek], args.e.py[ek], args.e.pz[ek], args.e.vx[ek],
+                                      args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk], args.q.pz[qk],
+                                      args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
+    append_hits(r, args.ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+}
+
 __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterArgs fa)
 {
     const PairArgs &args = fa.p;
+    __shared__ uint2 queue_all[kRefineWarps][64];
     DevCounters *ctr = args.ctr;
     const int lane = threadIdx.x & 31;
+    uint2 *queue = queue_all[threadIdx.x >> 5];
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t cap = args.out.capacity;
     const unsigned long long ns = min(ctr->survivors, (unsigned long long)fa.surv_cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned long long n_fp64 = 0;
-    // warp-uniform trip count (eval_pair_fp64 and append_hits vote over the warp)
+    int queued = 0;  // warp-uniform, < 32 between chunks
+    // warp-uniform trip count (the ballots, eval_pair_fp64 and append_hits vote over the warp)
     const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     for (unsigned long long wb = first; wb < ns; wb += stride) {
         const unsigned long long k = wb + lane;
         const bool valid = k < ns;
         const uint2 sv = valid ? fa.surv[k] : make_uint2(0u, 0u);
-        const int64_t ek = sv.x, qk = sv.y;
-        const int64_t ets_k = args.e.ts_key[ek], ete_k = args.e.te_key[ek];
-        const int64_t qts_k = args.q.ts_key[qk], qte_k = args.q.te_key[qk];
-        const bool active = valid && (ets_k < qte_k) && (ete_k > qts_k);
+        const bool active = valid && args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
+                            args.e.te_key[sv.x] > args.q.ts_key[sv.y];
         const unsigned am = __ballot_sync(kFull, active);
-        if (lane == 0) n_fp64 += (unsigned long long)__popc(am);
-        if (!am) continue;
-        const PairEval r = eval_pair_fp64(active, ets_k, ete_k, qts_k, qte_k, args.e.px[ek], args.e.py[ek],
-                                          args.e.pz[ek], args.e.vx[ek], args.e.vy[ek], args.e.vz[ek], args.q.px[qk],
-                                          args.q.py[qk], args.q.pz[qk], args.q.vx[qk], args.q.vy[qk], args.q.vz[qk],
-                                          args.q.d2[qk]);
-        append_hits(r, ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+        if (active) queue[queued + __popc(am & lt_mask)] = sv;
+        queued += __popc(am);
+        n_fp64 += __popc(am);
+        __syncwarp();
+        if (queued >= 32) {
+            const uint2 qv = queue[lane];
+            const uint2 rest = lane + 32 < queued ? queue[lane + 32] : make_uint2(0u, 0u);
+            __syncwarp();
+            if (lane + 32 < queued) queue[lane] = rest;
+            queued -= 32;
+            __syncwarp();
+            refine_batch(args, qv, true, cap, lane, lt_mask);
+        }
+    }
+    if (queued > 0) {  // the last, partial batch
+        const bool active = lane < queued;
+        refine_batch(args, active ? queue[lane] : make_uint2(0u, 0u), active, cap, lane, lt_mask);
     }
     if (lane == 0 && n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
 }
@@ -933,7 +960,7 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
     if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
         return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
     cfg->filter = params && params->mode == TDQ_MODE_FP32_FILTER;
-    cfg->chunk = (params && params->entry_chunk) ? params->entry_chunk : (cfg->filter ? 256u : 512u);
+    cfg->chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
     if (cfg->chunk % kPairThreads != 0 || cfg->chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
     if (params && params->query_tile && params->query_tile != (uint32_t)kQT)
