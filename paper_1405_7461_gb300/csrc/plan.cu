@@ -289,7 +289,8 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
         TDQ_CUDA(cudaStreamSynchronize(stream));
         bool grow_surv = false;
         uint64_t cnt = 0;
-        tdq_status st = finish_search(p->idx, w, p->cfg, p->res.capacity, true, &p->last, &cnt, &grow_surv);
+        tdq_status st = finish_search(p->idx, w, p->cfg, p->use_graph ? cls : nq, p->res.capacity, true, &p->last, &cnt,
+                                      &grow_surv);
         cudaGetLastError();
         if (st == TDQ_OK && !grow_surv) {
             *count = cnt;

@@ -968,11 +968,11 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
     return TDQ_OK;
 }
 
-int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg)
+int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
 {
-    // query_prep; with entries: sort passes x 3 kernels, query_gather,
+    // query_prep; with entries: the sort of the query keys, query_gather,
     // tile_plan, scan, pair kernel (filter mode: filter, refine, overlap count)
-    return idx->n > 0 ? 1 + 3 * sort_passes(bin_key_bits(idx->m)) + 3 + (cfg.filter ? 3 : 1) : 1;
+    return idx->n > 0 ? 1 + sort_kernel_launches(nq, bin_key_bits(idx->m)) + 3 + (cfg.filter ? 3 : 1) : 1;
 }
 
 // Events are recorded as external event-record nodes when the stream is being
@@ -1023,8 +1023,8 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     return cudaGetLastError();
 }
 
-tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t capacity,
-                         bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow)
+tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t nq,
+                         uint64_t capacity, bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow)
 {
     const DevCounters &h = *w.ctr_host;
     *surv_overflow = false;
@@ -1044,7 +1044,7 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
     s->results = h.results;
     s->work_items = h.work_items;
     s->filter_survivors = cfg.filter ? h.survivors : 0;
-    s->kernel_launches = (uint64_t)search_kernel_launches(idx, cfg);
+    s->kernel_launches = (uint64_t)search_kernel_launches(idx, cfg, nq);
     if (events) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s->pair_kernel_ms = ms;
@@ -1201,7 +1201,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
         TDQ_CUDA(enqueue_search(idx, w, in, nq, cfg, out, stream, true));
         TDQ_CUDA(cudaStreamSynchronize(stream));
         bool grow = false;
-        st = finish_search(idx, w, cfg, out.capacity, true, &idx->last, count, &grow);
+        st = finish_search(idx, w, cfg, nq, out.capacity, true, &idx->last, count, &grow);
         if (!grow) return st;
         if (attempt >= 2) return set_error(TDQ_ERR_NOMEM, "tdq_search: survivor list kept overflowing");
         const uint64_t need = w.ctr_host->survivors;

@@ -3,10 +3,13 @@
 // temporal-bin index (Sec. 4) and query segments by their clipped start
 // (Sec. 4: the query set is sorted by t_start before its bins are looked up).
 //
-// Each 8-bit digit pass runs three kernels: per-tile digit histograms, one
-// exclusive scan over (digit, tile) counts in digit-major order, and a stable
-// scatter that ranks equal digits in input order inside each tile with
-// warp match masks.
+// Each 8-bit digit pass runs per-tile digit histograms and a stable scatter
+// that ranks equal digits in input order inside each tile with warp match
+// masks.  The scatter offsets of a (digit, tile) are the keys of smaller
+// digits plus the keys of the same digit in earlier tiles: for large inputs
+// one exclusive scan over the counts in digit-major order computes them
+// between the two kernels; for up to kFusedTiles tiles each scatter block
+// derives its own from the tile-major counts (no scan kernel).
 #include "tdq_internal.cuh"
 
 namespace tdq {
@@ -19,8 +22,10 @@ constexpr int kWarps = kThreads / 32;
 // inputs up to 2^20 keys, so that small sorts still spread over the SMs.
 constexpr uint64_t kSmallSort = 1u << 20;
 inline int items_for(uint64_t n) { return n <= kSmallSort ? 4 : 16; }
+constexpr uint32_t kFusedTiles = 256;
 
-template <int kItems>
+// kTileMajor: counts stored as hist[tile][digit], else hist[digit][tile].
+template <int kItems, bool kTileMajor>
 __global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restrict__ keys, uint64_t n, int shift,
                                                        uint32_t *__restrict__ hist, uint32_t ntiles)
 {
@@ -35,10 +40,40 @@ __global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restric
         if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 0xff], 1u);
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    if (kTileMajor)
+        hist[(uint64_t)blockIdx.x * kRadix + threadIdx.x] = h[threadIdx.x];
+    else
+        hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-template <int kItems>
+// Scatter offset of digit `tid` for this block from the tile-major counts
+// of all tiles: keys of smaller digits (block scan of the digit totals) plus
+// keys of the same digit in earlier tiles.
+__device__ __forceinline__ uint32_t fused_offset(const uint32_t *__restrict__ hist, uint32_t ntiles, int tid)
+{
+    __shared__ uint32_t wsum[kWarps];
+    uint32_t before = 0, total = 0;
+#pragma unroll 8
+    for (uint32_t t = 0; t < ntiles; t++) {
+        const uint32_t c = hist[(uint64_t)t * kRadix + tid];
+        total += c;
+        before += t < blockIdx.x ? c : 0u;
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t x = total;  // inclusive scan over the digits
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; w++) wbase += wsum[w];
+    return wbase + x - total + before;
+}
+
+template <int kItems, bool kFused>
 __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__restrict__ keys,
                                                           const uint32_t *__restrict__ vals, uint64_t n, int shift,
                                                           const uint32_t *__restrict__ offsets, uint32_t ntiles,
@@ -50,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__rest
     __shared__ uint32_t run[kRadix];
     __shared__ uint32_t wcnt[kWarps][kRadix];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    off[tid] = offsets[(uint64_t)tid * ntiles + blockIdx.x];
+    off[tid] = kFused ? fused_offset(offsets, ntiles, tid) : offsets[(uint64_t)tid * ntiles + blockIdx.x];
     run[tid] = 0;
     const uint64_t base = (uint64_t)blockIdx.x * kTile;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -175,21 +210,39 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     uint64_t *src_k = keys, *dst_k = keys_alt;
     uint32_t *src_v = vals, *dst_v = vals_alt;
     const int passes = sort_passes(key_bits < 64 ? key_bits : 64);
+    const bool fused = items == 4 && ntiles <= kFusedTiles;
     for (int shift = 0; shift < 8 * passes; shift += 8) {
-        if (items == 4)
-            radix_hist<4><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
-        else
-            radix_hist<16><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
-        scan_exclusive_block<uint32_t, 8><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
-        if (items == 4)
-            radix_scatter<4><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
-        else
-            radix_scatter<16><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k, dst_v);
+        if (fused) {
+            radix_hist<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+            radix_scatter<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k,
+                                                                     dst_v);
+        } else {
+            if (items == 4)
+                radix_hist<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+            else
+                radix_hist<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+            scan_exclusive_block<uint32_t, 8><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
+            if (items == 4)
+                radix_scatter<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k,
+                                                                          dst_v);
+            else
+                radix_scatter<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles,
+                                                                           dst_k, dst_v);
+        }
         uint64_t *tk = src_k; src_k = dst_k; dst_k = tk;
         uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
     }
     // an even number of passes: the data is back in keys/vals
     return cudaGetLastError();
+}
+
+int sort_kernel_launches(uint64_t n, int key_bits)
+{
+    if (n <= 1) return 0;
+    const int passes = sort_passes(key_bits < 64 ? key_bits : 64);
+    const uint64_t tile = (uint64_t)kThreads * items_for(n);
+    const bool fused = items_for(n) == 4 && (n + tile - 1) / tile <= kFusedTiles;
+    return passes * (fused ? 2 : 3);
 }
 
 cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,

@@ -200,11 +200,11 @@ struct LaunchCfg {
 tdq_status ensure_queries(Workspace &w, uint64_t nq);
 tdq_status ensure_survivors(Workspace &w, uint64_t cap);
 tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg);
-int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg);
+int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq);
 cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq, const LaunchCfg &cfg,
                            const tdq_result_buffer &out, cudaStream_t stream, bool events);
-tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t capacity,
-                         bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
+tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t nq,
+                         uint64_t capacity, bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
 // Side stream and fork/join events of a workspace (created once).
 tdq_status workspace_streams(Workspace &w);
 void workspace_streams_free(Workspace &w);
@@ -259,6 +259,8 @@ uint64_t sort_hist_words(uint64_t n);
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
                              uint32_t *hist, cudaStream_t stream, int key_bits = 64);
 inline int sort_passes(int key_bits) { return 2 * ((key_bits + 15) / 16); }
+// Kernels radix_sort_pairs launches for n keys.
+int sort_kernel_launches(uint64_t n, int key_bits);
 // Bits of a query sort key: bin indices 0..m-1 and m for invalid segments.
 inline int bin_key_bits(uint32_t m)
 {
