@@ -385,7 +385,11 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // infinite radius and K = -inf, and are never rejected.  The survivors
 // (entry, query) are appended to a list (one atomic per lane that has any);
 // traj_dist_refine_kernel then evaluates them in FP64.
-constexpr int kFilterWarps = kPairThreads / 32;
+// Warps per block of the filter kernel.  It has no block-wide step, but the
+// warps of a block take adjacent item ranges, whose entry records largely
+// coincide, so that they share the SM's L1 cache.
+constexpr int kFilterWarps = 8;
+constexpr int kFilterThreads = 32 * kFilterWarps;
 constexpr int kPer = 4;            // entries per lane per pass
 constexpr int kPass = 32 * kPer;   // entries per pass
 
@@ -452,7 +456,7 @@ struct FilterArgs {
     uint64_t surv_cap;
 };
 
-__global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterArgs fa)
+__global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(FilterArgs fa)
 {
     const PairArgs &args = fa.p;
     __shared__ float4 qr_all[kFilterWarps][kQT];
@@ -523,13 +527,15 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                 // the next pass's records: this run, else the next run's first pass
                 {
                     const bool same = pe + kPass < ee;
-                    const int64_t nb = same ? pe + kPass : ebn, ne_ = same ? ee : een;
+                    const int64_t nb = same ? pe + kPass : ebn;
+                    const int left = (int)min(same ? ee - nb : een - nb, (int64_t)kPass);
+                    const float4 *ps = esph + nb + lane;
+                    const float *pse = esphe + nb + lane;
 #pragma unroll
                     for (int k = 0; k < kPer; k++) {
-                        const int64_t e = nb + lane + 32 * k;
-                        const bool in = e < ne_;
-                        ns[k] = in ? esph[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        nse[k] = in ? esphe[e] : 0.f;
+                        const bool in = lane + 32 * k < left;
+                        ns[k] = in ? ps[32 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        nse[k] = in ? pse[32 * k] : 0.f;
                     }
                 }
                 // radii are non-negative: their bit patterns order like the values
@@ -553,9 +559,10 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_filter_kernel(FilterAr
                     }
                 }
                 unsigned any = 0u;
+                const int here = (int)min(ee - pe, (int64_t)kPass);
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
-                    m[k] = pe + lane + 32 * k < ee ? (m[k] & qvalid) : 0u;
+                    m[k] = lane + 32 * k < here ? (m[k] & qvalid) : 0u;
                     any |= m[k];
                 }
                 if (any == 0u) continue;
@@ -838,10 +845,11 @@ cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, ui
     if (filter) {
         FilterArgs fa{pa, surv, surv_cap};
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_filter_kernel, kPairThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_filter_kernel, kFilterThreads,
+                                                                      0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        traj_dist_filter_kernel<<<sm_count * per_sm, kPairThreads, 0, stream>>>(fa);
+        traj_dist_filter_kernel<<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_refine_kernel, kPairThreads, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
