@@ -545,19 +545,25 @@ __global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(Filter
                 __syncwarp();  // the previous pass's K are no longer read
                 qrf[k_slot] = Kj;
                 __syncwarp();
-                unsigned m[kPer];
+                // two independent mask chains per entry (queries 0-15 and
+                // 16-31), joined afterwards: the funnel shifts of one chain
+                // depend on each other
+                unsigned m[kPer], mh[kPer];
 #pragma unroll
-                for (int k = 0; k < kPer; k++) m[k] = 0u;
+                for (int k = 0; k < kPer; k++) m[k] = mh[k] = 0u;
 #pragma unroll
                 for (int j = 0; j < kQT; j += 2) {
                     const float4 qa = qr[j], qb = qr[j + 1];
 #pragma unroll
                     for (int k = 0; k < kPer; k++) {
                         const float2 v = sphere_gap_pair(ed[k], qa, qb);
-                        m[k] = __funnelshift_l(__float_as_uint(v.x), m[k], 1);
-                        m[k] = __funnelshift_l(__float_as_uint(v.y), m[k], 1);
+                        unsigned &mm = j < kQT / 2 ? mh[k] : m[k];
+                        mm = __funnelshift_l(__float_as_uint(v.x), mm, 1);
+                        mm = __funnelshift_l(__float_as_uint(v.y), mm, 1);
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < kPer; k++) m[k] = __byte_perm(m[k], mh[k], 0x5410);
                 unsigned any = 0u;
                 const int here = (int)min(ee - pe, (int64_t)kPass);
 #pragma unroll
