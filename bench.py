@@ -48,10 +48,10 @@ from paper_1405_7461_gb300 import workloads  # noqa: E402
 # C 6, discriminant 3.
 FLOPS_PER_PAIR_FP64 = 32
 # Algorithmic FP32 flops per candidate pair in the filter kernel's sphere
-# pre-test, written as v = E_e + K_j - 2 (c_e . c_j + w_e w_j): one add and
-# four FMAs (9 flops); K_j is formed once per (query tile, query), E_e once
-# per entry when the index is built.
-FLOPS_PER_CANDIDATE_FP32 = 9
+# pre-test, written as v = E_e + K_j - 2 c_j . c_e: one add and three FMAs
+# (7 flops); K_j (with the pass's bound R_j^2) is formed once per (pass of
+# 128 entries, query), E_e once per entry when the index is built.
+FLOPS_PER_CANDIDATE_FP32 = 7
 # Peaks from unit counts and clocks (152 SMs, 2070 MHz): FP64 2 DFMA/clk/SM
 # (the 1.25 TFLOP/s nominal figure), FP32 128 FFMA/clk/SM.
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
