@@ -263,9 +263,12 @@ def roofline(mode, tot, n_launch):
     if kern_ms <= 0:
         return None
     achieved = work / (kern_ms / 1e3) / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_record(mode), "kernel": kernel, "kernel_ms_avg": kern_ms, "work_unit": per,
-            "peak_source": src}
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+         "traffic": traffic_record(mode), "kernel": kernel, "kernel_ms_avg": kern_ms, "work_unit": per,
+         "peak_source": src}
+    if mode != "fp64":
+        r["refine_kernel_ms_avg"] = tot["refine_ms"] / n_launch
+    return r
 
 
 def concat_thresholds(w):
@@ -460,7 +463,7 @@ def main():
 
     def step(mode):
         t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0,
-             "survivors": 0}
+             "survivors": 0, "refine_ms": 0.0}
         if mode == "batched":
             cnt = plan.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
             stats = [plan.stats()]
@@ -477,6 +480,7 @@ def main():
             t["survivors"] += s["filter_survivors"]
             t["launches"] += s["kernel_launches"]
             t["kernel_ms"] += s["pair_kernel_ms"]
+            t["refine_ms"] += s["refine_ms"]
         return t
 
     def timed(mode):

@@ -116,9 +116,12 @@ typedef struct {
     uint64_t results;           /* pairs within d (alpha * interactions) */
     uint64_t work_items;        /* (query tile, entry chunk) work items */
     uint64_t kernel_launches;   /* CUDA kernels the library launched for the search */
-    double pair_kernel_ms;      /* device time of the pair kernel (CUDA events) */
+    double pair_kernel_ms;      /* device time of the pair kernel (CUDA events; filter mode: the FP32
+                                   pre-test kernel) */
     double total_ms;            /* device time of the whole search on its stream */
     uint64_t filter_survivors;  /* filter mode: pairs that passed the FP32 pre-test (0 in FP64 mode) */
+    double refine_ms;           /* filter mode: device time of the FP64 refine kernel (pair_kernel_ms then
+                                   covers the FP32 pre-test kernel alone) */
 } tdq_stats;
 
 /*

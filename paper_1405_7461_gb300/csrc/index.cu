@@ -239,7 +239,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     cudaDeviceGetAttribute(&idx->sm_count, cudaDevAttrMultiProcessorCount, idx->device);
     idx->n = n;
     idx->m = m;
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < kSearchEvents; k++) {
         if (cudaEventCreate(&idx->ws.ev[k]) != cudaSuccess) {
             tdq_index_free(idx);
             return set_error(TDQ_ERR_CUDA, "tdq_build_index: cudaEventCreate failed");
@@ -447,7 +447,7 @@ extern "C" void tdq_index_free(tdq_index *idx)
     workspace_streams_free(w);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
-    for (int k = 0; k < 4; k++)
+    for (int k = 0; k < kSearchEvents; k++)
         if (w.ev[k]) cudaEventDestroy(w.ev[k]);
     cudaFree(idx->e_block);
     cudaFree(idx->b_block);

@@ -153,7 +153,7 @@ void plan_release(tdq_plan *p)
     cudaFree(w.s_block);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
-    for (int k = 0; k < 4; k++)
+    for (int k = 0; k < kSearchEvents; k++)
         if (w.ev[k]) cudaEventDestroy(w.ev[k]);
     workspace_streams_free(w);
     cudaFree(p->stage_block);
@@ -193,7 +193,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
             st = set_error(TDQ_ERR_NOMEM, "tdq_plan_create: allocation failed");
             break;
         }
-        for (int k = 0; k < 4 && st == TDQ_OK; k++)
+        for (int k = 0; k < kSearchEvents && st == TDQ_OK; k++)
             if (cudaEventCreate(&w.ev[k]) != cudaSuccess) st = set_error(TDQ_ERR_CUDA, "tdq_plan_create: events");
         if (st != TDQ_OK) break;
         if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -845,8 +845,10 @@ size_t pair_smem_bytes(uint32_t chunk)
 // CTAs as fit on every SM at once).  Filter mode: the FP32 pre-test kernel,
 // then the FP64 refine kernel over its survivors.  Neither counts the
 // overlapping pairs: launch_overlap_count does.
+// mid (filter mode, may be null): event recorded between the filter and the
+// refine kernel with the flags evflags.
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
-                               cudaStream_t stream)
+                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags)
 {
     if (filter) {
         FilterArgs fa{pa, surv, surv_cap};
@@ -856,6 +858,7 @@ cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, ui
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         traj_dist_filter_kernel<<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
+        if (mid && (e = cudaEventRecordWithFlags(mid, stream, evflags)) != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_refine_kernel, kPairThreads, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
@@ -1023,13 +1026,15 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
             if ((e = cudaEventRecord(w.join, w.side)) != cudaSuccess) return e;
         }
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
-        if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream)) != cudaSuccess)
+        if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
+                                    events ? w.ev[2] : nullptr, evflags)) != cudaSuccess)
             return e;
-        if (events && (e = cudaEventRecordWithFlags(w.ev[2], stream, evflags)) != cudaSuccess) return e;
+        if (events && (e = cudaEventRecordWithFlags(cfg.filter ? w.ev[4] : w.ev[2], stream, evflags)) != cudaSuccess)
+            return e;
         if (cfg.filter && (e = cudaStreamWaitEvent(stream, w.join, 0)) != cudaSuccess) return e;
     } else if (events) {
-        if ((e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
-        if ((e = cudaEventRecordWithFlags(w.ev[2], stream, evflags)) != cudaSuccess) return e;
+        for (int k : {1, 2, 4})
+            if ((e = cudaEventRecordWithFlags(w.ev[k], stream, evflags)) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return e;
@@ -1062,6 +1067,7 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
     if (events) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) s->pair_kernel_ms = ms;
+        if (cfg.filter && cudaEventElapsedTime(&ms, w.ev[2], w.ev[4]) == cudaSuccess) s->refine_ms = ms;
         if (cudaEventElapsedTime(&ms, w.ev[0], w.ev[3]) == cudaSuccess) s->total_ms = ms;
     }
     *count = h.results;
@@ -1518,7 +1524,7 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
                                                                  s->tile_work);
         TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
         PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk};
-        TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream));
+        TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream, nullptr, 0));
     }
     TDQ_CUDA(cudaGetLastError());
     DevCounters h{};

@@ -118,6 +118,8 @@ struct QuerySoA {
     float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
 };
 
+constexpr int kSearchEvents = 5;
+
 struct Workspace {
     uint64_t q_cap = 0;    // queries the buffers below hold
     void *q_block = nullptr;
@@ -154,7 +156,9 @@ struct Workspace {
     uint64_t s_cap_pairs = 0;
     void *s_block = nullptr;
     uint2 *surv = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // search start, pair kernel start, pair kernel end (filter mode: filter
+    // kernel end), search end, refine kernel end
+    cudaEvent_t ev[kSearchEvents] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 }  // namespace tdq
