@@ -88,7 +88,7 @@ __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, E
     // pre-test's per-entry term E = |c|^2 (1 - 2^-20), rounded down (the
     // squares of floats are exact in FP64).
     double hx = 0.5 * (in.c[4][i] - xs), hy = 0.5 * (in.c[5][i] - ys), hz = 0.5 * (in.c[6][i] - zs);
-    const float4 sp = sphere32(xs + hx, ys + hy, zs + hz, sqrt(hx * hx + hy * hy + hz * hz), 0.0);
+    const float4 sp = sphere32(xs + hx, ys + hy, zs + hz, norm_ru(hx, hy, hz), 0.f);
     if (isinf(sp.w)) {
         e.sph[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         e.sph_e[k] = __int_as_float(0xff800000);  // -inf: never rejected

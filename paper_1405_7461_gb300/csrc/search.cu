@@ -62,7 +62,14 @@ struct BinView {
     const int64_t *bin_begin, *bin_pmax_key;
     double t_min, width;
     uint32_t m;
+    float inv_width_f;  // 1 / width in FP32 (for sort keys only)
 };
+
+inline BinView bin_view(const tdq_index *idx)
+{
+    return BinView{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m,
+                   idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
+}
 
 // Validate and clip every query segment.  pre[] columns: px py pz vx vy vz d2
 // ts_key te_key (keys stored bitwise in the double arrays).
@@ -118,14 +125,21 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
         // d (and a relative 2^-30 of d): the pre-test of the filter mode
         float4 sp = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
         if (valid) {
-            double h = 0.5 * (key_double(ce) - key_double(cs));
-            double vn = sqrt(vx * vx + vy * vy + vz * vz);
-            sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), vn * h, fma(d, 0x1p-30, d));
+            const double h = 0.5 * (key_double(ce) - key_double(cs));
+            const float dw = __double2float_ru(d);
+            sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), __fmul_ru(norm_ru(vx, vy, vz),
+                          __double2float_ru(h)), __fmaf_ru(dw, 0x1p-30f, dw));
         }
         pre_sph[i] = sp;
-        // sort key: the temporal bin of the clipped start (tiles of 32 sorted
-        // query segments then span few bins); invalid segments sort last
-        keys[i] = valid ? (uint64_t)bin_of(key_double(cs), bins.t_min, bins.width, bins.m) : (uint64_t)bins.m;
+        // sort key: the temporal bin of the clipped start, in FP32 (it only
+        // groups the segments into tiles of 32 that span few bins); invalid
+        // segments sort last
+        uint64_t key = bins.m;
+        if (valid) {
+            const float f = floorf(__double2float_rn(key_double(cs) - bins.t_min) * bins.inv_width_f);
+            key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
+        }
+        keys[i] = key;
         vals[i] = (uint32_t)i;
     }
     unsigned vm = __ballot_sync(kFull, valid);
@@ -1005,7 +1019,7 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     if (e != cudaSuccess) return e;
     if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, evflags)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
-    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    const BinView bins = bin_view(idx);
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
@@ -1120,7 +1134,7 @@ cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
                         const QueryInput &in, uint64_t nq)
 {
-    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    const BinView bins = bin_view(idx);
     double *const *pre = w.pre_dev;
     {
         QueryInput a0 = in;
@@ -1512,7 +1526,7 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     in.t1 = t1;
     // the array keeps the previous call's contents: clear the counters
     TDQ_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), stream));
-    BinView bins{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m};
+    const BinView bins = bin_view(idx);
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr);
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {

@@ -57,26 +57,34 @@ __device__ __forceinline__ bool lt0(double x)  // x < 0
 __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }  // x >= 0
 
 // ---------------------------------------------------------------------------
-// Conservative FP32 bounding sphere of a segment piece whose FP64 center is
-// (cx,cy,cz) and radius r, for the filter mode's pre-test.  The center is
-// rounded to nearest.  The radius w is widened by 2^-22 * max|c| (more than
-// the sqrt(3) * 2^-24 * max|c| the center's rounding can move it, and more
-// than any FP64 rounding of the positions the FP64 path evaluates), by
-// r * 2^-40, by `extra` (the threshold d, for a query) and by 2^-60 (so that
-// w > 0 and w^2 stays a normal number), then scaled by (1 + 2^-20) and
-// rounded up.  Magnitudes beyond 2^60 get an infinite radius, which never
-// rejects.
-__device__ __forceinline__ float4 sphere32(double cx, double cy, double cz, double r, double extra)
+// FP32 upper bound of sqrt(a^2 + b^2 + c^2) (every rounding upward).
+__device__ __forceinline__ float norm_ru(double a, double b, double c)
 {
-    double m = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
-    float fr;
-    if (m < 0x1p60 && r < 0x1p60 && extra < 0x1p60) {
-        double w = fma(r, 0x1p-40, r) + fma(m, 0x1p-22, extra) + 0x1p-60;
-        fr = __double2float_ru(fma(w, 0x1p-20, w));
-    } else {
-        fr = __int_as_float(0x7f800000);
+    const float x = __double2float_ru(fabs(a)), y = __double2float_ru(fabs(b)), z = __double2float_ru(fabs(c));
+    return __fsqrt_ru(__fmaf_ru(z, z, __fmaf_ru(y, y, __fmul_ru(x, x))));
+}
+
+// Conservative FP32 bounding sphere of a segment piece whose FP64 center is
+// (cx,cy,cz) and whose radius is at most r (r and extra are FP32 upper
+// bounds), for the filter mode's pre-test.  The center is rounded to
+// nearest.  The radius w is widened by 2^-22 * max|c| (more than the
+// sqrt(3) * 2^-24 * max|c| the center's rounding can move it, and more than
+// any FP64 rounding of the positions the FP64 path evaluates; max|c| is
+// bounded through the rounded center, |c| <= |c~| (1 + 2^-23)), by r * 2^-40,
+// by `extra` (the threshold d, for a query) and by 2^-60 (so that w > 0 and
+// w^2 stays a normal number), then scaled by (1 + 2^-20); every rounding of
+// w is upward.  Magnitudes beyond 2^60 get an infinite radius, which never
+// rejects.
+__device__ __forceinline__ float4 sphere32(double cx, double cy, double cz, float r, float extra)
+{
+    const float x = __double2float_rn(cx), y = __double2float_rn(cy), z = __double2float_rn(cz);
+    const float m = __fmul_ru(fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))), 1.0f + 0x1p-23f);
+    float fr = __int_as_float(0x7f800000);
+    if (m < 0x1p60f && r < 0x1p60f && extra < 0x1p60f) {
+        const float w = __fadd_ru(__fadd_ru(__fmaf_ru(r, 0x1p-40f, r), __fmaf_ru(m, 0x1p-22f, extra)), 0x1p-60f);
+        fr = __fmaf_ru(w, 0x1p-20f, w);
     }
-    return make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz), fr);
+    return make_float4(x, y, z, fr);
 }
 
 // Device-side counters of one search, cleared by one memset per search.
