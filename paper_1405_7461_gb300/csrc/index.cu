@@ -143,6 +143,21 @@ __global__ void bin_assign(const int64_t *ts_key, const int64_t *te_key, uint64_
     atomicMax((long long *)&bin_end_key[bk], (long long)te_key[k]);
 }
 
+// Bin table over the sorted t_end keys: te_bin_begin[b] = first position
+// whose t_end lies in a bin >= b (same bins and bin function as the t_start
+// table, so that a count of t_end <= t narrows to the bin of t).
+__global__ void te_bin_assign(const int64_t *te_sorted, uint64_t n, double t_min, double width, uint32_t m,
+                              int64_t *te_bin_begin)
+{
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t bk = bin_of(key_double(te_sorted[k]), t_min, width, m);
+    int64_t bprev = (k == 0) ? -1 : bin_of(key_double(te_sorted[k - 1]), t_min, width, m);
+    for (int64_t j = bprev + 1; j <= bk; j++) te_bin_begin[j] = (int64_t)k;
+    if (k == n - 1)
+        for (int64_t j = bk + 1; j <= (int64_t)m; j++) te_bin_begin[j] = (int64_t)n;
+}
+
 // Prefix maximum of the bin ends (one block).
 __global__ void __launch_bounds__(1024) bin_prefix_max(const int64_t *bin_end_key, uint32_t m, int64_t *pmax)
 {
@@ -246,7 +261,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         }
     }
     if (dev_alloc(&idx->ws.ctr, sizeof(DevCounters)) != cudaSuccess ||
-        host_alloc(&idx->ws.ctr_host, sizeof(DevCounters)) != cudaSuccess) {
+        host_alloc_mapped(&idx->ws.ctr_host, &idx->ws.ctr_host_dev, sizeof(DevCounters)) != cudaSuccess) {
         tdq_index_free(idx);
         return set_error(TDQ_ERR_NOMEM, "tdq_build_index: counter allocation failed");
     }
@@ -257,7 +272,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
 
     // Resident sorted copy + bin table.
     uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 4) + carve_bytes(n, 16);
-    uint64_t bbytes = carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
+    uint64_t bbytes = 2 * carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (dev_alloc(&idx->e_block, ebytes) != cudaSuccess || dev_alloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
         tdq_index_free(idx);
@@ -278,6 +293,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         idx->bin_begin = carve<int64_t>(q, m + 1);
         idx->bin_end_key = carve<int64_t>(q, m);
         idx->bin_pmax_key = carve<int64_t>(q, m);
+        idx->te_bin_begin = carve<int64_t>(q, m + 1);
     }
 
     // Temporary build memory: staged input (host case), sort buffers, scratch.
@@ -380,6 +396,8 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             break;
         }
         te_store<<<grid_for(n), kBlock, 0, stream>>>(keys, n, idx->e.te_sorted);
+        te_bin_assign<<<grid_for(n), kBlock, 0, stream>>>(idx->e.te_sorted, n, idx->t_min, idx->width, m,
+                                                          idx->te_bin_begin);
         if (cudaStreamSynchronize(stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: index kernels");
             break;
@@ -444,7 +462,6 @@ extern "C" void tdq_index_free(tdq_index *idx)
     cudaFree(w.sort_hist);
     cudaFree(w.r_block);
     cudaFree(w.s_block);
-    workspace_streams_free(w);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < kSearchEvents; k++)

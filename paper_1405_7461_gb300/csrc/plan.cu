@@ -155,7 +155,6 @@ void plan_release(tdq_plan *p)
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < kSearchEvents; k++)
         if (w.ev[k]) cudaEventDestroy(w.ev[k]);
-    workspace_streams_free(w);
     cudaFree(p->stage_block);
     cudaFree(p->r_block);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -186,7 +185,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
     do {
         Workspace &w = p->ws;
         bool ok = dev_alloc(&w.ctr, sizeof(DevCounters)) == cudaSuccess &&
-                  host_alloc(&w.ctr_host, sizeof(DevCounters)) == cudaSuccess &&
+                  host_alloc_mapped(&w.ctr_host, &w.ctr_host_dev, sizeof(DevCounters)) == cudaSuccess &&
                   dev_alloc(&p->stage_block, 3 * p->cap_q * 8) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
@@ -203,8 +202,6 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
         p->d_arr = (double *)p->stage_block;
         p->t0_arr = p->d_arr + p->cap_q;
         p->t1_arr = p->t0_arr + p->cap_q;
-        st = workspace_streams(w);
-        if (st != TDQ_OK) break;
         st = ensure_queries(w, p->cap_q);
         if (st != TDQ_OK) break;
         const uint64_t rc = params->result_capacity ? params->result_capacity : (idx->n > 65536 ? idx->n : 65536);
@@ -279,7 +276,7 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
                 tdq_status st = capture(p, cls, &G);
                 if (st != TDQ_OK) return st;
             }
-            TDQ_CUDA(bind_inputs(G->exec, G->nodes, p->idx, w, in, cls));
+            TDQ_CUDA(bind_inputs(G->exec, G->nodes, p->idx, w, in, cls, p->cfg));
             TDQ_CUDA(cudaGraphLaunch(G->exec, stream));
         } else {
             QueryInput direct = in;

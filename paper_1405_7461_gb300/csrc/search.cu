@@ -6,10 +6,12 @@
 //                 start position at the clipped start, sort key
 //   radix sort    query segments by clipped start (Sec. 4 sorts Q by t_start)
 //   query_gather  sorted query SoA + candidate range [lo, hi) of sorted entry
-//                 positions per query segment, from the bin table
-//   tile_plan     tiles of 32 consecutive sorted query segments; a tile's
-//                 range is the union of its members' ranges, cut into chunks
-//                 of `entry_chunk` entries; one work item per (tile, chunk)
+//                 positions per query segment, from the bin table; one warp
+//                 per tile of 32 consecutive sorted query segments also
+//                 plans the tile: its range is the union of its members'
+//                 ranges, cut into chunks of `entry_chunk` entries, one work
+//                 item per (tile, chunk); filter mode: the exact number of
+//                 temporal-overlap pairs of each query segment
 //   scan          work-item offsets per tile
 //   traj_dist_search_kernel
 //                 persistent CTAs take work items from an atomic counter,
@@ -60,6 +62,7 @@ __device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, 
 
 struct BinView {
     const int64_t *bin_begin, *bin_pmax_key;
+    const int64_t *ts_key, *te_sorted, *te_bin_begin;  // sorted t_start / t_end keys and the t_end bin table
     double t_min, width;
     uint32_t m;
     float inv_width_f;  // 1 / width in FP32 (for sort keys only)
@@ -67,8 +70,8 @@ struct BinView {
 
 inline BinView bin_view(const tdq_index *idx)
 {
-    return BinView{idx->bin_begin, idx->bin_pmax_key, idx->t_min, idx->width, idx->m,
-                   idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
+    return BinView{idx->bin_begin, idx->bin_pmax_key, idx->e.ts_key, idx->e.te_sorted, idx->te_bin_begin,
+                   idx->t_min, idx->width, idx->m, idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
 }
 
 // Validate and clip every query segment.  pre[] columns: px py pz vx vy vz d2
@@ -80,6 +83,7 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
     bool valid = false;
     // slots at or beyond the device-side count are padding: empty, not errors
     const uint64_t nreal = in.n_real ? in.n_real : nq;
+    if (i == 0) ctr->sort_n = nreal < nq ? nreal : nq;
     if (i < nq && i >= nreal) {
         pre[7][i] = __longlong_as_double(INT64_MAX);
         pre[8][i] = __longlong_as_double(INT64_MIN);
@@ -146,72 +150,127 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
     if ((threadIdx.x & 31) == 0 && vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
 }
 
-// Sorted query SoA and the candidate range of each query segment.
-__global__ void query_gather(const double *const *pre, const float4 *pre_sph, const int64_t *seg_id,
-                             const uint32_t *order, uint64_t nq, const DevCounters *ctr, BinView bins, QuerySoA q)
+// Copy of the search's counters into the caller-visible pinned host mirror
+// (one warp; the counters are a few words).  A kernel, not a copy node: in a
+// replayed graph the copy engine's round trip costs more than this launch.
+static_assert(sizeof(DevCounters) % 8 == 0, "counters are copied as 64-bit words");
+__global__ void publish_counters(const DevCounters *src, DevCounters *dst)
 {
-    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nq || k >= ctr->valid_queries) return;
-    uint32_t i = order[k];
-    q.px[k] = pre[0][i]; q.py[k] = pre[1][i]; q.pz[k] = pre[2][i];
-    q.vx[k] = pre[3][i]; q.vy[k] = pre[4][i]; q.vz[k] = pre[5][i];
-    q.d2[k] = pre[6][i];
-    int64_t cs = __double_as_longlong(pre[7][i]);
-    int64_t ce = __double_as_longlong(pre[8][i]);
-    q.ts_key[k] = cs;
-    q.te_key[k] = ce;
-    q.qid[k] = seg_id[i];
-    q.sph[k] = pre_sph[i];
-    // First bin whose extent reaches past the query start: the prefix maximum
-    // of bin ends is non-decreasing, so this is a binary search (Sec. 4 uses
-    // an index tree over the bin extents for the same lookup).
-    uint32_t lo = 0, hi = bins.m;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (bins.bin_pmax_key[mid] > cs) hi = mid; else lo = mid + 1;
-    }
-    int64_t jlo = lo;
-    // Last bin that can hold an entry starting before the query end.
-    double te = key_double(ce);
-    int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
-    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
-    if (jlo < (int64_t)bins.m && jlo <= jhi) {
-        rlo = bins.bin_begin[jlo];
-        rhi = bins.bin_begin[jhi + 1];
-        if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
-    }
-    q.lo[k] = rlo;
-    q.hi[k] = rhi;
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / 8); i += 32) d[i] = s[i];
 }
 
-// One warp per tile of kQT sorted query segments.
-__global__ void tile_plan(const QuerySoA q, uint64_t ntiles, const DevCounters *ctr, uint32_t chunk,
-                          int64_t *tile_lo, int64_t *tile_hi, unsigned long long *tile_work)
+// Arguments of query_gather (one struct, so that a captured launch can be
+// re-bound to new inputs in one step).
+struct GatherArgs {
+    const double *const *pre;
+    const float4 *pre_sph;
+    const int64_t *seg_id;
+    const uint32_t *order;
+    uint64_t nq;
+    DevCounters *ctr;
+    BinView bins;
+    QuerySoA q;
+    uint64_t ntiles;
+    uint32_t chunk;
+    int64_t *tile_lo, *tile_hi;
+    unsigned long long *tile_work;  // chunks per tile (the scan turns it into offsets); ntiles + 1
+    bool count_overlaps;
+};
+
+// First position in keys[lo, hi) whose key is >= x (strict: > x).
+__device__ __forceinline__ int64_t lower_bound_key(const int64_t *keys, int64_t lo, int64_t hi, int64_t x, bool strict)
 {
-    uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (t >= ntiles) return;
-    uint64_t nv = ctr->valid_queries;
-    uint64_t k = t * kQT + lane;
-    int64_t lo = INT64_MAX, hi = INT64_MIN;
-    if (k < nv) { lo = q.lo[k]; hi = q.hi[k]; }
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int64_t v = keys[mid];
+        if (v < x || (strict && v == x)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Sorted query SoA and the candidate range of each query segment; then, one
+// warp per tile of kQT sorted query segments, the tile plan; in filter mode
+// also the exact number of temporal-overlap pairs of each query segment:
+// #{t_start < q.t_end} - #{t_end <= q.t_start} (the second set lies inside
+// the first because t_end > t_start).  The bin function is monotone in time,
+// so each count lies inside the bin of its bound: a short binary search in
+// the sorted t_start keys (bin table bin_begin) and in the sorted t_end keys
+// (bin table te_bin_begin).
+__global__ void query_gather(GatherArgs a)
+{
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const BinView &bins = a.bins;
+    QuerySoA &q = a.q;
+    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
+    unsigned long long n_overlap = 0;
+    if (k < a.nq && k < a.ctr->valid_queries) {
+        const uint32_t i = a.order[k];
+        q.px[k] = a.pre[0][i]; q.py[k] = a.pre[1][i]; q.pz[k] = a.pre[2][i];
+        q.vx[k] = a.pre[3][i]; q.vy[k] = a.pre[4][i]; q.vz[k] = a.pre[5][i];
+        q.d2[k] = a.pre[6][i];
+        const int64_t cs = __double_as_longlong(a.pre[7][i]);
+        const int64_t ce = __double_as_longlong(a.pre[8][i]);
+        q.ts_key[k] = cs;
+        q.te_key[k] = ce;
+        q.qid[k] = a.seg_id[i];
+        q.sph[k] = a.pre_sph[i];
+        // First bin whose extent reaches past the query start: the prefix
+        // maximum of bin ends is non-decreasing, so this is a binary search
+        // (Sec. 4 uses an index tree over the bin extents for the same lookup).
+        uint32_t lo = 0, hi = bins.m;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (bins.bin_pmax_key[mid] > cs) hi = mid; else lo = mid + 1;
+        }
+        const int64_t jlo = lo;
+        // Last bin that can hold an entry starting before the query end.
+        const double te = key_double(ce);
+        const int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
+        if (jlo < (int64_t)bins.m && jlo <= jhi) {
+            rlo = bins.bin_begin[jlo];
+            rhi = bins.bin_begin[jhi + 1];
+            if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
+        }
+        q.lo[k] = rlo;
+        q.hi[k] = rhi;
+        if (a.count_overlaps && jhi >= 0) {
+            const int64_t n_start = lower_bound_key(bins.ts_key, bins.bin_begin[jhi], bins.bin_begin[jhi + 1], ce,
+                                                    false);
+            const double ts = key_double(cs);
+            int64_t n_end = 0;
+            if (!le0(ts - bins.t_min)) {
+                const int64_t b = bin_of(ts, bins.t_min, bins.width, bins.m);
+                n_end = lower_bound_key(bins.te_sorted, bins.te_bin_begin[b], bins.te_bin_begin[b + 1], cs, true);
+            }
+            n_overlap = (unsigned long long)(n_start - n_end);
+        }
+    }
+    // the tile plan: this warp's 32 sorted query segments are tile k / kQT
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, (int64_t)__shfl_xor_sync(kFull, (long long)lo, o));
-        hi = max(hi, (int64_t)__shfl_xor_sync(kFull, (long long)hi, o));
+        rlo = min(rlo, (int64_t)__shfl_xor_sync(kFull, (long long)rlo, o));
+        rhi = max(rhi, (int64_t)__shfl_xor_sync(kFull, (long long)rhi, o));
+        n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
     }
+    const uint64_t t = k / kQT;
     if (lane == 0) {
-        unsigned long long w = 0;
-        if (hi > lo) {
-            w = (unsigned long long)((hi - lo + chunk - 1) / chunk);
-        } else {
-            lo = 0;
-            hi = 0;
+        if (n_overlap) atomicAdd(&a.ctr->overlap_pairs, n_overlap);
+        if (t < a.ntiles) {
+            unsigned long long w = 0;
+            if (rhi > rlo) {
+                w = (unsigned long long)((rhi - rlo + a.chunk - 1) / a.chunk);
+            } else {
+                rlo = 0;
+                rhi = 0;
+            }
+            a.tile_lo[t] = rlo;
+            a.tile_hi[t] = rhi;
+            a.tile_work[t] = w;
+            if (t == 0) a.tile_work[a.ntiles] = 0;  // the scan turns this slot into the total
         }
-        tile_lo[t] = lo;
-        tile_hi[t] = hi;
-        tile_work[t] = w;
-        if (t == 0) tile_work[ntiles] = 0;  // the scan turns this slot into the total
     }
 }
 
@@ -678,36 +737,6 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
     if (lane == 0 && n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
 }
 
-// Exact number of temporal-overlap pairs of each query segment: entries
-// with t_start < q.t_end minus entries with t_end <= q.t_start (the second
-// set lies inside the first because t_end > t_start), by binary searches in
-// the sorted t_start keys and the sorted t_end keys.
-__global__ void count_overlaps(const QuerySoA q, const int64_t *ts_sorted, const int64_t *te_sorted, uint64_t n,
-                               DevCounters *ctr)
-{
-    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long c = 0;
-    if (k < ctr->valid_queries) {
-        const int64_t cs = q.ts_key[k], ce = q.te_key[k];
-        uint64_t lo = 0, hi = n;  // first t_start >= ce
-        while (lo < hi) {
-            uint64_t mid = (lo + hi) >> 1;
-            if (ts_sorted[mid] < ce) lo = mid + 1; else hi = mid;
-        }
-        const uint64_t n1 = lo;
-        lo = 0;
-        hi = n;  // first t_end > cs
-        while (lo < hi) {
-            uint64_t mid = (lo + hi) >> 1;
-            if (te_sorted[mid] <= cs) lo = mid + 1; else hi = mid;
-        }
-        c = (unsigned long long)(n1 - lo);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->overlap_pairs, c);
-}
-
 // GPUTrajDistSearch (Sec. 5, Algorithm 1), tiled: one work item is a tile of
 // 32 sorted query segments against a chunk of the tile's candidate entries.
 // Every temporal-overlap pair is evaluated in FP64 (the plain method).
@@ -858,7 +887,7 @@ size_t pair_smem_bytes(uint32_t chunk)
 // Launch the pair kernel of the requested mode as a persistent grid (as many
 // CTAs as fit on every SM at once).  Filter mode: the FP32 pre-test kernel,
 // then the FP64 refine kernel over its survivors.  Neither counts the
-// overlapping pairs: launch_overlap_count does.
+// overlapping pairs: query_gather does.
 // mid (filter mode, may be null): event recorded between the filter and the
 // refine kernel with the flags evflags.
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
@@ -893,11 +922,6 @@ cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_overlap_count(const PairArgs &pa, uint64_t nq, uint64_t n, cudaStream_t stream)
-{
-    count_overlaps<<<grid_for(nq), kBlock, 0, stream>>>(pa.q, pa.e.ts_key, pa.e.te_sorted, n, pa.ctr);
-    return cudaGetLastError();
-}
 
 template <typename T>
 T *carve(char *&p, uint64_t count)
@@ -1001,9 +1025,9 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
 
 int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
 {
-    // query_prep; with entries: the sort of the query keys, query_gather,
-    // tile_plan, scan, pair kernel (filter mode: filter, refine, overlap count)
-    return idx->n > 0 ? 1 + sort_kernel_launches(nq, bin_key_bits(idx->m)) + 3 + (cfg.filter ? 3 : 1) : 1;
+    // query_prep and publish_counters; with entries: the sort of the query
+    // keys, query_gather, scan, pair kernel (filter mode: filter and refine)
+    return idx->n > 0 ? 2 + sort_kernel_launches(nq, bin_key_bits(idx->m)) + 2 + (cfg.filter ? 2 : 1) : 2;
 }
 
 // Events are recorded as external event-record nodes when the stream is being
@@ -1024,34 +1048,24 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
         if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
-                                  bin_key_bits(idx->m))) != cudaSuccess)
+                                  bin_key_bits(idx->m), &w.ctr->sort_n)) != cudaSuccess)
             return e;
-        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q);
-        tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(w.q, ntiles, w.ctr, cfg.chunk, w.tile_lo, w.tile_hi,
-                                                                 w.tile_work);
+        const GatherArgs ga{pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q, ntiles, cfg.chunk,
+                            w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
+        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
         if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk};
-        if (cfg.filter) {
-            // fork: the overlap count needs only the sorted queries, so it
-            // runs beside the pair kernels on the side stream
-            if ((e = cudaEventRecord(w.fork, stream)) != cudaSuccess) return e;
-            if ((e = cudaStreamWaitEvent(w.side, w.fork, 0)) != cudaSuccess) return e;
-            if ((e = launch_overlap_count(pa, nq, idx->n, w.side)) != cudaSuccess) return e;
-            if ((e = cudaEventRecord(w.join, w.side)) != cudaSuccess) return e;
-        }
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
                                     events ? w.ev[2] : nullptr, evflags)) != cudaSuccess)
             return e;
         if (events && (e = cudaEventRecordWithFlags(cfg.filter ? w.ev[4] : w.ev[2], stream, evflags)) != cudaSuccess)
             return e;
-        if (cfg.filter && (e = cudaStreamWaitEvent(stream, w.join, 0)) != cudaSuccess) return e;
     } else if (events) {
         for (int k : {1, 2, 4})
             if ((e = cudaEventRecordWithFlags(w.ev[k], stream, evflags)) != cudaSuccess) return e;
     }
-    if ((e = cudaMemcpyAsync(w.ctr_host, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        return e;
+    publish_counters<<<1, 32, 0, stream>>>(w.ctr, w.ctr_host_dev);
     if (events && (e = cudaEventRecordWithFlags(w.ev[3], stream, evflags)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1088,27 +1102,6 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
     return h.results > capacity ? TDQ_ERR_OVERFLOW : TDQ_OK;
 }
 
-tdq_status workspace_streams(Workspace &w)
-{
-    if (w.side) return TDQ_OK;
-    if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming) != cudaSuccess) {
-        workspace_streams_free(w);
-        return cuda_error(cudaGetLastError(), "search workspace: streams");
-    }
-    return TDQ_OK;
-}
-
-void workspace_streams_free(Workspace &w)
-{
-    if (w.side) cudaStreamDestroy(w.side);
-    if (w.fork) cudaEventDestroy(w.fork);
-    if (w.join) cudaEventDestroy(w.join);
-    w.side = nullptr;
-    w.fork = w.join = nullptr;
-}
-
 cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
 {
     size_t n = 0;
@@ -1132,7 +1125,7 @@ cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
 }
 
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
-                        const QueryInput &in, uint64_t nq)
+                        const QueryInput &in, uint64_t nq, const LaunchCfg &cfg)
 {
     const BinView bins = bin_view(idx);
     double *const *pre = w.pre_dev;
@@ -1156,15 +1149,9 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
         if (e != cudaSuccess) return e;
     }
     {
-        double *const *a0 = pre;
-        const float4 *a1 = w.pre_sph;
-        const int64_t *a2 = in.seg_id;
-        const uint32_t *a3 = w.vals;
-        uint64_t a4 = nq;
-        const DevCounters *a5 = w.ctr;
-        BinView a6 = bins;
-        QuerySoA a7 = w.q;
-        void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
+        GatherArgs a0{pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q, (nq + kQT - 1) / kQT, cfg.chunk,
+                      w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
+        void *args[] = {&a0};
         cudaKernelNodeParams kp{};
         kp.func = (void *)query_gather;
         kp.gridDim = dim3(grid_for(nq));
@@ -1222,8 +1209,6 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     in.t0_arr = spec.t0_arr;
     in.t1_arr = spec.t1_arr;
     in.n_real = 0;
-    st = workspace_streams(w);
-    if (st != TDQ_OK) return st;
 
     if (cfg.filter && idx->n > 0) {
         st = ensure_survivors(w, w.s_cap_pairs ? w.s_cap_pairs : (nq * 64 > (1u << 20) ? nq * 64 : (1u << 20)));
@@ -1532,10 +1517,9 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream,
                                   bin_key_bits(idx->m)));
-        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(s->pre_dev, s->pre_sph, in.seg_id, s->vals, nq, s->ctr,
-                                                          bins, s->q);
-        tile_plan<<<grid_for(ntiles * 32), kBlock, 0, stream>>>(s->q, ntiles, s->ctr, chunk, s->tile_lo, s->tile_hi,
-                                                                 s->tile_work);
+        const GatherArgs ga{s->pre_dev, s->pre_sph, in.seg_id, s->vals, nq, s->ctr, bins, s->q, ntiles, chunk,
+                            s->tile_lo, s->tile_hi, s->tile_work, false};
+        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
         TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
         PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk};
         TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream, nullptr, 0));

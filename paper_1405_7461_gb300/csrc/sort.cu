@@ -25,11 +25,19 @@ inline int items_for(uint64_t n) { return n <= kSmallSort ? 4 : 16; }
 constexpr uint32_t kFusedTiles = 256;
 
 // kTileMajor: counts stored as hist[tile][digit], else hist[digit][tile].
+// Keys to sort: n, or the device count n_dev when given (never above n).
+__device__ __forceinline__ uint64_t sort_count(uint64_t n, const unsigned long long *n_dev)
+{
+    return n_dev && *n_dev < n ? *n_dev : n;
+}
+
 template <int kItems, bool kTileMajor>
-__global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restrict__ keys, uint64_t n, int shift,
+__global__ void __launch_bounds__(kThreads) radix_hist(const uint64_t *__restrict__ keys, uint64_t n_launch,
+                                                       const unsigned long long *n_dev, int shift,
                                                        uint32_t *__restrict__ hist, uint32_t ntiles)
 {
     constexpr int kTile = kThreads * kItems;
+    const uint64_t n = sort_count(n_launch, n_dev);
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -73,9 +81,12 @@ __device__ __forceinline__ uint32_t fused_offset(const uint32_t *__restrict__ hi
     return wbase + x - total + before;
 }
 
+// Tiles past the keys to sort only write zero counts (radix_hist) or do
+// nothing (radix_scatter).
 template <int kItems, bool kFused>
 __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__restrict__ keys,
-                                                          const uint32_t *__restrict__ vals, uint64_t n, int shift,
+                                                          const uint32_t *__restrict__ vals, uint64_t n_launch,
+                                                          const unsigned long long *n_dev, int shift,
                                                           const uint32_t *__restrict__ offsets, uint32_t ntiles,
                                                           uint64_t *__restrict__ keys_out,
                                                           uint32_t *__restrict__ vals_out)
@@ -85,7 +96,10 @@ __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__rest
     __shared__ uint32_t run[kRadix];
     __shared__ uint32_t wcnt[kWarps][kRadix];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    off[tid] = kFused ? fused_offset(offsets, ntiles, tid) : offsets[(uint64_t)tid * ntiles + blockIdx.x];
+    const uint64_t n = sort_count(n_launch, n_dev);
+    if ((uint64_t)blockIdx.x * kTile >= n) return;  // the whole block: no key of this tile is sorted
+    off[tid] = kFused ? fused_offset(offsets, (uint32_t)((n + kTile - 1) / kTile), tid)
+                      : offsets[(uint64_t)tid * ntiles + blockIdx.x];
     run[tid] = 0;
     const uint64_t base = (uint64_t)blockIdx.x * kTile;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -200,7 +214,7 @@ uint64_t sort_hist_words(uint64_t n)
 }
 
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
-                             uint32_t *hist, cudaStream_t stream, int key_bits)
+                             uint32_t *hist, cudaStream_t stream, int key_bits, const unsigned long long *n_dev)
 {
     if (n <= 1) return cudaSuccess;
     if (n > 0xffffffffULL) return cudaErrorInvalidValue;  // 32-bit offsets
@@ -213,21 +227,21 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     const bool fused = items == 4 && ntiles <= kFusedTiles;
     for (int shift = 0; shift < 8 * passes; shift += 8) {
         if (fused) {
-            radix_hist<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
-            radix_scatter<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k,
-                                                                     dst_v);
+            radix_hist<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, n, n_dev, shift, hist, ntiles);
+            radix_scatter<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, hist, ntiles,
+                                                                     dst_k, dst_v);
         } else {
             if (items == 4)
-                radix_hist<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+                radix_hist<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, n_dev, shift, hist, ntiles);
             else
-                radix_hist<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, shift, hist, ntiles);
+                radix_hist<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, n_dev, shift, hist, ntiles);
             scan_exclusive_block<uint32_t, 8><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
             if (items == 4)
-                radix_scatter<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles, dst_k,
-                                                                          dst_v);
+                radix_scatter<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, hist,
+                                                                          ntiles, dst_k, dst_v);
             else
-                radix_scatter<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, shift, hist, ntiles,
-                                                                           dst_k, dst_v);
+                radix_scatter<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, hist,
+                                                                           ntiles, dst_k, dst_v);
         }
         uint64_t *tk = src_k; src_k = dst_k; dst_k = tk;
         uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;

@@ -98,6 +98,7 @@ struct DevCounters {
     unsigned long long valid_queries;  // query segments with a non-empty clipped span
     unsigned long long work_items;
     unsigned long long survivors;      // filter mode: pairs that passed the FP32 pre-test
+    unsigned long long sort_n;         // query slots the sort covers (the real ones; padding follows them)
     unsigned int error;                // bit 0: invalid query input
     unsigned int pad;
 };
@@ -151,15 +152,12 @@ struct Workspace {
     uint32_t *sort_hist = nullptr;
     // counters + host mirror
     DevCounters *ctr = nullptr;
-    DevCounters *ctr_host = nullptr;  // pinned
+    DevCounters *ctr_host = nullptr;      // pinned, mapped into the device address space
+    DevCounters *ctr_host_dev = nullptr;  // device view of ctr_host (publish_counters writes it)
     // results owned by tdq_search (device)
     uint64_t r_cap = 0;
     void *r_block = nullptr;
     tdq_result_buffer r{};
-    // second stream and events for the overlap count, forked off the main
-    // stream and joined before the counters are read
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
     // filter mode: survivors of the FP32 pre-test (entry, query) positions
     uint64_t s_cap_pairs = 0;
     void *s_block = nullptr;
@@ -183,6 +181,7 @@ struct tdq_index {
     int64_t *bin_begin = nullptr;   // m + 1 sorted positions
     int64_t *bin_end_key = nullptr; // m, largest t_end key (INT64_MIN when empty)
     int64_t *bin_pmax_key = nullptr;// m, prefix max of bin_end_key
+    int64_t *te_bin_begin = nullptr;// m + 1: first position in e.te_sorted whose t_end lies in bin >= b
     tdq::Workspace ws;
     tdq_stats last{};
 };
@@ -217,9 +216,6 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                            const tdq_result_buffer &out, cudaStream_t stream, bool events);
 tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t nq,
                          uint64_t capacity, bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
-// Side stream and fork/join events of a workspace (created once).
-tdq_status workspace_streams(Workspace &w);
-void workspace_streams_free(Workspace &w);
 // The two kernels of a captured search that read the caller's input (query
 // preparation and gather); re-pointed per batch without re-capturing.
 struct GraphInputNodes {
@@ -227,7 +223,7 @@ struct GraphInputNodes {
 };
 cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out);
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
-                        const QueryInput &in, uint64_t nq);
+                        const QueryInput &in, uint64_t nq, const LaunchCfg &cfg);
 
 // Allocation gate (api.cu).  Every device and pinned-host allocation of the
 // library goes through dev_alloc / host_alloc; tdq_debug_fail_allocations
@@ -253,6 +249,21 @@ inline cudaError_t host_alloc(T **p, size_t bytes)
     }
     return cudaMallocHost((void **)p, bytes);
 }
+// Pinned host memory that kernels write directly; *dev receives its device view.
+template <typename T>
+inline cudaError_t host_alloc_mapped(T **p, T **dev, size_t bytes)
+{
+    cudaError_t e = alloc_gate();
+    if (e != cudaSuccess) {
+        *p = *dev = nullptr;
+        return e;
+    }
+    if ((e = cudaHostAlloc((void **)p, bytes, cudaHostAllocMapped)) != cudaSuccess) {
+        *p = *dev = nullptr;
+        return e;
+    }
+    return cudaHostGetDevicePointer((void **)dev, (void *)*p, 0);
+}
 
 // Error reporting (api.cu).
 tdq_status set_error(tdq_status st, const char *fmt, ...);
@@ -268,8 +279,11 @@ tdq_status cuda_error(cudaError_t e, const char *what);
 // sort_hist_words(n) words.  The sorted data ends in keys/vals.
 // Only the low key_bits bits are sorted on (an even number of 8-bit passes).
 uint64_t sort_hist_words(uint64_t n);
+// n_dev (may be null): device count of the leading keys to sort (at most n);
+// the launch shapes follow n, the work the count.
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
-                             uint32_t *hist, cudaStream_t stream, int key_bits = 64);
+                             uint32_t *hist, cudaStream_t stream, int key_bits = 64,
+                             const unsigned long long *n_dev = nullptr);
 inline int sort_passes(int key_bits) { return 2 * ((key_bits + 15) / 16); }
 // Kernels radix_sort_pairs launches for n keys.
 int sort_kernel_launches(uint64_t n, int key_bits);
