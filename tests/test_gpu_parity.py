@@ -379,3 +379,29 @@ def test_filter_survivor_list_overflow_is_regrown(tdq):
     with tdq.build_index(ent) as idx:
         s64, s32 = _filter_vs_fp64(tdq, idx, qry, 3.0, (-np.inf, np.inf))
     assert s32["results"] == 20_000 * 64
+
+
+@pytest.mark.parametrize("bin_count", [1, 3, 64, 4096, 100_000])
+def test_filter_overlap_count_across_bins_and_windows(tdq, bin_count):
+    # the filter mode counts temporal-overlap pairs with searches confined to
+    # the bin of each bound (t_start table and t_end table): the count must be
+    # the oracle's for any bin width -- one bin, bins much wider and much
+    # narrower than a segment -- and for windows inside, cutting, before and
+    # after the data
+    w = workloads.scale_random_walk(n_traj=300, n_queries=12)
+    ts = np.concatenate([w.entries["ts"], w.entries["te"]])
+    lo, hi = float(ts.min()), float(ts.max())
+    mid = 0.5 * (lo + hi)
+    windows = [(-np.inf, np.inf), (mid - 7.25, mid + 3.5), (lo - 50.0, lo + 0.5), (hi - 0.25, hi + 10.0),
+               (lo - 20.0, lo - 10.0), (hi + 1.0, hi + 2.0)]
+    with tdq.build_index(w.entries, bin_count=bin_count) as idx:
+        for t0, t1 in windows:
+            r32 = tdq.search(idx, w.queries, 5.0, t0, t1, mode=tdq.MODE_FP32_FILTER)
+            s32 = tdq.get_stats(idx)
+            r64 = tdq.search(idx, w.queries, 5.0, t0, t1, mode=tdq.MODE_FP64)
+            s64 = tdq.get_stats(idx)
+            ref = oracle.search_sweep(w.entries, w.queries, 5.0, t0, t1)
+            assert s32["overlap_pairs"] == s64["overlap_pairs"] == ref.overlap_pairs
+            for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
+                assert np.array_equal(a, b)
+            assert len(r32) == len(ref.query_index)

@@ -65,11 +65,14 @@ def test_plan_batches_match_oracle_and_unbatched_search(tdq, mode_name):
                                         torch.from_numpy(w.q_t0).cuda(), torch.from_numpy(w.q_t1).cuda(), buf,
                                         mode=mode)
         ref = buf.to_host(cnt)
+        ref_overlap = tdq.get_stats(idx)["overlap_pairs"]
         # the same queries as uneven batches through one plan (graph replay,
-        # several size classes); host and device inputs
+        # several size classes, so most batches carry padding slots); host
+        # and device inputs
         cuts = [0, 7, 1500, 1501, 4000, n]
         with tdq.Plan(idx, max_query_segments=4000, mode=mode) as plan:
             got = []
+            overlap = 0
             for k, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
                 if b <= a:
                     continue
@@ -77,8 +80,12 @@ def test_plan_batches_match_oracle_and_unbatched_search(tdq, mode_name):
                 src = tdq.DeviceSegments(sub) if k % 2 else sub
                 c = plan.search(src, w.q_d[a:b], w.q_t0[a:b], w.q_t1[a:b])
                 r = plan.results()
-                assert len(r) == c == plan.stats()["results"]
+                st = plan.stats()
+                assert len(r) == c == st["results"]
+                overlap += st["overlap_pairs"]
                 got.append(r)
+        # the overlap count is exact integer work: batching does not change it
+        assert overlap == ref_overlap
         merged = tdq.Results(*[np.concatenate([getattr(r, f) for r in got])
                                for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit")])
     _same(merged, ref)
