@@ -13,7 +13,8 @@ value     temporal-overlap pair tests per second (pairs whose common span has
           events on the stream the library launches on; the plain FP64 mode
           is measured the same way and reported beside it;
 e2e       the same metric through the C ABI with host query arrays and host
-          results (host<->device copies inside the timed region);
+          results in pinned host memory (host<->device copies inside the
+          timed region);
 roofline  the dominant pair kernel of each mode against its pipe's peak
           (FP64 for the plain mode, FP32 for the filter mode);
 cpu_baseline / --impl reference
@@ -519,24 +520,36 @@ def main():
     plain = timed("fp64")
     clk = clocks.stop()
 
-    # end to end through the C ABI: host queries in, host results out
+    # end to end through the C ABI: host queries in, host results out, both
+    # in pinned host memory
     e2e = None
     if not args.no_e2e:
-        plan.search(q3, d3, t03, t13, stream=stream)
-        plan.results()
+        def pinned(a):
+            p = torch.empty(len(a), dtype=torch.from_numpy(np.asarray(a)).dtype, pin_memory=True).numpy()
+            p[:] = a
+            return p
+
+        q3h = tdq.HostSegments(workloads.Segments(*[pinned(q3[c]) for c in workloads.COLUMNS], pinned(q3.seg_id),
+                                                  pinned(q3.traj_id)))
+        d3h, t03h, t13h = pinned(d3), pinned(t03), pinned(t13)
+        cap = 1 << 22
+        outs = tuple(torch.empty(cap, dtype=dt, pin_memory=True).numpy()
+                     for dt in (torch.int64, torch.int64, torch.float64, torch.float64))
+        plan.search(q3h, d3h, t03h, t13h, stream=stream)
+        plan.results(out=outs)
         barrier()
         torch.cuda.synchronize()
         t = time.perf_counter()
         e_pairs = 0
         d2h = 0
         for _ in range(args.steps):
-            plan.search(q3, d3, t03, t13, stream=stream)
-            r = plan.results()
+            plan.search(q3h, d3h, t03h, t13h, stream=stream)
+            r = plan.results(out=outs)
             e_pairs += plan.stats()["overlap_pairs"]
             d2h += 32 * len(r) + 64
         torch.cuda.synchronize()
         e_dt, e_pairs = reduce_over_ranks(time.perf_counter() - t, e_pairs, device="cuda")
-        e2e = {"value": e_pairs / e_dt, "unit": "pair tests/s",
+        e2e = {"value": e_pairs / e_dt, "unit": "pair tests/s", "host_memory": "pinned",
                "h2d_bytes_per_step": len(q3) * 96, "d2h_bytes_per_step": d2h // args.steps,
                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / e_dt}
 

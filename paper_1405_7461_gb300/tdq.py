@@ -523,16 +523,27 @@ class Plan:
         del keep
         return int(cnt.value)
 
-    def results(self) -> Results:
-        """tdq_plan_copy_results: the last batch's results, copied to host."""
+    def results(self, out=None) -> Results:
+        """tdq_plan_copy_results: the last batch's results, copied to host --
+        into new arrays, or into `out` = (query_seg_id, entry_seg_id,
+        t_enter, t_exit), caller arrays (e.g. pinned memory) large enough for
+        the count, returned as views of their first entries."""
         view = tdq_result_buffer()
         cnt = ctypes.c_uint64()
         _check(load().tdq_plan_results(self._h, ctypes.byref(view), ctypes.byref(cnt)))
         n = int(cnt.value)
-        qi = np.empty(n, np.int64)
-        ei = np.empty(n, np.int64)
-        tin = np.empty(n, np.float64)
-        tout = np.empty(n, np.float64)
+        if out is not None:
+            if any(len(a) < n or not a.flags["C_CONTIGUOUS"] for a in out):
+                raise ValueError("tdq: result arrays too small or not contiguous")
+            if out[0].dtype != np.int64 or out[1].dtype != np.int64 or out[2].dtype != np.float64 \
+                    or out[3].dtype != np.float64:
+                raise ValueError("tdq: result arrays must be int64, int64, float64, float64")
+            qi, ei, tin, tout = (a[:n] for a in out)
+        else:
+            qi = np.empty(n, np.int64)
+            ei = np.empty(n, np.int64)
+            tin = np.empty(n, np.float64)
+            tout = np.empty(n, np.float64)
         if n:
             _check(load().tdq_plan_copy_results(self._h, qi.ctypes.data, ei.ctypes.data, tin.ctypes.data,
                                                 tout.ctypes.data, n, 0, None))

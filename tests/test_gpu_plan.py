@@ -162,3 +162,28 @@ def test_autotune_picks_measured_candidates(tdq):
     merged = tdq.Results(*[np.concatenate([getattr(r, f) for r in parts])
                            for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit")])
     _same(merged, ref)
+
+
+def test_plan_results_into_caller_arrays(tdq):
+    # results copied into caller-provided (pinned) host arrays equal the
+    # freshly allocated copy; too small or mistyped arrays are refused
+    w = workloads.tiny_random_walk()
+    q = w.queries
+    n = len(q)
+    d = np.full(n, w.d_values[0])
+    t0 = np.full(n, w.window[0])
+    t1 = np.full(n, w.window[1])
+    with tdq.build_index(w.entries) as idx, tdq.Plan(idx, n, mode=tdq.MODE_FP32_FILTER) as plan:
+        c = plan.search(q, d, t0, t1)
+        fresh = plan.results()
+        cap = c + 5
+        outs = tuple(torch.empty(cap, dtype=dt, pin_memory=True).numpy()
+                     for dt in (torch.int64, torch.int64, torch.float64, torch.float64))
+        got = plan.results(out=outs)
+        assert len(got) == c > 0
+        for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit"):
+            assert np.array_equal(getattr(got, f), getattr(fresh, f))
+        with pytest.raises(ValueError):
+            plan.results(out=tuple(a[: c - 1] for a in outs))
+        with pytest.raises(ValueError):
+            plan.results(out=(outs[2], outs[1], outs[2], outs[3]))
