@@ -82,7 +82,17 @@ typedef struct {
     uint32_t query_tile;  /* query segments per tile (multiple of 32, <= 32; default 32) */
     uint32_t entry_chunk; /* entry segments per work item (multiple of 256, <= 2048; default 512) */
     int mode;             /* TDQ_MODE_* (default TDQ_MODE_FP64) */
+    uint32_t flags;       /* TDQ_FLAG_* (default 0) */
 } tdq_search_params;
+
+/* Pair filters of tdq_search_params.flags (no counterpart in the paper's
+ * kernel; they express query (ii) of Sec. 2.1, see tdq_self_join).  Both
+ * leave the temporal-overlap count of tdq_stats unchanged (it covers every
+ * pair). */
+#define TDQ_FLAG_OTHER_TRAJECTORIES 1u /* report only pairs whose query and entry trajectory ids differ
+                                          (the queries' traj_id must be given) */
+#define TDQ_FLAG_UNORDERED_ONCE 2u     /* report a pair only if entry_seg_id > query_seg_id (with the
+                                          database as the query set: each unordered pair once) */
 
 /* Host-side results, owned by the library (release with tdq_results_free).
  * Item k: query segment query_seg_id[k] (the caller's id) is within d of
@@ -166,6 +176,19 @@ tdq_status tdq_index_bins(const tdq_index *idx, uint32_t *m, double *width, doub
  */
 tdq_status tdq_search(tdq_index *idx, const tdq_segments *queries, double d, double t0, double t1,
                       const tdq_search_params *params, void *stream, tdq_results **out);
+
+/*
+ * Self-join, query (ii) of Sec. 2.1 (every trajectory against all other
+ * trajectories) with the database as the query set: `entries` must be the
+ * segment set the index was built from (same count, traj_id given).  Reports
+ * every pair of segments of different trajectories within d during [t0, t1],
+ * each unordered pair once, as (query_seg_id < entry_seg_id).  A search with
+ * flags TDQ_FLAG_OTHER_TRAJECTORIES | TDQ_FLAG_UNORDERED_ONCE; other fields of
+ * params as for tdq_search.  Errors as tdq_search, and TDQ_ERR_INVALID when
+ * the count differs from the index's or traj_id is NULL.  Blocks.
+ */
+tdq_status tdq_self_join(tdq_index *idx, const tdq_segments *entries, double d, double t0, double t1,
+                         const tdq_search_params *params, void *stream, tdq_results **out);
 
 /* Release results from tdq_search (NULL is ignored). */
 void tdq_results_free(tdq_results *res);

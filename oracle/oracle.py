@@ -72,6 +72,8 @@ def _configure(lib):
             f = getattr(lib, name)
             f.restype = P
             f.argtypes = [P, i64, P, i64, dbl, dbl, dbl, ctypes.c_int]
+        lib.oracle_self_join.restype = P
+        lib.oracle_self_join.argtypes = [P, i64, P, P, dbl, dbl, dbl, ctypes.c_int]
         lib.oracle_result_count.restype = i64
         lib.oracle_result_count.argtypes = [P]
         lib.oracle_result_overlap_pairs.restype = i64
@@ -122,14 +124,7 @@ def default_threads() -> int:
     return int(_load().oracle_default_threads())
 
 
-def _search(fn_name, entries, queries, d, t0, t1, threads):
-    lib = _load()
-    ecols, earr = _columns(entries)
-    qcols, qarr = _columns(queries)
-    n = len(ecols[0])
-    nq = len(qcols[0])
-    h = getattr(lib, fn_name)(ctypes.cast(earr, ctypes.c_void_p), n, ctypes.cast(qarr, ctypes.c_void_p),
-                              nq, float(d), float(t0), float(t1), int(threads))
+def _collect(lib, h):
     if not h:
         raise MemoryError("oracle search failed to allocate")
     try:
@@ -145,8 +140,20 @@ def _search(fn_name, entries, queries, d, t0, t1, threads):
                            int(lib.oracle_result_visited_pairs(h)))
     finally:
         lib.oracle_result_free(h)
-    del ecols, qcols
     return res.sorted()
+
+
+def _search(fn_name, entries, queries, d, t0, t1, threads):
+    lib = _load()
+    ecols, earr = _columns(entries)
+    qcols, qarr = _columns(queries)
+    n = len(ecols[0])
+    nq = len(qcols[0])
+    h = getattr(lib, fn_name)(ctypes.cast(earr, ctypes.c_void_p), n, ctypes.cast(qarr, ctypes.c_void_p),
+                              nq, float(d), float(t0), float(t1), int(threads))
+    res = _collect(lib, h)
+    del ecols, qcols
+    return res
 
 
 def search_bruteforce(entries, queries, d, t0=-np.inf, t1=np.inf, threads=0) -> OracleResult:
@@ -157,6 +164,22 @@ def search_bruteforce(entries, queries, d, t0=-np.inf, t1=np.inf, threads=0) -> 
 def search_sweep(entries, queries, d, t0=-np.inf, t1=np.inf, threads=0) -> OracleResult:
     """Same result as :func:`search_bruteforce`, visiting only pairs whose starts can overlap."""
     return _search("oracle_search_sweep", entries, queries, d, t0, t1, threads)
+
+
+def self_join(entries, d, t0=-np.inf, t1=np.inf, threads=0) -> OracleResult:
+    """Query (ii) of Sec. 2.1 with the database as the query set: every
+    segment against the segments of every other trajectory, each unordered
+    pair once (query index = the segment with the smaller seg_id).  The
+    overlap count covers all pairs, the left-out ones included."""
+    lib = _load()
+    ecols, earr = _columns(entries)
+    traj = np.ascontiguousarray(entries.traj_id, np.int64)
+    seg = np.ascontiguousarray(entries.seg_id, np.int64)
+    h = lib.oracle_self_join(ctypes.cast(earr, ctypes.c_void_p), len(ecols[0]), _ptr(traj), _ptr(seg), float(d),
+                             float(t0), float(t1), int(threads))
+    res = _collect(lib, h)
+    del ecols, traj, seg
+    return res
 
 
 def pair(e8, q8, d, t0=-np.inf, t1=np.inf):

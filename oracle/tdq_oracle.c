@@ -20,7 +20,7 @@
  *                           linear interpolation, and
  *   calcTimeInterval     -- the time interval where the clipped segments are
  *                           within d, found from a degree-two polynomial.
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - pairs whose common span has zero length are not reported (a < b strict);
  *   - "within d" is inclusive (distance <= d);
  *   - the window [t0,t1] clips the common span like the segments do;
@@ -29,12 +29,16 @@
  *   - the roots use the cancellation-free quadratic formula (Numerical
  *     Recipes, Sec. 5.6).
  *
- * Two search drivers:
+ * Search drivers:
  *   oracle_search_bruteforce -- every query segment against every entry.
  *   oracle_search_sweep      -- the same per-pair function, but entries are
  *                               first sorted by t_start and only those whose
  *                               start lies in (q.t_start - maxdur, q.t_end)
  *                               are visited (pruning only; identical result).
+ *   oracle_self_join         -- the sweep with the database as the query
+ *                               set, pairs of one trajectory left out and
+ *                               each unordered pair reported once (query (ii)
+ *                               of Sec. 2.1).
  * And the temporal-bin index of Sec. 4 (Fig. 1) plus the interaction count of
  * a query batching over it (Fig. 2), for the index pins.
  *
@@ -333,12 +337,27 @@ static int cmp_ts(const void *pa, const void *pb)
     return (a > b) - (a < b);
 }
 
+/* Pair filter of the self-join (query (ii) of Sec. 2.1: every trajectory
+ * against all other trajectories): a pair is reported only if its two
+ * segments belong to different trajectories and, so that each unordered pair
+ * appears once, the entry's id is larger than the query's.  NULL: no filter. */
+typedef struct {
+    const int64_t *etraj, *eseg, *qtraj, *qseg;
+} pair_filter;
+
+static int pair_allowed(const pair_filter *f, int64_t qi, int64_t ei)
+{
+    if (!f) return 1;
+    return f->etraj[ei] != f->qtraj[qi] && f->eseg[ei] > f->qseg[qi];
+}
+
 /* Same result as oracle_search_bruteforce, visiting fewer pairs: entries are
  * sorted by t_start; an entry can share a span of positive length with query
  * segment q only if q.t_start - maxdur < e.t_start < q.t_end, where maxdur is
- * the longest entry duration. */
-oracle_result *oracle_search_sweep(const double *const *ent, int64_t n, const double *const *qry,
-                                   int64_t nq, double d, double wt0, double wt1, int nthreads)
+ * the longest entry duration.  The temporal-overlap count covers every pair,
+ * filtered or not. */
+static oracle_result *sweep(const double *const *ent, int64_t n, const double *const *qry, int64_t nq, double d,
+                            double wt0, double wt1, int nthreads, const pair_filter *filt)
 {
     nthreads = max_threads(nthreads);
     oracle_result *r = calloc(1, sizeof *r);
@@ -391,7 +410,7 @@ oracle_result *oracle_search_sweep(const double *const *ent, int64_t n, const do
             double tin, tout, dm;
             int hit = oracle_pair((const double *)&e, (const double *)&q, d, wt0, wt1, &tin, &tout, &dm);
             if (hit >= 0) ov[tid]++;
-            if (hit == 1 && obuf_push(&parts[tid], qi, ei, tin, tout, dm)) failed = 1;
+            if (hit == 1 && pair_allowed(filt, qi, ei) && obuf_push(&parts[tid], qi, ei, tin, tout, dm)) failed = 1;
         }
     }
     for (int i = 0; i < nthreads; i++) {
@@ -403,6 +422,23 @@ oracle_result *oracle_search_sweep(const double *const *ent, int64_t n, const do
     free(parts); free(ov); free(vis); free(order); free(sts);
     if (failed) { oracle_result_free(r); return NULL; }
     return r;
+}
+
+oracle_result *oracle_search_sweep(const double *const *ent, int64_t n, const double *const *qry,
+                                   int64_t nq, double d, double wt0, double wt1, int nthreads)
+{
+    return sweep(ent, n, qry, nq, d, wt0, wt1, nthreads, NULL);
+}
+
+/* Self-join (query (ii) of Sec. 2.1 with the query set equal to the
+ * database): every segment against every segment of another trajectory,
+ * each unordered pair once (reported with the smaller id as the query).
+ * traj and seg are the n trajectory and segment ids; results are indices. */
+oracle_result *oracle_self_join(const double *const *ent, int64_t n, const int64_t *traj, const int64_t *seg,
+                                double d, double wt0, double wt1, int nthreads)
+{
+    const pair_filter f = {traj, seg, traj, seg};
+    return sweep(ent, n, ent, n, d, wt0, wt1, nthreads, &f);
 }
 
 /* Number of OpenMP threads a search with nthreads<=0 would use. */

@@ -167,6 +167,7 @@ struct GatherArgs {
     const double *const *pre;
     const float4 *pre_sph;
     const int64_t *seg_id;
+    const int64_t *traj_id;  // may be null (then 0)
     const uint32_t *order;
     uint64_t nq;
     DevCounters *ctr;
@@ -215,6 +216,7 @@ __global__ void query_gather(GatherArgs a)
         q.ts_key[k] = cs;
         q.te_key[k] = ce;
         q.qid[k] = a.seg_id[i];
+        if (q.qtraj) q.qtraj[k] = a.traj_id ? a.traj_id[i] : 0;
         q.sph[k] = a.pre_sph[i];
         // First bin whose extent reaches past the query start: the prefix
         // maximum of bin ends is non-decreasing, so this is a binary search
@@ -293,7 +295,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r)
 // Shared-memory staging of one work item.
 struct PairSmem {
     double qp[3][kQT], qv[3][kQT], qd2[kQT];
-    int64_t qts[kQT], qte[kQT], qid[kQT];
+    int64_t qts[kQT], qte[kQT], qid[kQT], qtraj[kQT];
     long long item;
     long long tile;
     // followed by the entry chunk: FP64 mode: 6 double columns + 2 key
@@ -309,7 +311,18 @@ struct PairArgs {
     DevCounters *ctr;
     tdq_result_buffer out;
     uint32_t chunk;
+    uint32_t flags;  // TDQ_FLAG_* pair filters (0: every pair)
 };
+
+// The pair filters of TDQ_FLAG_OTHER_TRAJECTORIES / TDQ_FLAG_UNORDERED_ONCE
+// (query (ii) of Sec. 2.1: every trajectory against all other trajectories,
+// each unordered pair once when the database is the query set).
+__device__ __forceinline__ bool pair_allowed(uint32_t flags, int64_t qtraj, int64_t qseg, int64_t etraj, int64_t eseg)
+{
+    if ((flags & TDQ_FLAG_OTHER_TRAJECTORIES) && etraj == qtraj) return false;
+    if ((flags & TDQ_FLAG_UNORDERED_ONCE) && !(eseg > qseg)) return false;
+    return true;
+}
 
 // calcTimeInterval for a pair that is within d: the roots of
 // A tau^2 + 2 Bh tau + C over tau in [0, L] (tau = time since a), by the
@@ -713,8 +726,11 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
         const unsigned long long k = wb + lane;
         const bool valid = k < ns;
         const uint2 sv = valid ? fa.surv[k] : make_uint2(0u, 0u);
-        const bool active = valid && args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
-                            args.e.te_key[sv.x] > args.q.ts_key[sv.y];
+        bool active = valid && args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
+                      args.e.te_key[sv.x] > args.q.ts_key[sv.y];
+        if (args.flags && active)
+            active = pair_allowed(args.flags, args.q.qtraj[sv.y], args.q.qid[sv.y], args.e.traj_id[sv.x],
+                                  args.e.seg_id[sv.x]);
         const unsigned am = __ballot_sync(kFull, active);
         if (active) queue[queued + __popc(am & lt_mask)] = sv;
         queued += __popc(am);
@@ -798,6 +814,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 S.qts[tid] = args.q.ts_key[k];
                 S.qte[tid] = args.q.te_key[k];
                 S.qid[tid] = args.q.qid[k];
+                S.qtraj[tid] = args.flags ? args.q.qtraj[k] : 0;
             } else {  // padding: a span that overlaps nothing
                 S.qts[tid] = INT64_MAX;
                 S.qte[tid] = INT64_MIN;
@@ -856,10 +873,13 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
                 const int j = active ? nth_set_bit(mo, kk - eo) : 0;
                 const int ei = active ? (g + warp * 32 + owner) : el;
 
-                const PairEval r = eval_pair_fp64(active, ets[ei], ete[ei], S.qts[j], S.qte[j], epx[ei], epy[ei],
-                                                  epz[ei], evx[ei], evy[ei], evz[ei], S.qp[0][j], S.qp[1][j],
-                                                  S.qp[2][j], S.qv[0][j], S.qv[1][j], S.qv[2][j], S.qd2[j]);
-                append_hits(r, ctr, args.out, cap, S.qid[j], active ? args.e.seg_id[e0 + ei] : 0, lane, lt_mask);
+                PairEval r = eval_pair_fp64(active, ets[ei], ete[ei], S.qts[j], S.qte[j], epx[ei], epy[ei],
+                                            epz[ei], evx[ei], evy[ei], evz[ei], S.qp[0][j], S.qp[1][j],
+                                            S.qp[2][j], S.qv[0][j], S.qv[1][j], S.qv[2][j], S.qd2[j]);
+                const int64_t eseg = active ? args.e.seg_id[e0 + ei] : 0;
+                if (args.flags && r.hit)
+                    r.hit = pair_allowed(args.flags, S.qtraj[j], S.qid[j], args.e.traj_id[e0 + ei], eseg);
+                append_hits(r, ctr, args.out, cap, S.qid[j], eseg, lane, lt_mask);
             }
         }
         __syncthreads();  // the chunk is about to be restaged
@@ -939,10 +959,10 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     if (nq <= w.q_cap && w.q_block) return TDQ_OK;
     uint64_t cap = nq > 2 * w.q_cap ? nq : 2 * w.q_cap;
     if (cap < 1024) cap = 1024;
-    uint64_t bytes = 9 * cb(cap, 8)                    // staged host input
+    uint64_t bytes = 10 * cb(cap, 8)                   // staged host input
                      + 9 * cb(cap, 8)                  // pre
                      + 2 * cb(cap, 8) + 2 * cb(cap, 4) // sort
-                     + 12 * cb(cap, 8)                 // sorted query SoA
+                     + 13 * cb(cap, 8)                 // sorted query SoA
                      + 2 * cb(cap, 16)                 // query spheres (before / after sorting)
                      + cb(9, sizeof(double *));        // pre pointer table
     uint64_t ntiles = (cap + kQT - 1) / kQT;
@@ -968,6 +988,7 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     char *p = (char *)w.q_block;
     for (int c = 0; c < 8; c++) w.in_cols[c] = carve<double>(p, cap);
     w.in_seg = carve<int64_t>(p, cap);
+    w.in_traj = carve<int64_t>(p, cap);
     for (int c = 0; c < 9; c++) w.pre[c] = carve<double>(p, cap);
     w.keys = carve<uint64_t>(p, cap);
     w.keys_alt = carve<uint64_t>(p, cap);
@@ -979,6 +1000,7 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     q.d2 = carve<double>(p, cap);
     q.ts_key = carve<int64_t>(p, cap); q.te_key = carve<int64_t>(p, cap);
     q.qid = carve<int64_t>(p, cap); q.lo = carve<int64_t>(p, cap); q.hi = carve<int64_t>(p, cap);
+    q.qtraj = carve<int64_t>(p, cap);
     w.pre_sph = carve<float4>(p, cap);
     q.sph = carve<float4>(p, cap);
     w.pre_dev = carve<double *>(p, 9);
@@ -1015,6 +1037,9 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
     if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
         return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
     cfg->filter = params && params->mode == TDQ_MODE_FP32_FILTER;
+    cfg->flags = params ? params->flags : 0u;
+    if (cfg->flags & ~(TDQ_FLAG_OTHER_TRAJECTORIES | TDQ_FLAG_UNORDERED_ONCE))
+        return set_error(TDQ_ERR_INVALID, "tdq_search: unknown flags 0x%x", cfg->flags);
     cfg->chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
     if (cfg->chunk % kPairThreads != 0 || cfg->chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search: entry_chunk must be a multiple of 256, at most 2048");
@@ -1050,11 +1075,11 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
         if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
                                   bin_key_bits(idx->m), &w.ctr->sort_n)) != cudaSuccess)
             return e;
-        const GatherArgs ga{pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q, ntiles, cfg.chunk,
+        const GatherArgs ga{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, bins, w.q, ntiles, cfg.chunk,
                             w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
         if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
-        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk};
+        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags};
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
                                     events ? w.ev[2] : nullptr, evflags)) != cudaSuccess)
@@ -1149,8 +1174,8 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
         if (e != cudaSuccess) return e;
     }
     {
-        GatherArgs a0{pre, w.pre_sph, in.seg_id, w.vals, nq, w.ctr, bins, w.q, (nq + kQT - 1) / kQT, cfg.chunk,
-                      w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
+        GatherArgs a0{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, bins, w.q, (nq + kQT - 1) / kQT,
+                      cfg.chunk, w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
         void *args[] = {&a0};
         cudaKernelNodeParams kp{};
         kp.func = (void *)query_gather;
@@ -1187,6 +1212,8 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     LaunchCfg cfg;
     tdq_status st = parse_params(params, &cfg);
     if (st != TDQ_OK) return st;
+    if ((cfg.flags & TDQ_FLAG_OTHER_TRAJECTORIES) && !queries->traj_id)
+        return set_error(TDQ_ERR_INVALID, "tdq_search: TDQ_FLAG_OTHER_TRAJECTORIES needs the queries' traj_id");
     st = ensure_queries(w, nq);
     if (st != TDQ_OK) return st;
 
@@ -1198,9 +1225,14 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
         }
         TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, cudaMemcpyHostToDevice, stream));
         in.seg_id = w.in_seg;
+        if (cfg.flags && queries->traj_id) {
+            TDQ_CUDA(cudaMemcpyAsync(w.in_traj, queries->traj_id, nq * 8, cudaMemcpyHostToDevice, stream));
+            in.traj_id = w.in_traj;
+        }
     } else {
         for (int c = 0; c < 8; c++) in.c[c] = cols[c];
         in.seg_id = queries->seg_id;
+        in.traj_id = queries->traj_id;
     }
     in.d = spec.d;
     in.t0 = spec.t0;
@@ -1342,6 +1374,22 @@ extern "C" tdq_status tdq_search(tdq_index *idx, const tdq_segments *queries, do
     return TDQ_OK;
 }
 
+extern "C" tdq_status tdq_self_join(tdq_index *idx, const tdq_segments *entries, double d, double t0, double t1,
+                                    const tdq_search_params *params, void *stream, tdq_results **out)
+{
+    if (!out) return set_error(TDQ_ERR_INVALID, "tdq_self_join: out is NULL");
+    *out = nullptr;
+    if (!idx || !entries) return set_error(TDQ_ERR_INVALID, "tdq_self_join: NULL argument");
+    if (entries->n != idx->n)
+        return set_error(TDQ_ERR_INVALID, "tdq_self_join: %llu segments given, the index holds %llu",
+                         (unsigned long long)entries->n, (unsigned long long)idx->n);
+    if (!entries->traj_id) return set_error(TDQ_ERR_INVALID, "tdq_self_join: traj_id is NULL");
+    tdq_search_params p{};
+    if (params) p = *params;
+    p.flags |= TDQ_FLAG_OTHER_TRAJECTORIES | TDQ_FLAG_UNORDERED_ONCE;
+    return tdq_search(idx, entries, d, t0, t1, &p, stream, out);
+}
+
 extern "C" void tdq_results_free(tdq_results *res)
 {
     if (!res) return;
@@ -1439,6 +1487,7 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         q.ts_key = carve<int64_t>(p, kNoAllocMaxQueries); q.te_key = carve<int64_t>(p, kNoAllocMaxQueries);
         q.qid = carve<int64_t>(p, kNoAllocMaxQueries); q.lo = carve<int64_t>(p, kNoAllocMaxQueries);
         q.hi = carve<int64_t>(p, kNoAllocMaxQueries);
+        q.qtraj = nullptr;  // no pair filters here
         s.pre_sph = carve<float4>(p, kNoAllocMaxQueries);
         q.sph = carve<float4>(p, kNoAllocMaxQueries);
         s.tile_lo = carve<int64_t>(p, kNoAllocTiles);
@@ -1479,6 +1528,8 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search_device_noalloc: %llu query segments exceed the fixed maximum of %llu",
                          (unsigned long long)nq, (unsigned long long)kNoAllocMaxQueries);
+    if (params && params->flags)
+        return set_error(TDQ_ERR_INVALID, "tdq_search_device_noalloc: pair filters (flags) are not supported");
     if (params && params->mode == TDQ_MODE_FP32_FILTER)
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search_device_noalloc: the filter mode needs a survivor list; use TDQ_MODE_FP64");
@@ -1517,11 +1568,11 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream,
                                   bin_key_bits(idx->m)));
-        const GatherArgs ga{s->pre_dev, s->pre_sph, in.seg_id, s->vals, nq, s->ctr, bins, s->q, ntiles, chunk,
-                            s->tile_lo, s->tile_hi, s->tile_work, false};
+        const GatherArgs ga{s->pre_dev, s->pre_sph, in.seg_id, nullptr, s->vals, nq, s->ctr, bins, s->q, ntiles,
+                            chunk, s->tile_lo, s->tile_hi, s->tile_work, false};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
         TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
-        PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk};
+        PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk, 0u};
         TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream, nullptr, 0));
     }
     TDQ_CUDA(cudaGetLastError());

@@ -123,6 +123,7 @@ struct QuerySoA {
     double *d2;            // squared threshold
     int64_t *ts_key, *te_key;  // clipped span [max(ts,t0), min(te,t1)]
     int64_t *qid;          // caller's segment id
+    int64_t *qtraj;        // caller's trajectory id (0 when not given)
     int64_t *lo, *hi;      // candidate range of sorted entry positions
     float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
 };
@@ -135,6 +136,7 @@ struct Workspace {
     // host-query staging (8 columns + seg id)
     double *in_cols[8] = {nullptr};
     int64_t *in_seg = nullptr;
+    int64_t *in_traj = nullptr;
     // per-query arrays before sorting
     double *pre[9] = {nullptr};  // px,py,pz,vx,vy,vz,d2,ts',te'
     double **pre_dev = nullptr;  // device copy of pre[]
@@ -195,6 +197,7 @@ namespace tdq {
 struct QueryInput {
     const double *c[8];  // xs ys zs ts xe ye ze te
     const int64_t *seg_id;
+    const int64_t *traj_id;  // may be null
     double d, t0, t1;
     const double *d_arr, *t0_arr, *t1_arr;
     uint64_t n_real;
@@ -203,6 +206,7 @@ struct QueryInput {
 struct LaunchCfg {
     uint32_t chunk;
     bool filter;
+    uint32_t flags;  // TDQ_FLAG_*
 };
 
 // search.cu: workspace sizing, parameters, and one search split into a part

@@ -32,6 +32,8 @@ STATUS_NAMES = {0: "TDQ_OK", 1: "TDQ_ERR_INVALID", 2: "TDQ_ERR_NOMEM", 3: "TDQ_E
                 4: "TDQ_ERR_TIMEOUT", 5: "TDQ_ERR_OVERFLOW"}
 MODE_FP64 = 0
 MODE_FP32_FILTER = 1
+FLAG_OTHER_TRAJECTORIES = 1  # TDQ_FLAG_OTHER_TRAJECTORIES
+FLAG_UNORDERED_ONCE = 2  # TDQ_FLAG_UNORDERED_ONCE
 
 c_dbl_p = ctypes.c_void_p
 
@@ -47,7 +49,8 @@ class tdq_index_params(ctypes.Structure):
 
 
 class tdq_search_params(ctypes.Structure):
-    _fields_ = [("query_tile", ctypes.c_uint32), ("entry_chunk", ctypes.c_uint32), ("mode", ctypes.c_int)]
+    _fields_ = [("query_tile", ctypes.c_uint32), ("entry_chunk", ctypes.c_uint32), ("mode", ctypes.c_int),
+                ("flags", ctypes.c_uint32)]
 
 
 class tdq_results(ctypes.Structure):
@@ -123,6 +126,7 @@ SIGNATURES = {
     "tdq_index_size": (ctypes.c_uint64, [P]),
     "tdq_index_bins": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
     "tdq_search": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P]),
+    "tdq_self_join": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P]),
     "tdq_results_free": (None, [P]),
     "tdq_search_device": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P]),
     "tdq_search_device_batched": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
@@ -260,11 +264,12 @@ def _segments(seg):
     raise TypeError(f"expected Segments, HostSegments or DeviceSegments, got {type(seg)}")
 
 
-def _params(query_tile=0, entry_chunk=0, mode=MODE_FP64):
+def _params(query_tile=0, entry_chunk=0, mode=MODE_FP64, flags=0):
     p = tdq_search_params()
     p.query_tile = query_tile
     p.entry_chunk = entry_chunk
     p.mode = mode
+    p.flags = flags
     return p
 
 
@@ -354,13 +359,25 @@ class Results:
 def search(idx: Index, queries, d: float, t0: float = -np.inf, t1: float = np.inf, stream=None,
            **params) -> Results:
     """tdq_search: results copied to host memory (the library retries on overflow)."""
+    return _host_results("tdq_search", idx, queries, d, t0, t1, stream, params)
+
+
+def self_join(idx: Index, entries, d: float, t0: float = -np.inf, t1: float = np.inf, stream=None,
+              **params) -> Results:
+    """tdq_self_join: every pair of segments of different trajectories of
+    the indexed set (`entries`, the segments the index was built from) within
+    d, each unordered pair once (query_seg_id < entry_seg_id)."""
+    return _host_results("tdq_self_join", idx, entries, d, t0, t1, stream, params)
+
+
+def _host_results(fn, idx, queries, d, t0, t1, stream, params) -> Results:
     lib = load()
     q = _segments(queries)
     s = q.struct()
     prm = _params(**params)
     out = ctypes.POINTER(tdq_results)()
-    _check(lib.tdq_search(idx.handle, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(prm),
-                          _stream_ptr(stream), ctypes.byref(out)))
+    _check(getattr(lib, fn)(idx.handle, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(prm),
+                            _stream_ptr(stream), ctypes.byref(out)))
     try:
         r = out.contents
         n = int(r.count)

@@ -405,3 +405,58 @@ def test_filter_overlap_count_across_bins_and_windows(tdq, bin_count):
             for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
                 assert np.array_equal(a, b)
             assert len(r32) == len(ref.query_index)
+
+
+# --------------------------------------------------------------------------
+# Self-join: query (ii) of Sec. 2.1 with the database as the query set
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,mode", [("tiny", "fp64"), ("tiny", "fp32filter"), ("galaxy", "fp32filter"),
+                                       ("galaxy", "fp64")])
+def test_self_join_matches_oracle(tdq, name, mode):
+    if name == "tiny":
+        w = workloads.tiny_random_walk(n_traj=120, n_points=60)
+        d, window = 6.0, (-np.inf, np.inf)
+    else:
+        w = workloads.galaxy_disk(n_stars=300, n_queries=1)
+        d, window = 0.1, (20.0, 120.5)
+    ent = w.entries
+    # ids unrelated to positions, so that "each unordered pair once" is not
+    # an artefact of the sort order
+    ent.seg_id = ent.seg_id[np.random.default_rng(5).permutation(len(ent))]
+    m = tdq.MODE_FP64 if mode == "fp64" else tdq.MODE_FP32_FILTER
+    with tdq.build_index(ent) as idx:
+        res = tdq.self_join(idx, ent, d, *window, mode=m)
+        stats = tdq.get_stats(idx)
+    ref = oracle.self_join(ent, d, *window)
+    assert stats["overlap_pairs"] == ref.overlap_pairs
+    assert np.all(res.query_seg_id < res.entry_seg_id)
+    cmp = compare_results(gpu_as_index(res, ent, ent), oracle_as_dict(ref), ent, ent, d, *window,
+                          dmin_fn=lambda ei, qi: oracle.pair_dmin(ent, ei, ent, qi, *window))
+    assert cmp["matched"] == len(ref.query_index) > 0
+
+
+def test_pair_filter_arguments_are_checked(tdq):
+    w = workloads.tiny_random_walk(n_traj=20, n_points=10)
+    ent = w.entries
+    with tdq.build_index(ent) as idx:
+        with pytest.raises(tdq.TdqError):  # unknown flag bit
+            tdq.search(idx, ent, 1.0, flags=4)
+        with pytest.raises(tdq.TdqError):  # a different segment set than the index's
+            tdq.self_join(idx, ent.take(np.arange(len(ent) - 1)), 1.0)
+        # the flags alone, on a host query set without trajectory ids
+        q = ent.take(np.arange(50))
+        s = tdq.HostSegments(q)
+        st = s.struct()
+        st.traj_id = None
+        out = tdq.ctypes.POINTER(tdq.tdq_results)()
+        prm = tdq._params(flags=tdq.FLAG_OTHER_TRAJECTORIES)
+        rc = tdq.load().tdq_search(idx.handle, tdq.ctypes.byref(st), 1.0, -np.inf, np.inf, tdq.ctypes.byref(prm),
+                                   None, tdq.ctypes.byref(out))
+        assert rc == tdq.TDQ_ERR_INVALID
+        # filters on an ordinary search: same as the self-join
+        a = tdq.search(idx, ent, 3.0, flags=tdq.FLAG_OTHER_TRAJECTORIES | tdq.FLAG_UNORDERED_ONCE,
+                       mode=tdq.MODE_FP32_FILTER)
+        b = tdq.self_join(idx, ent, 3.0)
+        for x, y in zip(_sorted_arrays(a), _sorted_arrays(b)):
+            assert np.array_equal(x, y)

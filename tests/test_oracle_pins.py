@@ -368,3 +368,63 @@ def test_fig2_batch_interactions_documented_mismatch():
     assert printed == {10: 450, 20: 600, 30: 630, 60: 900}
     # the all-in-one batch (60 segments against all 15 entries) agrees everywhere
     assert t_min[60] == t_jb[60] == printed[60] == 60 * 15
+
+
+# --------------------------------------------------------------------------
+# Self-join (query (ii) of Sec. 2.1 with the database as the query set)
+# --------------------------------------------------------------------------
+
+def _segments_from_rows(rows, traj, seg_ids):
+    rows = np.asarray(rows, np.float64)
+    return workloads.Segments(*[rows[:, k].copy() for k in range(8)], np.asarray(seg_ids, np.int64),
+                              np.asarray(traj, np.int64))
+
+
+def test_self_join_head_on_pair_once():
+    """Two one-segment trajectories approaching head-on, and a second segment
+    of the first trajectory lying on top of the first: the self-join reports
+    the head-on pair once, with the closed-form interval, and never the pair
+    of one trajectory."""
+    X, u, d, T = 10.0, 2.0, 3.0, 10.0
+    rows = [moving((-X, 0, 0), (u, 0, 0), 0.0, T), moving((X, 0, 0), (-u, 0, 0), 0.0, T),
+            moving((-X, 0, 0), (u, 0, 0), 0.0, T)]
+    ent = _segments_from_rows(rows, traj=[7, 9, 7], seg_ids=[5, 3, 8])
+    r = oracle.self_join(ent, d)
+    # unordered pairs of different trajectories: (5,3) and (8,3); reported with the smaller id as the query
+    got = sorted((int(ent.seg_id[q]), int(ent.seg_id[e])) for q, e in zip(r.query_index, r.entry_index))
+    assert got == [(3, 5), (3, 8)]
+    lo, hi = (2 * X - d) / (2 * u), (2 * X + d) / (2 * u)
+    assert np.allclose(r.t_enter, lo, rtol=1e-12) and np.allclose(r.t_exit, hi, rtol=1e-12)
+    # the overlap count covers every ordered pair, the left-out ones included
+    assert r.overlap_pairs == 9
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_self_join_is_the_filtered_full_search(seed):
+    """The self-join equals the full search of the database against itself
+    with the pairs of one trajectory removed and, of the two orders of a
+    pair, the one whose entry id is larger kept; the removed order carries
+    the same interval (swap symmetry), so nothing is lost."""
+    w = workloads.tiny_random_walk(seed=seed, n_traj=60, n_points=30)
+    ent = w.entries
+    perm = np.random.default_rng(seed).permutation(len(ent))
+    ent.seg_id = ent.seg_id[perm]  # ids unrelated to positions
+    d = 12.0
+    sj = oracle.self_join(ent, d)
+    full = oracle.search_sweep(ent, ent, d)
+    assert sj.overlap_pairs == full.overlap_pairs
+    other = ent.traj_id[full.query_index] != ent.traj_id[full.entry_index]
+    keep = other & (ent.seg_id[full.entry_index] > ent.seg_id[full.query_index])
+    key = lambda qi, ei: list(zip(qi.tolist(), ei.tolist()))  # noqa: E731
+    assert key(sj.query_index, sj.entry_index) == key(full.query_index[keep], full.entry_index[keep])
+    assert np.array_equal(sj.t_enter, full.t_enter[keep]) and np.array_equal(sj.t_exit, full.t_exit[keep])
+    # swap symmetry: every dropped order of a cross-trajectory pair is the
+    # reverse of a kept one with the same interval
+    rev = {(e, q): (a, b) for q, e, a, b in zip(full.query_index[keep], full.entry_index[keep],
+                                                 full.t_enter[keep], full.t_exit[keep])}
+    dropped = other & ~keep
+    assert int(dropped.sum()) == int(keep.sum()) > 0
+    for q, e, a, b in zip(full.query_index[dropped], full.entry_index[dropped], full.t_enter[dropped],
+                          full.t_exit[dropped]):
+        ra, rb = rev[(q, e)]
+        assert ra == pytest.approx(a, rel=1e-12, abs=1e-12) and rb == pytest.approx(b, rel=1e-12, abs=1e-12)
