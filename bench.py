@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-plain-requests", type=int, default=400)
+    ap.add_argument("--no-self-join", action="store_true", help="skip the self-join (query (ii)) section")
+    ap.add_argument("--self-join-stars", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
@@ -341,6 +343,36 @@ def batching_section(args, tdq, torch, stream):
             "ms_per_step": 1e3 * tot / len(ms)}
 
 
+def self_join_section(args, tdq, torch):
+    """F4, query (ii) of Sec. 2.1 with the database as the query set: the
+    galaxy-disk workload's stars (200 points each) joined with themselves at
+    d = 0.1 kpc over the full extent, each pair of segments of different
+    stars once.  Filter mode timed over 3 runs after a warm-up; the plain FP64
+    path once for comparison.  pair tests = temporal-overlap pairs of the
+    ordered (query, entry) set, as for the searches."""
+    w = workloads.galaxy_disk(n_stars=args.self_join_stars, n_queries=1)
+    ent = w.entries
+    d = 0.1
+    idx = tdq.build_index(tdq.DeviceSegments(ent))
+    dev = tdq.DeviceSegments(ent)
+    out = {"workload": "galaxy_disk self-join: %d stars x 200 points (%d segments), d = %.2f kpc, full extent"
+                       % (args.self_join_stars, len(ent), d)}
+    for name, mode, reps in (("fp32filter", tdq.MODE_FP32_FILTER, 3), ("fp64", tdq.MODE_FP64, 1)):
+        tdq.self_join(idx, dev, d, mode=mode)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            res = tdq.self_join(idx, dev, d, mode=mode)
+        dt = (time.perf_counter() - t) / reps
+        st = tdq.get_stats(idx)
+        out[name] = {"ms": 1e3 * dt, "pair_tests_per_s": st["overlap_pairs"] / dt, "results": len(res),
+                     "overlap_pairs": st["overlap_pairs"], "interactions": st["interactions"],
+                     "fp64_pairs": st["fp64_pairs"]}
+    out["speedup_vs_plain_fp64"] = out["fp64"]["ms"] / out["fp32filter"]["ms"]
+    idx.free()
+    return out
+
+
 def serving_section(args, tdq, torch):
     """F3: 40,000 walks x 500 points resident (19.96 M entries); Poisson
     arrivals at 2,000/s for 10 s, each a fresh walk of 5..499 segments with
@@ -559,6 +591,9 @@ def main():
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_section(args, tdq, torch)
+    self_join = None
+    if rank == 0 and world == 1 and not args.no_self_join:
+        self_join = self_join_section(args, tdq, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -591,6 +626,7 @@ def main():
                                       "queries": head["queries_per_s"] / plain["queries_per_s"]},
             "batching_workload": batching,
             "serving_workload": serving,
+            "self_join_workload": self_join,
         }
         print(json.dumps(line), flush=True)
     plan.free()

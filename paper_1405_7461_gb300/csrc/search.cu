@@ -469,7 +469,9 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 // radii carry a factor 1 + 2^-20); R >= 2^-60 keeps every quantity normal.
 // Segments beyond 2^60 in magnitude carry a zero sphere and E = -inf, or an
 // infinite radius and K = -inf, and are never rejected.  The survivors
-// (entry, query) are appended to a list (one atomic per lane that has any);
+// (entry, query) are appended to a list through a per-warp shared-memory
+// buffer (one atomic per 256 survivors: dense workloads pass many pairs to
+// the refinement, and per-lane atomics on one counter would serialise);
 // traj_dist_refine_kernel then evaluates them in FP64.
 // Warps per block of the filter kernel.  It has no block-wide step, but the
 // warps of a block take adjacent item ranges, whose entry records largely
@@ -477,6 +479,7 @@ __device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr,
 constexpr int kFilterWarps = 8;
 constexpr int kFilterThreads = 32 * kFilterWarps;
 constexpr int kPer = 4;            // entries per lane per pass
+constexpr int kSurvBuf = 256;      // survivors a warp buffers before one atomic on the list
 constexpr int kPass = 32 * kPer;   // entries per pass
 
 // One entry's pre-test terms, each duplicated into both halves of a paired
@@ -542,12 +545,15 @@ struct FilterArgs {
     uint64_t surv_cap;
 };
 
-__global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(FilterArgs fa)
+__global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(FilterArgs fa)
 {
     const PairArgs &args = fa.p;
     __shared__ float4 qr_all[kFilterWarps][kQT];
+    __shared__ uint2 sbuf_all[kFilterWarps][kSurvBuf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *qr = qr_all[warp];
+    uint2 *sbuf = sbuf_all[warp];  // this warp's survivors not yet in the list
+    int nbuf = 0;                   // (warp-uniform)
     float *qrf = reinterpret_cast<float *>(qr);
     const int k_slot = (lane >> 1) * 8 + 6 + (lane & 1);  // this lane's K in qr[2i+1].zw
     DevCounters *ctr = args.ctr;
@@ -561,6 +567,18 @@ __global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(Filter
     const float4 *esph = args.e.sph;
     const float *esphe = args.e.sph_e;
     unsigned long long n_inter = 0;
+    // moves the buffered survivors to the list (called by the whole warp)
+    auto flush_survivors = [&]() {
+        if (nbuf == 0) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)nbuf);
+        base = __shfl_sync(kFull, base, 0);
+        __syncwarp();
+        for (int i = lane; i < nbuf; i += 32)
+            if (base + i < fa.surv_cap) fa.surv[base + i] = sbuf[i];
+        __syncwarp();
+        nbuf = 0;
+    };
 
     if (ibeg < iend) {
         uint64_t t = 0;
@@ -657,12 +675,29 @@ __global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(Filter
                     m[k] = lane + 32 * k < here ? (m[k] & qvalid) : 0u;
                     any |= m[k];
                 }
-                if (any == 0u) continue;
-                // append this lane's survivors (one atomic per lane that has any)
+                if (!__any_sync(kFull, any != 0u)) continue;
+                // append the warp's survivors: ranks by a warp scan, then into
+                // the warp's buffer (flushed to the list with one atomic per
+                // kSurvBuf survivors), or, for a pass with more survivors than
+                // the buffer holds, straight to the list
                 int cnt = 0;
 #pragma unroll
                 for (int k = 0; k < kPer; k++) cnt += __popc(m[k]);
-                unsigned long long pos = atomicAdd(&ctr->survivors, (unsigned long long)cnt);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                if (nbuf + total > kSurvBuf) flush_survivors();
+                const bool direct = total > kSurvBuf;
+                unsigned long long pos = nbuf + (incl - cnt);
+                if (direct) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)total);
+                    pos = __shfl_sync(kFull, base, 0) + (incl - cnt);
+                }
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
                     unsigned mk = m[k];
@@ -670,10 +705,15 @@ __global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(Filter
                     while (mk) {
                         const int bit = 31 - __clz(mk);
                         mk &= ~(1u << bit);
-                        if (pos < fa.surv_cap) fa.surv[pos] = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
+                        const uint2 sv = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
+                        if (!direct)
+                            sbuf[pos] = sv;
+                        else if (pos < fa.surv_cap)
+                            fa.surv[pos] = sv;
                         pos++;
                     }
                 }
+                if (!direct) nbuf += total;
             }
             if (!has_next) break;
             t = tn;
@@ -682,6 +722,7 @@ __global__ void __launch_bounds__(kFilterThreads) traj_dist_filter_kernel(Filter
             nqt = nqn;
             stage_queries(qn, lane < nqt, lane, qr, my_c2g, my_w);
         }
+        flush_survivors();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_inter += __shfl_xor_sync(kFull, n_inter, o);
