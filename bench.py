@@ -57,6 +57,19 @@ FLOPS_PER_CANDIDATE_FP32 = 7
 # (the 1.25 TFLOP/s nominal figure), FP32 128 FFMA/clk/SM.
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070
 FP32_PEAK_GFLOPS = 2 * 128 * 152 * 2.070
+# Algorithmic DRAM bytes of the dominant kernels: the filter kernel reads each
+# entry's 20 B pre-test record once per launch (the re-reads by neighbouring
+# query tiles are L2/L1 hits); the plain kernel stages 64 B of every entry of
+# a tile's range once per tile, i.e. 2 B per candidate pair of a full tile.
+FILTER_BYTES_PER_ENTRY = 20
+PLAIN_BYTES_PER_CANDIDATE = 2
+
+
+def hbm_peak_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0  # fallback figure of an earlier GB300 measurement
 CPU_SAMPLE_QUERIES = 20
 
 
@@ -205,9 +218,18 @@ def cpu_baseline(w, d_values, n_sample):
         r = oracle.search_sweep(w.entries, q, d, *w.window, threads=threads)
         pairs += r.overlap_pairs
     dt = time.perf_counter() - t
+    # one core, on a smaller sample of the same workload (2 query trajectories, d = the first threshold)
+    keep1 = keep[:2]
+    q1 = w.queries.take(np.nonzero(np.isin(w.queries.traj_id, keep1))[0])
+    t = time.perf_counter()
+    p1 = oracle.search_sweep(w.entries, q1, d_values[0], *w.window, threads=1).overlap_pairs
+    dt1 = time.perf_counter() - t
     return {"value": pairs / dt, "unit": "pair tests/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(keep)} of {w.n_query_traj} query trajectories ({len(q)} segments) x d in "
-                      f"{list(d_values)}, time-sweep oracle incl. its sort, {dt:.2f} s"}
+                      f"{list(d_values)}, time-sweep oracle incl. its sort, {dt:.2f} s",
+            "value_1_core": p1 / dt1,
+            "sample_1_core": f"{len(keep1)} query trajectories ({len(q1)} segments), d = {d_values[0]}, "
+                             f"1 thread, {dt1:.2f} s"}
 
 
 def run_reference(args):
@@ -249,9 +271,11 @@ def run_reference(args):
     return 0
 
 
-def roofline(mode, tot, n_launch):
+def roofline(mode, tot, n_launch, n_entries):
     """Roofline of the dominant kernel over the timed launches: algorithmic
-    work per launch / the kernel's average CUDA-event duration."""
+    work per launch / the kernel's average CUDA-event duration; beside it the
+    kernel's algorithmic DRAM bytes per second against the measured HBM
+    copy bandwidth."""
     kern_ms = tot["kernel_ms"] / n_launch
     if mode == "fp64":
         work = FLOPS_PER_PAIR_FP64 * tot["fp64_pairs"] / n_launch
@@ -271,6 +295,12 @@ def roofline(mode, tot, n_launch):
          "peak_source": src}
     if mode != "fp64":
         r["refine_kernel_ms_avg"] = tot["refine_ms"] / n_launch
+        hbm_bytes = FILTER_BYTES_PER_ENTRY * n_entries
+    else:
+        hbm_bytes = PLAIN_BYTES_PER_CANDIDATE * tot["interactions"] / n_launch
+    gbs = hbm_bytes / (kern_ms / 1e3) / 1e9
+    r["hbm"] = {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": gbs, "peak_gbs": hbm_peak_gbs(),
+                "frac": gbs / hbm_peak_gbs(), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     return r
 
 
@@ -542,7 +572,7 @@ def main():
                 "fp64_pairs_per_step": tot["fp64_pairs"] / args.steps,
                 "filter_survivors_per_step": tot["survivors"] / args.steps,
                 "results_per_step": tot["results"] / args.steps, "gpu_launches": int(tot["launches"]),
-                "roofline": roofline("fp64" if mode == "fp64" else "fp32filter", tot, n_launch)}
+                "roofline": roofline("fp64" if mode == "fp64" else "fp32filter", tot, n_launch, len(w.entries))}
 
     clocks = ClockSampler(dev)
     clocks.start()
