@@ -241,15 +241,28 @@ class DeviceSegments:
         self.n = int(self.cols[0].shape[0])
 
     def struct(self) -> tdq_segments:
+        # reused while the same tensor objects are attached
+        key = (id(self.cols), tuple(id(c) for c in self.cols), id(self.seg_id), id(self.traj_id), self.n)
+        cached = getattr(self, "_struct", None)
+        if cached is not None and cached[0] == key:
+            return cached[1]
         s = tdq_segments()
         for c, a in zip(COLUMNS, self.cols):
-            assert a.is_cuda and a.is_contiguous()
+            if not (a.is_cuda and a.is_contiguous() and a.dtype == self._f64()):
+                raise ValueError("tdq: device columns must be contiguous CUDA float64 tensors")
             setattr(s, c, a.data_ptr() if self.n else None)
         s.seg_id = self.seg_id.data_ptr() if self.n else None
         s.traj_id = self.traj_id.data_ptr() if self.n else None
         s.n = self.n
         s.on_device = 1
+        self._struct = (key, s)
         return s
+
+    @staticmethod
+    def _f64():
+        import torch
+
+        return torch.float64
 
     @property
     def nbytes(self):
@@ -493,8 +506,12 @@ def _per_query_ptrs(queries, d, t0, t1):
     if isinstance(queries, DeviceSegments):
         import torch
 
+        dev = queries.cols[0].device
+        if all(getattr(a, "is_cuda", False) and a.dtype == torch.float64 and a.device == dev and a.is_contiguous()
+               for a in (d, t0, t1)):
+            return None, [a.data_ptr() for a in (d, t0, t1)]  # already in place: no copies
         keep = [torch.as_tensor(np.asarray(a, np.float64) if not hasattr(a, "is_cuda") else a,
-                                dtype=torch.float64).to(queries.cols[0].device).contiguous() for a in (d, t0, t1)]
+                                dtype=torch.float64).to(dev).contiguous() for a in (d, t0, t1)]
         return keep, [k.data_ptr() for k in keep]
     keep = [np.ascontiguousarray(a, np.float64) for a in (d, t0, t1)]
     return keep, [k.ctypes.data for k in keep]
