@@ -298,8 +298,8 @@ struct PairSmem {
     int64_t qts[kQT], qte[kQT], qid[kQT], qtraj[kQT];
     long long item;
     long long tile;
-    // followed by the entry chunk: FP64 mode: 6 double columns + 2 key
-    // columns of `chunk` items; filter mode: 2 key columns + 1 float4 column
+    // followed by the entry chunk: 6 double columns + 2 key columns of
+    // `chunk` items (the plain FP64 kernel)
 };
 
 struct PairArgs {
