@@ -187,3 +187,45 @@ def test_plan_results_into_caller_arrays(tdq):
             plan.results(out=tuple(a[: c - 1] for a in outs))
         with pytest.raises(ValueError):
             plan.results(out=(outs[2], outs[1], outs[2], outs[3]))
+
+
+def test_batching_workload_full_size_sampled(tdq):
+    """The batching workload at full size (20,000 walks x 300 points = 5.98 M
+    entries; 5,000 query trajectories with their own d and window, 449 k
+    query segments) through one filter-mode plan with the batch size and
+    entry chunk the autotuner picks for the benchmark; a seeded sample of 8
+    query trajectories is checked pair by pair against the oracle."""
+    w = workloads.batching_walks()
+    q = w.queries
+    n = len(q)
+    batch = 42522
+    with tdq.build_index(tdq.DeviceSegments(w.entries), bin_count=10000) as idx:
+        qdev = tdq.DeviceSegments(q)
+        dd, t0, t1 = (torch.from_numpy(a).cuda() for a in (w.q_d, w.q_t0, w.q_t1))
+        got = []
+        with tdq.Plan(idx, batch, mode=tdq.MODE_FP32_FILTER, entry_chunk=256) as plan:
+            for a in range(0, n, batch):
+                e = min(a + batch, n)
+                sub = tdq.DeviceSegments(tensors=([c[a:e] for c in qdev.cols], qdev.seg_id[a:e], qdev.traj_id[a:e]))
+                plan.search(sub, dd[a:e], t0[a:e], t1[a:e])
+                got.append(plan.results())
+    merged = tdq.Results(*[np.concatenate([getattr(r, f) for r in got])
+                           for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit")])
+    # half of the sample among trajectories with results (pairs are rare:
+    # ~0.007 per query segment), half at random; the oracle checks both ways
+    rng = np.random.default_rng(11)
+    seg_traj = dict(zip(q.seg_id.tolist(), q.traj_id.tolist()))
+    with_hits = np.unique([seg_traj[s] for s in np.unique(merged.query_seg_id).tolist()])
+    keep = np.unique(np.concatenate([rng.choice(with_hits, size=min(6, len(with_hits)), replace=False),
+                                     rng.choice(np.unique(q.traj_id), size=6, replace=False)]))
+    sel = np.nonzero(np.isin(q.traj_id, keep))[0]
+    qs = q.take(sel)
+    qd, q0, q1 = w.q_d[sel], w.q_t0[sel], w.q_t1[sel]
+    mine = np.isin(merged.query_seg_id, qs.seg_id)
+    gi = {"qi": _positions(merged.query_seg_id[mine], qs.seg_id),
+          "ei": _positions(merged.entry_seg_id[mine], w.entries.seg_id),
+          "t_enter": merged.t_enter[mine], "t_exit": merged.t_exit[mine]}
+    ora = _oracle_per_trajectory(w, qs, qd, q0, q1)
+    dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, qs, qi, q0[qi], q1[qi])  # noqa: E731
+    cmp = compare_results(gi, ora, w.entries, qs, None, dmin_fn=dmin, d_per_query=qd)
+    assert cmp["matched"] == len(ora["qi"]) > 0

@@ -136,3 +136,30 @@ def test_timeouts_and_invalid_requests_are_reported_on_the_host(tdq, db, request
             assert e.status == tdq.TDQ_ERR_TIMEOUT
         for t in tickets:
             srv.wait(t)
+
+
+def test_serving_workload_full_size_sampled(tdq):
+    """The serving workload at full size: 40,000 walks x 500 points (19.96 M
+    entries) resident, the benchmark's server settings (3 lanes, 16 GiB cap,
+    batches up to 65,536 segments, filter mode); 64 requests submitted at
+    once; a seeded sample of 4 is checked pair by pair against the oracle."""
+    db = workloads.serving_database(n_traj=40_000, n_points=500)
+    reqs = workloads.serving_requests(n_requests=64, rate_per_s=2000.0, n_points=500)
+    with tdq.build_index(tdq.DeviceSegments(db)) as idx, \
+            tdq.Server(idx, max_batch_query_segments=65536, memory_cap_bytes=16 << 30, lanes=3,
+                       mode=tdq.MODE_FP32_FILTER, results_per_query_segment=1.0) as srv:
+        tickets = [srv.submit(rq.query, rq.d, rq.t0, rq.t1) for rq in reqs]
+        got = [srv.wait(t)[0] for t in tickets]
+    matched = 0
+    for k in np.random.default_rng(3).choice(len(reqs), size=4, replace=False):
+        rq, g = reqs[k], got[k]
+        ref = oracle.search_sweep(db, rq.query, rq.d, rq.t0, rq.t1)
+        qpos = {int(s): i for i, s in enumerate(rq.query.seg_id)}
+        gi = {"qi": np.array([qpos[int(s)] for s in g.query_seg_id], np.int64), "ei": g.entry_seg_id.copy(),
+              "t_enter": g.t_enter, "t_exit": g.t_exit}
+        cmp = compare_results(gi, {"qi": ref.query_index, "ei": ref.entry_index, "t_enter": ref.t_enter,
+                                   "t_exit": ref.t_exit}, db, rq.query, rq.d, rq.t0, rq.t1,
+                              dmin_fn=lambda ei, qi: oracle.pair_dmin(db, ei, rq.query, qi, rq.t0, rq.t1))
+        assert cmp["matched"] == len(ref.query_index)
+        matched += cmp["matched"]
+    assert matched > 0
