@@ -225,8 +225,10 @@ tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
  * It runs the same kernels as tdq_search_device, with the same arguments,
  * results and errors, but keeps its per-search scratch in one fixed
- * file-scope device array of about 1.5 MiB that every device loading the
- * library holds until the process exits.
+ * file-scope device array of about 1.5 MiB, held by the device until the
+ * process exits.  CUDA loads device code and arrays lazily; tdq_build_index
+ * loads all of the library's device code (this array included) on the
+ * index's device, so no search call -- this one in particular -- loads any.
  *  - Limit: at most 8192 query segments per call; more is rejected with
  *    TDQ_ERR_INVALID and a message naming the limit.
  *  - The first call on a device resolves the array's device address

@@ -1,0 +1,384 @@
+// Filter mode (TDQ_MODE_FP32_FILTER): a conservative FP32 bounding-sphere
+// pre-test of every candidate pair, then the FP64 evaluation of the
+// survivors with the plain path's per-pair code (Sec. 5, Algorithm 1), so
+// that the result set equals the plain FP64 search's.
+#include "pipeline.cuh"
+
+namespace tdq {
+namespace {
+
+// Work items of the filter kernel are (tile, chunk) pairs as for the plain
+// kernel, but each is processed by one warp: the warps of the grid split the
+// items into contiguous ranges, and a warp treats its items of one tile as
+// one run of consecutive sorted entries.  It walks those runs tile by tile,
+// keeps the tile's 32 query segments in its own slice of shared memory, and
+// streams the entries through registers, four per lane per pass over the
+// queries (128 per pass); the next pass's records -- in the same run or at
+// the start of the next one -- are loaded while the current pass is tested.
+// No CTA-wide barrier is involved.
+//
+// For a pass, lane j forms the bound R_j = w_max + w_j (rounded up), w_max
+// the largest entry radius of the pass (one warp max-reduction over the
+// records already in registers), and
+//   K_j = |c_j|^2 (1 - g) - R_j^2   (rounded down, g = 2^-20);
+// each entry carries E_e = |c_e|^2 (1 - g) rounded down.  Per candidate pair
+// the test is one add and three FMAs -- issued as paired FP32 instructions
+// that evaluate two queries at once -- and one funnel shift that moves the
+// sign of
+//   v = E_e + K_j - 2 c_j . c_e  =  |c_e - c_j|^2 - R_j^2 - g (|c_e|^2 + |c_j|^2)
+// into the lane's 32-bit mask.  v is negative whenever the exact spheres
+// meet: with u = 2^-24 the four roundings of v add at most
+// u (8 (|c_e|^2 + |c_j|^2) + 4 R^2), less than the g (|c_e|^2 + |c_j|^2) = 16u (...)
+// subtracted and the 32u R^2 by which R_j^2 exceeds the exact bound (the
+// radii carry a factor 1 + 2^-20); R >= 2^-60 keeps every quantity normal.
+// Segments beyond 2^60 in magnitude carry a zero sphere and E = -inf, or an
+// infinite radius and K = -inf, and are never rejected.  The survivors
+// (entry, query) are appended to a list through a per-warp shared-memory
+// buffer (one atomic per 256 survivors: dense workloads pass many pairs to
+// the refinement, and per-lane atomics on one counter would serialise);
+// traj_dist_refine_kernel then evaluates them in FP64.
+
+// Warps per block of the filter kernel.  It has no block-wide step, but the
+// warps of a block take adjacent item ranges, whose entry records largely
+// coincide, so that they share the SM's L1 cache.
+constexpr int kFilterWarps = 8;
+constexpr int kFilterThreads = 32 * kFilterWarps;
+constexpr int kPer = 4;            // entries per lane per pass
+constexpr int kSurvBuf = 256;      // survivors a warp buffers before one atomic on the list
+constexpr int kPass = 32 * kPer;   // entries per pass
+
+// One entry's pre-test terms, each duplicated into both halves of a paired
+// FP32 operand.
+struct EntryDup {
+    float2 x, y, z, e;
+};
+
+__device__ __forceinline__ EntryDup dup(float4 s, float e)
+{
+    return EntryDup{make_float2(s.x, s.x), make_float2(s.y, s.y), make_float2(s.z, s.z), make_float2(e, e)};
+}
+
+// v for the two queries j, j+1 of a pair at once; qa = (-2x_j, -2x_j+1,
+// -2y_j, -2y_j+1), qb = (-2z_j, -2z_j+1, K_j, K_j+1).
+__device__ __forceinline__ float2 sphere_gap_pair(const EntryDup &e, float4 qa, float4 qb)
+{
+    float2 v = __fadd2_rn(e.e, make_float2(qb.z, qb.w));
+    v = __ffma2_rn(make_float2(qa.x, qa.y), e.x, v);
+    v = __ffma2_rn(make_float2(qa.z, qa.w), e.y, v);
+    return __ffma2_rn(make_float2(qb.x, qb.y), e.z, v);
+}
+
+// The warp's run of entries in tile t: its items there are
+// [max(ibeg, tile_work[t]), min(iend, tile_work[t+1])), chunk_len entries each.
+__device__ __forceinline__ void filter_run(const PairArgs &args, uint64_t t, unsigned long long ibeg,
+                                           unsigned long long iend, int64_t &eb, int64_t &ee)
+{
+    const unsigned long long wb = args.tile_work[t], wn = args.tile_work[t + 1];
+    const int64_t lo = args.tile_lo[t], hi = args.tile_hi[t];
+    eb = lo + (int64_t)(max(ibeg, wb) - wb) * args.chunk;
+    ee = min(lo + (int64_t)(min(iend, wn) - wb) * args.chunk, hi);
+}
+
+// Query terms of lane j for its tile: -2 c_j into the warp's table (pairs of
+// queries interleaved: qr[2i] = (-2x, -2y of queries 2i, 2i+1), qr[2i+1].xy =
+// -2z of both; qr[2i+1].zw receives K of both every pass), and |c_j|^2 (1 - g)
+// and w_j kept in registers.  Lanes past the tile's last query hold zeros.
+__device__ __forceinline__ void stage_queries(float4 s, bool real, int lane, float4 *qr, float &c2g, float &w)
+{
+    if (!real) s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float X = -2.0f * s.x, Y = -2.0f * s.y, Z = -2.0f * s.z;
+    w = s.w;
+    if (isinf(s.w)) {  // huge magnitudes: K = -inf, never rejected
+        X = Y = Z = 0.f;
+        c2g = 0.f;
+    } else {
+        c2g = __fmul_rd(__fmaf_rd(s.z, s.z, __fmaf_rd(s.y, s.y, __fmul_rd(s.x, s.x))), 1.0f - 0x1p-20f);
+    }
+    const bool odd = lane & 1;
+    const float r1 = __shfl_xor_sync(kFull, odd ? X : Z, 1);
+    const float r2 = __shfl_xor_sync(kFull, Y, 1);
+    __syncwarp();  // the previous tile's table is no longer read
+    if (odd)
+        *reinterpret_cast<float2 *>(&qr[lane]) = make_float2(r1, Z);
+    else
+        qr[lane] = make_float4(X, r1, Y, r2);
+}
+
+__global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(FilterArgs fa)
+{
+    const PairArgs &args = fa.p;
+    __shared__ float4 qr_all[kFilterWarps][kQT];
+    __shared__ uint2 sbuf_all[kFilterWarps][kSurvBuf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *qr = qr_all[warp];
+    uint2 *sbuf = sbuf_all[warp];  // this warp's survivors not yet in the list
+    int nbuf = 0;                   // (warp-uniform)
+    float *qrf = reinterpret_cast<float *>(qr);
+    const int k_slot = (lane >> 1) * 8 + 6 + (lane & 1);  // this lane's K in qr[2i+1].zw
+    DevCounters *ctr = args.ctr;
+    const unsigned long long total = args.tile_work[args.ntiles];
+    const uint64_t nvalid = ctr->valid_queries;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * kFilterWarps;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * kFilterWarps + warp;
+    const unsigned long long per = (total + nwarps - 1) / nwarps;
+    const unsigned long long ibeg = min(gw * per, total);
+    const unsigned long long iend = min(ibeg + per, total);
+    const float4 *esph = args.e.sph;
+    const float *esphe = args.e.sph_e;
+    unsigned long long n_inter = 0;
+    // moves the buffered survivors to the list (called by the whole warp)
+    auto flush_survivors = [&]() {
+        if (nbuf == 0) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)nbuf);
+        base = __shfl_sync(kFull, base, 0);
+        __syncwarp();
+        for (int i = lane; i < nbuf; i += 32)
+            if (base + i < fa.surv_cap) fa.surv[base + i] = sbuf[i];
+        __syncwarp();
+        nbuf = 0;
+    };
+
+    if (ibeg < iend) {
+        uint64_t t = 0;
+        {
+            uint64_t lo = 0, hi = args.ntiles;  // last tile whose first item is <= ibeg
+            while (hi - lo > 1) {
+                uint64_t mid = (lo + hi) >> 1;
+                if (args.tile_work[mid] <= ibeg) lo = mid; else hi = mid;
+            }
+            t = lo;
+        }
+        int64_t eb, ee;
+        filter_run(args, t, ibeg, iend, eb, ee);
+        int nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)t * kQT);
+        float my_c2g, my_w;
+        stage_queries(args.q.sph[(int64_t)t * kQT + min(lane, nqt - 1)], lane < nqt, lane, qr, my_c2g, my_w);
+        float4 ns[kPer];
+        float nse[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const int64_t e = eb + lane + 32 * k;
+            ns[k] = e < ee ? esph[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            nse[k] = e < ee ? esphe[e] : 0.f;
+        }
+        for (;;) {
+            // the next run of this warp (a later tile with items in range),
+            // located and its queries fetched while this run is tested
+            uint64_t tn = t + 1;
+            const bool has_next = args.tile_work[tn] < iend;
+            int64_t ebn = 0, een = 0;
+            int nqn = 0;
+            float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (has_next) {
+                while (args.tile_work[tn + 1] == args.tile_work[tn]) tn++;
+                filter_run(args, tn, ibeg, iend, ebn, een);
+                nqn = (int)min((uint64_t)kQT, nvalid - tn * kQT);
+                qn = args.q.sph[(int64_t)tn * kQT + min(lane, nqn - 1)];
+            }
+            const int64_t q0 = (int64_t)t * kQT;
+            const unsigned qvalid = 0xffffffffu << (kQT - nqt);  // bit 31-j <-> query j
+            if (lane == 0) n_inter += (unsigned long long)(ee - eb) * (unsigned long long)nqt;
+            for (int64_t pe = eb; pe < ee; pe += kPass) {
+                EntryDup ed[kPer];
+                float wl = 0.f;
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    ed[k] = dup(ns[k], nse[k]);
+                    wl = fmaxf(wl, ns[k].w);
+                }
+                // the next pass's records: this run, else the next run's first pass
+                {
+                    const bool same = pe + kPass < ee;
+                    const int64_t nb = same ? pe + kPass : ebn;
+                    const int left = (int)min(same ? ee - nb : een - nb, (int64_t)kPass);
+                    const float4 *ps = esph + nb + lane;
+                    const float *pse = esphe + nb + lane;
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) {
+                        const bool in = lane + 32 * k < left;
+                        ns[k] = in ? ps[32 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        nse[k] = in ? pse[32 * k] : 0.f;
+                    }
+                }
+                // radii are non-negative: their bit patterns order like the values
+                const float wmax = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(wl)));
+                const float Rj = __fadd_ru(wmax, my_w);
+                const float Kj = __fsub_rd(my_c2g, __fmul_ru(Rj, Rj));
+                __syncwarp();  // the previous pass's K are no longer read
+                qrf[k_slot] = Kj;
+                __syncwarp();
+                // two independent mask chains per entry (queries 0-15 and
+                // 16-31), joined afterwards: the funnel shifts of one chain
+                // depend on each other
+                unsigned m[kPer], mh[kPer];
+#pragma unroll
+                for (int k = 0; k < kPer; k++) m[k] = mh[k] = 0u;
+#pragma unroll
+                for (int j = 0; j < kQT; j += 2) {
+                    const float4 qa = qr[j], qb = qr[j + 1];
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) {
+                        const float2 v = sphere_gap_pair(ed[k], qa, qb);
+                        unsigned &mm = j < kQT / 2 ? mh[k] : m[k];
+                        mm = __funnelshift_l(__float_as_uint(v.x), mm, 1);
+                        mm = __funnelshift_l(__float_as_uint(v.y), mm, 1);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kPer; k++) m[k] = __byte_perm(m[k], mh[k], 0x5410);
+                unsigned any = 0u;
+                const int here = (int)min(ee - pe, (int64_t)kPass);
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    m[k] = lane + 32 * k < here ? (m[k] & qvalid) : 0u;
+                    any |= m[k];
+                }
+                if (!__any_sync(kFull, any != 0u)) continue;
+                // append the warp's survivors: ranks by a warp scan, then into
+                // the warp's buffer (flushed to the list with one atomic per
+                // kSurvBuf survivors), or, for a pass with more survivors than
+                // the buffer holds, straight to the list
+                int cnt = 0;
+#pragma unroll
+                for (int k = 0; k < kPer; k++) cnt += __popc(m[k]);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                if (nbuf + total > kSurvBuf) flush_survivors();
+                const bool direct = total > kSurvBuf;
+                unsigned long long pos = nbuf + (incl - cnt);
+                if (direct) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)total);
+                    pos = __shfl_sync(kFull, base, 0) + (incl - cnt);
+                }
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    unsigned mk = m[k];
+                    const uint32_t ek = (uint32_t)(pe + lane + 32 * k);
+                    while (mk) {
+                        const int bit = 31 - __clz(mk);
+                        mk &= ~(1u << bit);
+                        const uint2 sv = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
+                        if (!direct)
+                            sbuf[pos] = sv;
+                        else if (pos < fa.surv_cap)
+                            fa.surv[pos] = sv;
+                        pos++;
+                    }
+                }
+                if (!direct) nbuf += total;
+            }
+            if (!has_next) break;
+            t = tn;
+            eb = ebn;
+            ee = een;
+            nqt = nqn;
+            stage_queries(qn, lane < nqt, lane, qr, my_c2g, my_w);
+        }
+        flush_survivors();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_inter += __shfl_xor_sync(kFull, n_inter, o);
+    if (lane == 0 && n_inter) atomicAdd(&ctr->interactions, n_inter);
+}
+
+// FP64 evaluation of the filter's survivors.  The pre-test ignores time, so
+// most survivors do not overlap in time; a warp checks the exact span keys
+// of 32 survivors at a time, queues the overlapping ones in its slice of
+// shared memory, and runs the FP64 code of the plain kernel (then the
+// warp-aggregated append) on full batches of 32 queued pairs: the FP64 pipe
+// is busy for a warp instruction whatever the number of active lanes.
+constexpr int kRefineWarps = kPairThreads / 32;
+
+__device__ __forceinline__ void refine_batch(const PairArgs &args, uint2 sv, bool active, uint64_t cap, int lane,
+                                             unsigned lt_mask)
+{
+    const int64_t ek = sv.x, qk = sv.y;
+    const PairEval r = eval_pair_fp64(active, args.e.ts_key[ek], args.e.te_key[ek], args.q.ts_key[qk],
+                                      args.q.te_key[qk], args.e.px[ek], args.e.py[ek], args.e.pz[ek], args.e.vx[ek],
+                                      args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk], args.q.pz[qk],
+                                      args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
+    append_hits(r, args.ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+}
+
+__global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterArgs fa)
+{
+    const PairArgs &args = fa.p;
+    __shared__ uint2 queue_all[kRefineWarps][64];
+    DevCounters *ctr = args.ctr;
+    const int lane = threadIdx.x & 31;
+    uint2 *queue = queue_all[threadIdx.x >> 5];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t cap = args.out.capacity;
+    const unsigned long long ns = min(ctr->survivors, (unsigned long long)fa.surv_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long n_fp64 = 0;
+    int queued = 0;  // warp-uniform, < 32 between chunks
+    // warp-uniform trip count (the ballots, eval_pair_fp64 and append_hits vote over the warp)
+    const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (unsigned long long wb = first; wb < ns; wb += stride) {
+        const unsigned long long k = wb + lane;
+        const bool valid = k < ns;
+        const uint2 sv = valid ? fa.surv[k] : make_uint2(0u, 0u);
+        bool active = valid && args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
+                      args.e.te_key[sv.x] > args.q.ts_key[sv.y];
+        if (args.flags && active)
+            active = pair_allowed(args.flags, args.q.qtraj[sv.y], args.q.qid[sv.y], args.e.traj_id[sv.x],
+                                  args.e.seg_id[sv.x]);
+        const unsigned am = __ballot_sync(kFull, active);
+        if (active) queue[queued + __popc(am & lt_mask)] = sv;
+        queued += __popc(am);
+        n_fp64 += __popc(am);
+        __syncwarp();
+        if (queued >= 32) {
+            const uint2 qv = queue[lane];
+            const uint2 rest = lane + 32 < queued ? queue[lane + 32] : make_uint2(0u, 0u);
+            __syncwarp();
+            if (lane + 32 < queued) queue[lane] = rest;
+            queued -= 32;
+            __syncwarp();
+            refine_batch(args, qv, true, cap, lane, lt_mask);
+        }
+    }
+    if (queued > 0) {  // the last, partial batch
+        const bool active = lane < queued;
+        refine_batch(args, active ? queue[lane] : make_uint2(0u, 0u), active, cap, lane, lt_mask);
+    }
+    if (lane == 0 && n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
+}
+
+}  // namespace
+
+// The filter mode's two kernels as persistent grids (as many CTAs as fit on
+// every SM at once): the FP32 pre-test, then the FP64 refinement of its
+// survivors; mid (may be null) is recorded between them with the flags
+// evflags.
+cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream_t stream, cudaEvent_t mid,
+                                  unsigned evflags)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_filter_kernel, kFilterThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    traj_dist_filter_kernel<<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
+    if (mid && (e = cudaEventRecordWithFlags(mid, stream, evflags)) != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_refine_kernel, kPairThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    traj_dist_refine_kernel<<<sm_count * per_sm, kPairThreads, 0, stream>>>(fa);
+    return cudaGetLastError();
+}
+
+cudaError_t load_filter_module()
+{
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, traj_dist_filter_kernel);
+}
+
+}  // namespace tdq

@@ -20,14 +20,6 @@
 namespace tdq {
 namespace {
 
-constexpr int kBlock = 256;
-
-inline unsigned grid_for(uint64_t n, int block = kBlock)
-{
-    uint64_t g = (n + block - 1) / block;
-    return (unsigned)(g > 0 ? g : 1);
-}
-
 struct EntryInput {
     const double *c[8];  // xs ys zs ts xe ye ze te
     const int64_t *seg_id, *traj_id;
@@ -113,14 +105,6 @@ __global__ void te_store(const uint64_t *keys, uint64_t n, int64_t *te_sorted)
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     te_sorted[k] = (int64_t)(keys[k] ^ 0x8000000000000000ULL);
-}
-
-__device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
-{
-    double f = floor((t - t_min) / width);
-    if (!(f < (double)(m - 1))) return (int64_t)m - 1;
-    if (f < 0.0) return 0;
-    return (int64_t)f;
 }
 
 __global__ void bin_init(int64_t *bin_end_key, uint32_t m)
@@ -214,17 +198,6 @@ __global__ void bin_export(const int64_t *bin_begin, const int64_t *bin_end_key,
     }
 }
 
-template <typename T>
-T *carve(char *&p, uint64_t count)
-{
-    T *r = (T *)p;
-    uint64_t bytes = (count * sizeof(T) + 255) & ~(uint64_t)255;
-    p += bytes;
-    return r;
-}
-
-inline uint64_t carve_bytes(uint64_t count, uint64_t size) { return (count * size + 255) & ~(uint64_t)255; }
-
 }  // namespace
 }  // namespace tdq
 
@@ -252,6 +225,10 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     if (!idx) return set_error(TDQ_ERR_NOMEM, "tdq_build_index: host allocation failed");
     cudaGetDevice(&idx->device);
     cudaDeviceGetAttribute(&idx->sm_count, cudaDevAttrMultiProcessorCount, idx->device);
+    if (load_device_code() != cudaSuccess) {
+        delete idx;
+        return cuda_error(cudaGetLastError(), "tdq_build_index: loading the device code");
+    }
     idx->n = n;
     idx->m = m;
     for (int k = 0; k < kSearchEvents; k++) {

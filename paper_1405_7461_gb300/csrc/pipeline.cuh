@@ -1,0 +1,213 @@
+// Definitions shared by the search pipeline's translation units -- search.cu
+// (query preparation, the plain FP64 pair kernel, the host side), filter.cu
+// (the FP32 pre-test and the FP64 refinement of its survivors) and
+// noalloc.cu (the allocation-free entry point): tile sizes, argument
+// structs, the kernels and launchers used by more than one file, and the
+// per-pair FP64 code (Sec. 5, Algorithm 1) that both pair paths run.
+#pragma once
+
+#include <math.h>
+
+#include "tdq_internal.cuh"
+
+namespace tdq {
+
+constexpr int kQT = 32;             // query segments per tile (one bit each in a lane mask)
+constexpr int kPairThreads = 256;   // threads of the pair kernels
+
+struct BinView {
+    const int64_t *bin_begin, *bin_pmax_key;
+    const int64_t *ts_key, *te_sorted, *te_bin_begin;  // sorted t_start / t_end keys and the t_end bin table
+    double t_min, width;
+    uint32_t m;
+    float inv_width_f;  // 1 / width in FP32 (for sort keys only)
+};
+
+inline BinView bin_view(const tdq_index *idx)
+{
+    return BinView{idx->bin_begin, idx->bin_pmax_key, idx->e.ts_key, idx->e.te_sorted, idx->te_bin_begin,
+                   idx->t_min, idx->width, idx->m, idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
+}
+
+// Arguments of query_gather (one struct, so that a captured launch can be
+// re-bound to new inputs in one step).
+struct GatherArgs {
+    const double *const *pre;
+    const float4 *pre_sph;
+    const int64_t *seg_id;
+    const int64_t *traj_id;  // may be null (then 0)
+    const uint32_t *order;
+    uint64_t nq;
+    DevCounters *ctr;
+    BinView bins;
+    QuerySoA q;
+    uint64_t ntiles;
+    uint32_t chunk;
+    int64_t *tile_lo, *tile_hi;
+    unsigned long long *tile_work;  // chunks per tile (the scan turns it into offsets); ntiles + 1
+    bool count_overlaps;
+};
+
+struct PairArgs {
+    EntrySoA e;
+    QuerySoA q;
+    const int64_t *tile_lo, *tile_hi;
+    const unsigned long long *tile_work;
+    uint64_t ntiles;
+    DevCounters *ctr;
+    tdq_result_buffer out;
+    uint32_t chunk;
+    uint32_t flags;  // TDQ_FLAG_* pair filters (0: every pair)
+};
+
+// The pair filters of TDQ_FLAG_OTHER_TRAJECTORIES / TDQ_FLAG_UNORDERED_ONCE
+// (query (ii) of Sec. 2.1: every trajectory against all other trajectories,
+// each unordered pair once when the database is the query set).
+__device__ __forceinline__ bool pair_allowed(uint32_t flags, int64_t qtraj, int64_t qseg, int64_t etraj, int64_t eseg)
+{
+    if ((flags & TDQ_FLAG_OTHER_TRAJECTORIES) && etraj == qtraj) return false;
+    if ((flags & TDQ_FLAG_UNORDERED_ONCE) && !(eseg > qseg)) return false;
+    return true;
+}
+
+struct FilterArgs {
+    PairArgs p;
+    uint2 *surv;            // survivor list: (sorted entry position, sorted query position)
+    uint64_t surv_cap;
+};
+
+// Kernels launched from more than one file (defined in search.cu).
+__global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *const *pre, float4 *pre_sph,
+                           uint64_t *keys, uint32_t *vals, DevCounters *ctr);
+__global__ void query_gather(GatherArgs a);
+__global__ void publish_counters(const DevCounters *src, DevCounters *dst);
+
+// Pair kernel of the requested mode as a persistent grid (search.cu); the
+// filter mode's pair (filter.cu).
+cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
+                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags);
+cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream_t stream, cudaEvent_t mid,
+                                  unsigned evflags);
+
+// TDQ_ERR_INVALID unless d is finite and >= 0 and [t0, t1] is a window (search.cu).
+tdq_status check_scalars(double d, double t0, double t1);
+
+namespace {
+
+// calcTimeInterval for a pair that is within d: the roots of
+// A tau^2 + 2 Bh tau + C over tau in [0, L] (tau = time since a), by the
+// cancellation-free quadratic formula; a tangent contact that rounding pushes
+// out of the root bracket collapses to the closest point.
+__device__ __noinline__ void pair_interval(double A, double Bh, double C, double disc, double a, double b,
+                                           double *tin, double *tout)
+{
+    double L = b - a;
+    double tlo, thi;
+    if (le0(A)) {  // no relative motion: the whole span
+        tlo = 0.0;
+        thi = L;
+    } else {
+        double sq = sqrt(lt0(disc) ? 0.0 : disc);
+        double qq = -(Bh + copysign(sq, Bh));
+        double r1, r2;
+        if (qq == 0.0) {
+            r1 = 0.0;
+            r2 = 0.0;
+        } else {
+            r1 = qq / A;
+            r2 = C / qq;
+        }
+        double lo = fmin(r1, r2), hi = fmax(r1, r2);
+        tlo = fmax(lo, 0.0);
+        thi = fmin(hi, L);
+        if (tlo > thi) {
+            double ts = fmin(fmax(-Bh / A, 0.0), L);
+            tlo = ts;
+            thi = ts;
+        }
+    }
+    *tin = le0(tlo) ? a : (tlo >= L ? b : a + tlo);
+    *tout = thi >= L ? b : (le0(thi) ? a : a + thi);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 evaluation of one pair, shared by both pair kernels so that a pair
+// gets bitwise the same decision and interval in either mode.
+//
+// temporalIntersection: common span [a, b] from the integer time keys; S is
+// the segment that starts at a, O the other one.  calcTimeInterval: with
+// tau = t - a, |dp + dv tau|^2 - d^2 = A tau^2 + 2 Bh tau + C, dp = O - S at
+// a, dv = v_O - v_S.  The minimum over [0, L] is <= 0 without dividing:
+// C <= 0 (in range at a), or approaching (Bh < 0) with a real root pair
+// (disc >= 0) whose closest point lies inside the span or whose value at L
+// is <= 0.  All lanes of the warp must call it (warp vote inside).
+// ---------------------------------------------------------------------------
+struct PairEval {
+    double A, Bh, C, disc, a, b;
+    bool hit;
+};
+
+__device__ __forceinline__ PairEval eval_pair_fp64(bool active, int64_t ets_k, int64_t ete_k, int64_t qts_k,
+                                                   int64_t qte_k, double epx_, double epy_, double epz_,
+                                                   double evx_, double evy_, double evz_, double qpx_, double qpy_,
+                                                   double qpz_, double qvx_, double qvy_, double qvz_, double d2)
+{
+    PairEval r;
+    const bool e_later = ets_k >= qts_k;
+    const int64_t a_k = e_later ? ets_k : qts_k;
+    const int64_t b_k = min(ete_k, qte_k);
+    const int64_t o_k = e_later ? qts_k : ets_k;
+    r.a = key_double(a_k);
+    r.b = key_double(b_k);
+    const double o_ts = key_double(o_k);
+    const double opx = e_later ? qpx_ : epx_, opy = e_later ? qpy_ : epy_, opz = e_later ? qpz_ : epz_;
+    const double ovx = e_later ? qvx_ : evx_, ovy = e_later ? qvy_ : evy_, ovz = e_later ? qvz_ : evz_;
+    const double spx = e_later ? epx_ : qpx_, spy = e_later ? epy_ : qpy_, spz = e_later ? epz_ : qpz_;
+    const double svx = e_later ? evx_ : qvx_, svy = e_later ? evy_ : qvy_, svz = e_later ? evz_ : qvz_;
+    const double dt = r.a - o_ts;
+    const double dpx = fma(ovx, dt, opx) - spx;
+    const double dpy = fma(ovy, dt, opy) - spy;
+    const double dpz = fma(ovz, dt, opz) - spz;
+    const double dvx = ovx - svx, dvy = ovy - svy, dvz = ovz - svz;
+    r.A = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
+    r.Bh = fma(dpz, dvz, fma(dpy, dvy, dpx * dvx));
+    r.C = fma(dpz, dpz, fma(dpy, dpy, fma(dpx, dpx, -d2)));
+    r.disc = fma(r.Bh, r.Bh, -(r.A * r.C));
+    bool hit = le0(r.C);
+    const bool need_L = !hit && lt0(r.Bh) && ge0(r.disc);
+    if (__any_sync(kFull, active && need_L)) {
+        const double L = r.b - r.a;
+        const double gL = fma(r.A, L, r.Bh);
+        const double fL = fma(gL + r.Bh, L, r.C);
+        hit = hit || (need_L && (gt0(gL) || le0(fL)));
+    }
+    r.hit = hit && active;
+    return r;
+}
+
+// Append the hits of a warp: one atomic per warp, writes past the capacity
+// skipped while the count keeps counting.
+__device__ __forceinline__ void append_hits(const PairEval &r, DevCounters *ctr, const tdq_result_buffer &out,
+                                            uint64_t cap, int64_t qid, int64_t eid, int lane, unsigned lt_mask)
+{
+    const unsigned hm = __ballot_sync(kFull, r.hit);
+    if (!hm) return;
+    unsigned long long rbase = 0;
+    const int leader = __ffs(hm) - 1;
+    if (lane == leader) rbase = atomicAdd(&ctr->results, (unsigned long long)__popc(hm));
+    rbase = __shfl_sync(kFull, rbase, leader);
+    if (r.hit) {
+        double tin, tout;
+        pair_interval(r.A, r.Bh, r.C, r.disc, r.a, r.b, &tin, &tout);
+        const unsigned long long pos = rbase + __popc(hm & lt_mask);
+        if (pos < cap) {
+            out.query_seg_id[pos] = qid;
+            out.entry_seg_id[pos] = eid;
+            out.t_enter[pos] = tin;
+            out.t_exit[pos] = tout;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace tdq

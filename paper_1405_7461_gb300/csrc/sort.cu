@@ -259,6 +259,12 @@ int sort_kernel_launches(uint64_t n, int key_bits)
     return passes * (fused ? 2 : 3);
 }
 
+cudaError_t load_sort_module()
+{
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, radix_hist<4, true>);
+}
+
 cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,
                                cudaStream_t stream)
 {

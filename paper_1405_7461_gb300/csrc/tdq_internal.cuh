@@ -57,6 +57,37 @@ __device__ __forceinline__ bool lt0(double x)  // x < 0
 __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }  // x >= 0
 
 // ---------------------------------------------------------------------------
+// Launch and allocation helpers shared by the translation units.
+constexpr int kBlock = 256;              // threads of the simple one-item-per-thread kernels
+constexpr unsigned kFull = 0xffffffffu;  // full warp mask
+
+inline unsigned grid_for(uint64_t n, int block = kBlock)
+{
+    uint64_t g = (n + block - 1) / block;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+// Sub-allocation of one device block: 256-byte aligned slices.
+template <typename T>
+T *carve(char *&p, uint64_t count)
+{
+    T *r = (T *)p;
+    p += (count * sizeof(T) + 255) & ~(uint64_t)255;
+    return r;
+}
+inline uint64_t carve_bytes(uint64_t count, uint64_t size) { return (count * size + 255) & ~(uint64_t)255; }
+
+// Temporal bin of time t (Sec. 4): min(m - 1, floor((t - t_min) / width)),
+// 0 below t_min.  Monotone non-decreasing in t: the index build, the
+// candidate lookup and the overlap counts rely on one and the same function.
+__device__ __forceinline__ int64_t bin_of(double t, double t_min, double width, uint32_t m)
+{
+    double f = floor((t - t_min) / width);
+    if (!(f < (double)(m - 1))) return (int64_t)m - 1;
+    if (f < 0.0) return 0;
+    return (int64_t)f;
+}
+
 // FP32 upper bound of sqrt(a^2 + b^2 + c^2) (every rounding upward).
 __device__ __forceinline__ float norm_ru(double a, double b, double c)
 {
@@ -228,6 +259,25 @@ struct GraphInputNodes {
 cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out);
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
                         const QueryInput &in, uint64_t nq, const LaunchCfg &cfg);
+
+// Loading of the library's device code.  CUDA loads a translation unit's
+// module (its kernels and file-scope device arrays) lazily, on first use,
+// and a module load allocates device memory; tdq_build_index loads them all
+// (load_device_code), so that no later search call does -- in particular
+// not the allocation-free one.  One loader per translation unit with
+// device code.
+cudaError_t load_search_module();   // search.cu
+cudaError_t load_filter_module();   // filter.cu
+cudaError_t load_noalloc_module();  // noalloc.cu
+cudaError_t load_sort_module();     // sort.cu
+inline cudaError_t load_device_code()
+{
+    cudaError_t e;
+    if ((e = load_search_module()) != cudaSuccess) return e;
+    if ((e = load_filter_module()) != cudaSuccess) return e;
+    if ((e = load_sort_module()) != cudaSuccess) return e;
+    return load_noalloc_module();
+}
 
 // Allocation gate (api.cu).  Every device and pinned-host allocation of the
 // library goes through dev_alloc / host_alloc; tdq_debug_fail_allocations
