@@ -191,15 +191,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def device_code_hash():
+    """Hash of the library's device sources with comments and blank space
+    removed: it changes when the code changes, not when a comment does."""
+    import re
+
+    csrc = os.path.join(ROOT, "paper_1405_7461_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            text = open(os.path.join(csrc, name)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", "", text)
+            h.update(name.encode())
+            h.update(re.sub(r"\s+", " ", text).encode())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(mode):
     """ncu DRAM bytes per pair-kernel launch of `mode`, if they were taken on
-    the current kernel source (else None)."""
+    the current device code (else None)."""
     path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_1405_7461_gb300", "csrc", "search.cu")
     try:
         rec = json.load(open(path)).get(mode)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if not rec or rec.get("search_cu_sha256_16") != h:
+        if not rec or rec.get("device_code_sha256_16") != device_code_hash():
             return None
         return rec.get("bytes_per_launch")
     except (OSError, ValueError, AttributeError):
