@@ -348,6 +348,8 @@ typedef struct {
 static int pair_allowed(const pair_filter *f, int64_t qi, int64_t ei)
 {
     if (!f) return 1;
+    if (ORACLE_MUTANT == 9) return f->eseg[ei] > f->qseg[qi];          /* same trajectory kept */
+    if (ORACLE_MUTANT == 10) return f->etraj[ei] != f->qtraj[qi];      /* both orders kept */
     return f->etraj[ei] != f->qtraj[qi] && f->eseg[ei] > f->qseg[qi];
 }
 

@@ -1,8 +1,8 @@
 """The oracle's pins catch plausible mistakes: each mutant build of the
 oracle (one deliberate mistake planted on the CPU: a dropped term, a flipped
 sign, a transposed operand, a wrong endpoint, an off-by-one in the overlap or
-threshold test, a wrong bin origin, an ignored window) must fail at least one
-pin of tests/test_oracle_pins.py."""
+threshold test, a wrong bin origin, an ignored window, a wrong self-join
+pair filter) must fail at least one pin of tests/test_oracle_pins.py."""
 import pytest
 
 from oracle import oracle
@@ -17,6 +17,8 @@ MUTANTS = {
     6: "transposed operands in the second root",
     7: "bin index ignores the start of the extent",
     8: "query window ignored",
+    9: "self-join keeps pairs of one trajectory",
+    10: "self-join keeps both orders of a pair",
 }
 
 PIN_CALLS = [
@@ -33,6 +35,8 @@ PIN_CALLS = [
     pins.test_invariants_on_random_pairs,
     pins.test_fig1_bin_table,
     pins.test_fig1_bin_table_time_shifted,
+    pins.test_self_join_head_on_pair_once,
+    lambda: [pins.test_self_join_is_the_filtered_full_search(s) for s in (1, 2)],
 ]
 
 
