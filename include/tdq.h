@@ -275,8 +275,10 @@ void tdq_plan_free(tdq_plan *plan);
  * Search one batch.  queries->n <= max_query_segments; d_per_query,
  * t0_per_query and t1_per_query hold one value per query segment, in the
  * same memory (host or device) as the query columns.  Host inputs are
- * copied into the plan's staging buffers; device inputs are read in place by
- * the replayed graph.  The call blocks until the batch is done and returns
+ * copied into the plan's staging buffers -- unless every array lies in
+ * page-locked memory mapped into the device's address space (cudaHostAlloc,
+ * cudaHostRegister): then, like device inputs, they are read in place by the
+ * replayed graph (over the coherent CPU-GPU link on a Grace-Blackwell node).  The call blocks until the batch is done and returns
  * the number of results in *count.  Errors as tdq_search.
  */
 tdq_status tdq_plan_search(tdq_plan *plan, const tdq_segments *queries, const double *d_per_query,

@@ -261,13 +261,28 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
         in.t0_arr = t0_per_query;
         in.t1_arr = t1_per_query;
     } else {
-        for (int c = 0; c < 8; c++)
-            TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, cudaMemcpyHostToDevice, stream));
-        TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, cudaMemcpyHostToDevice, stream));
-        TDQ_CUDA(cudaMemcpyAsync(p->d_arr, d_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
-        TDQ_CUDA(cudaMemcpyAsync(p->t0_arr, t0_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
-        TDQ_CUDA(cudaMemcpyAsync(p->t1_arr, t1_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
-        in = staged_input(p);
+        // page-locked, mapped host arrays are read in place; anything else
+        // is staged into the plan's buffers
+        const void *host[12] = {cols[0], cols[1], cols[2], cols[3], cols[4], cols[5], cols[6], cols[7],
+                                queries->seg_id, d_per_query, t0_per_query, t1_per_query};
+        const void *view[12];
+        bool mapped = true;
+        for (int k = 0; k < 12 && mapped; k++) mapped = (view[k] = mapped_view(host[k], nq * 8)) != nullptr;
+        if (mapped) {
+            for (int c = 0; c < 8; c++) in.c[c] = (const double *)view[c];
+            in.seg_id = (const int64_t *)view[8];
+            in.d_arr = (const double *)view[9];
+            in.t0_arr = (const double *)view[10];
+            in.t1_arr = (const double *)view[11];
+        } else {
+            for (int c = 0; c < 8; c++)
+                TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, cudaMemcpyHostToDevice, stream));
+            TDQ_CUDA(cudaMemcpyAsync(w.in_seg, queries->seg_id, nq * 8, cudaMemcpyHostToDevice, stream));
+            TDQ_CUDA(cudaMemcpyAsync(p->d_arr, d_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
+            TDQ_CUDA(cudaMemcpyAsync(p->t0_arr, t0_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
+            TDQ_CUDA(cudaMemcpyAsync(p->t1_arr, t1_per_query, nq * 8, cudaMemcpyHostToDevice, stream));
+            in = staged_input(p);
+        }
     }
     const uint64_t cls = size_class(nq);
     in.n_real = nq;

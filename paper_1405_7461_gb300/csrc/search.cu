@@ -704,7 +704,18 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     if (st != TDQ_OK) return st;
 
     QueryInput in{};
-    if (!queries->on_device) {
+    // host arrays in page-locked, mapped memory are read in place (as device
+    // arrays are); any other host input is staged into the workspace
+    bool mapped = !queries->on_device;
+    const void *view[10] = {nullptr};
+    for (int c = 0; c < 8 && mapped; c++) mapped = (view[c] = mapped_view(cols[c], nq * 8)) != nullptr;
+    if (mapped) mapped = (view[8] = mapped_view(queries->seg_id, nq * 8)) != nullptr;
+    if (mapped && queries->traj_id) mapped = (view[9] = mapped_view(queries->traj_id, nq * 8)) != nullptr;
+    if (mapped) {
+        for (int c = 0; c < 8; c++) in.c[c] = (const double *)view[c];
+        in.seg_id = (const int64_t *)view[8];
+        in.traj_id = (const int64_t *)view[9];
+    } else if (!queries->on_device) {
         for (int c = 0; c < 8; c++) {
             TDQ_CUDA(cudaMemcpyAsync(w.in_cols[c], cols[c], nq * 8, cudaMemcpyHostToDevice, stream));
             in.c[c] = w.in_cols[c];

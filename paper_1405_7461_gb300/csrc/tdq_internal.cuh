@@ -67,6 +67,26 @@ inline unsigned grid_for(uint64_t n, int block = kBlock)
     return (unsigned)(g > 0 ? g : 1);
 }
 
+// Device view of a host array of `bytes` bytes when all of it lies in
+// page-locked memory mapped into the device's address space (cudaHostAlloc,
+// cudaHostRegister, pinned tensors); null otherwise.  On a Grace-Blackwell
+// node the kernels then read such input in place over the coherent CPU-GPU
+// link, so a search needs no staging copies for it.
+inline const void *mapped_view(const void *host_ptr, uint64_t bytes)
+{
+    if (!host_ptr || bytes == 0) return nullptr;
+    cudaPointerAttributes a, b;
+    if (cudaPointerGetAttributes(&a, host_ptr) != cudaSuccess ||
+        cudaPointerGetAttributes(&b, (const char *)host_ptr + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if ((const char *)b.devicePointer - (const char *)a.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+    return a.devicePointer;
+}
+
 // Sub-allocation of one device block: 256-byte aligned slices.
 template <typename T>
 T *carve(char *&p, uint64_t count)

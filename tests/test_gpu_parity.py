@@ -460,3 +460,25 @@ def test_pair_filter_arguments_are_checked(tdq):
         b = tdq.self_join(idx, ent, 3.0)
         for x, y in zip(_sorted_arrays(a), _sorted_arrays(b)):
             assert np.array_equal(x, y)
+
+
+def test_pinned_host_queries_are_read_in_place(tdq):
+    # tdq_search reads page-locked host query arrays in place (no staging
+    # copy); the results equal those of the same queries in pageable memory
+    torch = pytest.importorskip("torch")
+    w = workloads.scale_random_walk(n_traj=600, n_queries=8)
+
+    def pinned(a):
+        p = torch.empty(len(a), dtype=torch.from_numpy(np.asarray(a)).dtype, pin_memory=True).numpy()
+        p[:] = a
+        return p
+
+    qp = workloads.Segments(*[pinned(w.queries[c]) for c in workloads.COLUMNS], pinned(w.queries.seg_id),
+                            pinned(w.queries.traj_id))
+    with tdq.build_index(w.entries) as idx:
+        for mode in (tdq.MODE_FP64, tdq.MODE_FP32_FILTER):
+            a = tdq.search(idx, w.queries, 5.0, *w.window, mode=mode)
+            b = tdq.search(idx, qp, 5.0, *w.window, mode=mode)
+            assert len(a) > 0
+            for x, y in zip(_sorted_arrays(a), _sorted_arrays(b)):
+                assert np.array_equal(x, y)

@@ -229,3 +229,29 @@ def test_batching_workload_full_size_sampled(tdq):
     dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, qs, qi, q0[qi], q1[qi])  # noqa: E731
     cmp = compare_results(gi, ora, w.entries, qs, None, dmin_fn=dmin, d_per_query=qd)
     assert cmp["matched"] == len(ora["qi"]) > 0
+
+
+def test_plan_reads_pinned_host_inputs_in_place(tdq):
+    # page-locked host arrays are read in place by the replayed graph; the
+    # results equal those of pageable host inputs (staged) and device inputs
+    w = workloads.batching_walks(n_traj=300, n_queries=30, box=40.0)
+    q = w.queries
+    n = len(q)
+
+    def pinned(a):
+        p = torch.empty(len(a), dtype=torch.from_numpy(np.asarray(a)).dtype, pin_memory=True).numpy()
+        p[:] = a
+        return p
+
+    qp = workloads.Segments(*[pinned(q[c]) for c in workloads.COLUMNS], pinned(q.seg_id), pinned(q.traj_id))
+    with tdq.build_index(w.entries) as idx, tdq.Plan(idx, n, mode=tdq.MODE_FP32_FILTER) as plan:
+        plan.search(q, w.q_d, w.q_t0, w.q_t1)
+        staged = plan.results()
+        plan.search(qp, pinned(w.q_d), pinned(w.q_t0), pinned(w.q_t1))
+        in_place = plan.results()
+        plan.search(tdq.DeviceSegments(q), torch.from_numpy(w.q_d).cuda(), torch.from_numpy(w.q_t0).cuda(),
+                    torch.from_numpy(w.q_t1).cuda())
+        device = plan.results()
+    assert len(staged) > 0
+    _same(in_place, staged)
+    _same(device, staged)
