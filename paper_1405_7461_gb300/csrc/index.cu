@@ -28,10 +28,10 @@ struct EntryInput {
 // Validate, and emit the sort key and time range of every entry.  The time
 // range is reduced per warp before one atomic per warp.
 __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *vals, unsigned int *err,
-                           unsigned long long *tmin_key, unsigned long long *tmax_key)
+                           unsigned long long *tmin_key, unsigned long long *tmax_key, unsigned long long *max_dur)
 {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long kmin = ~0ULL, kmax = 0ULL;
+    unsigned long long kmin = ~0ULL, kmax = 0ULL, dmax = 0ULL;
     if (i < n) {
         bool ok = true;
 #pragma unroll
@@ -45,15 +45,19 @@ __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *
         // time extent as unsigned keys (same order as the doubles)
         kmin = (uint64_t)ks ^ 0x8000000000000000ULL;
         kmax = (uint64_t)ke ^ 0x8000000000000000ULL;
+        // longest duration: positive doubles order like their bit patterns
+        if (ok) dmax = (unsigned long long)__double_as_longlong(in.c[7][i] - in.c[3][i]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (kmin != ~0ULL) atomicMin(tmin_key, kmin);
         if (kmax != 0ULL) atomicMax(tmax_key, kmax);
+        if (dmax != 0ULL) atomicMax(max_dur, dmax);
     }
 }
 
@@ -325,9 +329,9 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         uint32_t *vals = carve<uint32_t>(p, n);
         uint32_t *vals_alt = carve<uint32_t>(p, n);
         uint32_t *hist = carve<uint32_t>(p, sort_hist_words(n));
-        unsigned long long *small = carve<unsigned long long>(p, 4);  // err, tmin, tmax
+        unsigned long long *small = carve<unsigned long long>(p, 4);  // err, tmin, tmax, longest duration
 
-        unsigned long long init[3] = {0ULL, ~0ULL, 0ULL};
+        unsigned long long init[4] = {0ULL, ~0ULL, 0ULL, 0ULL};
         DevCounters *hc = idx->ws.ctr_host;
         memcpy(hc, init, sizeof init);
         if (cudaMemcpyAsync(small, hc, sizeof init, cudaMemcpyHostToDevice, stream) != cudaSuccess) {
@@ -335,13 +339,13 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             break;
         }
         entry_prep<<<grid_for(n), kBlock, 0, stream>>>(in, n, keys, vals, (unsigned int *)&small[0], &small[1],
-                                                        &small[2]);
+                                                        &small[2], &small[3]);
         if (cudaMemcpyAsync(hc, small, sizeof init, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: entry validation");
             break;
         }
-        unsigned long long back[3];
+        unsigned long long back[4];
         memcpy(back, hc, sizeof back);
         if (back[0] & 1ULL) {
             st = set_error(TDQ_ERR_INVALID,
@@ -356,6 +360,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             memcpy(&idx->t_min, &bmin, 8);
             memcpy(&idx->t_max, &bmax, 8);
             idx->width = (idx->t_max - idx->t_min) / (double)m;
+            memcpy(&idx->max_dur, &back[3], 8);
         }
         if (radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, hist, stream) != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: sort");

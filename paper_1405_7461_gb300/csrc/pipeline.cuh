@@ -19,6 +19,8 @@ struct BinView {
     const int64_t *bin_begin, *bin_pmax_key;
     const int64_t *ts_key, *te_sorted, *te_bin_begin;  // sorted t_start / t_end keys and the t_end bin table
     double t_min, width;
+    double inv_width;   // 1 / width (for estimates that are verified afterwards)
+    double max_dur;     // longest entry duration
     uint32_t m;
     float inv_width_f;  // 1 / width in FP32 (for sort keys only)
 };
@@ -26,7 +28,8 @@ struct BinView {
 inline BinView bin_view(const tdq_index *idx)
 {
     return BinView{idx->bin_begin, idx->bin_pmax_key, idx->e.ts_key, idx->e.te_sorted, idx->te_bin_begin,
-                   idx->t_min, idx->width, idx->m, idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
+                   idx->t_min, idx->width, idx->width > 0.0 ? 1.0 / idx->width : 0.0, idx->max_dur, idx->m,
+                   idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
 }
 
 // Arguments of query_gather (one struct, so that a captured launch can be

@@ -133,29 +133,11 @@ __global__ void publish_counters(const DevCounters *src, DevCounters *dst)
     for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / 8); i += 32) d[i] = s[i];
 }
 
-namespace {
-
-// First position in keys[lo, hi) whose key is >= x (strict: > x).
-__device__ __forceinline__ int64_t lower_bound_key(const int64_t *keys, int64_t lo, int64_t hi, int64_t x, bool strict)
-{
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const int64_t v = keys[mid];
-        if (v < x || (strict && v == x)) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-}  // namespace
-
 // Sorted query SoA and the candidate range of each query segment; then, one
 // warp per tile of kQT sorted query segments, the tile plan; in filter mode
 // also the exact number of temporal-overlap pairs of each query segment:
 // #{t_start < q.t_end} - #{t_end <= q.t_start} (the second set lies inside
-// the first because t_end > t_start).  The bin function is monotone in time,
-// so each count lies inside the bin of its bound: a short binary search in
-// the sorted t_start keys (bin table bin_begin) and in the sorted t_end keys
-// (bin table te_bin_begin).
+// the first because t_end > t_start).
 __global__ void query_gather(GatherArgs a)
 {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,36 +157,68 @@ __global__ void query_gather(GatherArgs a)
         q.qid[k] = a.seg_id[i];
         if (q.qtraj) q.qtraj[k] = a.traj_id ? a.traj_id[i] : 0;
         q.sph[k] = a.pre_sph[i];
-        // First bin whose extent reaches past the query start: the prefix
-        // maximum of bin ends is non-decreasing, so this is a binary search
-        // (Sec. 4 uses an index tree over the bin extents for the same lookup).
-        uint32_t lo = 0, hi = bins.m;
-        while (lo < hi) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (bins.bin_pmax_key[mid] > cs) hi = mid; else lo = mid + 1;
-        }
-        const int64_t jlo = lo;
+        // Three binary searches, advanced together so that their loads
+        // overlap (each thread's searches are a chain of dependent loads):
+        //  A  the first bin whose extent reaches past the query start -- the
+        //     prefix maximum of bin ends is non-decreasing (Sec. 4 uses an
+        //     index tree over the bin extents for the same lookup); an entry
+        //     that ends after cs starts after cs - max_dur, so the answer is
+        //     searched between the bins of cs - max_dur and cs, both ends of
+        //     that bracket verified (else the rest of the table);
+        //  B, C (filter mode) the exact overlap count, #{t_start < ce} -
+        //     #{t_end <= cs}: the bin function is monotone in time, so each
+        //     count lies inside the bin of its bound, in the sorted t_start
+        //     keys (bin table bin_begin) and the sorted t_end keys (bin table
+        //     te_bin_begin).
+        const double te = key_double(ce), ts = key_double(cs);
         // Last bin that can hold an entry starting before the query end.
-        const double te = key_double(ce);
         const int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
-        if (jlo < (int64_t)bins.m && jlo <= jhi) {
+        const int64_t m = bins.m;
+        const int64_t bts = bin_of(ts, bins.t_min, bins.width, bins.m);  // exact: C relies on it
+        int64_t a_lo, a_hi;
+        {
+            // the lower end only needs to be about right: it is verified
+            const double f0 = floor((ts - bins.max_dur - bins.t_min) * bins.inv_width) - 1.0;
+            const int64_t hb = bts + 1 < m ? bts + 1 : m - 1;
+            int64_t b0 = f0 > 0.0 ? (f0 < (double)(m - 1) ? (int64_t)f0 : m - 1) : 0;
+            if (b0 > hb) b0 = hb;
+            const bool below = b0 > 0 && bins.bin_pmax_key[b0 - 1] > cs;  // the answer lies before b0
+            const bool above = !below && bins.bin_pmax_key[hb] <= cs;     // the answer lies after hb
+            a_lo = below ? 0 : (above ? hb + 1 : b0);
+            a_hi = below ? b0 : (above ? m : hb + 1);
+        }
+        int64_t b_lo = 0, b_hi = 0, c_lo = 0, c_hi = 0;
+        if (a.count_overlaps && jhi >= 0) {
+            b_lo = bins.bin_begin[jhi];
+            b_hi = bins.bin_begin[jhi + 1];
+            if (!le0(ts - bins.t_min)) {
+                c_lo = bins.te_bin_begin[bts];
+                c_hi = bins.te_bin_begin[bts + 1];
+            }
+        }
+        while (a_lo < a_hi || b_lo < b_hi || c_lo < c_hi) {
+            if (a_lo < a_hi) {  // first bin with prefix-max end > cs
+                const int64_t mid = (a_lo + a_hi) >> 1;
+                if (bins.bin_pmax_key[mid] > cs) a_hi = mid; else a_lo = mid + 1;
+            }
+            if (b_lo < b_hi) {  // first sorted t_start >= ce
+                const int64_t mid = (b_lo + b_hi) >> 1;
+                if (bins.ts_key[mid] < ce) b_lo = mid + 1; else b_hi = mid;
+            }
+            if (c_lo < c_hi) {  // first sorted t_end > cs
+                const int64_t mid = (c_lo + c_hi) >> 1;
+                if (bins.te_sorted[mid] <= cs) c_lo = mid + 1; else c_hi = mid;
+            }
+        }
+        const int64_t jlo = a_lo;
+        if (jlo < m && jlo <= jhi) {
             rlo = bins.bin_begin[jlo];
             rhi = bins.bin_begin[jhi + 1];
             if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
         }
         q.lo[k] = rlo;
         q.hi[k] = rhi;
-        if (a.count_overlaps && jhi >= 0) {
-            const int64_t n_start = lower_bound_key(bins.ts_key, bins.bin_begin[jhi], bins.bin_begin[jhi + 1], ce,
-                                                    false);
-            const double ts = key_double(cs);
-            int64_t n_end = 0;
-            if (!le0(ts - bins.t_min)) {
-                const int64_t b = bin_of(ts, bins.t_min, bins.width, bins.m);
-                n_end = lower_bound_key(bins.te_sorted, bins.te_bin_begin[b], bins.te_bin_begin[b + 1], cs, true);
-            }
-            n_overlap = (unsigned long long)(n_start - n_end);
-        }
+        if (a.count_overlaps && jhi >= 0) n_overlap = (unsigned long long)(b_lo - c_lo);
     }
     // the tile plan: this warp's 32 sorted query segments are tile k / kQT
     const int lane = threadIdx.x & 31;

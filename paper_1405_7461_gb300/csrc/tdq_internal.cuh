@@ -228,6 +228,7 @@ struct tdq_index {
     uint64_t n = 0;
     uint32_t m = 0;
     double t_min = 0.0, t_max = 0.0, width = 0.0;
+    double max_dur = 0.0;  // longest entry duration (t_end - t_start)
     void *e_block = nullptr;
     tdq::EntrySoA e{};
     void *b_block = nullptr;
