@@ -482,3 +482,28 @@ def test_pinned_host_queries_are_read_in_place(tdq):
             assert len(a) > 0
             for x, y in zip(_sorted_arrays(a), _sorted_arrays(b)):
                 assert np.array_equal(x, y)
+
+
+def test_filter_with_magnitudes_beyond_two_to_the_sixty(tdq):
+    # segments beyond 2^60 in magnitude get an infinite bounding radius (and
+    # E or K = -inf): the pre-test never rejects them; mixed with ordinary
+    # segments, the filter mode must still return exactly the plain FP64 set
+    rng = np.random.default_rng(21)
+    far = workloads.random_segments(rng, 3000, box=2e5, t_span=20.0, max_dur=3.0, max_speed=5e3)
+    near = workloads.random_segments(rng, 3000, box=200.0, t_span=20.0, max_dur=3.0, max_speed=5.0)
+    shift = 3e18  # > 2^60 = 1.15e18
+    for c in ("xs", "xe"):
+        setattr(far, c, getattr(far, c) + shift)
+    ent = workloads.Segments.concat([far, near])
+    ent.seg_id = np.arange(len(ent), dtype=np.int64)
+    ent.traj_id = np.arange(len(ent), dtype=np.int64)
+    q = ent.take(np.concatenate([np.arange(0, 3000, 60), np.arange(3000, 6000, 60)]))
+    with tdq.build_index(ent) as idx:
+        for d in (50.0, 3e4):
+            r64 = tdq.search(idx, q, d, mode=tdq.MODE_FP64)
+            r32 = tdq.search(idx, q, d, mode=tdq.MODE_FP32_FILTER)
+            s32 = tdq.get_stats(idx)
+            for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
+                assert np.array_equal(a, b)
+            assert len(r32) >= len(q)  # every query segment meets itself
+            assert s32["fp64_pairs"] > 0
