@@ -290,10 +290,14 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
 
 // FP64 evaluation of the filter's survivors.  The pre-test ignores time, so
 // most survivors do not overlap in time; a warp checks the exact span keys
-// of 32 survivors at a time, queues the overlapping ones in its slice of
-// shared memory, and runs the FP64 code of the plain kernel (then the
-// warp-aggregated append) on full batches of 32 queued pairs: the FP64 pipe
-// is busy for a warp instruction whatever the number of active lanes.
+// of 32 survivors at a time (and the pair filters), queues the overlapping
+// ones in its slice of shared memory, and runs the FP64 code of the plain
+// kernel (then the warp-aggregated append) on full batches of 32 queued
+// pairs: the FP64 pipe is busy for a warp instruction whatever the number of
+// active lanes.  The warps of a block pool what is left in their queues at
+// the end (fewer than 32 pairs each), so that a block runs at most one
+// partial batch.  The block that finishes last copies the counters to the
+// host mirror.
 constexpr int kRefineWarps = kPairThreads / 32;
 
 __device__ __forceinline__ void refine_batch(const PairArgs &args, uint2 sv, bool active, uint64_t cap, int lane,
@@ -311,15 +315,18 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
 {
     const PairArgs &args = fa.p;
     __shared__ uint2 queue_all[kRefineWarps][64];
+    __shared__ uint2 pool[kRefineWarps * 32];
+    __shared__ int pooled;
     DevCounters *ctr = args.ctr;
-    const int lane = threadIdx.x & 31;
-    uint2 *queue = queue_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint2 *queue = queue_all[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t cap = args.out.capacity;
     const unsigned long long ns = min(ctr->survivors, (unsigned long long)fa.surv_cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned long long n_fp64 = 0;
     int queued = 0;  // warp-uniform, < 32 between chunks
+    if (threadIdx.x == 0) pooled = 0;
     // warp-uniform trip count (the ballots, eval_pair_fp64 and append_hits vote over the warp)
     const unsigned long long first = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     for (unsigned long long wb = first; wb < ns; wb += stride) {
@@ -346,11 +353,22 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
             refine_batch(args, qv, true, cap, lane, lt_mask);
         }
     }
-    if (queued > 0) {  // the last, partial batch
-        const bool active = lane < queued;
-        refine_batch(args, active ? queue[lane] : make_uint2(0u, 0u), active, cap, lane, lt_mask);
+    // pool the warps' remainders and run them as full batches (the last one partial)
+    __syncthreads();
+    if (queued > 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&pooled, queued);
+        base = __shfl_sync(kFull, base, 0);
+        if (lane < queued) pool[base + lane] = queue[lane];
+    }
+    __syncthreads();
+    const int np = pooled;
+    for (int bt = warp; bt * 32 < np; bt += kRefineWarps) {
+        const bool active = bt * 32 + lane < np;
+        refine_batch(args, active ? pool[bt * 32 + lane] : make_uint2(0u, 0u), active, cap, lane, lt_mask);
     }
     if (lane == 0 && n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
+    publish_when_last(ctr, args.publish);
 }
 
 }  // namespace

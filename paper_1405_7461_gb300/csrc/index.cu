@@ -241,11 +241,12 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             return set_error(TDQ_ERR_CUDA, "tdq_build_index: cudaEventCreate failed");
         }
     }
-    if (dev_alloc(&idx->ws.ctr, sizeof(DevCounters)) != cudaSuccess ||
+    if (dev_alloc(&idx->ws.ctr, kCtrBlockBytes) != cudaSuccess ||
         host_alloc_mapped(&idx->ws.ctr_host, &idx->ws.ctr_host_dev, sizeof(DevCounters)) != cudaSuccess) {
         tdq_index_free(idx);
         return set_error(TDQ_ERR_NOMEM, "tdq_build_index: counter allocation failed");
     }
+    idx->ws.sort_fused_hist = (uint32_t *)((char *)idx->ws.ctr + kCtrBytes);
     if (n == 0) {
         *out = idx;
         return TDQ_OK;

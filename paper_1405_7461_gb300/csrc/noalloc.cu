@@ -23,21 +23,21 @@ constexpr uint64_t kNoAllocTiles = kNoAllocMaxQueries / kQT;
 constexpr uint64_t kNoAllocHistWords = (kNoAllocMaxQueries + 1023) / 1024 * 256 + 1;  // 1024-key sort tiles
 constexpr uint64_t na_bytes(uint64_t count, uint64_t size) { return (count * size + 255) & ~(uint64_t)255; }
 constexpr uint64_t kNoAllocScratchBytes =
-    9 * na_bytes(kNoAllocMaxQueries, 8)                                      // pre columns
+    kPreCols * na_bytes(kNoAllocMaxQueries, 8)                               // pre columns
     + 2 * na_bytes(kNoAllocMaxQueries, 8) + 2 * na_bytes(kNoAllocMaxQueries, 4)  // sort keys / values
-    + 12 * na_bytes(kNoAllocMaxQueries, 8)                                   // sorted query SoA
+    + 10 * na_bytes(kNoAllocMaxQueries, 8)                                   // sorted query SoA
     + 2 * na_bytes(kNoAllocMaxQueries, 16)                                   // query spheres
     + 2 * na_bytes(kNoAllocTiles, 8) + na_bytes(kNoAllocTiles + 1, 8)        // tile table
     + na_bytes(kNoAllocHistWords, 4)                                         // sort histogram
     + na_bytes(1, sizeof(DevCounters))                                       // counters
-    + na_bytes(9, sizeof(double *));                                         // pre pointer table
+    + na_bytes(kPreCols, sizeof(double *));                                  // pre pointer table
 
 // The scratch.  In host code this name is only a host-side stand-in for the
 // symbol; its device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 struct NoAllocScratch {
-    double *pre[9];
+    double *pre[kPreCols];
     double **pre_dev;
     float4 *pre_sph;
     uint64_t *keys, *keys_alt;
@@ -67,7 +67,7 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         if (e != cudaSuccess) return cuda_error(e, "tdq_search_device_noalloc: cudaGetSymbolAddress");
         NoAllocScratch s{};
         char *p = (char *)base;
-        for (int c = 0; c < 9; c++) s.pre[c] = carve<double>(p, kNoAllocMaxQueries);
+        for (int c = 0; c < kPreCols; c++) s.pre[c] = carve<double>(p, kNoAllocMaxQueries);
         s.keys = carve<uint64_t>(p, kNoAllocMaxQueries);
         s.keys_alt = carve<uint64_t>(p, kNoAllocMaxQueries);
         s.vals = carve<uint32_t>(p, kNoAllocMaxQueries);
@@ -78,8 +78,7 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         q.vy = carve<double>(p, kNoAllocMaxQueries); q.vz = carve<double>(p, kNoAllocMaxQueries);
         q.d2 = carve<double>(p, kNoAllocMaxQueries);
         q.ts_key = carve<int64_t>(p, kNoAllocMaxQueries); q.te_key = carve<int64_t>(p, kNoAllocMaxQueries);
-        q.qid = carve<int64_t>(p, kNoAllocMaxQueries); q.lo = carve<int64_t>(p, kNoAllocMaxQueries);
-        q.hi = carve<int64_t>(p, kNoAllocMaxQueries);
+        q.qid = carve<int64_t>(p, kNoAllocMaxQueries);
         q.qtraj = nullptr;  // no pair filters here
         s.pre_sph = carve<float4>(p, kNoAllocMaxQueries);
         q.sph = carve<float4>(p, kNoAllocMaxQueries);
@@ -88,10 +87,10 @@ tdq_status noalloc_setup(int dev, NoAllocScratch **out)
         s.tile_work = carve<unsigned long long>(p, kNoAllocTiles + 1);
         s.hist = carve<uint32_t>(p, kNoAllocHistWords);
         s.ctr = carve<DevCounters>(p, 1);
-        s.pre_dev = carve<double *>(p, 9);
+        s.pre_dev = carve<double *>(p, kPreCols);
         if ((uint64_t)(p - (char *)base) > kNoAllocScratchBytes || sort_hist_words(kNoAllocMaxQueries) > kNoAllocHistWords)
             return set_error(TDQ_ERR_CUDA, "tdq_search_device_noalloc: scratch layout exceeds the array");
-        e = cudaMemcpy(s.pre_dev, s.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(s.pre_dev, s.pre, kPreCols * sizeof(double *), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_error(e, "tdq_search_device_noalloc: pointer table");
         g_noalloc[dev] = s;
         g_noalloc_ready[dev] = true;
@@ -165,16 +164,16 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     // the array keeps the previous call's contents: clear the counters
     TDQ_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), stream));
     const BinView bins = bin_view(idx);
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr);
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
+        PrepArgs{in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr, nullptr, idx->n > 0, false});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream,
                                   bin_key_bits(idx->m)));
-        const GatherArgs ga{s->pre_dev, s->pre_sph, in.seg_id, nullptr, s->vals, nq, s->ctr, bins, s->q, ntiles,
-                            chunk, s->tile_lo, s->tile_hi, s->tile_work, false};
+        const GatherArgs ga{s->pre_dev, s->pre_sph, in.seg_id, nullptr, s->vals, nq, s->ctr, s->q, ntiles,
+                            chunk, s->tile_lo, s->tile_hi, s->tile_work};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
-        TDQ_CUDA(exclusive_scan_u64(s->tile_work, ntiles + 1, &s->ctr->work_items, stream));
-        PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk, 0u};
+        PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk, 0u, nullptr};
         TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream, nullptr, 0));
     }
     TDQ_CUDA(cudaGetLastError());

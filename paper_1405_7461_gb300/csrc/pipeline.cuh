@@ -32,6 +32,26 @@ inline BinView bin_view(const tdq_index *idx)
                    idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f};
 }
 
+// Arguments of query_prep (one struct, so that a captured launch can be
+// re-bound to new inputs in one step).  ranges (the index has entries): also
+// the candidate range of every query segment into the pre columns kPreLo /
+// kPreHi; count_overlaps: also the exact number of temporal-overlap pairs;
+// sort_hist (may be null; zeroed beforehand): also the first sort pass's
+// digit counts per tile of kSortTileKeys keys (radix_sort_pairs' prep_hist).
+struct PrepArgs {
+    QueryInput in;
+    uint64_t nq;
+    BinView bins;
+    double *const *pre;
+    float4 *pre_sph;
+    uint64_t *keys;
+    uint32_t *vals;
+    DevCounters *ctr;
+    uint32_t *sort_hist;
+    bool ranges;
+    bool count_overlaps;
+};
+
 // Arguments of query_gather (one struct, so that a captured launch can be
 // re-bound to new inputs in one step).
 struct GatherArgs {
@@ -42,13 +62,11 @@ struct GatherArgs {
     const uint32_t *order;
     uint64_t nq;
     DevCounters *ctr;
-    BinView bins;
     QuerySoA q;
     uint64_t ntiles;
     uint32_t chunk;
     int64_t *tile_lo, *tile_hi;
-    unsigned long long *tile_work;  // chunks per tile (the scan turns it into offsets); ntiles + 1
-    bool count_overlaps;
+    unsigned long long *tile_work;  // chunks per tile, then (last block) their exclusive offsets; ntiles + 1
 };
 
 struct PairArgs {
@@ -61,6 +79,7 @@ struct PairArgs {
     tdq_result_buffer out;
     uint32_t chunk;
     uint32_t flags;  // TDQ_FLAG_* pair filters (0: every pair)
+    DevCounters *publish;  // may be null: host mirror the last pair kernel copies the counters to
 };
 
 // The pair filters of TDQ_FLAG_OTHER_TRAJECTORIES / TDQ_FLAG_UNORDERED_ONCE
@@ -80,8 +99,7 @@ struct FilterArgs {
 };
 
 // Kernels launched from more than one file (defined in search.cu).
-__global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *const *pre, float4 *pre_sph,
-                           uint64_t *keys, uint32_t *vals, DevCounters *ctr);
+__global__ void query_prep(PrepArgs a);
 __global__ void query_gather(GatherArgs a);
 __global__ void publish_counters(const DevCounters *src, DevCounters *dst);
 
@@ -96,6 +114,26 @@ cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream
 tdq_status check_scalars(double d, double t0, double t1);
 
 namespace {
+
+// Called by every thread of every block of the search's last kernel at its
+// end: the block that finishes last copies the counters to dst (when given).
+// Each thread fences its own counter updates before the block takes its
+// ticket, so the last block reads every block's final values (through L2).
+__device__ __forceinline__ void publish_when_last(DevCounters *ctr, DevCounters *dst)
+{
+    static_assert(sizeof(DevCounters) % 8 == 0 && sizeof(DevCounters) / 8 <= 32, "one warp copies the counters");
+    if (!dst) return;
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctr->pair_done, 1ULL) == (unsigned long long)gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x < sizeof(DevCounters) / 8) {
+        __threadfence();
+        const unsigned long long *s = reinterpret_cast<const unsigned long long *>(ctr);
+        reinterpret_cast<unsigned long long *>(dst)[threadIdx.x] = __ldcg(s + threadIdx.x);
+    }
+}
 
 // calcTimeInterval for a pair that is within d: the roots of
 // A tau^2 + 2 Bh tau + C over tau in [0, L] (tau = time since a), by the

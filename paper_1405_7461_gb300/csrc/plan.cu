@@ -186,7 +186,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
     p->use_graph = !params->no_graph;
     do {
         Workspace &w = p->ws;
-        bool ok = dev_alloc(&w.ctr, sizeof(DevCounters)) == cudaSuccess &&
+        bool ok = dev_alloc(&w.ctr, kCtrBlockBytes) == cudaSuccess &&
                   host_alloc_mapped(&w.ctr_host, &w.ctr_host_dev, sizeof(DevCounters)) == cudaSuccess &&
                   dev_alloc(&p->stage_block, 3 * p->cap_q * 8) == cudaSuccess;
         if (!ok) {
@@ -194,6 +194,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
             st = set_error(TDQ_ERR_NOMEM, "tdq_plan_create: allocation failed");
             break;
         }
+        w.sort_fused_hist = (uint32_t *)((char *)w.ctr + kCtrBytes);
         for (int k = 0; k < kSearchEvents && st == TDQ_OK; k++)
             if (cudaEventCreate(&w.ev[k]) != cudaSuccess) st = set_error(TDQ_ERR_CUDA, "tdq_plan_create: events");
         if (st != TDQ_OK) break;

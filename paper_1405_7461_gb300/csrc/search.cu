@@ -1,25 +1,26 @@
 // Distance threshold search on the device: candidate lookup in the
 // temporal-bin index (Sec. 4) and the pair kernel (Sec. 5, Algorithm 1).
 //
-// Pipeline of one search, all on the caller's stream:
+// Pipeline of one search on the caller's stream:
 //   query_prep    validate, clip each query segment to the window, velocity,
-//                 start position at the clipped start, sort key
+//                 start position at the clipped start, sort key, candidate
+//                 range [lo, hi) of sorted entry positions from the bin
+//                 table; filter mode: the exact number of temporal-overlap
+//                 pairs of each query segment
 //   radix sort    query segments by clipped start (Sec. 4 sorts Q by t_start)
-//   query_gather  sorted query SoA + candidate range [lo, hi) of sorted entry
-//                 positions per query segment, from the bin table; one warp
-//                 per tile of 32 consecutive sorted query segments also
-//                 plans the tile: its range is the union of its members'
-//                 ranges, cut into chunks of `entry_chunk` entries, one work
-//                 item per (tile, chunk); filter mode: the exact number of
-//                 temporal-overlap pairs of each query segment
-//   scan          work-item offsets per tile
+//   query_gather  sorted query SoA; one warp per tile of 32 consecutive
+//                 sorted query segments plans the tile: its range is the
+//                 union of its members' ranges, cut into chunks of
+//                 `entry_chunk` entries, one work item per (tile, chunk); the
+//                 last block to finish scans the work-item offsets per tile
 //   traj_dist_search_kernel
 //                 persistent CTAs take work items from an atomic counter,
 //                 stage the tile's queries and the chunk's entries in shared
 //                 memory, enumerate the pairs whose spans overlap with
 //                 integer time keys, compact them so that all 32 lanes of a
 //                 warp evaluate a real pair, and append every pair within d
-//                 with one atomic per warp.
+//                 with one atomic per warp; its last block to finish copies
+//                 the search's counters to the caller-visible host mirror.
 //
 // (The filter mode's pair kernels live in filter.cu, the allocation-free
 // entry point in noalloc.cu.)
@@ -34,6 +35,7 @@
 #include <string.h>
 
 #include "pipeline.cuh"
+#include "scan.cuh"
 
 namespace tdq {
 namespace {
@@ -46,22 +48,98 @@ __device__ __forceinline__ bool is_nan_bits(double x)
 
 }  // namespace
 
-// Validate and clip every query segment.  pre[] columns: px py pz vx vy vz d2
-// ts_key te_key (keys stored bitwise in the double arrays).
-__global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *const *pre, float4 *pre_sph,
-                           uint64_t *keys, uint32_t *vals, DevCounters *ctr)
+// Candidate range [lo, hi) of sorted entry positions of one valid query
+// segment with clipped span keys [cs, ce); with count_overlaps also its exact
+// number of temporal-overlap pairs: #{t_start < q.t_end} - #{t_end <=
+// q.t_start} (the second set lies inside the first because t_end > t_start).
+__device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs, int64_t ce, bool count_overlaps,
+                                                int64_t &rlo, int64_t &rhi, unsigned long long &n_overlap)
 {
+    // Three binary searches, advanced together so that their loads overlap
+    // (each thread's searches are a chain of dependent loads):
+    //  A  the first bin whose extent reaches past the query start -- the
+    //     prefix maximum of bin ends is non-decreasing (Sec. 4 uses an index
+    //     tree over the bin extents for the same lookup); an entry that ends
+    //     after cs starts after cs - max_dur, so the answer is searched
+    //     between the bins of cs - max_dur and cs, both ends of that bracket
+    //     verified (else the rest of the table);
+    //  B, C (count_overlaps) #{t_start < ce} - #{t_end <= cs}: the bin
+    //     function is monotone in time, so each count lies inside the bin of
+    //     its bound, in the sorted t_start keys (bin table bin_begin) and the
+    //     sorted t_end keys (bin table te_bin_begin).
+    const double te = key_double(ce), ts = key_double(cs);
+    // Last bin that can hold an entry starting before the query end.
+    const int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
+    const int64_t m = bins.m;
+    const int64_t bts = bin_of(ts, bins.t_min, bins.width, bins.m);  // exact: C relies on it
+    int64_t a_lo, a_hi;
+    {
+        // the lower end only needs to be about right: it is verified
+        const double f0 = floor((ts - bins.max_dur - bins.t_min) * bins.inv_width) - 1.0;
+        const int64_t hb = bts + 1 < m ? bts + 1 : m - 1;
+        int64_t b0 = f0 > 0.0 ? (f0 < (double)(m - 1) ? (int64_t)f0 : m - 1) : 0;
+        if (b0 > hb) b0 = hb;
+        const bool below = b0 > 0 && bins.bin_pmax_key[b0 - 1] > cs;  // the answer lies before b0
+        const bool above = !below && bins.bin_pmax_key[hb] <= cs;     // the answer lies after hb
+        a_lo = below ? 0 : (above ? hb + 1 : b0);
+        a_hi = below ? b0 : (above ? m : hb + 1);
+    }
+    int64_t b_lo = 0, b_hi = 0, c_lo = 0, c_hi = 0;
+    if (count_overlaps && jhi >= 0) {
+        b_lo = bins.bin_begin[jhi];
+        b_hi = bins.bin_begin[jhi + 1];
+        if (!le0(ts - bins.t_min)) {
+            c_lo = bins.te_bin_begin[bts];
+            c_hi = bins.te_bin_begin[bts + 1];
+        }
+    }
+    while (a_lo < a_hi || b_lo < b_hi || c_lo < c_hi) {
+        if (a_lo < a_hi) {  // first bin with prefix-max end > cs
+            const int64_t mid = (a_lo + a_hi) >> 1;
+            if (bins.bin_pmax_key[mid] > cs) a_hi = mid; else a_lo = mid + 1;
+        }
+        if (b_lo < b_hi) {  // first sorted t_start >= ce
+            const int64_t mid = (b_lo + b_hi) >> 1;
+            if (bins.ts_key[mid] < ce) b_lo = mid + 1; else b_hi = mid;
+        }
+        if (c_lo < c_hi) {  // first sorted t_end > cs
+            const int64_t mid = (c_lo + c_hi) >> 1;
+            if (bins.te_sorted[mid] <= cs) c_lo = mid + 1; else c_hi = mid;
+        }
+    }
+    const int64_t jlo = a_lo;
+    if (jlo < m && jlo <= jhi) {
+        rlo = bins.bin_begin[jlo];
+        rhi = bins.bin_begin[jhi + 1];
+        if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
+    }
+    if (count_overlaps && jhi >= 0) n_overlap = (unsigned long long)(b_lo - c_lo);
+}
+
+// Validate and clip every query segment into the pre columns (see kPreCols;
+// keys stored bitwise in the double arrays); with a.ranges also its candidate
+// range and, with a.count_overlaps, its exact temporal-overlap count.
+__global__ void query_prep(PrepArgs a)
+{
+    const QueryInput &in = a.in;
+    const uint64_t nq = a.nq;
+    const BinView &bins = a.bins;
+    double *const *pre = a.pre;
+    DevCounters *ctr = a.ctr;
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
+    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
+    unsigned long long n_overlap = 0;
+    uint32_t digit = 256;  // low byte of the sort key (256: not sorted)
     // slots at or beyond the device-side count are padding: empty, not errors
     const uint64_t nreal = in.n_real ? in.n_real : nq;
     if (i == 0) ctr->sort_n = nreal < nq ? nreal : nq;
     if (i < nq && i >= nreal) {
         pre[7][i] = __longlong_as_double(INT64_MAX);
         pre[8][i] = __longlong_as_double(INT64_MIN);
-        pre_sph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        keys[i] = (uint64_t)bins.m;
-        vals[i] = (uint32_t)i;
+        a.pre_sph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.keys[i] = (uint64_t)bins.m;
+        a.vals[i] = (uint32_t)i;
     } else if (i < nq) {
         bool ok = true;
         double c[8];
@@ -95,8 +173,9 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
         pre[0][i] = px; pre[1][i] = py; pre[2][i] = pz;
         pre[3][i] = vx; pre[4][i] = vy; pre[5][i] = vz;
         pre[6][i] = d * d;
-        pre[7][i] = __longlong_as_double(cs);
-        pre[8][i] = __longlong_as_double(ce);
+        // invalid segments get the empty span (ts' >= te'), like padding
+        pre[7][i] = __longlong_as_double(valid ? cs : INT64_MAX);
+        pre[8][i] = __longlong_as_double(valid ? ce : INT64_MIN);
         // FP32 bounding sphere of the clipped segment, its radius widened by
         // d (and a relative 2^-30 of d): the pre-test of the filter mode
         float4 sp = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
@@ -106,7 +185,7 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
             sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), __fmul_ru(norm_ru(vx, vy, vz),
                           __double2float_ru(h)), __fmaf_ru(dw, 0x1p-30f, dw));
         }
-        pre_sph[i] = sp;
+        a.pre_sph[i] = sp;
         // sort key: the temporal bin of the clipped start, in FP32 (it only
         // groups the segments into tiles of 32 that span few bins); invalid
         // segments sort last
@@ -115,11 +194,32 @@ __global__ void query_prep(QueryInput in, uint64_t nq, BinView bins, double *con
             const float f = floorf(__double2float_rn(key_double(cs) - bins.t_min) * bins.inv_width_f);
             key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
         }
-        keys[i] = key;
-        vals[i] = (uint32_t)i;
+        a.keys[i] = key;
+        a.vals[i] = (uint32_t)i;
+        digit = (uint32_t)(key & 0xff);
+        if (valid && a.ranges) candidate_range(bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
     }
-    unsigned vm = __ballot_sync(kFull, valid);
-    if ((threadIdx.x & 31) == 0 && vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
+    if (i < nq && a.ranges) {
+        pre[kPreLo][i] = __longlong_as_double(rlo);
+        pre[kPreHi][i] = __longlong_as_double(rhi);
+    }
+    const unsigned vm = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
+    if ((threadIdx.x & 31) == 0) {
+        if (vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
+        if (n_overlap) atomicAdd(&ctr->overlap_pairs, n_overlap);
+    }
+    if (a.sort_hist) {  // this block's keys lie in one sort tile (blockDim divides kSortTileKeys)
+        __shared__ uint32_t h[256];
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
+        __syncthreads();
+        if (digit < 256) atomicAdd(&h[digit], 1u);
+        __syncthreads();
+        uint32_t *th = a.sort_hist + (uint64_t)blockIdx.x * blockDim.x / kSortTileKeys * 256;
+        for (int d = threadIdx.x; d < 256; d += blockDim.x)
+            if (h[d]) atomicAdd(&th[d], h[d]);
+    }
 }
 
 // Copy of the search's counters into the caller-visible pinned host mirror
@@ -133,92 +233,28 @@ __global__ void publish_counters(const DevCounters *src, DevCounters *dst)
     for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / 8); i += 32) d[i] = s[i];
 }
 
-// Sorted query SoA and the candidate range of each query segment; then, one
-// warp per tile of kQT sorted query segments, the tile plan; in filter mode
-// also the exact number of temporal-overlap pairs of each query segment:
-// #{t_start < q.t_end} - #{t_end <= q.t_start} (the second set lies inside
-// the first because t_end > t_start).
+// Sorted query SoA; then, one warp per tile of kQT consecutive sorted query
+// segments, the tile plan: the tile's entry range is the union of its
+// members' candidate ranges, cut into chunks of `chunk` entries, one work item
+// per (tile, chunk).  The block that finishes last turns the per-tile chunk
+// counts into exclusive offsets (the total into the counters).
 __global__ void query_gather(GatherArgs a)
 {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const BinView &bins = a.bins;
     QuerySoA &q = a.q;
     int64_t rlo = INT64_MAX, rhi = INT64_MIN;
-    unsigned long long n_overlap = 0;
     if (k < a.nq && k < a.ctr->valid_queries) {
         const uint32_t i = a.order[k];
         q.px[k] = a.pre[0][i]; q.py[k] = a.pre[1][i]; q.pz[k] = a.pre[2][i];
         q.vx[k] = a.pre[3][i]; q.vy[k] = a.pre[4][i]; q.vz[k] = a.pre[5][i];
         q.d2[k] = a.pre[6][i];
-        const int64_t cs = __double_as_longlong(a.pre[7][i]);
-        const int64_t ce = __double_as_longlong(a.pre[8][i]);
-        q.ts_key[k] = cs;
-        q.te_key[k] = ce;
+        q.ts_key[k] = __double_as_longlong(a.pre[7][i]);
+        q.te_key[k] = __double_as_longlong(a.pre[8][i]);
         q.qid[k] = a.seg_id[i];
         if (q.qtraj) q.qtraj[k] = a.traj_id ? a.traj_id[i] : 0;
         q.sph[k] = a.pre_sph[i];
-        // Three binary searches, advanced together so that their loads
-        // overlap (each thread's searches are a chain of dependent loads):
-        //  A  the first bin whose extent reaches past the query start -- the
-        //     prefix maximum of bin ends is non-decreasing (Sec. 4 uses an
-        //     index tree over the bin extents for the same lookup); an entry
-        //     that ends after cs starts after cs - max_dur, so the answer is
-        //     searched between the bins of cs - max_dur and cs, both ends of
-        //     that bracket verified (else the rest of the table);
-        //  B, C (filter mode) the exact overlap count, #{t_start < ce} -
-        //     #{t_end <= cs}: the bin function is monotone in time, so each
-        //     count lies inside the bin of its bound, in the sorted t_start
-        //     keys (bin table bin_begin) and the sorted t_end keys (bin table
-        //     te_bin_begin).
-        const double te = key_double(ce), ts = key_double(cs);
-        // Last bin that can hold an entry starting before the query end.
-        const int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
-        const int64_t m = bins.m;
-        const int64_t bts = bin_of(ts, bins.t_min, bins.width, bins.m);  // exact: C relies on it
-        int64_t a_lo, a_hi;
-        {
-            // the lower end only needs to be about right: it is verified
-            const double f0 = floor((ts - bins.max_dur - bins.t_min) * bins.inv_width) - 1.0;
-            const int64_t hb = bts + 1 < m ? bts + 1 : m - 1;
-            int64_t b0 = f0 > 0.0 ? (f0 < (double)(m - 1) ? (int64_t)f0 : m - 1) : 0;
-            if (b0 > hb) b0 = hb;
-            const bool below = b0 > 0 && bins.bin_pmax_key[b0 - 1] > cs;  // the answer lies before b0
-            const bool above = !below && bins.bin_pmax_key[hb] <= cs;     // the answer lies after hb
-            a_lo = below ? 0 : (above ? hb + 1 : b0);
-            a_hi = below ? b0 : (above ? m : hb + 1);
-        }
-        int64_t b_lo = 0, b_hi = 0, c_lo = 0, c_hi = 0;
-        if (a.count_overlaps && jhi >= 0) {
-            b_lo = bins.bin_begin[jhi];
-            b_hi = bins.bin_begin[jhi + 1];
-            if (!le0(ts - bins.t_min)) {
-                c_lo = bins.te_bin_begin[bts];
-                c_hi = bins.te_bin_begin[bts + 1];
-            }
-        }
-        while (a_lo < a_hi || b_lo < b_hi || c_lo < c_hi) {
-            if (a_lo < a_hi) {  // first bin with prefix-max end > cs
-                const int64_t mid = (a_lo + a_hi) >> 1;
-                if (bins.bin_pmax_key[mid] > cs) a_hi = mid; else a_lo = mid + 1;
-            }
-            if (b_lo < b_hi) {  // first sorted t_start >= ce
-                const int64_t mid = (b_lo + b_hi) >> 1;
-                if (bins.ts_key[mid] < ce) b_lo = mid + 1; else b_hi = mid;
-            }
-            if (c_lo < c_hi) {  // first sorted t_end > cs
-                const int64_t mid = (c_lo + c_hi) >> 1;
-                if (bins.te_sorted[mid] <= cs) c_lo = mid + 1; else c_hi = mid;
-            }
-        }
-        const int64_t jlo = a_lo;
-        if (jlo < m && jlo <= jhi) {
-            rlo = bins.bin_begin[jlo];
-            rhi = bins.bin_begin[jhi + 1];
-            if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
-        }
-        q.lo[k] = rlo;
-        q.hi[k] = rhi;
-        if (a.count_overlaps && jhi >= 0) n_overlap = (unsigned long long)(b_lo - c_lo);
+        rlo = __double_as_longlong(a.pre[kPreLo][i]);
+        rhi = __double_as_longlong(a.pre[kPreHi][i]);
     }
     // the tile plan: this warp's 32 sorted query segments are tile k / kQT
     const int lane = threadIdx.x & 31;
@@ -226,24 +262,29 @@ __global__ void query_gather(GatherArgs a)
     for (int o = 16; o > 0; o >>= 1) {
         rlo = min(rlo, (int64_t)__shfl_xor_sync(kFull, (long long)rlo, o));
         rhi = max(rhi, (int64_t)__shfl_xor_sync(kFull, (long long)rhi, o));
-        n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
     }
     const uint64_t t = k / kQT;
-    if (lane == 0) {
-        if (n_overlap) atomicAdd(&a.ctr->overlap_pairs, n_overlap);
-        if (t < a.ntiles) {
-            unsigned long long w = 0;
-            if (rhi > rlo) {
-                w = (unsigned long long)((rhi - rlo + a.chunk - 1) / a.chunk);
-            } else {
-                rlo = 0;
-                rhi = 0;
-            }
-            a.tile_lo[t] = rlo;
-            a.tile_hi[t] = rhi;
-            a.tile_work[t] = w;
-            if (t == 0) a.tile_work[a.ntiles] = 0;  // the scan turns this slot into the total
+    if (lane == 0 && t < a.ntiles) {
+        unsigned long long w = 0;
+        if (rhi > rlo) {
+            w = (unsigned long long)((rhi - rlo + a.chunk - 1) / a.chunk);
+        } else {
+            rlo = 0;
+            rhi = 0;
         }
+        a.tile_lo[t] = rlo;
+        a.tile_hi[t] = rhi;
+        a.tile_work[t] = w;
+        if (t == 0) a.tile_work[a.ntiles] = 0;  // the scan turns this slot into the total
+    }
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&a.ctr->gather_done, 1ULL) == (unsigned long long)gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        block_exclusive_scan<unsigned long long, kBlock, 8>(a.tile_work, a.ntiles + 1, &a.ctr->work_items);
     }
 }
 
@@ -419,6 +460,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
             atomicAdd(&ctr->fp64_pairs, n_overlap);
         }
     }
+    publish_when_last(ctr, args.publish);
 }
 
 size_t pair_smem_bytes(uint32_t chunk)
@@ -431,7 +473,7 @@ size_t pair_smem_bytes(uint32_t chunk)
 // Launch the pair kernel of the requested mode as a persistent grid (as many
 // CTAs as fit on every SM at once).  Filter mode: the FP32 pre-test kernel,
 // then the FP64 refine kernel over its survivors.  Neither counts the
-// overlapping pairs: query_gather does.
+// overlapping pairs: query_prep does.
 // mid (filter mode, may be null): event recorded between the filter and the
 // refine kernel with the flags evflags.
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
@@ -460,11 +502,11 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     uint64_t cap = nq > 2 * w.q_cap ? nq : 2 * w.q_cap;
     if (cap < 1024) cap = 1024;
     uint64_t bytes = 10 * carve_bytes(cap, 8)                   // staged host input
-                     + 9 * carve_bytes(cap, 8)                  // pre
+                     + kPreCols * carve_bytes(cap, 8)           // pre
                      + 2 * carve_bytes(cap, 8) + 2 * carve_bytes(cap, 4) // sort
-                     + 13 * carve_bytes(cap, 8)                 // sorted query SoA
+                     + 11 * carve_bytes(cap, 8)                 // sorted query SoA
                      + 2 * carve_bytes(cap, 16)                 // query spheres (before / after sorting)
-                     + carve_bytes(9, sizeof(double *));        // pre pointer table
+                     + carve_bytes(kPreCols, sizeof(double *)); // pre pointer table
     uint64_t ntiles = (cap + kQT - 1) / kQT;
     uint64_t tbytes = 2 * carve_bytes(ntiles, 8) + carve_bytes(ntiles + 1, 8);
     uint64_t hwords = sort_hist_words(cap);
@@ -489,7 +531,7 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     for (int c = 0; c < 8; c++) w.in_cols[c] = carve<double>(p, cap);
     w.in_seg = carve<int64_t>(p, cap);
     w.in_traj = carve<int64_t>(p, cap);
-    for (int c = 0; c < 9; c++) w.pre[c] = carve<double>(p, cap);
+    for (int c = 0; c < kPreCols; c++) w.pre[c] = carve<double>(p, cap);
     w.keys = carve<uint64_t>(p, cap);
     w.keys_alt = carve<uint64_t>(p, cap);
     w.vals = carve<uint32_t>(p, cap);
@@ -499,12 +541,12 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     q.vx = carve<double>(p, cap); q.vy = carve<double>(p, cap); q.vz = carve<double>(p, cap);
     q.d2 = carve<double>(p, cap);
     q.ts_key = carve<int64_t>(p, cap); q.te_key = carve<int64_t>(p, cap);
-    q.qid = carve<int64_t>(p, cap); q.lo = carve<int64_t>(p, cap); q.hi = carve<int64_t>(p, cap);
+    q.qid = carve<int64_t>(p, cap);
     q.qtraj = carve<int64_t>(p, cap);
     w.pre_sph = carve<float4>(p, cap);
     q.sph = carve<float4>(p, cap);
-    w.pre_dev = carve<double *>(p, 9);
-    if (cudaMemcpy(w.pre_dev, w.pre, 9 * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
+    w.pre_dev = carve<double *>(p, kPreCols);
+    if (cudaMemcpy(w.pre_dev, w.pre, kPreCols * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
         return cuda_error(cudaGetLastError(), "search workspace: pointer table");
     char *tp = (char *)w.t_block;
     w.tile_lo = carve<int64_t>(tp, ntiles);
@@ -550,9 +592,11 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
 
 int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
 {
-    // query_prep and publish_counters; with entries: the sort of the query
-    // keys, query_gather, scan, pair kernel (filter mode: filter and refine)
-    return idx->n > 0 ? 2 + sort_kernel_launches(nq, bin_key_bits(idx->m)) + 2 + (cfg.filter ? 2 : 1) : 2;
+    // without entries: query_prep and publish_counters; with entries:
+    // query_prep, the sort of the query keys, query_gather and the pair
+    // kernel (filter mode: filter and refine), whose last block publishes the
+    // counters
+    return idx->n > 0 ? 2 + sort_kernel_launches(nq, bin_key_bits(idx->m), true) + (cfg.filter ? 2 : 1) : 2;
 }
 
 // Events are recorded as external event-record nodes when the stream is being
@@ -564,33 +608,41 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     cudaError_t e = cudaStreamIsCapturing(stream, &cs);
     if (e != cudaSuccess) return e;
     const unsigned evflags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-    e = cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), stream);
+    // the counters, and with the sort's small path its two fused histograms
+    const bool fuse = idx->n > 0 && sort_fusable(nq);
+    const uint64_t sort_tiles = (nq + kSortTileKeys - 1) / kSortTileKeys;
+    e = cudaMemsetAsync(w.ctr, 0, fuse ? kCtrBytes + 2 * sort_tiles * 256 * sizeof(uint32_t) : sizeof(DevCounters),
+                        stream);
     if (e != cudaSuccess) return e;
     if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, evflags)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
     const BinView bins = bin_view(idx);
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr);
+    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
+        PrepArgs{in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr, fuse ? w.sort_fused_hist : nullptr,
+                 idx->n > 0, cfg.filter});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
         if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
-                                  bin_key_bits(idx->m), &w.ctr->sort_n)) != cudaSuccess)
+                                  bin_key_bits(idx->m), &w.ctr->sort_n, fuse ? w.sort_fused_hist : nullptr)) !=
+            cudaSuccess)
             return e;
-        const GatherArgs ga{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, bins, w.q, ntiles, cfg.chunk,
-                            w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
+        const GatherArgs ga{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk,
+                            w.tile_lo, w.tile_hi, w.tile_work};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
-        if ((e = exclusive_scan_u64(w.tile_work, ntiles + 1, &w.ctr->work_items, stream)) != cudaSuccess) return e;
-        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags};
+        PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags,
+                    w.ctr_host_dev};
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
                                     events ? w.ev[2] : nullptr, evflags)) != cudaSuccess)
             return e;
         if (events && (e = cudaEventRecordWithFlags(cfg.filter ? w.ev[4] : w.ev[2], stream, evflags)) != cudaSuccess)
             return e;
-    } else if (events) {
-        for (int k : {1, 2, 4})
-            if ((e = cudaEventRecordWithFlags(w.ev[k], stream, evflags)) != cudaSuccess) return e;
+    } else {
+        if (events)
+            for (int k : {1, 2, 4})
+                if ((e = cudaEventRecordWithFlags(w.ev[k], stream, evflags)) != cudaSuccess) return e;
+        publish_counters<<<1, 32, 0, stream>>>(w.ctr, w.ctr_host_dev);
     }
-    publish_counters<<<1, 32, 0, stream>>>(w.ctr, w.ctr_host_dev);
     if (events && (e = cudaEventRecordWithFlags(w.ev[3], stream, evflags)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -655,15 +707,9 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
     const BinView bins = bin_view(idx);
     double *const *pre = w.pre_dev;
     {
-        QueryInput a0 = in;
-        uint64_t a1 = nq;
-        BinView a2 = bins;
-        double *const *a3 = pre;
-        float4 *a4 = w.pre_sph;
-        uint64_t *a5 = w.keys;
-        uint32_t *a6 = w.vals;
-        DevCounters *a7 = w.ctr;
-        void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
+        PrepArgs a0{in,    nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr,
+                    idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter};
+        void *args[] = {&a0};
         cudaKernelNodeParams kp{};
         kp.func = (void *)query_prep;
         kp.gridDim = dim3(grid_for(nq));
@@ -674,8 +720,8 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
         if (e != cudaSuccess) return e;
     }
     {
-        GatherArgs a0{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, bins, w.q, (nq + kQT - 1) / kQT,
-                      cfg.chunk, w.tile_lo, w.tile_hi, w.tile_work, cfg.filter};
+        GatherArgs a0{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, w.q, (nq + kQT - 1) / kQT,
+                      cfg.chunk, w.tile_lo, w.tile_hi, w.tile_work};
         void *args[] = {&a0};
         cudaKernelNodeParams kp{};
         kp.func = (void *)query_gather;

@@ -1,7 +1,7 @@
-// Stable LSD radix sort of (uint64 key, uint32 value) pairs and a
-// single-block exclusive scan.  Used to sort entry segments by t_start for the
-// temporal-bin index (Sec. 4) and query segments by their clipped start
-// (Sec. 4: the query set is sorted by t_start before its bins are looked up).
+// Stable LSD radix sort of (uint64 key, uint32 value) pairs.  Used to sort
+// entry segments by t_start for the temporal-bin index (Sec. 4) and query
+// segments by their clipped start (Sec. 4: the query set is sorted by
+// t_start before its bins are looked up).
 //
 // Each 8-bit digit pass runs per-tile digit histograms and a stable scatter
 // that ranks equal digits in input order inside each tile with warp match
@@ -10,6 +10,7 @@
 // one exclusive scan over the counts in digit-major order computes them
 // between the two kernels; for up to kFusedTiles tiles each scatter block
 // derives its own from the tile-major counts (no scan kernel).
+#include "scan.cuh"
 #include "tdq_internal.cuh"
 
 namespace tdq {
@@ -22,7 +23,8 @@ constexpr int kWarps = kThreads / 32;
 // inputs up to 2^20 keys, so that small sorts still spread over the SMs.
 constexpr uint64_t kSmallSort = 1u << 20;
 inline int items_for(uint64_t n) { return n <= kSmallSort ? 4 : 16; }
-constexpr uint32_t kFusedTiles = 256;
+constexpr uint32_t kFusedTiles = kSortFusedTiles;
+static_assert(kThreads * 4 == kSortTileKeys, "small-path tiles hold kSortTileKeys keys");
 
 // kTileMajor: counts stored as hist[tile][digit], else hist[digit][tile].
 // Keys to sort: n, or the device count n_dev when given (never above n).
@@ -82,14 +84,17 @@ __device__ __forceinline__ uint32_t fused_offset(const uint32_t *__restrict__ hi
 }
 
 // Tiles past the keys to sort only write zero counts (radix_hist) or do
-// nothing (radix_scatter).
+// nothing (radix_scatter).  next_hist (may be null, zeroed beforehand): the
+// scatter adds the digit counts of the pass at next_shift per destination
+// tile, tile-major (the next pass then needs no histogram kernel).
 template <int kItems, bool kFused>
 __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__restrict__ keys,
                                                           const uint32_t *__restrict__ vals, uint64_t n_launch,
                                                           const unsigned long long *n_dev, int shift,
                                                           const uint32_t *__restrict__ offsets, uint32_t ntiles,
                                                           uint64_t *__restrict__ keys_out,
-                                                          uint32_t *__restrict__ vals_out)
+                                                          uint32_t *__restrict__ vals_out, uint32_t *next_hist,
+                                                          int next_shift)
 {
     constexpr int kTile = kThreads * kItems;
     __shared__ uint32_t off[kRadix];
@@ -130,75 +135,17 @@ __global__ void __launch_bounds__(kThreads) radix_scatter(const uint64_t *__rest
             uint32_t dst = off[digit] + wcnt[warp][digit] + lrank;
             keys_out[dst] = k;
             vals_out[dst] = v;
+            if (next_hist) atomicAdd(&next_hist[(dst / kTile) * kRadix + ((k >> next_shift) & 0xff)], 1u);
         }
         __syncthreads();
     }
 }
 
-// Exclusive scan of n counters in one block of 1024 threads.  Each
-// iteration stages 1024 * kPer counters in shared memory with coalesced
-// loads (one padding word per 32 against bank conflicts), scans kPer
-// consecutive counters per thread, scans the thread sums across the block,
-// writes the prefixes back and stores them coalesced; a carry links the
-// iterations.
+// Exclusive scan of n counters in one block of 1024 threads.
 template <typename T, int kPer>
 __global__ void __launch_bounds__(1024) scan_exclusive_block(T *data, uint64_t n, T *total)
 {
-    constexpr int kChunk = 1024 * kPer;
-    __shared__ T buf[kChunk + kChunk / 32];
-    __shared__ T warp_sums[32];
-    __shared__ T carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    auto pad = [](int i) { return i + (i >> 5); };
-    if (tid == 0) carry = 0;
-    for (uint64_t start = 0; start < n; start += kChunk) {
-#pragma unroll
-        for (int j = 0; j < kPer; j++) {
-            const int i = j * 1024 + tid;
-            buf[pad(i)] = start + i < n ? data[start + i] : (T)0;
-        }
-        __syncthreads();
-        T v[kPer];
-        T s = 0;
-#pragma unroll
-        for (int j = 0; j < kPer; j++) {
-            v[j] = buf[pad(tid * kPer + j)];
-            s += v[j];
-        }
-        T x = s;  // inclusive scan of the thread sums
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sums[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            T w = warp_sums[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                T y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            warp_sums[lane] = w;  // inclusive over warps
-        }
-        __syncthreads();
-        T before = carry + (warp > 0 ? warp_sums[warp - 1] : 0) + (x - s);
-#pragma unroll
-        for (int j = 0; j < kPer; j++) {
-            buf[pad(tid * kPer + j)] = before;
-            before += v[j];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kPer; j++) {
-            const int i = j * 1024 + tid;
-            if (start + i < n) data[start + i] = buf[pad(i)];
-        }
-        if (tid == 0) carry += warp_sums[31];
-        __syncthreads();
-    }
-    if (tid == 0 && total) *total = carry;
+    block_exclusive_scan<T, 1024, kPer>(data, n, total);
 }
 
 }  // namespace
@@ -214,7 +161,8 @@ uint64_t sort_hist_words(uint64_t n)
 }
 
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
-                             uint32_t *hist, cudaStream_t stream, int key_bits, const unsigned long long *n_dev)
+                             uint32_t *hist, cudaStream_t stream, int key_bits, const unsigned long long *n_dev,
+                             uint32_t *prep_hist)
 {
     if (n <= 1) return cudaSuccess;
     if (n > 0xffffffffULL) return cudaErrorInvalidValue;  // 32-bit offsets
@@ -225,11 +173,17 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     uint32_t *src_v = vals, *dst_v = vals_alt;
     const int passes = sort_passes(key_bits < 64 ? key_bits : 64);
     const bool fused = items == 4 && ntiles <= kFusedTiles;
+    if (prep_hist && !fused) return cudaErrorInvalidValue;
     for (int shift = 0; shift < 8 * passes; shift += 8) {
         if (fused) {
-            radix_hist<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, n, n_dev, shift, hist, ntiles);
-            radix_scatter<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, hist, ntiles,
-                                                                     dst_k, dst_v);
+            // passes 0 and 1 with prep_hist: counts from the key producer and
+            // from the first scatter
+            const bool given = prep_hist && shift < 16;
+            uint32_t *h = given ? prep_hist + (shift ? (uint64_t)ntiles * kRadix : 0) : hist;
+            uint32_t *next = prep_hist && shift == 0 ? prep_hist + (uint64_t)ntiles * kRadix : nullptr;
+            if (!given) radix_hist<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, n, n_dev, shift, h, ntiles);
+            radix_scatter<4, true><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, h, ntiles,
+                                                                     dst_k, dst_v, next, shift + 8);
         } else {
             if (items == 4)
                 radix_hist<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, n, n_dev, shift, hist, ntiles);
@@ -238,10 +192,10 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
             scan_exclusive_block<uint32_t, 8><<<1, 1024, 0, stream>>>(hist, (uint64_t)ntiles * kRadix, nullptr);
             if (items == 4)
                 radix_scatter<4, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, hist,
-                                                                          ntiles, dst_k, dst_v);
+                                                                          ntiles, dst_k, dst_v, nullptr, 0);
             else
                 radix_scatter<16, false><<<ntiles, kThreads, 0, stream>>>(src_k, src_v, n, n_dev, shift, hist,
-                                                                           ntiles, dst_k, dst_v);
+                                                                           ntiles, dst_k, dst_v, nullptr, 0);
         }
         uint64_t *tk = src_k; src_k = dst_k; dst_k = tk;
         uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
@@ -250,26 +204,20 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
     return cudaGetLastError();
 }
 
-int sort_kernel_launches(uint64_t n, int key_bits)
+int sort_kernel_launches(uint64_t n, int key_bits, bool prep_hist)
 {
     if (n <= 1) return 0;
     const int passes = sort_passes(key_bits < 64 ? key_bits : 64);
     const uint64_t tile = (uint64_t)kThreads * items_for(n);
     const bool fused = items_for(n) == 4 && (n + tile - 1) / tile <= kFusedTiles;
-    return passes * (fused ? 2 : 3);
+    if (!fused) return passes * 3;
+    return passes * 2 - (prep_hist ? (passes < 2 ? passes : 2) : 0);
 }
 
 cudaError_t load_sort_module()
 {
     cudaFuncAttributes fa;
     return cudaFuncGetAttributes(&fa, radix_hist<4, true>);
-}
-
-cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,
-                               cudaStream_t stream)
-{
-    scan_exclusive_block<unsigned long long, 4><<<1, 1024, 0, stream>>>(data, n, total);
-    return cudaGetLastError();
 }
 
 }  // namespace tdq

@@ -150,6 +150,9 @@ struct DevCounters {
     unsigned long long work_items;
     unsigned long long survivors;      // filter mode: pairs that passed the FP32 pre-test
     unsigned long long sort_n;         // query slots the sort covers (the real ones; padding follows them)
+    unsigned long long gather_done;    // blocks of query_gather that have finished (the last one scans)
+    unsigned long long pair_done;      // blocks of the last pair kernel that have finished (the last one
+                                       // copies the counters to the host mirror)
     unsigned int error;                // bit 0: invalid query input
     unsigned int pad;
 };
@@ -175,11 +178,26 @@ struct QuerySoA {
     int64_t *ts_key, *te_key;  // clipped span [max(ts,t0), min(te,t1)]
     int64_t *qid;          // caller's segment id
     int64_t *qtraj;        // caller's trajectory id (0 when not given)
-    int64_t *lo, *hi;      // candidate range of sorted entry positions
     float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
 };
 
 constexpr int kSearchEvents = 5;
+
+// The counter block of a workspace: the counters, then two histograms of
+// the query sort's small path (kSortFusedTiles tiles of 256 digit counts
+// each), so that one memset clears them all.
+constexpr uint64_t kCtrBytes = 256;
+constexpr uint32_t kSortFusedTiles = 256;  // tiles of kSortTileKeys keys
+constexpr uint32_t kSortTileKeys = 1024;
+constexpr uint64_t kCtrBlockBytes = kCtrBytes + 2ull * kSortFusedTiles * 256 * sizeof(uint32_t);
+static_assert(sizeof(DevCounters) <= kCtrBytes, "counters fit their slot");
+
+// Per-query columns before sorting, in input order (64-bit words): px py pz
+// vx vy vz d2 at the clipped start, the clipped span keys ts' te' (stored
+// bitwise), and the candidate range [lo, hi) of sorted entry positions
+// (stored bitwise).
+constexpr int kPreCols = 11;
+constexpr int kPreLo = 9, kPreHi = 10;
 
 struct Workspace {
     uint64_t q_cap = 0;    // queries the buffers below hold
@@ -189,8 +207,8 @@ struct Workspace {
     int64_t *in_seg = nullptr;
     int64_t *in_traj = nullptr;
     // per-query arrays before sorting
-    double *pre[9] = {nullptr};  // px,py,pz,vx,vy,vz,d2,ts',te'
-    double **pre_dev = nullptr;  // device copy of pre[]
+    double *pre[kPreCols] = {nullptr};  // see kPreCols
+    double **pre_dev = nullptr;         // device copy of pre[]
     float4 *pre_sph = nullptr;   // per-query sphere before sorting
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;
@@ -203,10 +221,13 @@ struct Workspace {
     // sort scratch
     uint64_t s_cap = 0;
     uint32_t *sort_hist = nullptr;
-    // counters + host mirror
+    // counters (kCtrBytes, then the query sort's two fused histograms:
+    // kCtrBlockBytes in all, cleared together at the start of a search) + host
+    // mirror
     DevCounters *ctr = nullptr;
+    uint32_t *sort_fused_hist = nullptr;  // inside the counter block
     DevCounters *ctr_host = nullptr;      // pinned, mapped into the device address space
-    DevCounters *ctr_host_dev = nullptr;  // device view of ctr_host (publish_counters writes it)
+    DevCounters *ctr_host_dev = nullptr;  // device view of ctr_host (the last pair kernel writes it)
     // results owned by tdq_search (device)
     uint64_t r_cap = 0;
     void *r_block = nullptr;
@@ -356,12 +377,24 @@ tdq_status cuda_error(cudaError_t e, const char *what);
 uint64_t sort_hist_words(uint64_t n);
 // n_dev (may be null): device count of the leading keys to sort (at most n);
 // the launch shapes follow n, the work the count.
+// prep_hist (may be null; only with sort_fusable(n)): the producer of the
+// keys has stored the first pass's digit counts per tile of kSortTileKeys
+// keys (tile-major, prep_hist[tile * 256 + digit]) and zeroed the next
+// ceil(n / kSortTileKeys) * 256 words, into which the first scatter then adds
+// the second pass's counts: the sort runs no histogram kernel for its first
+// two passes.
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
                              uint32_t *hist, cudaStream_t stream, int key_bits = 64,
-                             const unsigned long long *n_dev = nullptr);
+                             const unsigned long long *n_dev = nullptr, uint32_t *prep_hist = nullptr);
 inline int sort_passes(int key_bits) { return 2 * ((key_bits + 15) / 16); }
-// Kernels radix_sort_pairs launches for n keys.
-int sort_kernel_launches(uint64_t n, int key_bits);
+// The small path of the sort (tiles of kSortTileKeys keys, at most
+// kSortFusedTiles of them), which can take prep_hist.
+inline bool sort_fusable(uint64_t n)
+{
+    return n > 1 && (n + kSortTileKeys - 1) / kSortTileKeys <= kSortFusedTiles;
+}
+// Kernels radix_sort_pairs launches for n keys (with prep_hist: fused).
+int sort_kernel_launches(uint64_t n, int key_bits, bool fused);
 // Bits of a query sort key: bin indices 0..m-1 and m for invalid segments.
 inline int bin_key_bits(uint32_t m)
 {
@@ -369,9 +402,5 @@ inline int bin_key_bits(uint32_t m)
     while (b < 32 && ((uint64_t)1 << b) <= (uint64_t)m) b++;
     return b;
 }
-
-// Single-block exclusive scan of n counters in place; total written to *total.
-cudaError_t exclusive_scan_u64(unsigned long long *data, uint64_t n, unsigned long long *total,
-                               cudaStream_t stream);
 
 }  // namespace tdq
