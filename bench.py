@@ -74,6 +74,8 @@ CPU_SAMPLE_QUERIES = 20
 # The benchmark's metric (both arms report it; the value is the segment-pair
 # test rate, queries/s and latencies are reported beside it).
 METRIC = "segment-pair tests/s & queries/s vs plain FP64 on 1 GB300; p50/p99 query latency"
+# Least wall time of the warm-up of each timed path (after its W steps).
+WARMUP_MIN_S = 0.5
 
 
 def parse():
@@ -134,7 +136,8 @@ def config_dict(args, w, extra=None):
     c = {"workload": "scale_random_walk: %d walks (%d entry segments), %d query trajectories (%d segments), "
                      "d in {1,5,15}, full window" % (args.n_traj, len(w.entries), args.n_queries, len(w.queries)),
          "entry_segments": len(w.entries), "query_segments": len(w.queries), "d_values": list(w.d_values),
-         "bin_count": 10000, "l2": "flushed (256 MiB write) between timed GPU steps"}
+         "bin_count": 10000, "l2": "flushed (256 MiB write) between timed GPU steps",
+         "warmup_rule": "W steps, then more until %.1f s of wall time" % WARMUP_MIN_S}
     if extra:
         c.update(extra)
     return c
@@ -268,7 +271,10 @@ def run_reference(args):
             p += oracle.search_sweep(w.entries, q, d, *w.window, threads=threads).overlap_pairs
         return p
 
+    t_w = time.perf_counter()
     for _ in range(args.warmup):
+        step()
+    while time.perf_counter() - t_w < WARMUP_MIN_S:
         step()
     t = time.perf_counter()
     pairs = 0
@@ -567,7 +573,12 @@ def main():
         return t
 
     def timed(mode):
+        # W warm-up steps, then more until WARMUP_MIN_S of wall time has passed:
+        # a few sub-millisecond steps do not bring the GPU to its steady clocks
+        t_w = time.perf_counter()
         for _ in range(args.warmup):
+            step(mode)
+        while time.perf_counter() - t_w < WARMUP_MIN_S:
             step(mode)
         torch.cuda.synchronize()
         barrier()

@@ -125,6 +125,31 @@ def test_random_sets_ragged(tdq, seed, n, nq, chunk):
         check(tdq, ent, qry, d, *win, bin_count=int(rng.integers(1, 300)), brute=True, entry_chunk=chunk)
 
 
+@pytest.mark.parametrize("nq", [262_144, 262_145])
+def test_query_sort_paths_at_the_small_path_limit(tdq, nq):
+    # The query sort's small path (at most 256 tiles of 1024 keys; its digit
+    # counts come from query_prep and the first scatter, no histogram kernel)
+    # ends at 262,144 query segments; one more takes the general path
+    # (histogram and scan kernels).  Both against the oracle, in both modes,
+    # directly and through a batched plan (whose graph sorts the padded size
+    # class: 262,144 and 524,288), with a window that empties some segments.
+    rng = np.random.default_rng(nq)
+    ent = workloads.random_segments(rng, 4000, box=30.0, t_span=2000.0, max_dur=3.0)
+    qry = workloads.random_segments(rng, nq, box=30.0, t_span=2000.0, max_dur=3.0)
+    qry.seg_id += 10 ** 9
+    t0, t1 = 10.0, 1990.0
+    with tdq.build_index(ent, bin_count=500) as idx:
+        for mode in (tdq.MODE_FP64, tdq.MODE_FP32_FILTER):
+            res, ref, stats, cmp = check(tdq, ent, qry, 2.0, t0, t1, idx=idx, mode=mode)
+            assert cmp["matched"] > 1000
+            with tdq.Plan(idx, nq, mode=mode, result_capacity=1 << 20) as plan:
+                cnt = plan.search(qry, np.full(nq, 2.0), np.full(nq, t0), np.full(nq, t1))
+                assert cnt == len(res)
+                assert plan.stats()["overlap_pairs"] == ref.overlap_pairs
+                for a, b in zip(_sorted_arrays(res), _sorted_arrays(plan.results())):
+                    assert np.array_equal(a, b)
+
+
 def test_scale_random_walk_reduced(tdq):
     w = workloads.scale_random_walk(n_traj=1500, n_queries=25)
     with tdq.build_index(w.entries) as idx:
