@@ -252,7 +252,8 @@ tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segments *queries
  * whole search (counter reset, query preparation and sort, candidate ranges,
  * tiles, pair kernels, overlap count, counter read-back) is captured once per
  * power-of-two size class of the batch and replayed.  The plan owns its
- * workspace, staging buffers and a device result buffer; it keeps a pointer
+ * workspace, staging buffers and a result buffer (device memory, or with
+ * host_results page-locked host memory); it keeps a pointer
  * to the index (free the plan before the index).  One search at a time per
  * plan; distinct plans on one index may run concurrently on distinct
  * streams.
@@ -266,6 +267,10 @@ typedef struct {
     uint32_t entry_chunk;        /* as in tdq_search_params (0: mode default) */
     int mode;                    /* TDQ_MODE_* */
     int no_graph;                /* 1: launch the kernels one by one instead of replaying a CUDA graph */
+    int host_results;            /* 1: the result buffer is page-locked host memory mapped into the device's address
+                                    space: the pair kernels write each result there over the CPU-GPU link, and
+                                    tdq_plan_results returns host pointers, readable once tdq_plan_search has
+                                    returned (no copy) */
 } tdq_plan_params;
 
 tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *params, tdq_plan **out);
@@ -284,12 +289,15 @@ void tdq_plan_free(tdq_plan *plan);
 tdq_status tdq_plan_search(tdq_plan *plan, const tdq_segments *queries, const double *d_per_query,
                            const double *t0_per_query, const double *t1_per_query, void *stream, uint64_t *count);
 
-/* Device view of the plan's results (valid until the next search on the
- * plan or its release): the first *count items of the four arrays. */
+/* View of the plan's results (valid until the next search on the plan or
+ * its release): the first *count items of the four arrays -- device
+ * pointers, or host pointers for a plan created with host_results. */
 tdq_status tdq_plan_results(const tdq_plan *plan, tdq_result_buffer *view, uint64_t *count);
 
 /* Copy the first n results of the plan's last search into caller arrays:
- * host memory (to_device = 0) or device memory (to_device = 1).  Blocks. */
+ * host memory (to_device = 0) or device memory (to_device = 1).  Page-locked
+ * host arrays (cudaHostAlloc, cudaHostRegister, pinned tensors) are written
+ * by one kernel over the CPU-GPU link; others through copies.  Blocks. */
 tdq_status tdq_plan_copy_results(const tdq_plan *plan, int64_t *query_seg_id, int64_t *entry_seg_id,
                                  double *t_enter, double *t_exit, uint64_t n, int to_device, void *stream);
 

@@ -170,8 +170,8 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream,
                                   bin_key_bits(idx->m)));
-        const GatherArgs ga{s->pre_dev, s->pre_sph, in.seg_id, nullptr, s->vals, nq, s->ctr, s->q, ntiles,
-                            chunk, s->tile_lo, s->tile_hi, s->tile_work};
+        const GatherArgs ga{s->pre_dev, s->pre_sph, s->vals, nq, s->ctr, s->q, ntiles, chunk, s->tile_lo,
+                            s->tile_hi, s->tile_work};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
         PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk, 0u, nullptr};
         TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream, nullptr, 0));

@@ -52,13 +52,10 @@ struct PrepArgs {
     bool count_overlaps;
 };
 
-// Arguments of query_gather (one struct, so that a captured launch can be
-// re-bound to new inputs in one step).
+// Arguments of query_gather (it reads workspace arrays only).
 struct GatherArgs {
     const double *const *pre;
     const float4 *pre_sph;
-    const int64_t *seg_id;
-    const int64_t *traj_id;  // may be null (then 0)
     const uint32_t *order;
     uint64_t nq;
     DevCounters *ctr;

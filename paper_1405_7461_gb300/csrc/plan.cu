@@ -7,9 +7,10 @@
 // overlap count, counter read-back -- as one CUDA graph launch.  Graphs are
 // captured once per power-of-two size class of the batch (the slots past the
 // batch's real size are empty padding), so batches of uneven size reuse a
-// few graphs.  Per batch, the two kernels that read the input are re-pointed
-// at it (device inputs in place, host inputs through staging buffers) and
-// told the batch's real size, without re-capturing.  The paper processes a query
+// few graphs.  Per batch, the kernel that reads the input (query
+// preparation) is re-pointed at it (device and page-locked host inputs in
+// place, other host inputs through staging buffers) and told the batch's real
+// size, without re-capturing.  The paper processes a query
 // in batches of s query segments, one kernel invocation and host round trip
 // per batch (Sec. 6.1); here a batch is one graph launch and the batch size
 // is chosen by measurement (tdq_autotune).
@@ -44,8 +45,10 @@ struct tdq_plan {
     tdq::Workspace ws;
     void *stage_block = nullptr;
     double *d_arr = nullptr, *t0_arr = nullptr, *t1_arr = nullptr;
-    void *r_block = nullptr;
-    tdq_result_buffer res{};
+    void *r_block = nullptr;     // device result buffer, or page-locked host memory (host_results)
+    bool host_results = false;
+    tdq_result_buffer res{};       // the kernels' view (device pointers)
+    tdq_result_buffer res_host{};  // host pointers of the same arrays (host_results)
     cudaStream_t cap_stream = nullptr;
     struct Graph {
         uint64_t cls;
@@ -73,24 +76,56 @@ void drop_graphs(tdq_plan *p)
     p->ngraphs = 0;
 }
 
+// The four result arrays of capacity cap in one block, each b bytes.
+tdq_result_buffer result_columns(char *c, uint64_t b, uint64_t cap)
+{
+    tdq_result_buffer r{};
+    r.query_seg_id = (int64_t *)c;
+    r.entry_seg_id = (int64_t *)(c + b);
+    r.t_enter = (double *)(c + 2 * b);
+    r.t_exit = (double *)(c + 3 * b);
+    r.capacity = cap;
+    return r;
+}
+
+void free_results(tdq_plan *p)
+{
+    if (p->r_block) {
+        if (p->host_results)
+            cudaFreeHost(p->r_block);
+        else
+            cudaFree(p->r_block);
+    }
+    p->r_block = nullptr;
+    p->res = tdq_result_buffer{};
+    p->res_host = tdq_result_buffer{};
+}
+
 tdq_status plan_results(tdq_plan *p, uint64_t cap)
 {
     if (cap <= p->res.capacity && p->r_block) return TDQ_OK;
     drop_graphs(p);  // captured graphs hold the old pointers
-    cudaFree(p->r_block);
-    p->r_block = nullptr;
-    p->res = tdq_result_buffer{};
+    free_results(p);
     const uint64_t b = (cap * 8 + 255) & ~(uint64_t)255;
-    if (dev_alloc(&p->r_block, 4 * b) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(TDQ_ERR_NOMEM, "tdq_plan: result buffer of %llu items", (unsigned long long)cap);
+    char *dev = nullptr;
+    if (p->host_results) {
+        void *d = nullptr;
+        if (cudaHostAlloc(&p->r_block, 4 * b, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&d, p->r_block, 0) != cudaSuccess) {
+            cudaGetLastError();
+            free_results(p);
+            return set_error(TDQ_ERR_NOMEM, "tdq_plan: host result buffer of %llu items", (unsigned long long)cap);
+        }
+        p->res_host = result_columns((char *)p->r_block, b, cap);
+        dev = (char *)d;
+    } else {
+        if (dev_alloc(&p->r_block, 4 * b) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(TDQ_ERR_NOMEM, "tdq_plan: result buffer of %llu items", (unsigned long long)cap);
+        }
+        dev = (char *)p->r_block;
     }
-    char *c = (char *)p->r_block;
-    p->res.query_seg_id = (int64_t *)c;
-    p->res.entry_seg_id = (int64_t *)(c + b);
-    p->res.t_enter = (double *)(c + 2 * b);
-    p->res.t_exit = (double *)(c + 3 * b);
-    p->res.capacity = cap;
+    p->res = result_columns(dev, b, cap);
     return TDQ_OK;
 }
 
@@ -158,7 +193,7 @@ void plan_release(tdq_plan *p)
     for (int k = 0; k < kSearchEvents; k++)
         if (w.ev[k]) cudaEventDestroy(w.ev[k]);
     cudaFree(p->stage_block);
-    cudaFree(p->r_block);
+    free_results(p);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
 }
 
@@ -184,6 +219,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
     p->cap_q = size_class(p->max_q);
     p->cfg = cfg;
     p->use_graph = !params->no_graph;
+    p->host_results = params->host_results != 0;
     do {
         Workspace &w = p->ws;
         bool ok = dev_alloc(&w.ctr, kCtrBlockBytes) == cudaSuccess &&
@@ -332,10 +368,29 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
 extern "C" tdq_status tdq_plan_results(const tdq_plan *p, tdq_result_buffer *view, uint64_t *count)
 {
     if (!p || !view || !count) return set_error(TDQ_ERR_INVALID, "tdq_plan_results: NULL argument");
-    *view = p->res;
+    *view = p->host_results ? p->res_host : p->res;
     *count = p->last_count;
     return TDQ_OK;
 }
+
+namespace {
+
+// The four result columns into caller arrays the device can write (device
+// memory, or page-locked host memory over the coherent CPU-GPU link): one
+// launch instead of four copies.
+__global__ void copy_result_columns(tdq_result_buffer src, uint64_t n, int64_t *qid, int64_t *eid, double *tin,
+                                    double *tout)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        qid[i] = src.query_seg_id[i];
+        eid[i] = src.entry_seg_id[i];
+        tin[i] = src.t_enter[i];
+        tout[i] = src.t_exit[i];
+    }
+}
+
+}  // namespace
 
 extern "C" tdq_status tdq_plan_copy_results(const tdq_plan *p, int64_t *query_seg_id, int64_t *entry_seg_id,
                                             double *t_enter, double *t_exit, uint64_t n, int to_device,
@@ -349,7 +404,21 @@ extern "C" tdq_status tdq_plan_copy_results(const tdq_plan *p, int64_t *query_se
     if (!query_seg_id || !entry_seg_id || !t_enter || !t_exit)
         return set_error(TDQ_ERR_INVALID, "tdq_plan_copy_results: NULL array");
     cudaStream_t stream = (cudaStream_t)stream_;
-    const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!to_device) {
+        void *v[4] = {(void *)mapped_view(query_seg_id, n * 8), (void *)mapped_view(entry_seg_id, n * 8),
+                      (void *)mapped_view(t_enter, n * 8), (void *)mapped_view(t_exit, n * 8)};
+        if (v[0] && v[1] && v[2] && v[3]) {  // all page-locked and mapped: written by one kernel
+            const uint64_t blocks = (n + kBlock - 1) / kBlock, most = 4ull * (uint64_t)p->idx->sm_count;
+            copy_result_columns<<<(unsigned)(blocks < most ? blocks : most), kBlock, 0, stream>>>(
+                p->res, n, (int64_t *)v[0], (int64_t *)v[1], (double *)v[2], (double *)v[3]);
+            TDQ_CUDA(cudaGetLastError());
+            TDQ_CUDA(cudaStreamSynchronize(stream));
+            return TDQ_OK;
+        }
+    }
+    // (the plan's buffer may be page-locked host memory: the runtime tells the
+    // directions apart by address)
+    const cudaMemcpyKind kind = cudaMemcpyDefault;
     TDQ_CUDA(cudaMemcpyAsync(query_seg_id, p->res.query_seg_id, n * 8, kind, stream));
     TDQ_CUDA(cudaMemcpyAsync(entry_seg_id, p->res.entry_seg_id, n * 8, kind, stream));
     TDQ_CUDA(cudaMemcpyAsync(t_enter, p->res.t_enter, n * 8, kind, stream));

@@ -197,6 +197,8 @@ __global__ void query_prep(PrepArgs a)
         a.keys[i] = key;
         a.vals[i] = (uint32_t)i;
         digit = (uint32_t)(key & 0xff);
+        pre[kPreSeg][i] = __longlong_as_double(in.seg_id[i]);
+        pre[kPreTraj][i] = __longlong_as_double(in.traj_id ? in.traj_id[i] : 0);
         if (valid && a.ranges) candidate_range(bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
     }
     if (i < nq && a.ranges) {
@@ -250,8 +252,8 @@ __global__ void query_gather(GatherArgs a)
         q.d2[k] = a.pre[6][i];
         q.ts_key[k] = __double_as_longlong(a.pre[7][i]);
         q.te_key[k] = __double_as_longlong(a.pre[8][i]);
-        q.qid[k] = a.seg_id[i];
-        if (q.qtraj) q.qtraj[k] = a.traj_id ? a.traj_id[i] : 0;
+        q.qid[k] = __double_as_longlong(a.pre[kPreSeg][i]);
+        if (q.qtraj) q.qtraj[k] = __double_as_longlong(a.pre[kPreTraj][i]);
         q.sph[k] = a.pre_sph[i];
         rlo = __double_as_longlong(a.pre[kPreLo][i]);
         rhi = __double_as_longlong(a.pre[kPreHi][i]);
@@ -626,8 +628,8 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                   bin_key_bits(idx->m), &w.ctr->sort_n, fuse ? w.sort_fused_hist : nullptr)) !=
             cudaSuccess)
             return e;
-        const GatherArgs ga{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk,
-                            w.tile_lo, w.tile_hi, w.tile_work};
+        const GatherArgs ga{pre, w.pre_sph, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk, w.tile_lo, w.tile_hi,
+                            w.tile_work};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags,
                     w.ctr_host_dev};
@@ -694,43 +696,25 @@ cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
         cudaKernelNodeParams kp;
         if ((e = cudaGraphKernelNodeGetParams(nodes[k], &kp)) != cudaSuccess) break;
         if (kp.func == (void *)query_prep) out->prep = nodes[k];
-        if (kp.func == (void *)query_gather) out->gather = nodes[k];
     }
     free(nodes);
-    if (e == cudaSuccess && (!out->prep || !out->gather)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && !out->prep) e = cudaErrorInvalidValue;
     return e;
 }
 
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
                         const QueryInput &in, uint64_t nq, const LaunchCfg &cfg)
 {
-    const BinView bins = bin_view(idx);
-    double *const *pre = w.pre_dev;
-    {
-        PrepArgs a0{in,    nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr,
-                    idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter};
-        void *args[] = {&a0};
-        cudaKernelNodeParams kp{};
-        kp.func = (void *)query_prep;
-        kp.gridDim = dim3(grid_for(nq));
-        kp.blockDim = dim3(kBlock);
-        kp.sharedMemBytes = 0;
-        kp.kernelParams = args;
-        cudaError_t e = cudaGraphExecKernelNodeSetParams(exec, nodes.prep, &kp);
-        if (e != cudaSuccess) return e;
-    }
-    {
-        GatherArgs a0{pre, w.pre_sph, in.seg_id, in.traj_id, w.vals, nq, w.ctr, w.q, (nq + kQT - 1) / kQT,
-                      cfg.chunk, w.tile_lo, w.tile_hi, w.tile_work};
-        void *args[] = {&a0};
-        cudaKernelNodeParams kp{};
-        kp.func = (void *)query_gather;
-        kp.gridDim = dim3(grid_for(nq));
-        kp.blockDim = dim3(kBlock);
-        kp.sharedMemBytes = 0;
-        kp.kernelParams = args;
-        return cudaGraphExecKernelNodeSetParams(exec, nodes.gather, &kp);
-    }
+    PrepArgs a0{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, w.vals, w.ctr,
+                idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter};
+    void *args[] = {&a0};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)query_prep;
+    kp.gridDim = dim3(grid_for(nq));
+    kp.blockDim = dim3(kBlock);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return cudaGraphExecKernelNodeSetParams(exec, nodes.prep, &kp);
 }
 
 namespace {

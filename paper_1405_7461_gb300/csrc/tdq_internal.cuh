@@ -193,11 +193,13 @@ constexpr uint64_t kCtrBlockBytes = kCtrBytes + 2ull * kSortFusedTiles * 256 * s
 static_assert(sizeof(DevCounters) <= kCtrBytes, "counters fit their slot");
 
 // Per-query columns before sorting, in input order (64-bit words): px py pz
-// vx vy vz d2 at the clipped start, the clipped span keys ts' te' (stored
-// bitwise), and the candidate range [lo, hi) of sorted entry positions
-// (stored bitwise).
-constexpr int kPreCols = 11;
-constexpr int kPreLo = 9, kPreHi = 10;
+// vx vy vz d2 at the clipped start, the clipped span keys ts' te', the
+// candidate range [lo, hi) of sorted entry positions, and the caller's
+// segment and trajectory ids (integers stored bitwise).  The ids are copied
+// here with coalesced loads, so that the gather into sorted order never reads
+// the caller's arrays at random (they may be host memory read in place).
+constexpr int kPreCols = 13;
+constexpr int kPreLo = 9, kPreHi = 10, kPreSeg = 11, kPreTraj = 12;
 
 struct Workspace {
     uint64_t q_cap = 0;    // queries the buffers below hold
@@ -293,10 +295,10 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                            const tdq_result_buffer &out, cudaStream_t stream, bool events);
 tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchCfg &cfg, uint64_t nq,
                          uint64_t capacity, bool events, tdq_stats *s, uint64_t *count, bool *surv_overflow);
-// The two kernels of a captured search that read the caller's input (query
-// preparation and gather); re-pointed per batch without re-capturing.
+// The kernel of a captured search that reads the caller's input (query
+// preparation); re-pointed per batch without re-capturing.
 struct GraphInputNodes {
-    cudaGraphNode_t prep = nullptr, gather = nullptr;
+    cudaGraphNode_t prep = nullptr;
 };
 cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out);
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,

@@ -76,7 +76,8 @@ class tdq_stats(ctypes.Structure):
 
 class tdq_plan_params(ctypes.Structure):
     _fields_ = [("max_query_segments", ctypes.c_uint64), ("result_capacity", ctypes.c_uint64),
-                ("entry_chunk", ctypes.c_uint32), ("mode", ctypes.c_int), ("no_graph", ctypes.c_int)]
+                ("entry_chunk", ctypes.c_uint32), ("mode", ctypes.c_int), ("no_graph", ctypes.c_int),
+                ("host_results", ctypes.c_int)]
 
 
 class tdq_autotune_params(ctypes.Structure):
@@ -522,10 +523,11 @@ class Plan:
     window, each batch one CUDA graph launch."""
 
     def __init__(self, idx: Index, max_query_segments: int, mode=MODE_FP64, entry_chunk=0, result_capacity=0,
-                 use_graph=True):
+                 use_graph=True, host_results=False):
         self.idx = idx
+        self.host_results = bool(host_results)
         prm = tdq_plan_params(int(max_query_segments), int(result_capacity), int(entry_chunk), int(mode),
-                              0 if use_graph else 1)
+                              0 if use_graph else 1, 1 if host_results else 0)
         h = ctypes.c_void_p()
         _check(load().tdq_plan_create(idx.handle, ctypes.byref(prm), ctypes.byref(h)))
         self._h = h.value
@@ -557,15 +559,29 @@ class Plan:
         del keep
         return int(cnt.value)
 
-    def results(self, out=None) -> Results:
+    def results(self, out=None, view=False) -> Results:
         """tdq_plan_copy_results: the last batch's results, copied to host --
         into new arrays, or into `out` = (query_seg_id, entry_seg_id,
         t_enter, t_exit), caller arrays (e.g. pinned memory) large enough for
-        the count, returned as views of their first entries."""
-        view = tdq_result_buffer()
+        the count, returned as views of their first entries.  view=True (a
+        plan with host_results): arrays over the plan's own page-locked
+        result buffer, where the kernels wrote them -- no copy; valid until
+        the next search on the plan or its release."""
+        buf = tdq_result_buffer()
         cnt = ctypes.c_uint64()
-        _check(load().tdq_plan_results(self._h, ctypes.byref(view), ctypes.byref(cnt)))
+        _check(load().tdq_plan_results(self._h, ctypes.byref(buf), ctypes.byref(cnt)))
         n = int(cnt.value)
+        if view:
+            if not self.host_results:
+                raise ValueError("tdq: results(view=True) needs a plan created with host_results=True")
+
+            def arr(p, dt):
+                if n == 0:
+                    return np.empty(0, dt)
+                return np.frombuffer((ctypes.c_char * (n * 8)).from_address(p), dtype=dt)
+
+            return Results(arr(buf.query_seg_id, np.int64), arr(buf.entry_seg_id, np.int64),
+                           arr(buf.t_enter, np.float64), arr(buf.t_exit, np.float64))
         if out is not None:
             if any(len(a) < n or not a.flags["C_CONTIGUOUS"] for a in out):
                 raise ValueError("tdq: result arrays too small or not contiguous")

@@ -187,6 +187,55 @@ def test_plan_results_into_caller_arrays(tdq):
             plan.results(out=tuple(a[: c - 1] for a in outs))
         with pytest.raises(ValueError):
             plan.results(out=(outs[2], outs[1], outs[2], outs[3]))
+        # every overlapping pair a hit: 396,000 results, more than the
+        # one-kernel copy's threads (grid-stride); then arrays of which one
+        # is pageable (the copy-engine path)
+        c = plan.search(q, np.full(n, 1e6), t0, t1)
+        assert c == 20 * 99 * 200 == plan.stats()["overlap_pairs"]
+        fresh = plan.results()
+        big = tuple(torch.empty(c, dtype=dt, pin_memory=True).numpy()
+                    for dt in (torch.int64, torch.int64, torch.float64, torch.float64))
+        mixed = (big[0], big[1], np.empty(c, np.float64), big[3])
+        for out in (big, mixed):
+            got = plan.results(out=out)
+            for f in ("query_seg_id", "entry_seg_id", "t_enter", "t_exit"):
+                assert np.array_equal(getattr(got, f), getattr(fresh, f))
+
+
+def _sorted(r):
+    o = np.lexsort((r.entry_seg_id, r.query_seg_id))
+    return r.query_seg_id[o], r.entry_seg_id[o], r.t_enter[o], r.t_exit[o]
+
+
+def test_plan_with_host_results(tdq):
+    # a plan whose result buffer is page-locked host memory: the kernels
+    # write the results there, results(view=True) reads them in place (no
+    # copy); the same items as a plan with a device buffer, in both modes,
+    # also after the buffer overflowed and was regrown (every overlapping
+    # pair a hit, 396,000 results); a device plan refuses view=True
+    w = workloads.tiny_random_walk()
+    q = w.queries
+    n = len(q)
+    t0 = np.full(n, w.window[0])
+    t1 = np.full(n, w.window[1])
+    with tdq.build_index(w.entries) as idx:
+        for mode in (tdq.MODE_FP64, tdq.MODE_FP32_FILTER):
+            with tdq.Plan(idx, n, mode=mode) as dev, tdq.Plan(idx, n, mode=mode, host_results=True) as host:
+                for d in (w.d_values[0], 1e6):
+                    dd = np.full(n, d)
+                    c_dev = dev.search(q, dd, t0, t1)
+                    c_host = host.search(q, dd, t0, t1)
+                    assert c_dev == c_host > 0
+                    ref = _sorted(dev.results())
+                    got = host.results(view=True)
+                    assert len(got) == c_host
+                    for a, b in zip(ref, _sorted(got)):
+                        assert np.array_equal(a, b)
+                    for a, b in zip(ref, _sorted(host.results())):  # the copying path too
+                        assert np.array_equal(a, b)
+                assert c_host == 20 * 99 * 200
+                with pytest.raises(ValueError):
+                    dev.results(view=True)
 
 
 def test_batching_workload_full_size_sampled(tdq):
