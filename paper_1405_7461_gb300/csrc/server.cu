@@ -63,9 +63,6 @@ struct Lane {
     double *h_cols[8] = {nullptr};
     int64_t *h_seg = nullptr;
     double *h_d = nullptr, *h_t0 = nullptr, *h_t1 = nullptr;
-    uint64_t r_cap = 0;
-    int64_t *h_rq = nullptr, *h_re = nullptr;
-    double *h_rin = nullptr, *h_rout = nullptr;
     std::thread th;
 };
 
@@ -123,24 +120,6 @@ tdq_status lane_alloc(Lane &L, uint64_t cap)
     return TDQ_OK;
 }
 
-tdq_status lane_results(Lane &L, uint64_t n)
-{
-    if (n <= L.r_cap) return TDQ_OK;
-    cudaFreeHost(L.h_rq);
-    cudaFreeHost(L.h_re);
-    cudaFreeHost(L.h_rin);
-    cudaFreeHost(L.h_rout);
-    L.h_rq = L.h_re = nullptr;
-    L.h_rin = L.h_rout = nullptr;
-    L.r_cap = 0;
-    const uint64_t cap = n + n / 2 + 1024;
-    if (host_alloc(&L.h_rq, cap * 8) != cudaSuccess || host_alloc(&L.h_re, cap * 8) != cudaSuccess ||
-        host_alloc(&L.h_rin, cap * 8) != cudaSuccess || host_alloc(&L.h_rout, cap * 8) != cudaSuccess)
-        return set_error(TDQ_ERR_NOMEM, "server: result staging");
-    L.r_cap = cap;
-    return TDQ_OK;
-}
-
 void lane_free(Lane &L)
 {
     if (L.plan) tdq_plan_free(L.plan);
@@ -150,10 +129,6 @@ void lane_free(Lane &L)
     cudaFreeHost(L.h_d);
     cudaFreeHost(L.h_t0);
     cudaFreeHost(L.h_t1);
-    cudaFreeHost(L.h_rq);
-    cudaFreeHost(L.h_re);
-    cudaFreeHost(L.h_rin);
-    cudaFreeHost(L.h_rout);
 }
 
 // Search one packed batch on a lane and split its results per request.
@@ -181,9 +156,9 @@ tdq_status run_batch(tdq_server *s, Lane &L, std::vector<Request *> &batch, uint
     uint64_t cnt = 0;
     tdq_status st = tdq_plan_search(L.plan, &q, L.h_d, L.h_t0, L.h_t1, L.stream, &cnt);
     if (st != TDQ_OK) return st;
-    st = lane_results(L, cnt);
-    if (st != TDQ_OK) return st;
-    st = tdq_plan_copy_results(L.plan, L.h_rq, L.h_re, L.h_rin, L.h_rout, cnt, 0, L.stream);
+    // the lane's plan keeps its results in page-locked host memory: read in place
+    tdq_result_buffer res{};
+    st = tdq_plan_results(L.plan, &res, &cnt);
     if (st != TDQ_OK) return st;
     for (Request *r : batch) {
         r->r_q.clear();
@@ -192,13 +167,13 @@ tdq_status run_batch(tdq_server *s, Lane &L, std::vector<Request *> &batch, uint
         r->r_tout.clear();
     }
     for (uint64_t i = 0; i < cnt; i++) {
-        const uint64_t pos = (uint64_t)L.h_rq[i];
+        const uint64_t pos = (uint64_t)res.query_seg_id[i];
         const size_t k = (size_t)(std::upper_bound(offs.begin(), offs.end(), pos) - offs.begin()) - 1;
         Request *r = batch[k];
         r->r_q.push_back(r->seg_id[pos - offs[k]]);
-        r->r_e.push_back(L.h_re[i]);
-        r->r_tin.push_back(L.h_rin[i]);
-        r->r_tout.push_back(L.h_rout[i]);
+        r->r_e.push_back(res.entry_seg_id[i]);
+        r->r_tin.push_back(res.t_enter[i]);
+        r->r_tout.push_back(res.t_exit[i]);
     }
     return TDQ_OK;
 }
@@ -288,6 +263,7 @@ extern "C" tdq_status tdq_server_create(tdq_index *idx, const tdq_server_params 
         pp.mode = s->prm.mode;
         pp.entry_chunk = s->prm.entry_chunk;
         pp.result_capacity = (uint64_t)(s->rate * 2.0 * (double)pp.max_query_segments) + 65536;
+        pp.host_results = 1;
         st = tdq_plan_create(idx, &pp, &L.plan);
         if (st == TDQ_OK) st = lane_alloc(L, s->prm.max_batch_query_segments);
     }
