@@ -49,9 +49,11 @@ __device__ __forceinline__ bool is_nan_bits(double x)
 }  // namespace
 
 // Candidate range [lo, hi) of sorted entry positions of one valid query
-// segment with clipped span keys [cs, ce); with count_overlaps also its exact
-// number of temporal-overlap pairs: #{t_start < q.t_end} - #{t_end <=
-// q.t_start} (the second set lies inside the first because t_end > t_start).
+// segment with clipped span keys [cs, ce): from the first bin whose entries
+// can end after cs up to the last entry that starts before ce; with
+// count_overlaps also its exact number of temporal-overlap pairs: #{t_start <
+// q.t_end} - #{t_end <= q.t_start} (the second set lies inside the first
+// because t_end > t_start).
 __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs, int64_t ce, bool count_overlaps,
                                                 int64_t &rlo, int64_t &rhi, unsigned long long &n_overlap)
 {
@@ -63,10 +65,13 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     //     after cs starts after cs - max_dur, so the answer is searched
     //     between the bins of cs - max_dur and cs, both ends of that bracket
     //     verified (else the rest of the table);
-    //  B, C (count_overlaps) #{t_start < ce} - #{t_end <= cs}: the bin
-    //     function is monotone in time, so each count lies inside the bin of
-    //     its bound, in the sorted t_start keys (bin table bin_begin) and the
-    //     sorted t_end keys (bin table te_bin_begin).
+    //  B  #{t_start < ce}, the end of the range: the bin function is
+    //     monotone in time, so the count lies inside the bin of ce in the
+    //     sorted t_start keys (bin table bin_begin) -- entries of that bin
+    //     that start at or after ce (on a time grid: the whole next step)
+    //     are left out;
+    //  C  (count_overlaps) #{t_end <= cs}, likewise inside the bin of cs in
+    //     the sorted t_end keys (bin table te_bin_begin).
     const double te = key_double(ce), ts = key_double(cs);
     // Last bin that can hold an entry starting before the query end.
     const int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
@@ -85,10 +90,10 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
         a_hi = below ? b0 : (above ? m : hb + 1);
     }
     int64_t b_lo = 0, b_hi = 0, c_lo = 0, c_hi = 0;
-    if (count_overlaps && jhi >= 0) {
+    if (jhi >= 0) {
         b_lo = bins.bin_begin[jhi];
         b_hi = bins.bin_begin[jhi + 1];
-        if (!le0(ts - bins.t_min)) {
+        if (count_overlaps && !le0(ts - bins.t_min)) {
             c_lo = bins.te_bin_begin[bts];
             c_hi = bins.te_bin_begin[bts + 1];
         }
@@ -110,7 +115,7 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     const int64_t jlo = a_lo;
     if (jlo < m && jlo <= jhi) {
         rlo = bins.bin_begin[jlo];
-        rhi = bins.bin_begin[jhi + 1];
+        rhi = b_lo;  // first sorted t_start >= ce
         if (rlo >= rhi) { rlo = INT64_MAX; rhi = INT64_MIN; }
     }
     if (count_overlaps && jhi >= 0) n_overlap = (unsigned long long)(b_lo - c_lo);
