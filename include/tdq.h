@@ -97,7 +97,9 @@ typedef struct {
 /* Host-side results, owned by the library (release with tdq_results_free).
  * Item k: query segment query_seg_id[k] (the caller's id) is within d of
  * entry segment entry_seg_id[k] over [t_enter[k], t_exit[k]].  Order is
- * unspecified. */
+ * unspecified.  The searches place the arrays in page-locked host memory
+ * that tdq_results_free keeps for reuse by later results (up to 1 GiB; the
+ * rest is released). */
 typedef struct {
     int64_t *query_seg_id;
     int64_t *entry_seg_id;

@@ -904,10 +904,20 @@ extern "C" tdq_status tdq_search(tdq_index *idx, const tdq_segments *queries, do
     if (!r) return set_error(TDQ_ERR_NOMEM, "tdq_search: host allocation failed");
     r->count = count;
     if (count) {
-        r->query_seg_id = (int64_t *)malloc(count * 8);
-        r->entry_seg_id = (int64_t *)malloc(count * 8);
-        r->t_enter = (double *)malloc(count * 8);
-        r->t_exit = (double *)malloc(count * 8);
+        // one recycled page-locked block for the four arrays (fast copies,
+        // no page population); else plain allocations
+        char *blk = (char *)host_block_get(4 * count * 8);
+        if (blk) {
+            r->query_seg_id = (int64_t *)blk;
+            r->entry_seg_id = (int64_t *)(blk + count * 8);
+            r->t_enter = (double *)(blk + 2 * count * 8);
+            r->t_exit = (double *)(blk + 3 * count * 8);
+        } else {
+            r->query_seg_id = (int64_t *)malloc(count * 8);
+            r->entry_seg_id = (int64_t *)malloc(count * 8);
+            r->t_enter = (double *)malloc(count * 8);
+            r->t_exit = (double *)malloc(count * 8);
+        }
         if (!r->query_seg_id || !r->entry_seg_id || !r->t_enter || !r->t_exit) {
             tdq_results_free(r);
             return set_error(TDQ_ERR_NOMEM, "tdq_search: host allocation failed");
@@ -947,10 +957,12 @@ extern "C" tdq_status tdq_self_join(tdq_index *idx, const tdq_segments *entries,
 extern "C" void tdq_results_free(tdq_results *res)
 {
     if (!res) return;
-    free(res->query_seg_id);
-    free(res->entry_seg_id);
-    free(res->t_enter);
-    free(res->t_exit);
+    if (!host_block_put(res->query_seg_id)) {  // not a recycled block: four allocations
+        free(res->query_seg_id);
+        free(res->entry_seg_id);
+        free(res->t_enter);
+        free(res->t_exit);
+    }
     free(res);
 }
 

@@ -363,6 +363,13 @@ inline cudaError_t host_alloc_mapped(T **p, T **dev, size_t bytes)
     return cudaHostGetDevicePointer((void **)dev, (void *)*p, 0);
 }
 
+// Page-locked host blocks for the result arrays handed to callers, recycled
+// by size class (host_pool.cu): host_block_get returns a block of at least
+// `bytes` bytes (null when page-locked memory cannot be had);
+// host_block_put takes a block back (false: p is not one of its blocks).
+void *host_block_get(uint64_t bytes);
+bool host_block_put(void *p);
+
 // Error reporting (api.cu).
 tdq_status set_error(tdq_status st, const char *fmt, ...);
 tdq_status cuda_error(cudaError_t e, const char *what);

@@ -392,21 +392,22 @@ def _host_results(fn, idx, queries, d, t0, t1, stream, params) -> Results:
     out = ctypes.POINTER(tdq_results)()
     _check(getattr(lib, fn)(idx.handle, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(prm),
                             _stream_ptr(stream), ctypes.byref(out)))
-    try:
-        r = out.contents
-        n = int(r.count)
+    return _take_results(out)
 
-        def arr(ptr, dt):
-            if n == 0:
-                return np.empty(0, dt)
-            buf = (ctypes.c_char * (n * 8)).from_address(ptr)
-            return np.frombuffer(buf, dtype=dt).copy()
 
-        res = Results(arr(r.query_seg_id, np.int64), arr(r.entry_seg_id, np.int64), arr(r.t_enter, np.float64),
-                      arr(r.t_exit, np.float64))
-    finally:
-        lib.tdq_results_free(out)
-    return res
+class _LibResults:
+    """Owner of a library-allocated tdq_results: the numpy arrays handed out
+    are views of its columns (no copy); it is released with tdq_results_free
+    when the last of them is gone."""
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+
+    def __del__(self):
+        lib = _lib  # None once the module is torn down at exit
+        if self._ptr is not None and lib is not None:
+            lib.tdq_results_free(self._ptr)
+            self._ptr = None
 
 
 class DeviceResultBuffer:
@@ -641,20 +642,22 @@ def autotune(entries, sample, d, t0, t1, mode=MODE_FP64, bin_counts=None, entry_
 # --------------------------------------------------------------------------
 
 def _take_results(ptr) -> Results:
-    lib = load()
-    try:
-        r = ptr.contents
-        n = int(r.count)
+    """Results over a library-allocated tdq_results (no copy): the arrays are
+    views of its columns, released with tdq_results_free when the last of
+    them is gone."""
+    owner = _LibResults(ptr)
+    r = ptr.contents
+    n = int(r.count)
 
-        def arr(p, dt):
-            if n == 0:
-                return np.empty(0, dt)
-            return np.frombuffer((ctypes.c_char * (n * 8)).from_address(p), dtype=dt).copy()
+    def arr(p, dt):
+        if n == 0:
+            return np.empty(0, dt)
+        buf = (ctypes.c_char * (n * 8)).from_address(p)
+        buf._owner = owner  # the library's arrays live as long as any view of them
+        return np.frombuffer(buf, dtype=dt)
 
-        return Results(arr(r.query_seg_id, np.int64), arr(r.entry_seg_id, np.int64), arr(r.t_enter, np.float64),
-                       arr(r.t_exit, np.float64))
-    finally:
-        lib.tdq_results_free(ptr)
+    return Results(arr(r.query_seg_id, np.int64), arr(r.entry_seg_id, np.int64), arr(r.t_enter, np.float64),
+                   arr(r.t_exit, np.float64))
 
 
 class Server:

@@ -222,6 +222,29 @@ def _segs(rows, ids=None):
     return workloads.Segments.from_columns([a[:, k] for k in range(8)], seg_id=ids)
 
 
+def test_host_results_stay_valid_while_held(tdq):
+    # library-owned host results live in recycled page-locked blocks: a result
+    # set still held is never handed out again, and later searches (reusing
+    # released blocks of the same size class) leave it intact
+    import gc
+    w = workloads.tiny_random_walk()
+    with tdq.build_index(w.entries) as idx:
+        a = tdq.search(idx, w.queries, 5.0, *w.window)
+        keep_a = [x.copy() for x in _sorted_arrays(a)]
+        b = tdq.search(idx, w.queries, 5.0, *w.window)
+        assert a.query_seg_id.ctypes.data != b.query_seg_id.ctypes.data
+        keep_b = [x.copy() for x in _sorted_arrays(b)]
+        for x, y in zip(keep_a, keep_b):
+            assert np.array_equal(x, y)
+        del a
+        gc.collect()
+        for _ in range(3):  # reuse a's block with other contents
+            c = tdq.search(idx, w.queries, 2.5, *w.window)
+            assert 0 < len(c) < len(b)
+        for x, y in zip(keep_b, _sorted_arrays(b)):
+            assert np.array_equal(x, y)
+
+
 def test_empty_inputs(tdq):
     rng = np.random.default_rng(9)
     ent = workloads.random_segments(rng, 100)
