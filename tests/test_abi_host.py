@@ -140,3 +140,36 @@ def test_batching_walks_shape_small():
     assert np.all((w.q_d >= 0.5) & (w.q_d <= 10.0))
     assert np.all(w.q_t0 <= w.q_t1)
     assert np.all(w.queries.te <= 299.0)
+
+
+def test_host_results_are_views_released_with_their_last_array(monkeypatch):
+    # library-owned host results reach Python as views of the library's own
+    # arrays (no copy); the block goes back through tdq_results_free exactly
+    # once, after the last of the four arrays is gone
+    import gc
+
+    from paper_1405_7461_gb300 import tdq
+
+    cols = [np.arange(5, dtype=np.int64) + 100, np.arange(5, dtype=np.int64) + 200,
+            np.linspace(0.0, 1.0, 5), np.linspace(2.0, 3.0, 5)]
+    r = tdq.tdq_results(cols[0].ctypes.data, cols[1].ctypes.data, cols[2].ctypes.data, cols[3].ctypes.data, 5)
+    ptr = ctypes.pointer(r)
+    freed = []
+
+    class FakeLib:
+        def tdq_results_free(self, p):
+            freed.append(ctypes.addressof(p.contents))
+
+    monkeypatch.setattr(tdq, "_lib", FakeLib())
+    res = tdq._take_results(ptr)
+    for got, want in zip((res.query_seg_id, res.entry_seg_id, res.t_enter, res.t_exit), cols):
+        assert got.ctypes.data == want.ctypes.data  # a view, not a copy
+        assert np.array_equal(got, want)
+    t_exit = res.t_exit
+    del res, got, want
+    gc.collect()
+    assert freed == []  # one array still alive
+    assert t_exit[-1] == 3.0
+    del t_exit
+    gc.collect()
+    assert freed == [ctypes.addressof(r)]
