@@ -236,6 +236,21 @@ def test_plan_with_host_results(tdq):
                 assert c_host == 20 * 99 * 200
                 with pytest.raises(ValueError):
                     dev.results(view=True)
+                # the bench's end-to-end path: page-locked query arrays read
+                # in place by the kernels, results read in place on the host
+                def pinned(a):
+                    p = torch.empty(len(a), dtype=torch.from_numpy(np.asarray(a)).dtype, pin_memory=True).numpy()
+                    p[:] = a
+                    return p
+
+                qp = tdq.HostSegments(workloads.Segments(*[pinned(q[c]) for c in workloads.COLUMNS],
+                                                         pinned(q.seg_id), pinned(q.traj_id)))
+                dd = pinned(np.full(n, w.d_values[0]))
+                c_dev = dev.search(q, np.full(n, w.d_values[0]), t0, t1)
+                c_host = host.search(qp, dd, pinned(t0), pinned(t1))
+                assert c_dev == c_host > 0
+                for a, b in zip(_sorted(dev.results()), _sorted(host.results(view=True))):
+                    assert np.array_equal(a, b)
 
 
 def test_batching_workload_full_size_sampled(tdq):
