@@ -98,8 +98,10 @@ typedef struct {
  * Item k: query segment query_seg_id[k] (the caller's id) is within d of
  * entry segment entry_seg_id[k] over [t_enter[k], t_exit[k]].  Order is
  * unspecified.  The searches place the arrays in page-locked host memory
- * that tdq_results_free keeps for reuse by later results (up to 1 GiB; the
- * rest is released). */
+ * (one block per result set, its size rounded up to a power of two, at least
+ * 64 KiB; plain host memory when no page-locked memory can be had) that
+ * tdq_results_free keeps for reuse by later results (up to 1 GiB; the rest
+ * is released).  Result sets held at the same time each keep their block. */
 typedef struct {
     int64_t *query_seg_id;
     int64_t *entry_seg_id;
