@@ -59,3 +59,28 @@ def test_single_process_reduction_is_identity():
 
     assert bench.reduce_over_ranks(2.0, 7.0) == (2.0, 7.0)
     assert np.isfinite(bench.FP64_PEAK_GFLOPS) and bench.FP64_PEAK_GFLOPS == pytest.approx(1258.56)
+
+
+def test_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference times the CPU oracle and prints one JSON line
+    # with the fields both arms share (a reduced workload keeps this quick)
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+                          "--n-traj", "1500", "--n-queries", "10"], cwd=root, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["unit"] == "pair tests/s" and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("scale_random_walk")
