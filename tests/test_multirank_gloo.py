@@ -84,3 +84,24 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("scale_random_walk")
+
+
+def test_roofline_arithmetic():
+    # the bench line's roofline object: algorithmic work per launch over the
+    # kernel's average event time, against the derived peaks; algorithmic
+    # DRAM bytes beside it
+    import bench
+
+    tot = {"kernel_ms": 2.0, "fp64_pairs": 1e9, "interactions": 4e9, "refine_ms": 0.5}
+    r = bench.roofline("fp64", tot, 2, 1000)
+    assert r["kernel_ms_avg"] == 1.0
+    assert r["achieved"] == pytest.approx(32 * 0.5e9 / 1e-3 / 1e9)  # 32 flops per overlap pair, GFLOP/s
+    assert r["frac"] == pytest.approx(r["achieved"] / 1258.56)
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == pytest.approx(2 * 2e9)  # 2 B per candidate
+    f = bench.roofline("fp32filter", tot, 2, 1000)
+    assert f["achieved"] == pytest.approx(7 * 2e9 / 1e-3 / 1e9)  # 7 flops per candidate
+    assert f["frac"] == pytest.approx(f["achieved"] / 80547.84)
+    assert f["refine_kernel_ms_avg"] == 0.25
+    assert f["hbm"]["algorithmic_bytes_per_launch"] == 20 * 1000  # the 20 B record of each entry
+    assert f["hbm"]["frac"] == pytest.approx(f["hbm"]["achieved_gbs"] / bench.hbm_peak_gbs())
+    assert bench.roofline("fp64", dict(tot, kernel_ms=0.0), 2, 1000) is None
