@@ -390,7 +390,7 @@ static oracle_result *sweep(const double *const *ent, int64_t n, const double *c
         tid = omp_get_thread_num();
 #endif
         oseg q = load_seg(qry, qi);
-        double lo_t = q.t0 - maxdur, hi_t = q.t1;
+        double lo_t = ORACLE_MUTANT == 11 ? q.t0 : q.t0 - maxdur, hi_t = q.t1;
         /* first sorted position with t_start > lo_t */
         int64_t lo = 0, hi = n;
         while (lo < hi) {

@@ -2,7 +2,8 @@
 oracle (one deliberate mistake planted on the CPU: a dropped term, a flipped
 sign, a transposed operand, a wrong endpoint, an off-by-one in the overlap or
 threshold test, a wrong bin origin, an ignored window, a wrong self-join
-pair filter) must fail at least one pin of tests/test_oracle_pins.py."""
+pair filter, a time sweep that prunes too much) must fail at least one pin
+of tests/test_oracle_pins.py."""
 import pytest
 
 from oracle import oracle
@@ -19,6 +20,7 @@ MUTANTS = {
     8: "query window ignored",
     9: "self-join keeps pairs of one trajectory",
     10: "self-join keeps both orders of a pair",
+    11: "time sweep skips entries that start before the query segment",
 }
 
 PIN_CALLS = [
@@ -37,6 +39,7 @@ PIN_CALLS = [
     pins.test_fig1_bin_table_time_shifted,
     pins.test_self_join_head_on_pair_once,
     lambda: [pins.test_self_join_is_the_filtered_full_search(s) for s in (1, 2)],
+    pins.test_bruteforce_equals_sweep_on_random_sets,
 ]
 
 
