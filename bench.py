@@ -78,7 +78,7 @@ METRIC = "segment-pair tests/s & queries/s vs plain FP64 on 1 GB300; p50/p99 que
 WARMUP_MIN_S = 0.5
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -101,7 +101,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
     ap.add_argument("--n-queries", type=int, default=100)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -330,6 +330,35 @@ def roofline(mode, tot, n_launch, n_entries):
     return r
 
 
+# Result capacity of the headline and end-to-end plans (4 Mi items; a step
+# of the default workload returns ~2.3e4).
+HEADLINE_RESULT_CAPACITY = 1 << 22
+
+
+def headline_plan(tdq, idx, n_query_segments, host_results=False):
+    """The plan the headline (device inputs, device results) and the
+    end-to-end leg (pinned host inputs read in place, results written into a
+    page-locked host buffer: host_results) time: filter mode, one batch of
+    all thresholds' query segments, default bin count and chunk."""
+    return tdq.Plan(idx, n_query_segments, mode=tdq.MODE_FP32_FILTER, result_capacity=HEADLINE_RESULT_CAPACITY,
+                    host_results=host_results)
+
+
+def pinned_copy(torch, a):
+    """A copy of numpy array `a` in page-locked host memory."""
+    p = torch.empty(len(a), dtype=torch.from_numpy(np.asarray(a)).dtype, pin_memory=True).numpy()
+    p[:] = a
+    return p
+
+
+def pinned_queries(tdq, torch, q, d, t0, t1):
+    """The end-to-end leg's inputs: every query column, d and window in
+    page-locked host memory."""
+    qh = tdq.HostSegments(workloads.Segments(*[pinned_copy(torch, q[c]) for c in workloads.COLUMNS],
+                                             pinned_copy(torch, q.seg_id), pinned_copy(torch, q.traj_id)))
+    return qh, pinned_copy(torch, d), pinned_copy(torch, t0), pinned_copy(torch, t1)
+
+
 def concat_thresholds(w):
     """The step's searches (one per threshold d) as one batch: the query set
     repeated once per d, each copy with its own segment ids and threshold."""
@@ -548,7 +577,7 @@ def main():
     q3, d3, t03, t13 = concat_thresholds(w)
     q3dev = tdq.DeviceSegments(q3)
     d3dev, t03dev, t13dev = (torch.from_numpy(a).cuda() for a in (d3, t03, t13))
-    plan = tdq.Plan(idx, len(q3), mode=tdq.MODE_FP32_FILTER, result_capacity=1 << 22)
+    plan = headline_plan(tdq, idx, len(q3))
 
     def step(mode):
         t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0,
@@ -617,17 +646,10 @@ def main():
     # in pinned host memory
     e2e = None
     if not args.no_e2e:
-        def pinned(a):
-            p = torch.empty(len(a), dtype=torch.from_numpy(np.asarray(a)).dtype, pin_memory=True).numpy()
-            p[:] = a
-            return p
-
-        q3h = tdq.HostSegments(workloads.Segments(*[pinned(q3[c]) for c in workloads.COLUMNS], pinned(q3.seg_id),
-                                                  pinned(q3.traj_id)))
-        d3h, t03h, t13h = pinned(d3), pinned(t03), pinned(t13)
+        q3h, d3h, t03h, t13h = pinned_queries(tdq, torch, q3, d3, t03, t13)
         # the kernels read the pinned inputs and write the results into the
         # plan's page-locked host buffer over the CPU-GPU link
-        eplan = tdq.Plan(idx, len(q3), mode=tdq.MODE_FP32_FILTER, result_capacity=1 << 22, host_results=True)
+        eplan = headline_plan(tdq, idx, len(q3), host_results=True)
         t_w = time.perf_counter()
         for _ in range(max(args.warmup, 1)):
             eplan.search(q3h, d3h, t03h, t13h, stream=stream)

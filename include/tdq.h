@@ -227,10 +227,15 @@ tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries
  * latency-critical loop that cannot afford cudaMalloc/cudaFree, which may
  * synchronize the whole device.  Build the index beforehand; then this call
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
- * It runs the same kernels as tdq_search_device, with the same arguments,
- * results and errors, but keeps its per-search scratch in one fixed
- * file-scope device array of about 1.5 MiB, held by the device until the
- * process exits.  CUDA loads device code and arrays lazily; tdq_build_index
+ * It runs the plain FP64 kernels of tdq_search_device, with the same
+ * arguments, results and errors, but keeps its per-search scratch in one
+ * fixed file-scope device array of about 1.5 MiB, held by the device until
+ * the process exits.
+ *  - Modes: only TDQ_MODE_FP64 with no pair filters.  TDQ_MODE_FP32_FILTER
+ *    (whose survivor list has no fixed bound) and any TDQ_FLAG_* are
+ *    rejected with TDQ_ERR_INVALID.
+ *  - Synchronous: the call copies the counters back to the host and waits
+ *    for its stream before it returns.  CUDA loads device code and arrays lazily; tdq_build_index
  * loads all of the library's device code (this array included) on the
  * index's device, so no search call -- this one in particular -- loads any.
  *  - Limit: at most 8192 query segments per call; more is rejected with

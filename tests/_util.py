@@ -46,19 +46,86 @@ def dist_at(e8, q8, t):
     return np.linalg.norm(pos_at(q8, t) - pos_at(e8, t), axis=1)
 
 
+# Ill-conditioned endpoints allowed on the galaxy workload.  A root moves by
+# about (rounding of the squared distance) / (slope there), and the slope at a
+# root is 2 |dv| sqrt(d^2 - dmin^2): only pairs whose closest approach lies
+# within ~1e-18 relative of d, i.e. ties in all but name, can move a root by
+# more than 1e-9 relative.  Co-orbiting stars come close to that; random
+# walks never do, so there the allowance is zero.
+GALAXY_ILL_CONDITIONED_MAX = 4
+
+
+def common_span(entries, queries, qi, ei, t0=-np.inf, t1=np.inf):
+    """[a, b]: the common time span of each (query qi, entry ei) pair inside
+    the window, from the segments' end times (Sec. 3; numpy, independent of
+    both sides).  t0 / t1 are scalars or per-pair arrays."""
+    a = np.maximum(np.maximum(np.asarray(entries["ts"])[ei], np.asarray(queries["ts"])[qi]), t0)
+    b = np.minimum(np.minimum(np.asarray(entries["te"])[ei], np.asarray(queries["te"])[qi]), t1)
+    return a, b
+
+
+def _min_dist_between(e8, q8, ta, tb):
+    """Smallest distance of the pair over the time interval between ta and tb
+    (the relative position is linear in t, so the closest point of that chord
+    to the origin)."""
+    pa = pos_at(q8, ta)[0] - pos_at(e8, ta)[0]
+    pb = pos_at(q8, tb)[0] - pos_at(e8, tb)[0]
+    w = pb - pa
+    ww = float(w @ w)
+    s = 0.0 if ww == 0.0 else min(1.0, max(0.0, -float(pa @ w) / ww))
+    return float(np.linalg.norm(pa + s * w))
+
+
 def compare_results(gpu, ora, entries, queries, d, t0=-np.inf, t1=np.inf, dmin_fn=None,
-                    d_per_query=None, win_per_query=None):
+                    d_per_query=None, win_per_query=None, max_ill_conditioned=0):
     """Compare two result sets keyed by (query index, entry index).
 
     gpu / ora: dicts with arrays 'qi', 'ei', 't_enter', 't_exit'.
-    Pairs present on one side only must be ties (|dmin - d| <= TIE_REL * d),
-    checked with dmin_fn(ei, qi) supplied by the caller (the oracle).  Matched
-    pairs must agree on both endpoints within ENDPOINT_REL * max(1, |t|),
-    unless the endpoint is ill-conditioned, in which case the reported time
-    must still put the pair at distance d within the same relative band.
-    Returns a dict of counts."""
+
+    - Every GPU interval lies inside the pair's common span clipped to the
+      window, in order: a <= t_enter <= t_exit <= b (Sec. 3: the result is a
+      sub-interval of the time both segments are defined and the window
+      allows).  The span is recomputed here from the inputs.
+    - Pairs present on one side only must be ties (|dmin - d| <= TIE_REL * d),
+      checked with dmin_fn(ei, qi) supplied by the caller (the oracle).
+    - Matched pairs agree on both endpoints within ENDPOINT_REL * max(1, |t|).
+      An endpoint outside that band is accepted only as an ill-conditioned
+      root: the pair is at distance d within TIE_REL * d at the GPU's time, the
+      GPU's time lies on the oracle's side of the interval (t_enter not past
+      the oracle's t_exit, t_exit not before its t_enter), and between the two
+      times the distance never drops below d (1 - TIE_REL), so both name the
+      same root of the quadratic (calcTimeInterval, Sec. 5) and not the other
+      one.  At most max_ill_conditioned endpoints may take this branch.
+
+    win_per_query: optional (t0 array, t1 array) indexed by query, overriding
+    t0 / t1.  Returns a dict of counts."""
     def key(r):
         return r["qi"].astype(np.int64) * (1 << 32) + r["ei"].astype(np.int64)
+
+    def window_of(qi):
+        if win_per_query is None:
+            return t0, t1
+        return np.asarray(win_per_query[0])[qi], np.asarray(win_per_query[1])[qi]
+
+    def d_of(qi):
+        return d if d_per_query is None else float(d_per_query[qi])
+
+    gq = np.asarray(gpu["qi"], np.int64)
+    ge = np.asarray(gpu["ei"], np.int64)
+    gin = np.asarray(gpu["t_enter"], np.float64)
+    gout = np.asarray(gpu["t_exit"], np.float64)
+    if len(gq):
+        w0, w1 = window_of(gq)
+        a, b = common_span(entries, queries, gq, ge, w0, w1)
+        # a + tau rounds to at most half an ulp of (b - a) past b
+        slack = 4 * np.finfo(np.float64).eps * np.maximum(np.abs(a), np.abs(b))
+        bad = ~((a < b) & np.isfinite(gin) & np.isfinite(gout) & (a <= gin) & (gin <= gout + slack)
+                & (gout <= b + slack))
+        if np.any(bad):
+            j = int(np.nonzero(bad)[0][0])
+            raise AssertionError(
+                f"GPU interval of pair (q={gq[j]}, e={ge[j]}) is not inside its common span: "
+                f"[{gin[j]!r}, {gout[j]!r}] vs span [{a[j]!r}, {b[j]!r}] ({int(bad.sum())} such rows)")
 
     kg, ko = key(gpu), key(ora)
     assert len(np.unique(kg)) == len(kg), "duplicate pair in the GPU result"
@@ -71,29 +138,44 @@ def compare_results(gpu, ora, entries, queries, d, t0=-np.inf, t1=np.inf, dmin_f
     ties = 0
     for k in np.concatenate([only_g, only_o]):
         qi, ei = int(k >> 32), int(k & 0xFFFFFFFF)
-        dd = d if d_per_query is None else float(d_per_query[qi])
+        dd = d_of(qi)
         dm = dmin_fn(ei, qi)
         assert np.isfinite(dm) and abs(dm - dd) <= TIE_REL * dd, (
             f"pair (q={qi}, e={ei}) reported by one side only; dmin={dm!r}, d={dd!r}")
         ties += 1
-    bad = 0
+    ga = {n: np.asarray(gpu[n], np.float64)[og][ig] for n in ("t_enter", "t_exit")}
+    oa = {n: np.asarray(ora[n], np.float64)[oo][io] for n in ("t_enter", "t_exit")}
+    ill = 0
     max_rel = 0.0
-    for name in ("t_enter", "t_exit"):
-        a = gpu[name][og][ig]
-        b = ora[name][oo][io]
-        tol = ENDPOINT_REL * np.maximum(1.0, np.abs(b))
-        if len(a):
-            max_rel = max(max_rel, float(np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b)))))
-        off = np.nonzero(np.abs(a - b) > tol)[0]
+    for name, other in (("t_enter", "t_exit"), ("t_exit", "t_enter")):
+        g, o = ga[name], oa[name]
+        tol = ENDPOINT_REL * np.maximum(1.0, np.abs(o))
+        if len(g):
+            max_rel = max(max_rel, float(np.max(np.abs(g - o) / np.maximum(1.0, np.abs(o)))))
+        off = np.nonzero(np.abs(g - o) > tol)[0]
         for j in off:
             k = int(common[j])
             qi, ei = k >> 32, k & 0xFFFFFFFF
-            dd = d if d_per_query is None else float(d_per_query[qi])
+            dd = d_of(qi)
             e8 = entries.row(ei)
             q8 = queries.row(qi)
-            dist = float(dist_at(e8, q8, a[j])[0])
+            dist = float(dist_at(e8, q8, g[j])[0])
             assert abs(dist - dd) <= TIE_REL * dd + 1e-12, (
-                f"{name} mismatch for pair (q={qi}, e={ei}): {a[j]!r} vs {b[j]!r}, dist at ours {dist!r}")
-            bad += 1
-    return {"matched": len(common), "ties": ties, "ill_conditioned_endpoints": bad, "max_endpoint_rel": max_rel,
+                f"{name} mismatch for pair (q={qi}, e={ei}): {g[j]!r} vs {o[j]!r}, dist at ours {dist!r}")
+            # the same root: on the oracle's side of the interval ...
+            if name == "t_enter":
+                assert g[j] <= oa[other][j] + tol[j], (
+                    f"t_enter of pair (q={qi}, e={ei}) lies past the oracle's t_exit: {g[j]!r} > {oa[other][j]!r}")
+            else:
+                assert g[j] >= oa[other][j] - tol[j], (
+                    f"t_exit of pair (q={qi}, e={ei}) lies before the oracle's t_enter: {g[j]!r} < {oa[other][j]!r}")
+            # ... with no dip inside d between the two times
+            dm = _min_dist_between(e8, q8, min(g[j], o[j]), max(g[j], o[j]))
+            assert dm >= dd * (1 - TIE_REL) - 1e-12, (
+                f"{name} of pair (q={qi}, e={ei}) is on the other root: {g[j]!r} vs {o[j]!r}, the distance "
+                f"drops to {dm!r} < d={dd!r} between them")
+            ill += 1
+    assert ill <= max_ill_conditioned, (
+        f"{ill} ill-conditioned endpoints, more than the {max_ill_conditioned} allowed for this workload")
+    return {"matched": len(common), "ties": ties, "ill_conditioned_endpoints": ill, "max_endpoint_rel": max_rel,
             "gpu_only": len(only_g), "oracle_only": len(only_o)}

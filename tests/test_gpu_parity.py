@@ -9,7 +9,7 @@ import pytest
 
 from oracle import oracle
 from paper_1405_7461_gb300 import workloads
-from tests._util import compare_results, read_golden
+from tests._util import GALAXY_ILL_CONDITIONED_MAX, compare_results, read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +43,7 @@ def oracle_as_dict(r):
     return {"qi": r.query_index, "ei": r.entry_index, "t_enter": r.t_enter, "t_exit": r.t_exit}
 
 
-def check(tdq, entries, queries, d, t0=-np.inf, t1=np.inf, bin_count=0, brute=False, idx=None, **params):
+def check(tdq, entries, queries, d, t0=-np.inf, t1=np.inf, bin_count=0, brute=False, idx=None, max_ill=0, **params):
     own = idx is None
     if own:
         idx = tdq.build_index(entries, bin_count=bin_count)
@@ -55,7 +55,8 @@ def check(tdq, entries, queries, d, t0=-np.inf, t1=np.inf, bin_count=0, brute=Fa
             idx.free()
     ref = (oracle.search_bruteforce if brute else oracle.search_sweep)(entries, queries, d, t0, t1)
     cmp = compare_results(gpu_as_index(res, entries, queries), oracle_as_dict(ref), entries, queries, d, t0, t1,
-                          dmin_fn=lambda ei, qi: oracle.pair_dmin(entries, ei, queries, qi, t0, t1))
+                          dmin_fn=lambda ei, qi: oracle.pair_dmin(entries, ei, queries, qi, t0, t1),
+                          max_ill_conditioned=max_ill)
     # the temporal-overlap count is exact integer work: identical
     assert stats["overlap_pairs"] == ref.overlap_pairs
     assert stats["interactions"] >= stats["overlap_pairs"] >= stats["results"] == len(res)
@@ -171,19 +172,19 @@ def test_galaxy_disk_near_tangent(tdq):
     w = workloads.galaxy_disk(n_stars=3000, n_queries=30)
     with tdq.build_index(w.entries) as idx:
         for d in w.d_values:
-            check(tdq, w.entries, w.queries, d, *w.window, idx=idx)
+            check(tdq, w.entries, w.queries, d, *w.window, idx=idx, max_ill=GALAXY_ILL_CONDITIONED_MAX)
 
 
 def test_galaxy_disk_full_size_sampled(tdq):
-    """Full-size galaxy database (9.95 M segments); a seeded sample of query
-    trajectories is checked pair by pair against the oracle."""
+    """Full-size galaxy database (9.95 M segments); a seeded sample of 20
+    query trajectories is checked pair by pair against the oracle."""
     w = workloads.galaxy_disk()
     rng = np.random.default_rng(5)
-    keep = rng.choice(np.unique(w.queries.traj_id), size=6, replace=False)
+    keep = rng.choice(np.unique(w.queries.traj_id), size=20, replace=False)
     q = w.queries.take(np.nonzero(np.isin(w.queries.traj_id, keep))[0])
     with tdq.build_index(w.entries) as idx:
         for d in w.d_values:
-            check(tdq, w.entries, q, d, *w.window, idx=idx)
+            check(tdq, w.entries, q, d, *w.window, idx=idx, max_ill=GALAXY_ILL_CONDITIONED_MAX)
 
 
 def test_batched_per_query_threshold_and_window(tdq):
@@ -209,7 +210,8 @@ def test_batched_per_query_threshold_and_window(tdq):
         parts["t_exit"].append(r.t_exit)
     ref = {k: np.concatenate(v) for k, v in parts.items()}
     dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, q, qi, w.q_t0[qi], w.q_t1[qi])  # noqa: E731
-    cmp = compare_results(got, ref, w.entries, q, None, dmin_fn=dmin, d_per_query=w.q_d)
+    cmp = compare_results(got, ref, w.entries, q, None, dmin_fn=dmin, d_per_query=w.q_d,
+                          win_per_query=(w.q_t0, w.q_t1))
     assert cmp["matched"] > 1000
 
 
@@ -480,7 +482,8 @@ def test_self_join_matches_oracle(tdq, name, mode):
     assert stats["overlap_pairs"] == ref.overlap_pairs
     assert np.all(res.query_seg_id < res.entry_seg_id)
     cmp = compare_results(gpu_as_index(res, ent, ent), oracle_as_dict(ref), ent, ent, d, *window,
-                          dmin_fn=lambda ei, qi: oracle.pair_dmin(ent, ei, ent, qi, *window))
+                          dmin_fn=lambda ei, qi: oracle.pair_dmin(ent, ei, ent, qi, *window),
+                          max_ill_conditioned=GALAXY_ILL_CONDITIONED_MAX if name == "galaxy" else 0)
     assert cmp["matched"] == len(ref.query_index) > 0
 
 

@@ -94,7 +94,8 @@ def test_plan_batches_match_oracle_and_unbatched_search(tdq, mode_name):
     gi = {"qi": _positions(merged.query_seg_id, q.seg_id), "ei": _positions(merged.entry_seg_id, w.entries.seg_id),
           "t_enter": merged.t_enter, "t_exit": merged.t_exit}
     dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, q, qi, w.q_t0[qi], w.q_t1[qi])  # noqa: E731
-    cmp = compare_results(gi, ora, w.entries, q, None, dmin_fn=dmin, d_per_query=w.q_d)
+    cmp = compare_results(gi, ora, w.entries, q, None, dmin_fn=dmin, d_per_query=w.q_d,
+                          win_per_query=(w.q_t0, w.q_t1))
     assert cmp["matched"] > 1000
 
 
@@ -291,7 +292,7 @@ def test_batching_workload_full_size_sampled(tdq):
           "t_enter": merged.t_enter[mine], "t_exit": merged.t_exit[mine]}
     ora = _oracle_per_trajectory(w, qs, qd, q0, q1)
     dmin = lambda ei, qi: oracle.pair_dmin(w.entries, ei, qs, qi, q0[qi], q1[qi])  # noqa: E731
-    cmp = compare_results(gi, ora, w.entries, qs, None, dmin_fn=dmin, d_per_query=qd)
+    cmp = compare_results(gi, ora, w.entries, qs, None, dmin_fn=dmin, d_per_query=qd, win_per_query=(q0, q1))
     assert cmp["matched"] == len(ora["qi"]) > 0
 
 

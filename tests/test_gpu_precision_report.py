@@ -1,8 +1,13 @@
 """Precision report: for each workload and threshold, the filter-mode
 results against the CPU FP64 oracle -- matched pairs, ties (pairs within
 1e-9*d of the threshold that one side reports), ill-conditioned endpoints
-and the largest relative endpoint difference.  Asserts the parity bar and,
-when TDQ_REPORT_DIR is set, writes the table there as JSON."""
+and the largest relative endpoint difference.  Asserts the parity bar:
+on the random walks no tie decided differently, no ill-conditioned endpoint
+and every endpoint within 1e-9 relative; on the galaxy workload (co-orbiting
+stars, many near-tangent pairs; 20 query stars against the full 9.95 M
+segments) at most GALAXY_ILL_CONDITIONED_MAX ill-conditioned endpoints, each
+on the oracle's root, and at most 2 + 1e-5 of the matched pairs as ties.  When
+TDQ_REPORT_DIR is set, writes the table there as JSON."""
 import json
 import os
 
@@ -11,7 +16,7 @@ import pytest
 
 from oracle import oracle
 from paper_1405_7461_gb300 import workloads
-from tests._util import compare_results
+from tests._util import GALAXY_ILL_CONDITIONED_MAX, compare_results
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +33,7 @@ def test_precision_report():
     cases = [("tiny_random_walk", workloads.tiny_random_walk(), None),
              ("scale_random_walk (2,000 walks, 20 queries)", workloads.scale_random_walk(n_traj=2000, n_queries=20),
               None),
-             ("galaxy_disk (full 9.95 M entries, 4 query stars)", workloads.galaxy_disk(), 4)]
+             ("galaxy_disk (full 9.95 M entries, 20 query stars)", workloads.galaxy_disk(), 20)]
     for name, w, nq in cases:
         q = w.queries
         if nq:
@@ -46,11 +51,18 @@ def test_precision_report():
                 cmp = compare_results({"qi": qi, "ei": ei, "t_enter": r.t_enter, "t_exit": r.t_exit},
                                       {"qi": ref.query_index, "ei": ref.entry_index, "t_enter": ref.t_enter,
                                        "t_exit": ref.t_exit}, w.entries, q, d, *w.window,
-                                      dmin_fn=lambda e, k: oracle.pair_dmin(w.entries, e, q, k, *w.window))
+                                      dmin_fn=lambda e, k: oracle.pair_dmin(w.entries, e, q, k, *w.window),
+                                      max_ill_conditioned=GALAXY_ILL_CONDITIONED_MAX if nq else 0)
                 rows.append({"workload": name, "d": d, "query_segments": len(q), "overlap_pairs": st["overlap_pairs"],
                              "fp64_pairs": st["fp64_pairs"], "oracle_pairs": len(ref.query_index), **cmp})
     for row in rows:
-        assert row["max_endpoint_rel"] <= 1e-9 or row["ill_conditioned_endpoints"] > 0
+        if row["workload"].startswith("galaxy"):
+            assert row["ill_conditioned_endpoints"] <= GALAXY_ILL_CONDITIONED_MAX
+            assert row["ties"] <= 2 + 1e-5 * row["matched"]
+        else:
+            assert row["ill_conditioned_endpoints"] == 0 and row["ties"] == 0
+            assert row["max_endpoint_rel"] <= 1e-9
+        assert row["matched"] > 0
     out = os.environ.get("TDQ_REPORT_DIR")
     if out:
         os.makedirs(out, exist_ok=True)

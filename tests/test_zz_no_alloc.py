@@ -81,3 +81,22 @@ def test_noalloc_rejects_more_than_the_limit(tdq):
         n = tdq.search_device_noalloc(idx, tdq.DeviceSegments(ok), 1.0, -np.inf, np.inf, buf,
                                       allow_overflow=True)
         assert n >= 0
+
+
+def test_noalloc_accepts_only_the_plain_fp64_mode(tdq):
+    # the filter mode's survivor list has no fixed bound, and the pair
+    # filters belong to the self-join: both are refused with a message
+    rng = np.random.default_rng(4)
+    ent = workloads.random_segments(rng, 200)
+    q = tdq.DeviceSegments(workloads.random_segments(rng, 40))
+    with tdq.build_index(ent) as idx:
+        buf = tdq.DeviceResultBuffer(1 << 12)
+        with pytest.raises(tdq.TdqError) as ei:
+            tdq.search_device_noalloc(idx, q, 1.0, -np.inf, np.inf, buf, mode=tdq.MODE_FP32_FILTER)
+        assert ei.value.status == tdq.TDQ_ERR_INVALID and "TDQ_MODE_FP64" in str(ei.value)
+        with pytest.raises(tdq.TdqError) as ei:
+            tdq.search_device_noalloc(idx, q, 1.0, -np.inf, np.inf, buf, flags=tdq.FLAG_OTHER_TRAJECTORIES)
+        assert ei.value.status == tdq.TDQ_ERR_INVALID and "flags" in str(ei.value)
+        # the plain mode still runs after the refusals
+        assert tdq.search_device_noalloc(idx, q, 1.0, -np.inf, np.inf, buf, mode=tdq.MODE_FP64,
+                                         allow_overflow=True) >= 0
