@@ -309,17 +309,23 @@ def roofline(mode, tot, n_launch, n_entries):
         src = "derived: 2 DFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal FP64)"
         per = f"{FLOPS_PER_PAIR_FP64} FP64 flops per temporal-overlap pair"
     else:
-        work = FLOPS_PER_CANDIDATE_FP32 * tot["interactions"] / n_launch
+        # the unit of work is the temporal-overlap pair; the kernel tests every
+        # candidate of its ranges, so the per-candidate figure is given beside it
+        work = FLOPS_PER_CANDIDATE_FP32 * tot["pairs"] / n_launch
         peak, kernel = FP32_PEAK_GFLOPS, "traj_dist_filter_kernel"
         src = "derived: 128 FFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz"
-        per = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per candidate pair (sphere pre-test)"
+        per = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per temporal-overlap pair (sphere pre-test)"
     if kern_ms <= 0:
         return None
     achieved = work / (kern_ms / 1e3) / 1e9
     r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
          "traffic": traffic_record(mode), "kernel": kernel, "kernel_ms_avg": kern_ms, "work_unit": per,
-         "peak_source": src}
+         "peak_source": src, "clock_mhz_of_peak": 2070}
     if mode != "fp64":
+        ach_c = FLOPS_PER_CANDIDATE_FP32 * tot["interactions"] / n_launch / (kern_ms / 1e3) / 1e9
+        r["achieved_candidates"] = ach_c
+        r["frac_candidates"] = ach_c / peak
+        r["work_unit_candidates"] = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per candidate pair of the ranges"
         r["refine_kernel_ms_avg"] = tot["refine_ms"] / n_launch
         hbm_bytes = FILTER_BYTES_PER_ENTRY * n_entries
     else:

@@ -72,6 +72,8 @@ def _configure(lib):
             f = getattr(lib, name)
             f.restype = P
             f.argtypes = [P, i64, P, i64, dbl, dbl, dbl, ctypes.c_int]
+        lib.oracle_search_sweep_per_query.restype = P
+        lib.oracle_search_sweep_per_query.argtypes = [P, i64, P, i64, P, P, P, ctypes.c_int]
         lib.oracle_self_join.restype = P
         lib.oracle_self_join.argtypes = [P, i64, P, P, dbl, dbl, dbl, ctypes.c_int]
         lib.oracle_result_count.restype = i64
@@ -164,6 +166,23 @@ def search_bruteforce(entries, queries, d, t0=-np.inf, t1=np.inf, threads=0) -> 
 def search_sweep(entries, queries, d, t0=-np.inf, t1=np.inf, threads=0) -> OracleResult:
     """Same result as :func:`search_bruteforce`, visiting only pairs whose starts can overlap."""
     return _search("oracle_search_sweep", entries, queries, d, t0, t1, threads)
+
+
+def search_sweep_per_query(entries, queries, d, t0, t1, threads=0) -> OracleResult:
+    """The time sweep with query segment i searched at its own threshold
+    d[i] over its own window [t0[i], t1[i]] (arrays, one value per query
+    segment)."""
+    lib = _load()
+    ecols, earr = _columns(entries)
+    qcols, qarr = _columns(queries)
+    nq = len(qcols[0])
+    dd, w0, w1 = (np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (nq,))) for a in (d, t0, t1))
+    h = lib.oracle_search_sweep_per_query(ctypes.cast(earr, ctypes.c_void_p), len(ecols[0]),
+                                          ctypes.cast(qarr, ctypes.c_void_p), nq, _ptr(dd), _ptr(w0), _ptr(w1),
+                                          int(threads))
+    res = _collect(lib, h)
+    del ecols, qcols, dd, w0, w1
+    return res
 
 
 def self_join(entries, d, t0=-np.inf, t1=np.inf, threads=0) -> OracleResult:

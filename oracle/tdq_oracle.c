@@ -35,6 +35,8 @@
  *                               first sorted by t_start and only those whose
  *                               start lies in (q.t_start - maxdur, q.t_end)
  *                               are visited (pruning only; identical result).
+ *   oracle_search_sweep_per_query -- the sweep with a threshold and window
+ *                               of its own for every query segment.
  *   oracle_self_join         -- the sweep with the database as the query
  *                               set, pairs of one trajectory left out and
  *                               each unordered pair reported once (query (ii)
@@ -359,7 +361,8 @@ static int pair_allowed(const pair_filter *f, int64_t qi, int64_t ei)
  * the longest entry duration.  The temporal-overlap count covers every pair,
  * filtered or not. */
 static oracle_result *sweep(const double *const *ent, int64_t n, const double *const *qry, int64_t nq, double d,
-                            double wt0, double wt1, int nthreads, const pair_filter *filt)
+                            double wt0, double wt1, int nthreads, const pair_filter *filt, const double *dv,
+                            const double *w0v, const double *w1v)
 {
     nthreads = max_threads(nthreads);
     oracle_result *r = calloc(1, sizeof *r);
@@ -390,6 +393,10 @@ static oracle_result *sweep(const double *const *ent, int64_t n, const double *c
         tid = omp_get_thread_num();
 #endif
         oseg q = load_seg(qry, qi);
+        /* this query segment's threshold and window (its own, when given) */
+        const double dq = dv ? dv[qi] : d;
+        const double w0 = w0v ? w0v[qi] : wt0;
+        const double w1 = w1v ? w1v[qi] : wt1;
         double lo_t = ORACLE_MUTANT == 11 ? q.t0 : q.t0 - maxdur, hi_t = q.t1;
         /* first sorted position with t_start > lo_t */
         int64_t lo = 0, hi = n;
@@ -410,7 +417,7 @@ static oracle_result *sweep(const double *const *ent, int64_t n, const double *c
             int64_t ei = order[k];
             oseg e = load_seg(ent, ei);
             double tin, tout, dm;
-            int hit = oracle_pair((const double *)&e, (const double *)&q, d, wt0, wt1, &tin, &tout, &dm);
+            int hit = oracle_pair((const double *)&e, (const double *)&q, dq, w0, w1, &tin, &tout, &dm);
             if (hit >= 0) ov[tid]++;
             if (hit == 1 && pair_allowed(filt, qi, ei) && obuf_push(&parts[tid], qi, ei, tin, tout, dm)) failed = 1;
         }
@@ -429,7 +436,18 @@ static oracle_result *sweep(const double *const *ent, int64_t n, const double *c
 oracle_result *oracle_search_sweep(const double *const *ent, int64_t n, const double *const *qry,
                                    int64_t nq, double d, double wt0, double wt1, int nthreads)
 {
-    return sweep(ent, n, qry, nq, d, wt0, wt1, nthreads, NULL);
+    return sweep(ent, n, qry, nq, d, wt0, wt1, nthreads, NULL, NULL, NULL, NULL);
+}
+
+/* The time sweep with a threshold and a window per query segment: query
+ * segment i is searched with d[i] over [t0[i], t1[i]] (a query trajectory's
+ * own d and window, Sec. 3, given to each of its segments), so that query
+ * trajectories with different parameters are searched in one call. */
+oracle_result *oracle_search_sweep_per_query(const double *const *ent, int64_t n, const double *const *qry,
+                                             int64_t nq, const double *d, const double *wt0, const double *wt1,
+                                             int nthreads)
+{
+    return sweep(ent, n, qry, nq, 0.0, 0.0, 0.0, nthreads, NULL, d, wt0, wt1);
 }
 
 /* Self-join (query (ii) of Sec. 2.1 with the query set equal to the
@@ -440,7 +458,7 @@ oracle_result *oracle_self_join(const double *const *ent, int64_t n, const int64
                                 double d, double wt0, double wt1, int nthreads)
 {
     const pair_filter f = {traj, seg, traj, seg};
-    return sweep(ent, n, ent, n, d, wt0, wt1, nthreads, &f);
+    return sweep(ent, n, ent, n, d, wt0, wt1, nthreads, &f, NULL, NULL, NULL);
 }
 
 /* Number of OpenMP threads a search with nthreads<=0 would use. */

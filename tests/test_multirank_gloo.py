@@ -92,15 +92,17 @@ def test_roofline_arithmetic():
     # DRAM bytes beside it
     import bench
 
-    tot = {"kernel_ms": 2.0, "fp64_pairs": 1e9, "interactions": 4e9, "refine_ms": 0.5}
+    tot = {"kernel_ms": 2.0, "fp64_pairs": 1e9, "interactions": 4e9, "refine_ms": 0.5, "pairs": 3e9}
     r = bench.roofline("fp64", tot, 2, 1000)
     assert r["kernel_ms_avg"] == 1.0
     assert r["achieved"] == pytest.approx(32 * 0.5e9 / 1e-3 / 1e9)  # 32 flops per overlap pair, GFLOP/s
     assert r["frac"] == pytest.approx(r["achieved"] / 1258.56)
     assert r["hbm"]["algorithmic_bytes_per_launch"] == pytest.approx(2 * 2e9)  # 2 B per candidate
     f = bench.roofline("fp32filter", tot, 2, 1000)
-    assert f["achieved"] == pytest.approx(7 * 2e9 / 1e-3 / 1e9)  # 7 flops per candidate
+    assert f["achieved"] == pytest.approx(7 * 1.5e9 / 1e-3 / 1e9)  # 7 flops per temporal-overlap pair
     assert f["frac"] == pytest.approx(f["achieved"] / 80547.84)
+    assert f["achieved_candidates"] == pytest.approx(7 * 2e9 / 1e-3 / 1e9)  # 7 flops per candidate
+    assert f["frac_candidates"] == pytest.approx(f["achieved_candidates"] / 80547.84)
     assert f["refine_kernel_ms_avg"] == 0.25
     assert f["hbm"]["algorithmic_bytes_per_launch"] == 20 * 1000  # the 20 B record of each entry
     assert f["hbm"]["frac"] == pytest.approx(f["hbm"]["achieved_gbs"] / bench.hbm_peak_gbs())

@@ -290,6 +290,30 @@ def test_bruteforce_equals_sweep_on_random_sets():
               oracle.search_sweep(ent, qry, d, t0, t1, threads=2))
 
 
+def test_per_query_sweep_equals_brute_force_per_segment():
+    # each query segment with its own d and window: the same pairs and
+    # intervals as brute force run segment by segment with those parameters
+    rng = np.random.default_rng(16)
+    for k in range(40):
+        ent = workloads.random_segments(rng, int(rng.integers(0, 60)), box=5.0, t_span=8.0, max_dur=3.0)
+        nq = int(rng.integers(1, 20))
+        qry = workloads.random_segments(rng, nq, box=5.0, t_span=8.0, max_dur=3.0)
+        d = rng.uniform(0.0, 2.0, nq)
+        w = np.sort(rng.uniform(-1, 9, (nq, 2)), axis=1)
+        if k % 4 == 0:
+            w[:, 0], w[:, 1] = -np.inf, np.inf
+        got = oracle.search_sweep_per_query(ent, qry, d, w[:, 0], w[:, 1], threads=2)
+        parts = [oracle.search_bruteforce(ent, qry.take([i]), d[i], w[i, 0], w[i, 1], threads=1) for i in range(nq)]
+        qi = np.concatenate([np.full(len(p.query_index), i, np.int64) for i, p in enumerate(parts)])
+        ei = np.concatenate([p.entry_index for p in parts])
+        tin = np.concatenate([p.t_enter for p in parts])
+        tout = np.concatenate([p.t_exit for p in parts])
+        o = np.lexsort((ei, qi))
+        assert np.array_equal(got.query_index, qi[o]) and np.array_equal(got.entry_index, ei[o])
+        assert np.array_equal(got.t_enter, tin[o]) and np.array_equal(got.t_exit, tout[o])
+        assert got.overlap_pairs == sum(p.overlap_pairs for p in parts)
+
+
 def test_bruteforce_equals_sweep_on_tiny_random_walk():
     w = workloads.tiny_random_walk()
     assert len(w.entries) == 19_800 and len(w.queries) == 20 * 99
