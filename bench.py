@@ -90,13 +90,20 @@ def parse(argv=None):
     ap.add_argument("--no-batching", action="store_true", help="skip the batching-workload section")
     ap.add_argument("--batch-n-traj", type=int, default=20_000)
     ap.add_argument("--batch-n-queries", type=int, default=5_000)
+    ap.add_argument("--batch-oracle-queries", type=int, default=100)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-workload section")
     ap.add_argument("--serve-n-traj", type=int, default=40_000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-plain-requests", type=int, default=400)
+    ap.add_argument("--serve-oracle-requests", type=int, default=20)
     ap.add_argument("--no-self-join", action="store_true", help="skip the self-join (query (ii)) section")
     ap.add_argument("--self-join-stars", type=int, default=10_000)
+    ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-workload section")
+    ap.add_argument("--no-precision", action="store_true", help="skip the galaxy precision-workload section")
+    ap.add_argument("--galaxy-stars", type=int, default=50_000)
+    ap.add_argument("--galaxy-queries", type=int, default=500)
+    ap.add_argument("--galaxy-oracle-stars", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
@@ -378,7 +385,7 @@ def concat_thresholds(w):
     return q, d, t0, t1
 
 
-def batching_section(args, tdq, torch, stream):
+def batching_section(args, tdq, torch, stream, with_oracle=False):
     """F2 on the batching workload: 20,000 walks x 300 points (5.98 M entries),
     5,000 fresh query trajectories of lognormal length with their own d and
     window; autotuned bin count, chunk and batch size; batches replayed as
@@ -427,11 +434,25 @@ def batching_section(args, tdq, torch, stream):
     plan.free()
     idx.free()
     tot = sum(ms) / 1e3
-    return {"workload": "batching_walks: %d walks x 300 points (%d entries), %d query trajectories (%d segments), "
-                        "own d and window each" % (args.batch_n_traj, len(w.entries), args.batch_n_queries, n),
-            "tuning": tun, "autotune_s": tune_s, "batches_per_step": len(batches),
-            "pair_tests_per_s": pairs / tot, "queries_per_s": len(ms) * args.batch_n_queries / tot,
-            "ms_per_step": 1e3 * tot / len(ms)}
+    out = {"workload": "batching_walks: %d walks x 300 points (%d entries), %d query trajectories (%d segments), "
+                       "own d and window each" % (args.batch_n_traj, len(w.entries), args.batch_n_queries, n),
+           "tuning": tun, "autotune_s": tune_s, "batches_per_step": len(batches),
+           "pair_tests_per_s": pairs / tot, "queries_per_s": len(ms) * args.batch_n_queries / tot,
+           "ms_per_step": 1e3 * tot / len(ms)}
+    if with_oracle:
+        from oracle import oracle
+
+        ns = min(args.batch_oracle_queries, args.batch_n_queries)
+        keep = np.random.default_rng(41).choice(args.batch_n_queries, size=ns, replace=False)
+        osel = np.nonzero(np.isin(q.traj_id - 10_000_000, keep))[0]
+        qs = q.take(osel)
+        _, out["cpu_baseline"] = _oracle_leg(
+            lambda th: oracle.search_sweep_per_query(w.entries, qs, w.q_d[osel], w.q_t0[osel], w.q_t1[osel],
+                                                     threads=th),
+            lambda r: r.overlap_pairs, ns,
+            f"{ns} of {args.batch_n_queries} query trajectories ({len(qs)} segments, own d and window each), "
+            "time-sweep oracle incl. its sort")
+    return out
 
 
 def self_join_section(args, tdq, torch):
@@ -464,7 +485,7 @@ def self_join_section(args, tdq, torch):
     return out
 
 
-def serving_section(args, tdq, torch):
+def serving_section(args, tdq, torch, with_oracle=False):
     """F3: 40,000 walks x 500 points resident (19.96 M entries); Poisson
     arrivals at 2,000/s for 10 s, each a fresh walk of 5..499 segments with
     its own d and window; p50/p99 latency and queries/s of the serving loop,
@@ -524,7 +545,22 @@ def serving_section(args, tdq, torch):
         plat[k] = 1e3 * (time.perf_counter() - a)
     plain_s = time.perf_counter() - tp
     idx.free()
-    return {"workload": "serving_walks: %d walks x 500 points resident (%d entries); Poisson arrivals %.0f/s for "
+    cpu = None
+    if with_oracle:
+        from oracle import oracle
+
+        ns = min(args.serve_oracle_requests, len(reqs))
+        picked = [reqs[k] for k in np.random.default_rng(43).choice(len(reqs), size=ns, replace=False)]
+        qs = workloads.Segments.concat([rq.query for rq in picked])
+        rep = [len(rq.query) for rq in picked]
+        qd, q0, q1 = (np.repeat([getattr(rq, f) for rq in picked], rep) for f in ("d", "t0", "t1"))
+        db = workloads.serving_database(n_traj=args.serve_n_traj, n_points=500)
+        _, cpu = _oracle_leg(lambda th: oracle.search_sweep_per_query(db, qs, qd, q0, q1, threads=th),
+                             lambda r: r.overlap_pairs, ns,
+                             f"{ns} of {len(reqs)} requests ({len(qs)} segments, own d and window each), time-sweep "
+                             "oracle incl. its sort")
+        del db
+    return {"cpu_baseline": cpu, "workload": "serving_walks: %d walks x 500 points resident (%d entries); Poisson arrivals %.0f/s for "
                         "%.0f s (%d requests of 5..499 segments, own d in [1,20] and window)"
                         % (args.serve_n_traj, args.serve_n_traj * 499, args.serve_rate, args.serve_seconds,
                            len(reqs)),
@@ -538,6 +574,155 @@ def serving_section(args, tdq, torch):
                                          "p99_latency_ms": float(np.percentile(plat, 99)),
                                          "sample_requests": n_plain},
             "lanes": 3, "memory_cap_bytes": 16 << 30}
+
+
+def _event_time(torch, stream, fn, reps):
+    """fn() run `reps` times between two CUDA events on `stream`, after one
+    untimed call; returns (ms per call, last return value)."""
+    out = fn()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        out = fn()
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / reps, out
+
+
+def _oracle_leg(run, pairs_of, n_query_traj, sample):
+    """The CPU oracle timed on a bounded sample: run() -> oracle result(s);
+    pairs_of(result) -> temporal-overlap pairs."""
+    from oracle import oracle
+
+    threads = oracle.default_threads()
+    t = time.perf_counter()
+    res = run(threads)
+    dt = time.perf_counter() - t
+    pairs = pairs_of(res)
+    return res, {"value": pairs / dt, "unit": "pair tests/s", "queries_per_s": n_query_traj / dt, "cores": threads,
+                 "kind": "oracle", "sample": sample + f", {dt:.2f} s"}
+
+
+def _compare_sample(gpu_q, gpu_e, gpu_in, gpu_out, ref, q_ids, e_ids):
+    """Pair sets and endpoint differences of the GPU's results for a sample
+    of query segments against the oracle's on the same sample (ids on both
+    sides): pairs on one side only, and the largest relative endpoint
+    difference over the matched pairs."""
+    ko = q_ids[ref.query_index].astype(np.int64), e_ids[ref.entry_index].astype(np.int64)
+    go = np.lexsort((gpu_e, gpu_q))
+    oo = np.lexsort((ko[1], ko[0]))
+    gk = np.stack([gpu_q[go], gpu_e[go]], 1)
+    ok = np.stack([ko[0][oo], ko[1][oo]], 1)
+    same = len(gk) == len(ok) and np.array_equal(gk, ok)
+    rel = 0.0
+    if same and len(gk):
+        for g, o in ((gpu_in[go], ref.t_enter[oo]), (gpu_out[go], ref.t_exit[oo])):
+            rel = max(rel, float(np.max(np.abs(g - o) / np.maximum(1.0, np.abs(o)))))
+    only = len(set(map(tuple, gk.tolist())) ^ set(map(tuple, ok.tolist()))) if not same else 0
+    return {"pairs": int(len(ok)), "pairs_on_one_side_only": int(only), "max_endpoint_rel_diff": rel}
+
+
+def tiny_section(args, tdq, torch, stream, with_oracle):
+    """Configuration 1: 200 random walks x 100 points (19,800 entries), 20
+    query trajectories from the set (1,980 segments), d = 5, window [0, 99];
+    both modes device-timed; the oracle (time sweep) over the whole query set."""
+    w = workloads.tiny_random_walk()
+    idx = tdq.build_index(tdq.DeviceSegments(w.entries), stream=stream)
+    qdev = tdq.DeviceSegments(w.queries)
+    buf = tdq.DeviceResultBuffer(1 << 16)
+    d = w.d_values[0]
+    out = {"workload": "tiny_random_walk: 200 walks x 100 points (%d entries), 20 query trajectories (%d segments), "
+                       "d = 5, window [0, 99]" % (len(w.entries), len(w.queries))}
+    for name, mode in (("fp32filter", tdq.MODE_FP32_FILTER), ("fp64", tdq.MODE_FP64)):
+        ms, n = _event_time(torch, stream, lambda: tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream,
+                                                                     mode=mode), 50)
+        st = tdq.get_stats(idx)
+        out[name] = {"ms_per_search": ms, "pair_tests_per_s": st["overlap_pairs"] / (ms / 1e3),
+                     "queries_per_s": w.n_query_traj / (ms / 1e3), "results": n, "overlap_pairs": st["overlap_pairs"]}
+    if with_oracle:
+        from oracle import oracle
+
+        _, out["cpu_baseline"] = _oracle_leg(
+            lambda th: oracle.search_sweep(w.entries, w.queries, d, *w.window, threads=th),
+            lambda r: r.overlap_pairs, w.n_query_traj, "all 20 query trajectories, time-sweep oracle incl. its sort")
+    idx.free()
+    return out
+
+
+def precision_section(args, tdq, torch, stream, with_oracle):
+    """Configuration 3: 50,000 disk-galaxy stars x 200 points (9.95 M
+    entries), 500 query stars from the set, d in {0.01, 0.1, 1} kpc over the
+    full extent; per d the filter mode and the plain FP64 path, device-timed
+    on device inputs and results (the result buffer sized by a first call);
+    pre-test survivors and FP64 pairs per temporal-overlap pair; the oracle on
+    a seeded sample of query stars beside it, with the sample's pair set and
+    endpoint difference against the GPU's."""
+    w = workloads.galaxy_disk(n_stars=args.galaxy_stars, n_queries=args.galaxy_queries)
+    idx = tdq.build_index(tdq.DeviceSegments(w.entries), stream=stream)
+    qdev = tdq.DeviceSegments(w.queries)
+    reps = max(1, min(args.steps, 3))
+    rows = []
+    sample_traj = np.random.default_rng(31).choice(np.unique(w.queries.traj_id), size=args.galaxy_oracle_stars,
+                                                   replace=False)
+    sample = w.queries.take(np.nonzero(np.isin(w.queries.traj_id, sample_traj))[0])
+    for d in w.d_values:
+        row = {"d": d}
+        small = tdq.DeviceResultBuffer(1)
+        n_res = tdq.search_device(idx, qdev, d, *w.window, small, stream=stream, allow_overflow=True,
+                                  mode=tdq.MODE_FP32_FILTER)
+        buf = tdq.DeviceResultBuffer(max(1, n_res))
+        for name, mode in (("fp32filter", tdq.MODE_FP32_FILTER), ("fp64", tdq.MODE_FP64)):
+            tot = {"kernel_ms": 0.0, "refine_ms": 0.0, "interactions": 0, "pairs": 0, "fp64_pairs": 0,
+                   "survivors": 0}
+
+            def one():
+                n = tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=mode)
+                st = tdq.get_stats(idx)
+                tot["kernel_ms"] += st["pair_kernel_ms"]
+                tot["refine_ms"] += st["refine_ms"]
+                tot["interactions"] += st["interactions"]
+                tot["pairs"] += st["overlap_pairs"]
+                tot["fp64_pairs"] += st["fp64_pairs"]
+                tot["survivors"] += st["filter_survivors"]
+                return n
+
+            ms, n = _event_time(torch, stream, one, reps)
+            tot = {k: v * reps / (reps + 1) for k, v in tot.items()}  # the untimed first call removed
+            pairs = tot["pairs"] / reps
+            row[name] = {"ms_per_search": ms, "pair_tests_per_s": pairs / (ms / 1e3),
+                         "queries_per_s": w.n_query_traj / (ms / 1e3), "results": n, "overlap_pairs": pairs,
+                         "candidates": tot["interactions"] / reps, "fp64_pairs": tot["fp64_pairs"] / reps,
+                         "roofline": roofline(name, tot, reps, len(w.entries))}
+            if name == "fp32filter":
+                row[name]["survivors"] = tot["survivors"] / reps
+                row[name]["survivors_per_overlap_pair"] = tot["survivors"] / max(1.0, tot["pairs"])
+                row[name]["fp64_pairs_per_overlap_pair"] = tot["fp64_pairs"] / max(1.0, tot["pairs"])
+        row["speedup_vs_plain_fp64"] = row["fp64"]["ms_per_search"] / row["fp32filter"]["ms_per_search"]
+        if with_oracle:
+            from oracle import oracle
+
+            ref, row["cpu_baseline"] = _oracle_leg(
+                lambda th: oracle.search_sweep(w.entries, sample, d, *w.window, threads=th),
+                lambda r: r.overlap_pairs, len(sample_traj),
+                f"{len(sample_traj)} of {w.n_query_traj} query stars ({len(sample)} segments), time-sweep oracle "
+                "incl. its sort")
+            # the filter mode's results for the sample (ids: the segments' own)
+            tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=tdq.MODE_FP32_FILTER)
+            sel = torch.isin(buf.query_seg_id[:n_res], torch.from_numpy(sample.seg_id).cuda())
+            row["error_vs_oracle"] = _compare_sample(
+                buf.query_seg_id[:n_res][sel].cpu().numpy(), buf.entry_seg_id[:n_res][sel].cpu().numpy(),
+                buf.t_enter[:n_res][sel].cpu().numpy(), buf.t_exit[:n_res][sel].cpu().numpy(), ref, sample.seg_id,
+                w.entries.seg_id)
+        rows.append(row)
+        del buf, small
+        torch.cuda.empty_cache()
+    idx.free()
+    return {"workload": "galaxy_disk: %d stars x 200 points (%d entries), %d query stars from the set (%d segments), "
+                        "d in {0.01, 0.1, 1} kpc, full extent" % (args.galaxy_stars, len(w.entries), w.n_query_traj,
+                                                                 len(w.queries)),
+            "per_d": rows}
 
 
 def main():
@@ -682,12 +867,19 @@ def main():
                        "page-locked host buffer (tdq_plan host_results), read there; counters through mapped memory",
                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / e_dt}
 
+    with_oracle = not args.no_cpu_baseline
+    tiny = None
+    if rank == 0 and world == 1 and not args.no_tiny:
+        tiny = tiny_section(args, tdq, torch, stream, with_oracle)
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        precision = precision_section(args, tdq, torch, stream, with_oracle)
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
-        batching = batching_section(args, tdq, torch, stream)
+        batching = batching_section(args, tdq, torch, stream, with_oracle)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
-        serving = serving_section(args, tdq, torch)
+        serving = serving_section(args, tdq, torch, with_oracle)
     self_join = None
     if rank == 0 and world == 1 and not args.no_self_join:
         self_join = self_join_section(args, tdq, torch)
@@ -722,6 +914,8 @@ def main():
                                                  "gpu_launches")},
             "speedup_vs_plain_fp64": {"pair_tests": head["value"] / plain["value"],
                                       "queries": head["queries_per_s"] / plain["queries_per_s"]},
+            "tiny_workload": tiny,
+            "precision_workload": precision,
             "batching_workload": batching,
             "serving_workload": serving,
             "self_join_workload": self_join,

@@ -71,10 +71,16 @@ typedef struct {
  * and the bin table, plus the search workspace.  Owns its device memory. */
 typedef struct tdq_index tdq_index;
 
-/* Search modes. */
+/* Search modes.  All three return the same pairs and intervals: the
+ * pre-tests only drop pairs whose bounding spheres (the query's grown by d)
+ * cannot meet, which therefore never come within d (Sec. 3), and the FP64
+ * evaluation of Sec. 5 / Algorithm 1 decides the rest. */
 enum {
     TDQ_MODE_FP64 = 0,        /* every temporal-overlap pair in FP64 (plain method) */
-    TDQ_MODE_FP32_FILTER = 1  /* conservative FP32 pre-test, FP64 for the survivors */
+    TDQ_MODE_FP32_FILTER = 1, /* conservative FP32 pre-test, FP64 for the survivors */
+    TDQ_MODE_TC_FILTER = 2    /* the sphere pre-test as an exact integer GEMM on the tensor cores (centers
+                                 and radii on an 11-bit grid over the entries' extent, radii rounded up to
+                                 cover the snapping), FP64 for the survivors */
 };
 
 /* Search tuning.  Zero fields select defaults. */
@@ -130,12 +136,12 @@ typedef struct {
     uint64_t results;           /* pairs within d (alpha * interactions) */
     uint64_t work_items;        /* (query tile, entry chunk) work items */
     uint64_t kernel_launches;   /* CUDA kernels the library launched for the search */
-    double pair_kernel_ms;      /* device time of the pair kernel (CUDA events; filter mode: the FP32
+    double pair_kernel_ms;      /* device time of the pair kernel (CUDA events; filter modes: the
                                    pre-test kernel) */
     double total_ms;            /* device time of the whole search on its stream */
-    uint64_t filter_survivors;  /* filter mode: pairs that passed the FP32 pre-test (0 in FP64 mode) */
-    double refine_ms;           /* filter mode: device time of the FP64 refine kernel (pair_kernel_ms then
-                                   covers the FP32 pre-test kernel alone) */
+    uint64_t filter_survivors;  /* filter modes: pairs that passed the pre-test (0 in FP64 mode) */
+    double refine_ms;           /* filter modes: device time of the FP64 refine kernel (pair_kernel_ms then
+                                   covers the pre-test kernel alone) */
 } tdq_stats;
 
 /*
@@ -231,7 +237,7 @@ tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries
  * arguments, results and errors, but keeps its per-search scratch in one
  * fixed file-scope device array of about 1.5 MiB, held by the device until
  * the process exits.
- *  - Modes: only TDQ_MODE_FP64 with no pair filters.  TDQ_MODE_FP32_FILTER
+ *  - Modes: only TDQ_MODE_FP64 with no pair filters.  The filter modes
  *    (whose survivor list has no fixed bound) and any TDQ_FLAG_* are
  *    rejected with TDQ_ERR_INVALID.
  *  - Synchronous: the call copies the counters back to the host and waits

@@ -386,7 +386,13 @@ cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream
     if (per_sm < 1) per_sm = 1;
     traj_dist_filter_kernel<<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
     if (mid && (e = cudaEventRecordWithFlags(mid, stream, evflags)) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_refine_kernel, kPairThreads, 0);
+    return launch_refine_kernel(fa, sm_count, stream);
+}
+
+cudaError_t launch_refine_kernel(const FilterArgs &fa, int sm_count, cudaStream_t stream)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_refine_kernel, kPairThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     traj_dist_refine_kernel<<<sm_count * per_sm, kPairThreads, 0, stream>>>(fa);

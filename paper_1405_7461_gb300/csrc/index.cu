@@ -28,10 +28,14 @@ struct EntryInput {
 // Validate, and emit the sort key and time range of every entry.  The time
 // range is reduced per warp before one atomic per warp.
 __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *vals, unsigned int *err,
-                           unsigned long long *tmin_key, unsigned long long *tmax_key, unsigned long long *max_dur)
+                           unsigned long long *tmin_key, unsigned long long *tmax_key, unsigned long long *max_dur,
+                           unsigned long long *cbox)
 {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long kmin = ~0ULL, kmax = 0ULL, dmax = 0ULL;
+    // bounding box of the segments' midpoints (the tensor-core pre-test's
+    // grid), as order-preserving unsigned keys: cbox = min x, y, z, max x, y, z
+    unsigned long long cmin[3] = {~0ULL, ~0ULL, ~0ULL}, cmax[3] = {0ULL, 0ULL, 0ULL};
     if (i < n) {
         bool ok = true;
 #pragma unroll
@@ -47,21 +51,39 @@ __global__ void entry_prep(EntryInput in, uint64_t n, uint64_t *keys, uint32_t *
         kmax = (uint64_t)ke ^ 0x8000000000000000ULL;
         // longest duration: positive doubles order like their bit patterns
         if (ok) dmax = (unsigned long long)__double_as_longlong(in.c[7][i] - in.c[3][i]);
+        if (ok) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const unsigned long long kc = ukey(0.5 * in.c[a][i] + 0.5 * in.c[4 + a][i]);
+                cmin[a] = kc;
+                cmax[a] = kc;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cmin[a] = min(cmin[a], __shfl_xor_sync(0xffffffffu, cmin[a], o));
+            cmax[a] = max(cmax[a], __shfl_xor_sync(0xffffffffu, cmax[a], o));
+        }
     }
     if ((threadIdx.x & 31) == 0) {
         if (kmin != ~0ULL) atomicMin(tmin_key, kmin);
         if (kmax != 0ULL) atomicMax(tmax_key, kmax);
         if (dmax != 0ULL) atomicMax(max_dur, dmax);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (cmin[a] != ~0ULL) atomicMin(&cbox[a], cmin[a]);
+            if (cmax[a] != 0ULL) atomicMax(&cbox[3 + a], cmax[a]);
+        }
     }
 }
 
-__global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e)
+__global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, EntrySoA e, TcGrid grid)
 {
     uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -93,6 +115,10 @@ __global__ void entry_gather(EntryInput in, uint64_t n, const uint32_t *order, E
         e.sph[k] = sp;
         e.sph_e[k] = __double2float_rd(__dmul_rd(c2, 1.0 - 0x1p-20));
     }
+    // the tensor-core pre-test's record: the same sphere in FP64 on the grid
+    uint4 lo, hi;
+    tc_entry_record(xs + hx, ys + hy, zs + hz, sqrt(fma(hz, hz, fma(hy, hy, hx * hx))), grid, lo, hi);
+    tc_store(e.tc_rec, k, lo, hi);
 }
 
 // Unsigned radix keys of the sorted entries' t_end (values unused).
@@ -253,7 +279,9 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     }
 
     // Resident sorted copy + bin table.
-    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 4) + carve_bytes(n, 16);
+    idx->n_rec = (n + 7) / 8 * 8 + 128;  // whole groups of 8, and room for a pass of 128 from any group
+    uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 4) + carve_bytes(n, 16) +
+                      carve_bytes(2 * idx->n_rec, 16);
     uint64_t bbytes = 2 * carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (dev_alloc(&idx->e_block, ebytes) != cudaSuccess || dev_alloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -271,6 +299,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         e.te_sorted = carve<int64_t>(p, n);
         e.sph_e = carve<float>(p, n);
         e.sph = carve<float4>(p, n);
+        e.tc_rec = carve<uint4>(p, 2 * idx->n_rec);
         char *q = (char *)idx->b_block;
         idx->bin_begin = carve<int64_t>(q, m + 1);
         idx->bin_end_key = carve<int64_t>(q, m);
@@ -330,9 +359,11 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         uint32_t *vals = carve<uint32_t>(p, n);
         uint32_t *vals_alt = carve<uint32_t>(p, n);
         uint32_t *hist = carve<uint32_t>(p, sort_hist_words(n));
-        unsigned long long *small = carve<unsigned long long>(p, 4);  // err, tmin, tmax, longest duration
+        // err, tmin, tmax, longest duration, midpoint box (min x y z, max x y z)
+        unsigned long long *small = carve<unsigned long long>(p, 10);
 
-        unsigned long long init[4] = {0ULL, ~0ULL, 0ULL, 0ULL};
+        unsigned long long init[10] = {0ULL, ~0ULL, 0ULL, 0ULL, ~0ULL, ~0ULL, ~0ULL, 0ULL, 0ULL, 0ULL};
+        static_assert(sizeof init <= sizeof(DevCounters), "the host mirror stages the reduction words");
         DevCounters *hc = idx->ws.ctr_host;
         memcpy(hc, init, sizeof init);
         if (cudaMemcpyAsync(small, hc, sizeof init, cudaMemcpyHostToDevice, stream) != cudaSuccess) {
@@ -340,13 +371,13 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             break;
         }
         entry_prep<<<grid_for(n), kBlock, 0, stream>>>(in, n, keys, vals, (unsigned int *)&small[0], &small[1],
-                                                        &small[2], &small[3]);
+                                                        &small[2], &small[3], &small[4]);
         if (cudaMemcpyAsync(hc, small, sizeof init, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: entry validation");
             break;
         }
-        unsigned long long back[4];
+        unsigned long long back[10];
         memcpy(back, hc, sizeof back);
         if (back[0] & 1ULL) {
             st = set_error(TDQ_ERR_INVALID,
@@ -362,12 +393,23 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             memcpy(&idx->t_max, &bmax, 8);
             idx->width = (idx->t_max - idx->t_min) / (double)m;
             memcpy(&idx->max_dur, &back[3], 8);
+            double box[6];
+            for (int a = 0; a < 6; a++) {
+                const int64_t b = key_from_bits((int64_t)(back[4 + a] ^ 0x8000000000000000ULL));
+                memcpy(&box[a], &b, 8);
+            }
+            idx->grid = tc_grid_from_box(box[0], box[3], box[1], box[4], box[2], box[5]);
         }
         if (radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, hist, stream) != cudaSuccess) {
             st = cuda_error(cudaGetLastError(), "tdq_build_index: sort");
             break;
         }
-        entry_gather<<<grid_for(n), kBlock, 0, stream>>>(in, n, vals, idx->e);
+        if (cudaMemsetAsync(idx->e.tc_rec + 2 * (n / 8 * 8), 0, 32 * (idx->n_rec - n / 8 * 8), stream) !=
+            cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "tdq_build_index: record padding");
+            break;
+        }
+        entry_gather<<<grid_for(n), kBlock, 0, stream>>>(in, n, vals, idx->e, idx->grid);
         bin_init<<<grid_for(m), kBlock, 0, stream>>>(idx->bin_end_key, m);
         bin_assign<<<grid_for(n), kBlock, 0, stream>>>(idx->e.ts_key, idx->e.te_key, n, idx->t_min, idx->width, m,
                                                        idx->bin_begin, idx->bin_end_key);

@@ -131,9 +131,9 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
                          (unsigned long long)nq, (unsigned long long)kNoAllocMaxQueries);
     if (params && params->flags)
         return set_error(TDQ_ERR_INVALID, "tdq_search_device_noalloc: pair filters (flags) are not supported");
-    if (params && params->mode == TDQ_MODE_FP32_FILTER)
+    if (params && params->mode != TDQ_MODE_FP64)
         return set_error(TDQ_ERR_INVALID,
-                         "tdq_search_device_noalloc: the filter mode needs a survivor list; use TDQ_MODE_FP64");
+                         "tdq_search_device_noalloc: the filter modes need a survivor list; use TDQ_MODE_FP64");
     uint32_t chunk = (params && params->entry_chunk) ? params->entry_chunk : 512u;
     if (chunk % kPairThreads != 0 || chunk > 2048)
         return set_error(TDQ_ERR_INVALID, "tdq_search_device_noalloc: entry_chunk must be a multiple of 256, <= 2048");

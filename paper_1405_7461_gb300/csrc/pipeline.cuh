@@ -50,6 +50,8 @@ struct PrepArgs {
     uint32_t *sort_hist;
     bool ranges;
     bool count_overlaps;
+    uint4 *pre_tc;  // may be null: also the tensor-core pre-test record of every valid query segment
+    TcGrid grid;    // the index's grid (with pre_tc)
 };
 
 // Arguments of query_gather (it reads workspace arrays only).
@@ -64,6 +66,13 @@ struct GatherArgs {
     uint32_t chunk;
     int64_t *tile_lo, *tile_hi;
     unsigned long long *tile_work;  // chunks per tile, then (last block) their exclusive offsets; ntiles + 1
+    // tensor-core pre-test (q_rec may be null): records in sorted order, and
+    // the supertile plan (4 tiles of 32) instead of the tile plan's offsets
+    const uint4 *pre_tc;
+    uint4 *q_rec;
+    int64_t *st_lo, *st_hi;
+    unsigned long long *st_work;    // chunks per supertile, then their exclusive offsets; nsuper + 1
+    uint64_t nsuper;
 };
 
 struct PairArgs {
@@ -95,6 +104,19 @@ struct FilterArgs {
     uint64_t surv_cap;
 };
 
+// The tensor-core pre-test's arguments (tcfilter.cu): the pair arguments
+// (tile ranges, counters, chunk), the entry and query records, the
+// supertile plan and the survivor list.
+struct TcArgs {
+    PairArgs p;
+    const uint4 *e_rec, *q_rec;
+    const int64_t *st_lo, *st_hi;
+    const unsigned long long *st_work;
+    uint64_t nsuper;
+    uint2 *surv;
+    uint64_t surv_cap;
+};
+
 // Kernels launched from more than one file (defined in search.cu).
 __global__ void query_prep(PrepArgs a);
 __global__ void query_gather(GatherArgs a);
@@ -106,6 +128,11 @@ cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, ui
                                cudaStream_t stream, cudaEvent_t mid, unsigned evflags);
 cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream_t stream, cudaEvent_t mid,
                                   unsigned evflags);
+// The FP64 refine kernel of the filter modes alone (filter.cu).
+cudaError_t launch_refine_kernel(const FilterArgs &fa, int sm_count, cudaStream_t stream);
+// The tensor-core pre-test, then the refine kernel (tcfilter.cu).
+cudaError_t launch_tc_filter_kernels(const TcArgs &ta, int sm_count, cudaStream_t stream, cudaEvent_t mid,
+                                     unsigned evflags);
 
 // TDQ_ERR_INVALID unless d is finite and >= 0 and [t0, t1] is a window (search.cu).
 tdq_status check_scalars(double d, double t0, double t1);

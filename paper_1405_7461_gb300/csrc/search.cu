@@ -191,6 +191,16 @@ __global__ void query_prep(PrepArgs a)
                           __double2float_ru(h)), __fmaf_ru(dw, 0x1p-30f, dw));
         }
         a.pre_sph[i] = sp;
+        // tensor-core pre-test record of the clipped segment's sphere: center
+        // and radius in FP64, snapped to the index's grid
+        if (a.pre_tc && valid) {
+            const double h = 0.5 * (key_double(ce) - key_double(cs));
+            const double r = sqrt(fma(vz, vz, fma(vy, vy, vx * vx))) * h;
+            uint4 lo, hi;
+            tc_query_record(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), r, d, a.grid, lo, hi);
+            a.pre_tc[2 * i] = lo;
+            a.pre_tc[2 * i + 1] = hi;
+        }
         // sort key: the temporal bin of the clipped start, in FP32 (it only
         // groups the segments into tiles of 32 that span few bins); invalid
         // segments sort last
@@ -263,12 +273,30 @@ __global__ void query_gather(GatherArgs a)
         rlo = __double_as_longlong(a.pre[kPreLo][i]);
         rhi = __double_as_longlong(a.pre[kPreHi][i]);
     }
+    // tensor-core records in sorted order; zero records fill the last supertile
+    if (a.q_rec && k < a.nsuper * 128) {
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        if (k < a.nq && k < a.ctr->valid_queries) {
+            const uint32_t i = a.order[k];
+            lo = a.pre_tc[2 * i];
+            hi = a.pre_tc[2 * i + 1];
+        }
+        tc_store(a.q_rec, k, lo, hi);
+    }
     // the tile plan: this warp's 32 sorted query segments are tile k / kQT
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         rlo = min(rlo, (int64_t)__shfl_xor_sync(kFull, (long long)rlo, o));
         rhi = max(rhi, (int64_t)__shfl_xor_sync(kFull, (long long)rhi, o));
+    }
+    // supertiles (tensor-core pre-test): the union of 4 consecutive tiles'
+    // ranges, from the block's 8 warps (two supertiles per block)
+    static_assert(kBlock == 8 * 32, "two supertiles of 4 warps per block");
+    __shared__ int64_t w_lo[8], w_hi[8];
+    if (a.q_rec && lane == 0) {
+        w_lo[threadIdx.x >> 5] = rlo;
+        w_hi[threadIdx.x >> 5] = rhi;
     }
     const uint64_t t = k / kQT;
     if (lane == 0 && t < a.ntiles) {
@@ -284,6 +312,31 @@ __global__ void query_gather(GatherArgs a)
         a.tile_work[t] = w;
         if (t == 0) a.tile_work[a.ntiles] = 0;  // the scan turns this slot into the total
     }
+    if (a.q_rec) {
+        __syncthreads();
+        const uint64_t st = k / 128;
+        if ((threadIdx.x & 127) == 0 && st < a.nsuper) {
+            int64_t lo = INT64_MAX, hi = INT64_MIN;
+            const int w0 = threadIdx.x >> 5;
+            for (int w = w0; w < w0 + 4; w++) {
+                if (w_hi[w] > w_lo[w]) {
+                    lo = min(lo, w_lo[w]);
+                    hi = max(hi, w_hi[w]);
+                }
+            }
+            unsigned long long wk = 0;
+            if (hi > lo) {
+                wk = (unsigned long long)((hi - lo + a.chunk - 1) / a.chunk);
+            } else {
+                lo = 0;
+                hi = 0;
+            }
+            a.st_lo[st] = lo;
+            a.st_hi[st] = hi;
+            a.st_work[st] = wk;
+            if (st == 0) a.st_work[a.nsuper] = 0;  // the scan turns this slot into the total
+        }
+    }
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -291,7 +344,10 @@ __global__ void query_gather(GatherArgs a)
     __syncthreads();
     if (last) {
         __threadfence();
-        block_exclusive_scan<unsigned long long, kBlock, 8>(a.tile_work, a.ntiles + 1, &a.ctr->work_items);
+        if (a.q_rec)
+            block_exclusive_scan<unsigned long long, kBlock, 8>(a.st_work, a.nsuper + 1, &a.ctr->work_items);
+        else
+            block_exclusive_scan<unsigned long long, kBlock, 8>(a.tile_work, a.ntiles + 1, &a.ctr->work_items);
     }
 }
 
@@ -513,9 +569,13 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
                      + 2 * carve_bytes(cap, 8) + 2 * carve_bytes(cap, 4) // sort
                      + 11 * carve_bytes(cap, 8)                 // sorted query SoA
                      + 2 * carve_bytes(cap, 16)                 // query spheres (before / after sorting)
+                     + carve_bytes(2 * cap, 16)                 // tensor-core records before sorting
+                     + carve_bytes(2 * ((cap + 127) / 128 * 128), 16)  // ... sorted, whole supertiles
                      + carve_bytes(kPreCols, sizeof(double *)); // pre pointer table
     uint64_t ntiles = (cap + kQT - 1) / kQT;
-    uint64_t tbytes = 2 * carve_bytes(ntiles, 8) + carve_bytes(ntiles + 1, 8);
+    uint64_t nsuper = (cap + 127) / 128;
+    uint64_t tbytes = 2 * carve_bytes(ntiles, 8) + carve_bytes(ntiles + 1, 8) + 2 * carve_bytes(nsuper, 8) +
+                      carve_bytes(nsuper + 1, 8);
     uint64_t hwords = sort_hist_words(cap);
     cudaFree(w.q_block);
     cudaFree(w.t_block);
@@ -552,6 +612,8 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     q.qtraj = carve<int64_t>(p, cap);
     w.pre_sph = carve<float4>(p, cap);
     q.sph = carve<float4>(p, cap);
+    w.pre_tc = carve<uint4>(p, 2 * cap);
+    q.tc_rec = carve<uint4>(p, 2 * ((cap + 127) / 128 * 128));
     w.pre_dev = carve<double *>(p, kPreCols);
     if (cudaMemcpy(w.pre_dev, w.pre, kPreCols * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess)
         return cuda_error(cudaGetLastError(), "search workspace: pointer table");
@@ -559,6 +621,9 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     w.tile_lo = carve<int64_t>(tp, ntiles);
     w.tile_hi = carve<int64_t>(tp, ntiles);
     w.tile_work = carve<unsigned long long>(tp, ntiles + 1);
+    w.st_lo = carve<int64_t>(tp, nsuper);
+    w.st_hi = carve<int64_t>(tp, nsuper);
+    w.st_work = carve<unsigned long long>(tp, nsuper + 1);
     w.q_cap = cap;
     w.t_cap = ntiles;
     w.s_cap = hwords;
@@ -583,9 +648,11 @@ tdq_status ensure_survivors(Workspace &w, uint64_t cap)
 
 tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
 {
-    if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER)
+    if (params && params->mode != TDQ_MODE_FP64 && params->mode != TDQ_MODE_FP32_FILTER &&
+        params->mode != TDQ_MODE_TC_FILTER)
         return set_error(TDQ_ERR_INVALID, "tdq_search: unknown mode %d", params->mode);
-    cfg->filter = params && params->mode == TDQ_MODE_FP32_FILTER;
+    cfg->filter = params && (params->mode == TDQ_MODE_FP32_FILTER || params->mode == TDQ_MODE_TC_FILTER);
+    cfg->tc = params && params->mode == TDQ_MODE_TC_FILTER;
     cfg->flags = params ? params->flags : 0u;
     if (cfg->flags & ~(TDQ_FLAG_OTHER_TRAJECTORIES | TDQ_FLAG_UNORDERED_ONCE))
         return set_error(TDQ_ERR_INVALID, "tdq_search: unknown flags 0x%x", cfg->flags);
@@ -624,24 +691,31 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, evflags)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
     const BinView bins = bin_view(idx);
+    const bool tc = cfg.tc && idx->n > 0;
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
         PrepArgs{in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr, fuse ? w.sort_fused_hist : nullptr,
-                 idx->n > 0, cfg.filter});
+                 idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
+    const uint64_t nsuper = (nq + 127) / 128;
     if (idx->n > 0) {
         if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
                                   bin_key_bits(idx->m), &w.ctr->sort_n, fuse ? w.sort_fused_hist : nullptr)) !=
             cudaSuccess)
             return e;
         const GatherArgs ga{pre, w.pre_sph, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk, w.tile_lo, w.tile_hi,
-                            w.tile_work};
-        query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
+                            w.tile_work, w.pre_tc, tc ? w.q.tc_rec : nullptr, w.st_lo, w.st_hi, w.st_work, nsuper};
+        query_gather<<<grid_for(tc ? nsuper * 128 : nq), kBlock, 0, stream>>>(ga);
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags,
                     w.ctr_host_dev};
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
-        if ((e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
-                                    events ? w.ev[2] : nullptr, evflags)) != cudaSuccess)
-            return e;
+        if (tc)
+            e = launch_tc_filter_kernels(TcArgs{pa, idx->e.tc_rec, w.q.tc_rec, w.st_lo, w.st_hi, w.st_work, nsuper,
+                                                w.surv, w.s_cap_pairs},
+                                         idx->sm_count, stream, events ? w.ev[2] : nullptr, evflags);
+        else
+            e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
+                                   events ? w.ev[2] : nullptr, evflags);
+        if (e != cudaSuccess) return e;
         if (events && (e = cudaEventRecordWithFlags(cfg.filter ? w.ev[4] : w.ev[2], stream, evflags)) != cudaSuccess)
             return e;
     } else {
@@ -663,6 +737,10 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
                          "NaN window or t0 > t1)");
+    if (h.error & 2u)
+        return set_error(TDQ_ERR_TIMEOUT,
+                         "tdq_search: a wait of the tensor-core pre-test pipeline ran out of time (the search "
+                         "was abandoned; its results are incomplete)");
     if (cfg.filter && idx->n > 0 && h.survivors > w.s_cap_pairs) {
         *surv_overflow = true;
         return TDQ_OK;
@@ -711,7 +789,8 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
                         const QueryInput &in, uint64_t nq, const LaunchCfg &cfg)
 {
     PrepArgs a0{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, w.vals, w.ctr,
-                idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter};
+                idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter,
+                cfg.tc && idx->n > 0 ? w.pre_tc : nullptr, idx->grid};
     void *args[] = {&a0};
     cudaKernelNodeParams kp{};
     kp.func = (void *)query_prep;

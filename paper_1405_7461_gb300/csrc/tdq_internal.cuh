@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tcgrid.cuh"
 #include "tdq.h"
 
 namespace tdq {
@@ -168,6 +169,8 @@ struct EntrySoA {
     float *sph_e;          // E = |center|^2 (1 - 2^-20), rounded down; -inf for huge magnitudes (the
                            // pair is then never rejected)
     int64_t *te_sorted;    // t_end keys in ascending order (for exact overlap counts)
+    uint4 *tc_rec;         // tensor-core pre-test records (tcgrid.cuh), groups of 8, padded with zero
+                           // records to n_rec
 };
 
 // Sorted, clipped query segments in device memory.
@@ -179,6 +182,8 @@ struct QuerySoA {
     int64_t *qid;          // caller's segment id
     int64_t *qtraj;        // caller's trajectory id (0 when not given)
     float4 *sph;           // FP32 bounding sphere of the clipped segment; w = radius + d, rounded up
+    uint4 *tc_rec;         // tensor-core pre-test records in sorted order, groups of 8, zero records up
+                           // to a whole supertile of 128
 };
 
 constexpr int kSearchEvents = 5;
@@ -212,6 +217,7 @@ struct Workspace {
     double *pre[kPreCols] = {nullptr};  // see kPreCols
     double **pre_dev = nullptr;         // device copy of pre[]
     float4 *pre_sph = nullptr;   // per-query sphere before sorting
+    uint4 *pre_tc = nullptr;     // per-query tensor-core record before sorting (2 x uint4 each)
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;
     QuerySoA q{};
@@ -220,6 +226,10 @@ struct Workspace {
     void *t_block = nullptr;
     int64_t *tile_lo = nullptr, *tile_hi = nullptr;
     unsigned long long *tile_work = nullptr;  // chunks per tile, then exclusive offsets (t_cap+1)
+    // supertiles of 4 tiles (tensor-core pre-test): union range, chunks then
+    // exclusive offsets (ceil(t_cap / 4) + 1)
+    int64_t *st_lo = nullptr, *st_hi = nullptr;
+    unsigned long long *st_work = nullptr;
     // sort scratch
     uint64_t s_cap = 0;
     uint32_t *sort_hist = nullptr;
@@ -259,6 +269,8 @@ struct tdq_index {
     int64_t *bin_end_key = nullptr; // m, largest t_end key (INT64_MIN when empty)
     int64_t *bin_pmax_key = nullptr;// m, prefix max of bin_end_key
     int64_t *te_bin_begin = nullptr;// m + 1: first position in e.te_sorted whose t_end lies in bin >= b
+    tdq::TcGrid grid{};             // integer grid of the tensor-core pre-test (over the entries' centers)
+    uint64_t n_rec = 0;             // tensor-core records held (n rounded up to 8, plus one pass of 128)
     tdq::Workspace ws;
     tdq_stats last{};
 };
@@ -280,8 +292,9 @@ struct QueryInput {
 
 struct LaunchCfg {
     uint32_t chunk;
-    bool filter;
+    bool filter;     // a pre-test, then the FP64 refine of its survivors
     uint32_t flags;  // TDQ_FLAG_*
+    bool tc;         // the pre-test runs on the tensor cores (TDQ_MODE_TC_FILTER)
 };
 
 // search.cu: workspace sizing, parameters, and one search split into a part
@@ -314,11 +327,13 @@ cudaError_t load_search_module();   // search.cu
 cudaError_t load_filter_module();   // filter.cu
 cudaError_t load_noalloc_module();  // noalloc.cu
 cudaError_t load_sort_module();     // sort.cu
+cudaError_t load_tc_module();       // tcfilter.cu
 inline cudaError_t load_device_code()
 {
     cudaError_t e;
     if ((e = load_search_module()) != cudaSuccess) return e;
     if ((e = load_filter_module()) != cudaSuccess) return e;
+    if ((e = load_tc_module()) != cudaSuccess) return e;
     if ((e = load_sort_module()) != cudaSuccess) return e;
     return load_noalloc_module();
 }

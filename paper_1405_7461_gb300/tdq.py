@@ -32,6 +32,7 @@ STATUS_NAMES = {0: "TDQ_OK", 1: "TDQ_ERR_INVALID", 2: "TDQ_ERR_NOMEM", 3: "TDQ_E
                 4: "TDQ_ERR_TIMEOUT", 5: "TDQ_ERR_OVERFLOW"}
 MODE_FP64 = 0
 MODE_FP32_FILTER = 1
+MODE_TC_FILTER = 2
 FLAG_OTHER_TRAJECTORIES = 1  # TDQ_FLAG_OTHER_TRAJECTORIES
 FLAG_UNORDERED_ONCE = 2  # TDQ_FLAG_UNORDERED_ONCE
 

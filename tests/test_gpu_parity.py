@@ -351,10 +351,17 @@ def _sorted_arrays(r):
     return r.query_seg_id[o], r.entry_seg_id[o], r.t_enter[o], r.t_exit[o]
 
 
-def _filter_vs_fp64(tdq, idx, queries, d, window):
+FILTER_MODES = ["fp32filter", "tcfilter"]
+
+
+def _mode(tdq, name):
+    return {"fp64": tdq.MODE_FP64, "fp32filter": tdq.MODE_FP32_FILTER, "tcfilter": tdq.MODE_TC_FILTER}[name]
+
+
+def _filter_vs_fp64(tdq, idx, queries, d, window, mode="fp32filter"):
     r64 = tdq.search(idx, queries, d, *window, mode=tdq.MODE_FP64)
     s64 = tdq.get_stats(idx)
-    r32 = tdq.search(idx, queries, d, *window, mode=tdq.MODE_FP32_FILTER)
+    r32 = tdq.search(idx, queries, d, *window, mode=_mode(tdq, mode))
     s32 = tdq.get_stats(idx)
     # the filter drops only pairs the FP64 test rejects, and survivors run the
     # same FP64 code: the results are bitwise identical
@@ -365,8 +372,9 @@ def _filter_vs_fp64(tdq, idx, queries, d, window):
     return s64, s32
 
 
+@pytest.mark.parametrize("mode", FILTER_MODES)
 @pytest.mark.parametrize("name", ["tiny", "scale", "galaxy", "batching"])
-def test_filter_mode_equals_plain_fp64(tdq, name):
+def test_filter_mode_equals_plain_fp64(tdq, name, mode):
     if name == "tiny":
         w = workloads.tiny_random_walk()
     elif name == "scale":
@@ -378,21 +386,24 @@ def test_filter_mode_equals_plain_fp64(tdq, name):
         w.d_values = (0.5, 4.0, 10.0)
     with tdq.build_index(w.entries) as idx:
         for d in w.d_values:
-            s64, s32 = _filter_vs_fp64(tdq, idx, w.queries, d, w.window)
+            s64, s32 = _filter_vs_fp64(tdq, idx, w.queries, d, w.window, mode)
         # and against the oracle, through the filter path
-        check(tdq, w.entries, w.queries, w.d_values[-1], *w.window, idx=idx, mode=tdq.MODE_FP32_FILTER)
+        check(tdq, w.entries, w.queries, w.d_values[-1], *w.window, idx=idx, mode=_mode(tdq, mode),
+              max_ill=GALAXY_ILL_CONDITIONED_MAX if name == "galaxy" else 0)
 
 
-def test_filter_mode_full_size_scale_walk(tdq):
+@pytest.mark.parametrize("mode", FILTER_MODES)
+def test_filter_mode_full_size_scale_walk(tdq, mode):
     w = workloads.scale_random_walk()
     with tdq.build_index(w.entries) as idx:
         for d in w.d_values:
-            s64, s32 = _filter_vs_fp64(tdq, idx, w.queries, d, w.window)
+            s64, s32 = _filter_vs_fp64(tdq, idx, w.queries, d, w.window, mode)
             assert s32["fp64_pairs"] < 0.01 * s32["overlap_pairs"]
 
 
+@pytest.mark.parametrize("mode", FILTER_MODES)
 @pytest.mark.parametrize("offset", [0.0, 1e3, 1e5, 3e6])
-def test_filter_is_conservative_at_the_threshold(tdq, offset):
+def test_filter_is_conservative_at_the_threshold(tdq, offset, mode):
     """Pairs whose closest distance is d(1 - 1e-7) .. d(1 + 1e-7), far from
     the origin where FP32 rounding is coarse: the filter must keep every
     pair the FP64 test accepts (the two modes agree pair for pair)."""
@@ -414,11 +425,40 @@ def test_filter_is_conservative_at_the_threshold(tdq, offset):
     ent = workloads.Segments.from_columns([x, y, z, t0, x, y, z, t1])
     qry = workloads.Segments.from_columns([q[:, k] for k in range(8)], seg_id=[10 ** 9])
     with tdq.build_index(ent) as idx:
-        s64, s32 = _filter_vs_fp64(tdq, idx, qry, d, (-np.inf, np.inf))
+        s64, s32 = _filter_vs_fp64(tdq, idx, qry, d, (-np.inf, np.inf), mode)
     assert s64["results"] > 0.3 * n
 
 
-def test_filter_survivor_list_overflow_is_regrown(tdq):
+@pytest.mark.parametrize("mode", FILTER_MODES)
+@pytest.mark.parametrize("offset", [0.0, 1e3, 1e5, 3e6])
+def test_filter_keeps_touching_stationary_spheres(tdq, offset, mode):
+    """Stationary query and entry points (zero-radius spheres) at distance
+    d (1 + rel), rel in [-1e-7, 1e-7]: the sphere test is then as tight as the
+    FP64 decision itself, so the pre-test's margin alone keeps the pairs the
+    FP64 test accepts (the two modes agree pair for pair)."""
+    rng = np.random.default_rng(int(offset) + 29)
+    n = 3000
+    d = 0.625
+    rel = rng.uniform(-1e-7, 1e-7, n)
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    c = offset + 7.0 + u * (d * (1 + rel))[:, None]
+    # a spread of other stationary entries, so that the grid is not centred
+    # on the query
+    far = offset + rng.uniform(-40.0, 60.0, (n, 3))
+    p = np.concatenate([c, far])
+    t0 = np.zeros(2 * n)
+    t1 = np.full(2 * n, 4.0)
+    ent = workloads.Segments.from_columns([p[:, 0], p[:, 1], p[:, 2], t0, p[:, 0], p[:, 1], p[:, 2], t1])
+    q = np.array([offset + 7.0, offset + 7.0, offset + 7.0, 1.0, offset + 7.0, offset + 7.0, offset + 7.0, 3.0])
+    qry = workloads.Segments.from_columns([q[[k]] for k in range(8)], seg_id=[10 ** 9])
+    with tdq.build_index(ent) as idx:
+        s64, s32 = _filter_vs_fp64(tdq, idx, qry, d, (-np.inf, np.inf), mode)
+    assert 0.3 * n < s64["results"] < 0.7 * n
+
+
+@pytest.mark.parametrize("mode", FILTER_MODES)
+def test_filter_survivor_list_overflow_is_regrown(tdq, mode):
     """A cluster where every pair survives the pre-test: 1.3 M survivors
     overflow the initial survivor list (2^20 pairs), which is grown and the
     search re-run; the results equal the plain FP64 mode's."""
@@ -427,7 +467,7 @@ def test_filter_survivor_list_overflow_is_regrown(tdq):
     qry = workloads.random_segments(rng, 64, box=0.2, t_span=0.5, max_dur=20.0, max_speed=0.01)
     qry.seg_id += 10 ** 7
     with tdq.build_index(ent) as idx:
-        s64, s32 = _filter_vs_fp64(tdq, idx, qry, 3.0, (-np.inf, np.inf))
+        s64, s32 = _filter_vs_fp64(tdq, idx, qry, 3.0, (-np.inf, np.inf), mode)
     assert s32["results"] == 20_000 * 64
 
 
@@ -446,23 +486,24 @@ def test_filter_overlap_count_across_bins_and_windows(tdq, bin_count):
                (lo - 20.0, lo - 10.0), (hi + 1.0, hi + 2.0)]
     with tdq.build_index(w.entries, bin_count=bin_count) as idx:
         for t0, t1 in windows:
-            r32 = tdq.search(idx, w.queries, 5.0, t0, t1, mode=tdq.MODE_FP32_FILTER)
-            s32 = tdq.get_stats(idx)
             r64 = tdq.search(idx, w.queries, 5.0, t0, t1, mode=tdq.MODE_FP64)
             s64 = tdq.get_stats(idx)
             ref = oracle.search_sweep(w.entries, w.queries, 5.0, t0, t1)
-            assert s32["overlap_pairs"] == s64["overlap_pairs"] == ref.overlap_pairs
-            for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
-                assert np.array_equal(a, b)
-            assert len(r32) == len(ref.query_index)
+            for mode in (tdq.MODE_FP32_FILTER, tdq.MODE_TC_FILTER):
+                r32 = tdq.search(idx, w.queries, 5.0, t0, t1, mode=mode)
+                s32 = tdq.get_stats(idx)
+                assert s32["overlap_pairs"] == s64["overlap_pairs"] == ref.overlap_pairs
+                for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
+                    assert np.array_equal(a, b)
+                assert len(r32) == len(ref.query_index)
 
 
 # --------------------------------------------------------------------------
 # Self-join: query (ii) of Sec. 2.1 with the database as the query set
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,mode", [("tiny", "fp64"), ("tiny", "fp32filter"), ("galaxy", "fp32filter"),
-                                       ("galaxy", "fp64")])
+@pytest.mark.parametrize("name,mode", [("tiny", "fp64"), ("tiny", "fp32filter"), ("tiny", "tcfilter"),
+                                       ("galaxy", "fp32filter"), ("galaxy", "tcfilter"), ("galaxy", "fp64")])
 def test_self_join_matches_oracle(tdq, name, mode):
     if name == "tiny":
         w = workloads.tiny_random_walk(n_traj=120, n_points=60)
@@ -474,7 +515,7 @@ def test_self_join_matches_oracle(tdq, name, mode):
     # ids unrelated to positions, so that "each unordered pair once" is not
     # an artefact of the sort order
     ent.seg_id = ent.seg_id[np.random.default_rng(5).permutation(len(ent))]
-    m = tdq.MODE_FP64 if mode == "fp64" else tdq.MODE_FP32_FILTER
+    m = _mode(tdq, mode)
     with tdq.build_index(ent) as idx:
         res = tdq.self_join(idx, ent, d, *window, mode=m)
         stats = tdq.get_stats(idx)
@@ -552,9 +593,10 @@ def test_filter_with_magnitudes_beyond_two_to_the_sixty(tdq):
     with tdq.build_index(ent) as idx:
         for d in (50.0, 3e4):
             r64 = tdq.search(idx, q, d, mode=tdq.MODE_FP64)
-            r32 = tdq.search(idx, q, d, mode=tdq.MODE_FP32_FILTER)
-            s32 = tdq.get_stats(idx)
-            for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
-                assert np.array_equal(a, b)
-            assert len(r32) >= len(q)  # every query segment meets itself
-            assert s32["fp64_pairs"] > 0
+            for mode in (tdq.MODE_FP32_FILTER, tdq.MODE_TC_FILTER):
+                r32 = tdq.search(idx, q, d, mode=mode)
+                s32 = tdq.get_stats(idx)
+                for a, b in zip(_sorted_arrays(r64), _sorted_arrays(r32)):
+                    assert np.array_equal(a, b)
+                assert len(r32) >= len(q)  # every query segment meets itself
+                assert s32["fp64_pairs"] > 0

@@ -52,9 +52,9 @@ def _oracle_per_trajectory(w, q, qd, q0, q1):
     return {k: np.concatenate(v) for k, v in parts.items()}
 
 
-@pytest.mark.parametrize("mode_name", ["fp64", "filter"])
+@pytest.mark.parametrize("mode_name", ["fp64", "filter", "tcfilter"])
 def test_plan_batches_match_oracle_and_unbatched_search(tdq, mode_name):
-    mode = tdq.MODE_FP64 if mode_name == "fp64" else tdq.MODE_FP32_FILTER
+    mode = {"fp64": tdq.MODE_FP64, "filter": tdq.MODE_FP32_FILTER, "tcfilter": tdq.MODE_TC_FILTER}[mode_name]
     w = workloads.batching_walks(n_traj=500, n_queries=80, box=50.0)
     q = w.queries
     n = len(q)

@@ -46,9 +46,9 @@ def _same(a, b):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("mode_name", ["filter", "fp64"])
+@pytest.mark.parametrize("mode_name", ["filter", "tcfilter", "fp64"])
 def test_results_same_alone_and_in_the_mix(tdq, db, requests, mode_name):
-    mode = tdq.MODE_FP32_FILTER if mode_name == "filter" else tdq.MODE_FP64
+    mode = {"fp64": tdq.MODE_FP64, "filter": tdq.MODE_FP32_FILTER, "tcfilter": tdq.MODE_TC_FILTER}[mode_name]
     with tdq.build_index(db) as idx:
         with tdq.Server(idx, max_batch_query_segments=2048, lanes=3, mode=mode) as srv:
             alone = []
