@@ -63,6 +63,14 @@ FP32_PEAK_GFLOPS = 2 * 128 * 152 * 2.070
 # a tile's range once per tile, i.e. 2 B per candidate pair of a full tile.
 FILTER_BYTES_PER_ENTRY = 20
 PLAIN_BYTES_PER_CANDIDATE = 2
+# Tensor-core pre-test: the algorithmic work per pair is the rank-8 integer
+# form of the sphere test (8 products accumulated, FMA = 2 flops); each MMA
+# issues 128 entries x 128 query slots x 16 record elements; each entry's
+# 32 B record is read from DRAM once per launch (re-reads by other
+# supertiles hit L2).
+FLOPS_PER_PAIR_TC = 16
+TC_MMA_FLOPS = 2 * 128 * 128 * 16
+TC_BYTES_PER_ENTRY = 32
 
 
 def hbm_peak_gbs():
@@ -70,6 +78,17 @@ def hbm_peak_gbs():
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except (OSError, ValueError, KeyError):
         return 6800.0  # fallback figure of an earlier GB300 measurement
+
+
+def tensor_peak_tflops():
+    """Dense FP16 tensor peak for a kernel timed alone: the measured bf16
+    burst figure (FP16 and BF16 run at the same dense rate), else the
+    fallback of an earlier GB300 measurement.  Returns (value, source)."""
+    try:
+        return (float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]),
+                "MEASURED_PEAKS.json bf16_tflops, burst (of measured; FP16 dense rate = BF16)")
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 burst of an earlier GB300 measurement (of fallback)"
 CPU_SAMPLE_QUERIES = 20
 # The benchmark's metric (both arms report it; the value is the segment-pair
 # test rate, queries/s and latencies are reported beside it).
@@ -108,6 +127,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n-traj", type=int, default=10_000)
     ap.add_argument("--n-queries", type=int, default=100)
+    ap.add_argument("--min-warmup-s", type=float, default=WARMUP_MIN_S,
+                    help="least wall time of each timed path's warm-up (0 for profiling runs)")
     return ap.parse_args(argv)
 
 
@@ -310,6 +331,26 @@ def roofline(mode, tot, n_launch, n_entries):
     kernel's algorithmic DRAM bytes per second against the measured HBM
     copy bandwidth."""
     kern_ms = tot["kernel_ms"] / n_launch
+    if kern_ms <= 0:
+        return None
+    if mode == "tcfilter":
+        peak, src = tensor_peak_tflops()
+        sec = kern_ms / 1e3
+        achieved = FLOPS_PER_PAIR_TC * tot["pairs"] / n_launch / sec / 1e12
+        issued = TC_MMA_FLOPS * tot.get("mma", 0) / n_launch / sec / 1e12
+        hbm_bytes = TC_BYTES_PER_ENTRY * n_entries
+        gbs = hbm_bytes / sec / 1e9
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_record(mode), "kernel": "traj_dist_tc_filter_kernel", "kernel_ms_avg": kern_ms,
+                "work_unit": f"{FLOPS_PER_PAIR_TC} flops per temporal-overlap pair (rank-8 integer sphere test)",
+                "peak_source": src,
+                "achieved_mma_issued": issued, "frac_mma_issued": issued / peak,
+                "work_unit_mma_issued": "128 x 128 x 16 MACs per MMA issued (all candidates of a supertile's "
+                                        "range, padded record elements included)",
+                "refine_kernel_ms_avg": tot["refine_ms"] / n_launch,
+                "hbm": {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": gbs, "peak_gbs": hbm_peak_gbs(),
+                        "frac": gbs / hbm_peak_gbs(),
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
     if mode == "fp64":
         work = FLOPS_PER_PAIR_FP64 * tot["fp64_pairs"] / n_launch
         peak, kernel = FP64_PEAK_GFLOPS, "traj_dist_search_kernel"
@@ -322,8 +363,6 @@ def roofline(mode, tot, n_launch, n_entries):
         peak, kernel = FP32_PEAK_GFLOPS, "traj_dist_filter_kernel"
         src = "derived: 128 FFMA/clk/SM x 2 flops x 152 SMs x 2070 MHz"
         per = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per temporal-overlap pair (sphere pre-test)"
-    if kern_ms <= 0:
-        return None
     achieved = work / (kern_ms / 1e3) / 1e9
     r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
          "traffic": traffic_record(mode), "kernel": kernel, "kernel_ms_avg": kern_ms, "work_unit": per,
@@ -348,13 +387,14 @@ def roofline(mode, tot, n_launch, n_entries):
 HEADLINE_RESULT_CAPACITY = 1 << 22
 
 
-def headline_plan(tdq, idx, n_query_segments, host_results=False):
+def headline_plan(tdq, idx, n_query_segments, host_results=False, mode=None):
     """The plan the headline (device inputs, device results) and the
     end-to-end leg (pinned host inputs read in place, results written into a
-    page-locked host buffer: host_results) time: filter mode, one batch of
-    all thresholds' query segments, default bin count and chunk."""
-    return tdq.Plan(idx, n_query_segments, mode=tdq.MODE_FP32_FILTER, result_capacity=HEADLINE_RESULT_CAPACITY,
-                    host_results=host_results)
+    page-locked host buffer: host_results) time: the FP32 pre-test mode (or
+    `mode`), one batch of all thresholds' query segments, default bin count
+    and chunk."""
+    return tdq.Plan(idx, n_query_segments, mode=tdq.MODE_FP32_FILTER if mode is None else mode,
+                    result_capacity=HEADLINE_RESULT_CAPACITY, host_results=host_results)
 
 
 def pinned_copy(torch, a):
@@ -469,7 +509,8 @@ def self_join_section(args, tdq, torch):
     dev = tdq.DeviceSegments(ent)
     out = {"workload": "galaxy_disk self-join: %d stars x 200 points (%d segments), d = %.2f kpc, full extent"
                        % (args.self_join_stars, len(ent), d)}
-    for name, mode, reps in (("fp32filter", tdq.MODE_FP32_FILTER, 3), ("fp64", tdq.MODE_FP64, 1)):
+    for name, mode, reps in (("tcfilter", tdq.MODE_TC_FILTER, 3), ("fp32filter", tdq.MODE_FP32_FILTER, 3),
+                             ("fp64", tdq.MODE_FP64, 1)):
         tdq.self_join(idx, dev, d, mode=mode)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -635,7 +676,8 @@ def tiny_section(args, tdq, torch, stream, with_oracle):
     d = w.d_values[0]
     out = {"workload": "tiny_random_walk: 200 walks x 100 points (%d entries), 20 query trajectories (%d segments), "
                        "d = 5, window [0, 99]" % (len(w.entries), len(w.queries))}
-    for name, mode in (("fp32filter", tdq.MODE_FP32_FILTER), ("fp64", tdq.MODE_FP64)):
+    for name, mode in (("tcfilter", tdq.MODE_TC_FILTER), ("fp32filter", tdq.MODE_FP32_FILTER),
+                       ("fp64", tdq.MODE_FP64)):
         ms, n = _event_time(torch, stream, lambda: tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream,
                                                                      mode=mode), 50)
         st = tdq.get_stats(idx)
@@ -671,15 +713,17 @@ def precision_section(args, tdq, torch, stream, with_oracle):
         row = {"d": d}
         small = tdq.DeviceResultBuffer(1)
         n_res = tdq.search_device(idx, qdev, d, *w.window, small, stream=stream, allow_overflow=True,
-                                  mode=tdq.MODE_FP32_FILTER)
+                                  mode=tdq.MODE_TC_FILTER)
         buf = tdq.DeviceResultBuffer(max(1, n_res))
-        for name, mode in (("fp32filter", tdq.MODE_FP32_FILTER), ("fp64", tdq.MODE_FP64)):
+        for name, mode in (("tcfilter", tdq.MODE_TC_FILTER), ("fp32filter", tdq.MODE_FP32_FILTER),
+                           ("fp64", tdq.MODE_FP64)):
             tot = {"kernel_ms": 0.0, "refine_ms": 0.0, "interactions": 0, "pairs": 0, "fp64_pairs": 0,
-                   "survivors": 0}
+                   "survivors": 0, "mma": 0}
 
             def one():
                 n = tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=mode)
                 st = tdq.get_stats(idx)
+                tot["mma"] += st["mma_issued"]
                 tot["kernel_ms"] += st["pair_kernel_ms"]
                 tot["refine_ms"] += st["refine_ms"]
                 tot["interactions"] += st["interactions"]
@@ -695,7 +739,7 @@ def precision_section(args, tdq, torch, stream, with_oracle):
                          "queries_per_s": w.n_query_traj / (ms / 1e3), "results": n, "overlap_pairs": pairs,
                          "candidates": tot["interactions"] / reps, "fp64_pairs": tot["fp64_pairs"] / reps,
                          "roofline": roofline(name, tot, reps, len(w.entries))}
-            if name == "fp32filter":
+            if name != "fp64":
                 row[name]["survivors"] = tot["survivors"] / reps
                 row[name]["survivors_per_overlap_pair"] = tot["survivors"] / max(1.0, tot["pairs"])
                 row[name]["fp64_pairs_per_overlap_pair"] = tot["fp64_pairs"] / max(1.0, tot["pairs"])
@@ -769,13 +813,16 @@ def main():
     q3dev = tdq.DeviceSegments(q3)
     d3dev, t03dev, t13dev = (torch.from_numpy(a).cuda() for a in (d3, t03, t13))
     plan = headline_plan(tdq, idx, len(q3))
+    plantc = headline_plan(tdq, idx, len(q3), mode=tdq.MODE_TC_FILTER)
+    modes["tcfilter"] = tdq.MODE_TC_FILTER
 
     def step(mode):
         t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0,
-             "survivors": 0, "refine_ms": 0.0}
-        if mode == "batched":
-            cnt = plan.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
-            stats = [plan.stats()]
+             "survivors": 0, "refine_ms": 0.0, "mma": 0}
+        if mode in ("batched", "batched_tc"):
+            p = plan if mode == "batched" else plantc
+            cnt = p.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
+            stats = [p.stats()]
             t["results"] = cnt
         else:
             stats = []
@@ -790,6 +837,7 @@ def main():
             t["launches"] += s["kernel_launches"]
             t["kernel_ms"] += s["pair_kernel_ms"]
             t["refine_ms"] += s["refine_ms"]
+            t["mma"] += s["mma_issued"]
         return t
 
     def timed(mode):
@@ -798,7 +846,7 @@ def main():
         t_w = time.perf_counter()
         for _ in range(args.warmup):
             step(mode)
-        while time.perf_counter() - t_w < WARMUP_MIN_S:
+        while time.perf_counter() - t_w < args.min_warmup_s:
             step(mode)
         torch.cuda.synchronize()
         barrier()
@@ -816,19 +864,23 @@ def main():
         torch.cuda.synchronize()
         barrier()
         total_ms, pairs = reduce_over_ranks(sum(ms), float(tot["pairs"]), device="cuda")
-        n_launch = args.steps * (1 if mode == "batched" else len(w.d_values))
+        batched = mode in ("batched", "batched_tc")
+        n_launch = args.steps * (1 if batched else len(w.d_values))
+        kmode = {"batched": "fp32filter", "batched_tc": "tcfilter"}.get(mode, mode)
         return {"value": pairs / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                 "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / (total_ms / 1e3),
                 "interactions_per_s": world * tot["interactions"] / (total_ms / 1e3),
                 "fp64_pairs_per_step": tot["fp64_pairs"] / args.steps,
                 "filter_survivors_per_step": tot["survivors"] / args.steps,
                 "results_per_step": tot["results"] / args.steps, "gpu_launches": int(tot["launches"]),
-                "roofline": roofline("fp64" if mode == "fp64" else "fp32filter", tot, n_launch, len(w.entries))}
+                "roofline": roofline(kmode, tot, n_launch, len(w.entries))}
 
     clocks = ClockSampler(dev)
     clocks.start()
     time.sleep(0.3)
     head = timed("batched")
+    headtc = timed("batched_tc")
+    unb_tc = timed("tcfilter")
     unb = timed("fp32filter")
     plain = timed("fp64")
     clk = clocks.stop()
@@ -845,7 +897,7 @@ def main():
         for _ in range(max(args.warmup, 1)):
             eplan.search(q3h, d3h, t03h, t13h, stream=stream)
             eplan.results(view=True)
-        while time.perf_counter() - t_w < WARMUP_MIN_S:
+        while time.perf_counter() - t_w < args.min_warmup_s:
             eplan.search(q3h, d3h, t03h, t13h, stream=stream)
             eplan.results(view=True)
         barrier()
@@ -908,6 +960,10 @@ def main():
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": head["gpu_launches"],
+            "batched_tcfilter": {k: headtc[k] for k in ("value", "ms_per_step", "queries_per_s", "roofline",
+                                                        "gpu_launches", "filter_survivors_per_step")},
+            "unbatched_tcfilter": {k: unb_tc[k] for k in ("value", "ms_per_step", "queries_per_s", "roofline",
+                                                          "gpu_launches")},
             "unbatched_fp32filter": {k: unb[k] for k in ("value", "ms_per_step", "queries_per_s", "roofline",
                                                          "gpu_launches")},
             "plain_fp64": {k: plain[k] for k in ("value", "ms_per_step", "queries_per_s", "roofline",
@@ -922,6 +978,7 @@ def main():
         }
         print(json.dumps(line), flush=True)
     plan.free()
+    plantc.free()
     idx.free()
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -142,6 +142,8 @@ typedef struct {
     uint64_t filter_survivors;  /* filter modes: pairs that passed the pre-test (0 in FP64 mode) */
     double refine_ms;           /* filter modes: device time of the FP64 refine kernel (pair_kernel_ms then
                                    covers the pre-test kernel alone) */
+    uint64_t mma_issued;        /* TDQ_MODE_TC_FILTER: tensor-core MMAs issued (each 128 entries x 128 query
+                                   slots x 16 record elements) */
 } tdq_stats;
 
 /*

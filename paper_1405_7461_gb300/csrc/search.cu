@@ -753,6 +753,7 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
     s->results = h.results;
     s->work_items = h.work_items;
     s->filter_survivors = cfg.filter ? h.survivors : 0;
+    s->mma_issued = h.mma_issued;
     s->kernel_launches = (uint64_t)search_kernel_launches(idx, cfg, nq);
     if (events) {
         float ms = 0.f;

@@ -14,17 +14,20 @@
 //     tcgen05.mma.cta_group::1.kind::f16  M = 128 entries, N = 128 queries, K = 16
 // from shared memory into a 128 x 128 FP32 accumulator in tensor memory.
 //
-// Roles in a CTA of 5 warps (two CTAs per SM):
-//   warp 4, one thread: the producer -- bulk copies (cp.async.bulk, the TMA
-//     engine) of each pass's 4 KB of entry records into an 8-stage ring, of
-//     each run's 4 KB of query records into one of two buffers, and the MMA
-//     of each pass into one of two accumulator stages (256 TMEM columns),
-//     each completion signalled through an mbarrier by tcgen05.commit;
-//   warps 0-3: the epilogue -- warp w reads accumulator lanes 32w..32w+31
-//     (one entry each) with tcgen05.ld, 32 columns (one tile) at a time, ORs
-//     the 32 values' bits and, only where a sign bit is set (v < 0: the
-//     spheres can meet), builds the entry's 32-bit survivor mask, then
-//     appends the survivors (entry, query) through a per-warp buffer.
+// Roles in a CTA of 10 warps (two CTAs per SM):
+//   warp 8, one thread: the loader -- bulk copies (cp.async.bulk, the TMA
+//     engine) of each pass's 4 KB of entry records into an 8-stage ring and
+//     of each run's 4 KB of query records into one of two buffers;
+//   warp 9, one thread: the MMA issuer -- the MMA of each pass into one of
+//     two accumulator stages (256 TMEM columns), its completion signalled
+//     through the stage's mbarrier by tcgen05.commit;
+//   warps 0-7: the epilogue -- warp w reads accumulator lanes
+//     32 (w % 4) .. + 31 (one entry each) and the 32 columns of each of its
+//     tiles 2 (w / 4) and 2 (w / 4) + 1 whose own range meets the pass, with
+//     tcgen05.ld, hands the stage back at once, ORs each tile's 32 values
+//     and, only where a sign bit is set (v < 0: the spheres can meet), builds
+//     the entry's 32-bit survivor mask and appends the survivors (entry,
+//     query) through a per-warp shared-memory buffer.
 // Tiles whose own range misses a pass are skipped.  Every wait is bounded;
 // a wait that runs out sets error bit 2 (reported as TDQ_ERR_TIMEOUT) and the
 // CTA winds down, waiting for its own copies and MMAs in flight before it
@@ -35,13 +38,13 @@
 namespace tdq {
 namespace {
 
-constexpr int kTcEpiWarps = 4;
-constexpr int kTcThreads = 32 * (kTcEpiWarps + 1);
+constexpr int kTcEpiWarps = 8;             // two warpgroups: lanes by warp % 4, tiles 2 (warp / 4) and + 1
+constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);  // + the loader warp and the MMA warp
 constexpr int kTcM = 128;                   // entries per pass (MMA M)
 constexpr int kTcN = 128;                   // query slots per supertile (MMA N)
 constexpr int kTcTiles = kTcN / kQT;        // tiles of 32 per supertile
 constexpr int kTcAStages = 8;               // ring of entry-record stages
-constexpr int kTcAcc = 2;                   // accumulator stages
+constexpr int kTcAcc = 2;                   // accumulator stages (256 TMEM columns; two CTAs fill an SM)
 constexpr uint32_t kTcPassBytes = kTcM * 32;
 constexpr uint32_t kTcBBytes = kTcN * 32;
 constexpr uint32_t kTcCols = kTcAcc * kTcN;  // tensor-memory columns per CTA
@@ -60,8 +63,9 @@ struct TcSmem {
     uint4 a[kTcAStages][kTcPassBytes / 16];
     uint4 b[2][kTcBBytes / 16];
     uint2 surv[kTcEpiWarps][kTcSurvBuf];
-    unsigned long long a_full[kTcAStages], a_empty[kTcAStages];
-    unsigned long long acc_full[kTcAcc], acc_empty[kTcAcc];
+    int nsurv[kTcEpiWarps];  // survivors in each warp's buffer
+    unsigned long long a_full[kTcAStages], mma_done[kTcAStages];
+    unsigned long long acc_empty[kTcAcc];
     unsigned long long b_full[2], b_free[2], drain;
     uint32_t tmem_base;
     int abort;
@@ -69,6 +73,26 @@ struct TcSmem {
 static_assert(sizeof(TcSmem) + 1024 <= kTcSmemRequest, "shared memory layout fits the request");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory word access by 32-bit shared-space address (the shared
+// block is reached through a realigned pointer, which the compiler no longer
+// knows to be shared).
+__device__ __forceinline__ uint32_t atoms_add_u32(uint32_t saddr, uint32_t x)
+{
+    uint32_t old;
+    asm volatile("atom.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(saddr), "r"(x) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr)
+{
+    uint32_t x;
+    asm volatile("ld.volatile.shared::cta.u32 %0, [%1];" : "=r"(x) : "r"(saddr) : "memory");
+    return x;
+}
+__device__ __forceinline__ void sts_u32(uint32_t saddr, uint32_t x)
+{
+    asm volatile("st.volatile.shared::cta.u32 [%0], %1;" ::"r"(saddr), "r"(x) : "memory");
+}
 
 __device__ __forceinline__ void bar_init(unsigned long long *b, uint32_t count)
 {
@@ -82,21 +106,32 @@ __device__ __forceinline__ void bar_expect(unsigned long long *b, uint32_t bytes
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
 }
+// Non-blocking test of the completion of the phase of parity `parity`.
+// (try_wait was measured to suspend the waiting thread for 1000-2000 cycles
+// past the phase's completion, which at one MMA per pass dominated the
+// pipeline; every wait here is a spin on test_wait instead.)
+__device__ __forceinline__ bool bar_test(unsigned long long *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return ok;
+}
 // Wait for the completion of the phase of parity `parity`; false when it did
 // not come within kTcWaitCycles or the CTA is winding down.
-__device__ __noinline__ bool bar_wait(unsigned long long *b, uint32_t parity, volatile int *abort)
+__device__ __noinline__ bool bar_wait_slow(unsigned long long *b, uint32_t parity, volatile int *abort)
 {
     const long long t0 = clock64();
     for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(ok)
-            : "r"(smem_addr(b)), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (bar_test(b, parity)) return true;
         if (*abort || clock64() - t0 > kTcWaitCycles) return false;
     }
+}
+__device__ __forceinline__ bool bar_wait(unsigned long long *b, uint32_t parity, volatile int *abort)
+{
+    return bar_test(b, parity) || bar_wait_slow(b, parity, abort);
 }
 
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *b)
@@ -133,20 +168,47 @@ __device__ __forceinline__ void tc_commit(unsigned long long *b)
                  : "memory");
 }
 
-// 32 consecutive accumulator columns of this warp's 32 lanes (one value per
-// column into v[0..31]) and the wait for them.
-__device__ __forceinline__ void tc_load32(uint32_t taddr, uint32_t (&v)[32])
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this warp's 32 lanes into v[0..31],
+// and the wait for them.
+__device__ __forceinline__ void tc_load32(uint32_t taddr, uint32_t *v)
 {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr)
+                 : "memory");
+    tc_wait_ld();
+}
+
+// Sign bits of 32 words as a mask (bit j = sign of v[j]): four independent
+// chains of funnel shifts, joined.
+__device__ __forceinline__ uint32_t signs32(const uint32_t *v)
+{
+    uint32_t m[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 7; j >= 0; j--) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) m[c] = __funnelshift_l(v[8 * c + j], m[c], 1);
+    }
+    return m[0] | (m[1] << 8) | (m[2] << 16) | (m[3] << 24);
+}
+
+// Bitwise OR of 32 words as a tree of three-input ORs (depth 4, not a chain
+// of 16 dependent operations).
+__device__ __forceinline__ uint32_t or32(const uint32_t *v)
+{
+    uint32_t a[11];
+#pragma unroll
+    for (int k = 0; k < 10; k++) a[k] = v[3 * k] | v[3 * k + 1] | v[3 * k + 2];
+    a[10] = v[30] | v[31];
+    const uint32_t b0 = a[0] | a[1] | a[2], b1 = a[3] | a[4] | a[5], b2 = a[6] | a[7] | a[8], b3 = a[9] | a[10];
+    return (b0 | b1 | b2) | b3;
 }
 
 // A run: the CTA's items in supertile s, as sorted entry positions [eb, ee);
@@ -193,78 +255,76 @@ __device__ __forceinline__ bool tc_next_run(const TcArgs &a, unsigned long long 
     return true;
 }
 
-// The producer: bulk copies and MMAs, in pass order, loads running up to
-// kTcAStages passes ahead.  Returns false if a wait ran out.
-__device__ bool tc_produce(const TcArgs &a, TcSmem &sm, uint32_t tmem, unsigned long long ibeg,
-                           unsigned long long iend, uint64_t &n_loaded, uint64_t &n_mma, uint32_t &b_loaded,
-                           uint32_t &b_used)
+// The loader: bulk copies of the entry records of every pass into the ring
+// of kTcAStages stages (a stage is reused once the MMA that read it is done)
+// and of each run's query records into one of two buffers (reused once the
+// run before the previous one has finished its MMAs).  Returns false if a
+// wait ran out; n_loaded / b_loaded: copies issued.
+__device__ bool tc_load_all(const TcArgs &a, TcSmem &sm, unsigned long long ibeg, unsigned long long iend,
+                            uint64_t &n_loaded, uint32_t &b_loaded)
 {
     volatile int *abort = &sm.abort;
-    TcRun rl, rm;
-    bool hl = tc_first_run(a, ibeg, iend, rl);
-    bool hm = hl;
-    rm = rl;
-    uint32_t pl = 0, pm = 0;  // pass within the load / MMA cursor's run
-    uint64_t gl = 0, gm = 0;  // passes loaded / multiplied
-    uint32_t rix = 0;         // index of the MMA cursor's run (B buffer rix & 1)
-    b_loaded = b_used = 0;    // runs whose query records were fetched / waited for
-    if (hm) {
-        bar_expect(&sm.b_full[0], kTcBBytes);
-        bulk_load(sm.b[0], a.q_rec + rm.s * (kTcBBytes / 16), kTcBBytes, &sm.b_full[0]);
-        b_loaded = 1;
-    }
+    TcRun r;
+    bool h = tc_first_run(a, ibeg, iend, r);
+    uint32_t p = 0, rix = 0;
+    uint64_t g = 0;
     bool ok = true;
-    while (hm && ok) {
-        while (hl && gl < gm + kTcAStages) {
-            const uint32_t s = (uint32_t)(gl % kTcAStages);
-            if (gl >= kTcAStages && !(ok = bar_wait(&sm.a_empty[s], (uint32_t)((gl / kTcAStages - 1) & 1), abort)))
-                break;
-            bar_expect(&sm.a_full[s], kTcPassBytes);
-            bulk_load(sm.a[s], a.e_rec + (uint64_t)(rl.p0 + (int64_t)kTcM * pl) * 2, kTcPassBytes, &sm.a_full[s]);
-            gl++;
-            if (++pl == rl.np) {
-                pl = 0;
-                hl = tc_next_run(a, ibeg, iend, rl);
-            }
+    b_loaded = 0;
+    while (h) {
+        if (p == 0) {
+            const uint32_t bb = rix & 1;
+            if (rix >= 2 && !(ok = bar_wait(&sm.b_free[bb], ((rix - 2) >> 1) & 1, abort))) break;
+            bar_expect(&sm.b_full[bb], kTcBBytes);
+            bulk_load(sm.b[bb], a.q_rec + r.s * (kTcBBytes / 16), kTcBBytes, &sm.b_full[bb]);
+            b_loaded = rix + 1;
         }
-        if (!ok) break;
-        const uint32_t bsel = rix & 1;
-        if (pm == 0) {
-            if (!(ok = bar_wait(&sm.b_full[bsel], (rix >> 1) & 1, abort))) break;
-            b_used = rix + 1;
-        }
-        const uint32_t s = (uint32_t)(gm % kTcAStages), acc = (uint32_t)(gm % kTcAcc);
-        if (!(ok = bar_wait(&sm.a_full[s], (uint32_t)((gm / kTcAStages) & 1), abort))) break;
-        if (gm >= kTcAcc && !(ok = bar_wait(&sm.acc_empty[acc], (uint32_t)((gm / kTcAcc - 1) & 1), abort))) break;
-        tc_fence_after();
-        tc_mma(tmem + acc * kTcN, smem_desc(sm.a[s]), smem_desc(sm.b[bsel]));
-        tc_commit(&sm.acc_full[acc]);
-        tc_commit(&sm.a_empty[s]);
-        gm++;
-        const bool last_of_run = pm + 1 == rm.np;
-        if (last_of_run) tc_commit(&sm.b_free[bsel]);
-        if (pm == 0) {
-            // fetch the next run's query records into the other buffer once
-            // the run before this one no longer reads it
-            TcRun nx = rm;
-            if (tc_next_run(a, ibeg, iend, nx)) {
-                const uint32_t nb = bsel ^ 1;
-                if (rix >= 1 && !(ok = bar_wait(&sm.b_free[nb], ((rix - 1) >> 1) & 1, abort))) break;
-                bar_expect(&sm.b_full[nb], kTcBBytes);
-                bulk_load(sm.b[nb], a.q_rec + nx.s * (kTcBBytes / 16), kTcBBytes, &sm.b_full[nb]);
-                b_loaded = rix + 2;
-            }
-        }
-        if (last_of_run) {
-            pm = 0;
+        const uint32_t s = (uint32_t)(g % kTcAStages);
+        if (g >= kTcAStages && !(ok = bar_wait(&sm.mma_done[s], (uint32_t)((g / kTcAStages - 1) & 1), abort))) break;
+        bar_expect(&sm.a_full[s], kTcPassBytes);
+        bulk_load(sm.a[s], a.e_rec + (uint64_t)(r.p0 + (int64_t)kTcM * p) * 2, kTcPassBytes, &sm.a_full[s]);
+        g++;
+        if (++p == r.np) {
+            p = 0;
             rix++;
-            hm = tc_next_run(a, ibeg, iend, rm);
-        } else {
-            pm++;
+            h = tc_next_run(a, ibeg, iend, r);
         }
     }
-    n_loaded = gl;
-    n_mma = gm;
+    n_loaded = g;
+    return ok;
+}
+
+// The MMA issuer: per pass, once its entry records (and, first in a run, the
+// run's query records) have landed and the epilogue has handed back the
+// accumulator stage, one MMA and one commit to the pass's stage barrier
+// (which the epilogue waits on and which frees the stage for the loader);
+// after a run's last MMA a commit frees its query buffer.
+__device__ bool tc_mma_all(const TcArgs &a, TcSmem &sm, uint32_t tmem, unsigned long long ibeg,
+                           unsigned long long iend, uint64_t &n_mma)
+{
+    volatile int *abort = &sm.abort;
+    TcRun r;
+    bool h = tc_first_run(a, ibeg, iend, r);
+    uint32_t p = 0, rix = 0;
+    uint64_t g = 0;
+    bool ok = true;
+    while (h) {
+        const uint32_t bb = rix & 1;
+        if (p == 0 && !(ok = bar_wait(&sm.b_full[bb], (rix >> 1) & 1, abort))) break;
+        const uint32_t s = (uint32_t)(g % kTcAStages), acc = (uint32_t)(g % kTcAcc);
+        if (!(ok = bar_wait(&sm.a_full[s], (uint32_t)((g / kTcAStages) & 1), abort))) break;
+        if (g >= kTcAcc && !(ok = bar_wait(&sm.acc_empty[acc], (uint32_t)((g / kTcAcc - 1) & 1), abort))) break;
+        tc_fence_after();
+        tc_mma(tmem + acc * kTcN, smem_desc(sm.a[s]), smem_desc(sm.b[bb]));
+        tc_commit(&sm.mma_done[s]);
+        g++;
+        if (++p == r.np) {
+            tc_commit(&sm.b_free[bb]);
+            p = 0;
+            rix++;
+            h = tc_next_run(a, ibeg, iend, r);
+        }
+    }
+    n_mma = g;
     return ok;
 }
 
@@ -286,18 +346,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
     if (threadIdx.x == 0) {
         for (int i = 0; i < kTcAStages; i++) {
             bar_init(&sm.a_full[i], 1);
-            bar_init(&sm.a_empty[i], 1);
+            bar_init(&sm.mma_done[i], 1);
         }
-        for (int i = 0; i < kTcAcc; i++) {
-            bar_init(&sm.acc_full[i], 1);
-            bar_init(&sm.acc_empty[i], kTcEpiWarps);
-        }
+        for (int i = 0; i < kTcAcc; i++) bar_init(&sm.acc_empty[i], kTcEpiWarps);
         for (int i = 0; i < 2; i++) {
             bar_init(&sm.b_full[i], 1);
             bar_init(&sm.b_free[i], 1);
         }
         bar_init(&sm.drain, 1);
         sm.abort = 0;
+        for (int i = 0; i < kTcEpiWarps; i++) sm.nsurv[i] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -315,68 +373,87 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
 
     if (warp == kTcEpiWarps) {
         if (lane == 0) {
-            uint64_t n_loaded = 0, n_mma = 0;
-            uint32_t b_loaded = 0, b_used = 0;
-            const bool ok = tc_produce(a, sm, tmem, ibeg, iend, n_loaded, n_mma, b_loaded, b_used);
-            if (!ok) {
+            uint64_t n_loaded = 0;
+            uint32_t b_loaded = 0;
+            if (!tc_load_all(a, sm, ibeg, iend, n_loaded, b_loaded)) {
                 atomicOr(&ctr->error, 2u);
                 *abort = 1;
             }
-            // wind down: every MMA issued has finished (before the tensor
-            // memory is freed) and every copy issued has landed (before the
-            // CTA's shared memory goes away)
+            // wind down: every copy issued has landed before the CTA's
+            // shared memory goes away (copies the MMA issuer consumed have
+            // landed already; the waits then return at once)
+            int quiet = 0;
+            for (uint64_t g = n_loaded > kTcAStages ? n_loaded - kTcAStages : 0; g < n_loaded; g++)
+                bar_wait(&sm.a_full[g % kTcAStages], (uint32_t)((g / kTcAStages) & 1), &quiet);
+            for (uint32_t j = b_loaded > 2 ? b_loaded - 2 : 0; j < b_loaded; j++)
+                bar_wait(&sm.b_full[j & 1], (j >> 1) & 1, &quiet);
+        }
+    } else if (warp == kTcEpiWarps + 1) {
+        if (lane == 0) {
+            uint64_t n_mma = 0;
+            if (!tc_mma_all(a, sm, tmem, ibeg, iend, n_mma)) {
+                atomicOr(&ctr->error, 2u);
+                *abort = 1;
+            }
+            if (n_mma) atomicAdd(&ctr->mma_issued, (unsigned long long)n_mma);
+            // wind down: every MMA issued has finished before the tensor
+            // memory is freed
             tc_commit(&sm.drain);
             int quiet = 0;
             bar_wait(&sm.drain, 0, &quiet);
-            for (uint64_t g = n_mma; g < n_loaded; g++)
-                bar_wait(&sm.a_full[g % kTcAStages], (uint32_t)((g / kTcAStages) & 1), &quiet);
-            for (uint32_t j = b_used; j < b_loaded; j++) bar_wait(&sm.b_full[j & 1], (j >> 1) & 1, &quiet);
         }
     } else {
-        // epilogue warp: accumulator lanes 32*warp .. 32*warp + 31
+        // epilogue warp: accumulator lanes 32 quarter .. 32 quarter + 31 (one
+        // entry each) and the columns of tiles 2 half and 2 half + 1
+        const int quarter = warp & 3, half = warp >> 2;
         uint2 *sbuf = sm.surv[warp];
-        int nbuf = 0;
+        const uint32_t nsurv_s = smem_addr(&sm.nsurv[warp]);  // this warp's buffer count (shared space)
         unsigned long long n_inter = 0;
         const uint64_t nvalid = ctr->valid_queries;
+        // moves the buffered survivors to the list (called by the whole warp)
         auto flush = [&]() {
-            if (nbuf == 0) return;
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)nbuf);
-            base = __shfl_sync(kFull, base, 0);
             __syncwarp();
-            for (int i = lane; i < nbuf; i += 32)
+            const int nb = min((int)lds_u32(nsurv_s), kTcSurvBuf);
+            if (nb == 0) return;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)nb);
+            base = __shfl_sync(kFull, base, 0);
+            for (int i = lane; i < nb; i += 32)
                 if (base + i < a.surv_cap) a.surv[base + i] = sbuf[i];
             __syncwarp();
-            nbuf = 0;
+            if (lane == 0) sts_u32(nsurv_s, 0u);
+            __syncwarp();
         };
         TcRun r;
         bool h = tc_first_run(a, ibeg, iend, r);
         uint32_t p = 0;
         uint64_t gm = 0;
-        int64_t tlo[kTcTiles], thi[kTcTiles];
-        int tnq[kTcTiles];
+        // this warp's two tiles in the current run: query segments, and the
+        // part of each tile's own range inside the run, relative to p0
+        int nq[2] = {0, 0};
+        int32_t tlo[2] = {0, 0}, thi[2] = {0, 0};
         auto run_tiles = [&]() {
 #pragma unroll
-            for (int g = 0; g < kTcTiles; g++) {
-                const uint64_t t = r.s * kTcTiles + g;
+            for (int k = 0; k < 2; k++) {
+                const uint64_t t = r.s * kTcTiles + 2 * half + k;
                 const int64_t left = (int64_t)nvalid - (int64_t)t * kQT;
-                tnq[g] = t < args.ntiles ? (int)max((int64_t)0, min(left, (int64_t)kQT)) : 0;
-                tlo[g] = tnq[g] ? args.tile_lo[t] : 0;
-                thi[g] = tnq[g] ? args.tile_hi[t] : 0;
+                int n = t < args.ntiles ? (int)max((int64_t)0, min(left, (int64_t)kQT)) : 0;
+                const int64_t lo = n ? max(args.tile_lo[t], r.eb) : 0, hi = n ? min(args.tile_hi[t], r.ee) : 0;
+                if (hi <= lo) n = 0;
+                nq[k] = n;
+                tlo[k] = (int32_t)(lo - r.p0);
+                thi[k] = (int32_t)(hi - r.p0);
                 // candidates: the tile's range inside this run, times its query segments
-                if (warp == 0 && lane == 0 && tnq[g]) {
-                    const int64_t c0 = max(tlo[g], r.eb), c1 = min(thi[g], r.ee);
-                    if (c1 > c0) n_inter += (unsigned long long)(c1 - c0) * (unsigned long long)tnq[g];
-                }
+                if (quarter == 0 && lane == 0 && n) n_inter += (unsigned long long)(hi - lo) * (unsigned long long)n;
             }
         };
         if (h) run_tiles();
         while (h) {
             const uint32_t acc = (uint32_t)(gm % kTcAcc);
-            // one lane waits, the warp follows its verdict (the tensor-memory
-            // loads below need all 32 lanes)
+            // the pass's MMA is done: one lane waits, the warp follows its
+            // verdict (the tensor-memory loads below need all 32 lanes)
             int got = 0;
-            if (lane == 0) got = bar_wait(&sm.acc_full[acc], (uint32_t)((gm / kTcAcc) & 1), abort);
+            if (lane == 0) got = bar_wait(&sm.mma_done[gm % kTcAStages], (uint32_t)((gm / kTcAStages) & 1), abort);
             got = __shfl_sync(kFull, got, 0);
             if (!got) {
                 if (lane == 0) {
@@ -385,61 +462,54 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
                 }
                 break;
             }
+            // the pass's entries relative to p0; which of the two tiles' own
+            // ranges meet them (warp-uniform)
+            const int32_t pr = (int32_t)(kTcM * p);
+            const bool act0 = nq[0] > 0 && tlo[0] < pr + kTcM && thi[0] > pr;
+            const bool act1 = nq[1] > 0 && tlo[1] < pr + kTcM && thi[1] > pr;
+            uint32_t v0[kQT], v1[kQT];
+            const uint32_t tcol = tmem + ((uint32_t)(32 * quarter) << 16) + acc * kTcN + 2 * half * kQT;
             tc_fence_after();
-            const int64_t pb = r.p0 + (int64_t)kTcM * p;
-            const int64_t lo_run = max(pb, r.eb), hi_run = min(pb + kTcM, r.ee);
-            const int64_t e = pb + 32 * warp + lane;
-            const bool e_in = e >= lo_run && e < hi_run;
-#pragma unroll
-            for (int g = 0; g < kTcTiles; g++) {
-                if (tnq[g] == 0 || tlo[g] >= hi_run || thi[g] <= lo_run) continue;  // warp-uniform
-                uint32_t v[32];
-                tc_load32(tmem + ((uint32_t)(32 * warp) << 16) + acc * kTcN + g * kQT, v);
-                uint32_t any = 0;
-#pragma unroll
-                for (int j = 0; j < 32; j += 2) any |= v[j] | v[j + 1];
-                const bool hit = (any >> 31) && e_in && e >= tlo[g] && e < thi[g];
-                if (!__any_sync(kFull, hit)) continue;
-                uint32_t m = 0;
-                if (hit) {
-#pragma unroll
-                    for (int j = 0; j < 32; j++) m |= (v[j] >> 31) << j;
-                    if (tnq[g] < 32) m &= (1u << tnq[g]) - 1u;
-                }
-                const int cnt = __popc(m);
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int tot = __shfl_sync(kFull, incl, 31);
-                if (tot == 0) continue;
-                if (nbuf + tot > kTcSurvBuf) flush();
-                const bool direct = tot > kTcSurvBuf;
-                unsigned long long pos = nbuf + (incl - cnt);
-                if (direct) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)tot);
-                    pos = __shfl_sync(kFull, base, 0) + (incl - cnt);
-                }
-                const uint32_t q0 = (uint32_t)((r.s * kTcTiles + g) * kQT);
-                while (m) {
-                    const int bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    const uint2 sv = make_uint2((uint32_t)e, q0 + bit);
-                    if (!direct)
-                        sbuf[pos] = sv;
-                    else if (pos < a.surv_cap)
-                        a.surv[pos] = sv;
-                    pos++;
-                }
-                __syncwarp();
-                if (!direct) nbuf += tot;
-            }
+            if (act0) tc_load32(tcol, v0);
+            if (act1) tc_load32(tcol + kQT, v1);
+            // the stage goes back to the MMA issuer before the values are looked at
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&sm.acc_empty[acc]);
+            const int32_t el = pr + 32 * quarter + lane;  // this lane's entry, relative to p0
+            // common case: none of the values is negative
+            const bool hit0 = act0 && el >= tlo[0] && el < thi[0] && (or32(v0) >> 31);
+            const bool hit1 = act1 && el >= tlo[1] && el < thi[1] && (or32(v1) >> 31);
+            if (__any_sync(kFull, hit0 || hit1)) {
+                // some entry may meet some query segment: the lanes that hit
+                // append their survivors at places taken with a shared atomic
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    const bool hit = k ? hit1 : hit0;
+                    if (!hit) continue;
+                    uint32_t m = signs32(k ? v1 : v0);
+                    if (nq[k] < 32) m &= (1u << nq[k]) - 1u;
+                    const int cnt = __popc(m);
+                    if (!cnt) continue;
+                    int pos = (int)atoms_add_u32(nsurv_s, (uint32_t)cnt);
+                    const uint32_t e = (uint32_t)(r.p0 + el);
+                    const uint32_t q0 = (uint32_t)((r.s * kTcTiles + 2 * half + k) * kQT);
+                    while (m) {
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        const uint2 sv = make_uint2(e, q0 + bit);
+                        if (pos < kTcSurvBuf) {
+                            sbuf[pos] = sv;
+                        } else {  // the buffer is full: straight to the list
+                            const unsigned long long kk = atomicAdd(&ctr->survivors, 1ULL);
+                            if (kk < a.surv_cap) a.surv[kk] = sv;
+                        }
+                        pos++;
+                    }
+                }
+                __syncwarp();
+                if ((int)lds_u32(nsurv_s) >= kTcSurvBuf / 2) flush();
+            }
             gm++;
             if (++p == r.np) {
                 p = 0;
@@ -448,7 +518,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
             }
         }
         flush();
-        if (warp == 0 && lane == 0 && n_inter) atomicAdd(&ctr->interactions, n_inter);
+        if (n_inter) atomicAdd(&ctr->interactions, n_inter);
     }
     tc_fence_before();
     __syncthreads();

@@ -154,7 +154,8 @@ struct DevCounters {
     unsigned long long gather_done;    // blocks of query_gather that have finished (the last one scans)
     unsigned long long pair_done;      // blocks of the last pair kernel that have finished (the last one
                                        // copies the counters to the host mirror)
-    unsigned int error;                // bit 0: invalid query input
+    unsigned long long mma_issued;     // tensor-core pre-test: MMAs issued
+    unsigned int error;                // bit 0: invalid query input; bit 1: a pipeline wait ran out
     unsigned int pad;
 };
 

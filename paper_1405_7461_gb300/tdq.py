@@ -69,7 +69,8 @@ class tdq_stats(ctypes.Structure):
                 ("overlap_pairs", ctypes.c_uint64), ("fp64_pairs", ctypes.c_uint64), ("results", ctypes.c_uint64),
                 ("work_items", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("pair_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
-                ("filter_survivors", ctypes.c_uint64), ("refine_ms", ctypes.c_double)]
+                ("filter_survivors", ctypes.c_uint64), ("refine_ms", ctypes.c_double),
+                ("mma_issued", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

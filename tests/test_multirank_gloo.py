@@ -107,3 +107,13 @@ def test_roofline_arithmetic():
     assert f["hbm"]["algorithmic_bytes_per_launch"] == 20 * 1000  # the 20 B record of each entry
     assert f["hbm"]["frac"] == pytest.approx(f["hbm"]["achieved_gbs"] / bench.hbm_peak_gbs())
     assert bench.roofline("fp64", dict(tot, kernel_ms=0.0), 2, 1000) is None
+    # the tensor-core pre-test: 16 flops (the rank-8 integer form) per
+    # temporal-overlap pair against the dense tensor peak; the MMAs issued
+    # (128 x 128 x 16 MACs each) beside it; 32 B record per entry from DRAM
+    t = bench.roofline("tcfilter", dict(tot, mma=1000), 2, 1000)
+    peak, _ = bench.tensor_peak_tflops()
+    assert t["bound"] == "tensor" and t["unit"] == "TFLOP/s"
+    assert t["achieved"] == pytest.approx(16 * 1.5e9 / 1e-3 / 1e12)
+    assert t["frac"] == pytest.approx(t["achieved"] / peak)
+    assert t["achieved_mma_issued"] == pytest.approx(2 * 128 * 128 * 16 * 500 / 1e-3 / 1e12)
+    assert t["hbm"]["algorithmic_bytes_per_launch"] == 32 * 1000
