@@ -487,6 +487,7 @@ extern "C" void tdq_index_free(tdq_index *idx)
     cudaFree(w.sort_hist);
     cudaFree(w.r_block);
     cudaFree(w.s_block);
+    cudaFree(w.bin_cnt);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < kSearchEvents; k++)

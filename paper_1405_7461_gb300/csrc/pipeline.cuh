@@ -52,6 +52,26 @@ struct PrepArgs {
     bool count_overlaps;
     uint4 *pre_tc;  // may be null: also the tensor-core pre-test record of every valid query segment
     TcGrid grid;    // the index's grid (with pre_tc)
+    // may be null: the counting sort instead of the radix sort's digit
+    // counts -- each valid segment takes its place in its bin (vals) with
+    // an atomic on bin_cnt (zeroed beforehand, bins.m words), and the last
+    // block turns the counts into offsets
+    uint32_t *bin_cnt;
+};
+
+// Arguments of query_scatter (counting sort): every valid query segment's
+// columns to its sorted position bin offset + rank.
+struct ScatterArgs {
+    const double *const *pre;
+    const float4 *pre_sph;
+    const uint4 *pre_tc;       // may be null
+    const uint64_t *keys;      // bin of each segment
+    const uint32_t *ranks;     // place inside its bin
+    const uint32_t *bin_off;   // offsets of the bins
+    uint64_t nq;
+    QuerySoA q;
+    uint4 *q_rec;              // may be null (tensor-core records)
+    int64_t *srt_lo, *srt_hi;  // candidate ranges in sorted order
 };
 
 // Arguments of query_gather (it reads workspace arrays only).
@@ -73,6 +93,9 @@ struct GatherArgs {
     int64_t *st_lo, *st_hi;
     unsigned long long *st_work;    // chunks per supertile, then their exclusive offsets; nsuper + 1
     uint64_t nsuper;
+    // may be null: the sorted columns are in place already (query_scatter);
+    // only the tile plan is made, from these candidate ranges in sorted order
+    const int64_t *srt_lo, *srt_hi;
 };
 
 struct PairArgs {
@@ -120,6 +143,7 @@ struct TcArgs {
 // Kernels launched from more than one file (defined in search.cu).
 __global__ void query_prep(PrepArgs a);
 __global__ void query_gather(GatherArgs a);
+__global__ void query_scatter(ScatterArgs a);
 __global__ void publish_counters(const DevCounters *src, DevCounters *dst);
 
 // Pair kernel of the requested mode as a persistent grid (search.cu); the

@@ -188,6 +188,7 @@ void plan_release(tdq_plan *p)
     cudaFree(w.t_block);
     cudaFree(w.sort_hist);
     cudaFree(w.s_block);
+    cudaFree(w.bin_cnt);
     cudaFree(w.ctr);
     if (w.ctr_host) cudaFreeHost(w.ctr_host);
     for (int k = 0; k < kSearchEvents; k++)
@@ -241,7 +242,7 @@ extern "C" tdq_status tdq_plan_create(tdq_index *idx, const tdq_plan_params *par
         p->d_arr = (double *)p->stage_block;
         p->t0_arr = p->d_arr + p->cap_q;
         p->t1_arr = p->t0_arr + p->cap_q;
-        st = ensure_queries(w, p->cap_q);
+        st = ensure_queries(w, p->cap_q, p->idx->m);
         if (st != TDQ_OK) break;
         const uint64_t rc = params->result_capacity ? params->result_capacity : (idx->n > 65536 ? idx->n : 65536);
         st = plan_results(p, rc);

@@ -210,8 +210,12 @@ __global__ void query_prep(PrepArgs a)
             key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
         }
         a.keys[i] = key;
-        a.vals[i] = (uint32_t)i;
-        digit = (uint32_t)(key & 0xff);
+        if (a.bin_cnt) {
+            if (valid) a.vals[i] = atomicAdd(&a.bin_cnt[key], 1u);
+        } else {
+            a.vals[i] = (uint32_t)i;
+            digit = (uint32_t)(key & 0xff);
+        }
         pre[kPreSeg][i] = __longlong_as_double(in.seg_id[i]);
         pre[kPreTraj][i] = __longlong_as_double(in.traj_id ? in.traj_id[i] : 0);
         if (valid && a.ranges) candidate_range(bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
@@ -227,7 +231,18 @@ __global__ void query_prep(PrepArgs a)
         if (vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
         if (n_overlap) atomicAdd(&ctr->overlap_pairs, n_overlap);
     }
-    if (a.sort_hist) {  // this block's keys lie in one sort tile (blockDim divides kSortTileKeys)
+    if (a.bin_cnt) {
+        // the block that finishes last turns the bin counts into offsets
+        __shared__ bool last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&ctr->prep_done, 1ULL) == (unsigned long long)gridDim.x - 1;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            block_exclusive_scan<uint32_t, kBlock, 8>(a.bin_cnt, bins.m, nullptr);
+        }
+    } else if (a.sort_hist) {  // this block's keys lie in one sort tile (blockDim divides kSortTileKeys)
         __shared__ uint32_t h[256];
         for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
         __syncthreads();
@@ -250,6 +265,32 @@ __global__ void publish_counters(const DevCounters *src, DevCounters *dst)
     for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / 8); i += 32) d[i] = s[i];
 }
 
+// Counting sort, second half: every valid query segment's columns go to
+// its sorted position (its bin's offset plus its place in the bin), with its
+// candidate range for the tile plan.  Segments of one bin keep no
+// particular order (a tile groups segments of nearby bins whatever their
+// order; results come in no particular order anyway).
+__global__ void query_scatter(ScatterArgs a)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nq) return;
+    const int64_t ts = __double_as_longlong(a.pre[7][i]), te = __double_as_longlong(a.pre[8][i]);
+    if (!(ts < te)) return;  // invalid or padding: not sorted
+    const uint64_t k = (uint64_t)a.bin_off[a.keys[i]] + a.ranks[i];
+    QuerySoA &q = a.q;
+    q.px[k] = a.pre[0][i]; q.py[k] = a.pre[1][i]; q.pz[k] = a.pre[2][i];
+    q.vx[k] = a.pre[3][i]; q.vy[k] = a.pre[4][i]; q.vz[k] = a.pre[5][i];
+    q.d2[k] = a.pre[6][i];
+    q.ts_key[k] = ts;
+    q.te_key[k] = te;
+    q.qid[k] = __double_as_longlong(a.pre[kPreSeg][i]);
+    if (q.qtraj) q.qtraj[k] = __double_as_longlong(a.pre[kPreTraj][i]);
+    q.sph[k] = a.pre_sph[i];
+    a.srt_lo[k] = __double_as_longlong(a.pre[kPreLo][i]);
+    a.srt_hi[k] = __double_as_longlong(a.pre[kPreHi][i]);
+    if (a.q_rec) tc_store(a.q_rec, k, a.pre_tc[2 * i], a.pre_tc[2 * i + 1]);
+}
+
 // Sorted query SoA; then, one warp per tile of kQT consecutive sorted query
 // segments, the tile plan: the tile's entry range is the union of its
 // members' candidate ranges, cut into chunks of `chunk` entries, one work item
@@ -260,7 +301,13 @@ __global__ void query_gather(GatherArgs a)
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     QuerySoA &q = a.q;
     int64_t rlo = INT64_MAX, rhi = INT64_MIN;
-    if (k < a.nq && k < a.ctr->valid_queries) {
+    if (a.srt_lo) {
+        // the sorted columns are in place (query_scatter): the ranges only
+        if (k < a.nq && k < a.ctr->valid_queries) {
+            rlo = a.srt_lo[k];
+            rhi = a.srt_hi[k];
+        }
+    } else if (k < a.nq && k < a.ctr->valid_queries) {
         const uint32_t i = a.order[k];
         q.px[k] = a.pre[0][i]; q.py[k] = a.pre[1][i]; q.pz[k] = a.pre[2][i];
         q.vx[k] = a.pre[3][i]; q.vy[k] = a.pre[4][i]; q.vz[k] = a.pre[5][i];
@@ -273,15 +320,16 @@ __global__ void query_gather(GatherArgs a)
         rlo = __double_as_longlong(a.pre[kPreLo][i]);
         rhi = __double_as_longlong(a.pre[kPreHi][i]);
     }
-    // tensor-core records in sorted order; zero records fill the last supertile
+    // tensor-core records in sorted order (written by query_scatter when
+    // srt_lo is given); zero records fill the last supertile
     if (a.q_rec && k < a.nsuper * 128) {
-        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-        if (k < a.nq && k < a.ctr->valid_queries) {
+        const bool real = k < a.nq && k < a.ctr->valid_queries;
+        if (!real) {
+            tc_store(a.q_rec, k, make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u));
+        } else if (!a.srt_lo) {
             const uint32_t i = a.order[k];
-            lo = a.pre_tc[2 * i];
-            hi = a.pre_tc[2 * i + 1];
+            tc_store(a.q_rec, k, a.pre_tc[2 * i], a.pre_tc[2 * i + 1]);
         }
-        tc_store(a.q_rec, k, lo, hi);
     }
     // the tile plan: this warp's 32 sorted query segments are tile k / kQT
     const int lane = threadIdx.x & 31;
@@ -559,8 +607,18 @@ cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, ui
 
 
 
-tdq_status ensure_queries(Workspace &w, uint64_t nq)
+tdq_status ensure_queries(Workspace &w, uint64_t nq, uint32_t m)
 {
+    if (m <= kCountSortMaxBins && m > w.bin_cap) {
+        cudaFree(w.bin_cnt);
+        w.bin_cnt = nullptr;
+        w.bin_cap = 0;
+        if (dev_alloc(&w.bin_cnt, (uint64_t)m * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(TDQ_ERR_NOMEM, "search workspace: device allocation of %u bin counters failed", m);
+        }
+        w.bin_cap = m;
+    }
     if (nq <= w.q_cap && w.q_block) return TDQ_OK;
     uint64_t cap = nq > 2 * w.q_cap ? nq : 2 * w.q_cap;
     if (cap < 1024) cap = 1024;
@@ -569,6 +627,7 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
                      + 2 * carve_bytes(cap, 8) + 2 * carve_bytes(cap, 4) // sort
                      + 11 * carve_bytes(cap, 8)                 // sorted query SoA
                      + 2 * carve_bytes(cap, 16)                 // query spheres (before / after sorting)
+                     + 2 * carve_bytes(cap, 8)                  // candidate ranges in sorted order
                      + carve_bytes(2 * cap, 16)                 // tensor-core records before sorting
                      + carve_bytes(2 * ((cap + 127) / 128 * 128), 16)  // ... sorted, whole supertiles
                      + carve_bytes(kPreCols, sizeof(double *)); // pre pointer table
@@ -612,6 +671,8 @@ tdq_status ensure_queries(Workspace &w, uint64_t nq)
     q.qtraj = carve<int64_t>(p, cap);
     w.pre_sph = carve<float4>(p, cap);
     q.sph = carve<float4>(p, cap);
+    w.srt_lo = carve<int64_t>(p, cap);
+    w.srt_hi = carve<int64_t>(p, cap);
     w.pre_tc = carve<uint4>(p, 2 * cap);
     q.tc_rec = carve<uint4>(p, 2 * ((cap + 127) / 128 * 128));
     w.pre_dev = carve<double *>(p, kPreCols);
@@ -667,10 +728,12 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
 int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
 {
     // without entries: query_prep and publish_counters; with entries:
-    // query_prep, the sort of the query keys, query_gather and the pair
-    // kernel (filter mode: filter and refine), whose last block publishes the
+    // query_prep, the sort of the query keys (counting sort: query_scatter;
+    // else the radix sort's kernels), query_gather and the pair kernel
+    // (filter mode: filter and refine), whose last block publishes the
     // counters
-    return idx->n > 0 ? 2 + sort_kernel_launches(nq, bin_key_bits(idx->m), true) + (cfg.filter ? 2 : 1) : 2;
+    const int sort = idx->m <= kCountSortMaxBins ? 1 : sort_kernel_launches(nq, bin_key_bits(idx->m), true);
+    return idx->n > 0 ? 2 + sort + (cfg.filter ? 2 : 1) : 2;
 }
 
 // Events are recorded as external event-record nodes when the stream is being
@@ -682,28 +745,39 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     cudaError_t e = cudaStreamIsCapturing(stream, &cs);
     if (e != cudaSuccess) return e;
     const unsigned evflags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-    // the counters, and with the sort's small path its two fused histograms
-    const bool fuse = idx->n > 0 && sort_fusable(nq);
+    // the counters, and with the radix sort's small path its two fused
+    // histograms (counting sort: the bin counts)
+    const bool csort = idx->n > 0 && idx->m <= kCountSortMaxBins;
+    if (csort && (!w.bin_cnt || w.bin_cap < idx->m)) return cudaErrorInvalidValue;  // workspace not sized
+    const bool fuse = !csort && idx->n > 0 && sort_fusable(nq);
     const uint64_t sort_tiles = (nq + kSortTileKeys - 1) / kSortTileKeys;
     e = cudaMemsetAsync(w.ctr, 0, fuse ? kCtrBytes + 2 * sort_tiles * 256 * sizeof(uint32_t) : sizeof(DevCounters),
                         stream);
     if (e != cudaSuccess) return e;
+    if (csort && (e = cudaMemsetAsync(w.bin_cnt, 0, (size_t)idx->m * sizeof(uint32_t), stream)) != cudaSuccess)
+        return e;
     if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, evflags)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
     const BinView bins = bin_view(idx);
     const bool tc = cfg.tc && idx->n > 0;
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
         PrepArgs{in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr, fuse ? w.sort_fused_hist : nullptr,
-                 idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid});
+                 idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     const uint64_t nsuper = (nq + 127) / 128;
     if (idx->n > 0) {
-        if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
-                                  bin_key_bits(idx->m), &w.ctr->sort_n, fuse ? w.sort_fused_hist : nullptr)) !=
-            cudaSuccess)
+        if (csort) {
+            query_scatter<<<grid_for(nq), kBlock, 0, stream>>>(ScatterArgs{
+                pre, w.pre_sph, w.pre_tc, w.keys, w.vals, w.bin_cnt, nq, w.q, tc ? w.q.tc_rec : nullptr, w.srt_lo,
+                w.srt_hi});
+        } else if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
+                                         bin_key_bits(idx->m), &w.ctr->sort_n,
+                                         fuse ? w.sort_fused_hist : nullptr)) != cudaSuccess) {
             return e;
+        }
         const GatherArgs ga{pre, w.pre_sph, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk, w.tile_lo, w.tile_hi,
-                            w.tile_work, w.pre_tc, tc ? w.q.tc_rec : nullptr, w.st_lo, w.st_hi, w.st_work, nsuper};
+                            w.tile_work, w.pre_tc, tc ? w.q.tc_rec : nullptr, w.st_lo, w.st_hi, w.st_work, nsuper,
+                            csort ? w.srt_lo : nullptr, csort ? w.srt_hi : nullptr};
         query_gather<<<grid_for(tc ? nsuper * 128 : nq), kBlock, 0, stream>>>(ga);
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags,
                     w.ctr_host_dev};
@@ -789,9 +863,10 @@ cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
                         const QueryInput &in, uint64_t nq, const LaunchCfg &cfg)
 {
+    const bool csort = idx->n > 0 && idx->m <= kCountSortMaxBins;
     PrepArgs a0{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, w.vals, w.ctr,
-                idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter,
-                cfg.tc && idx->n > 0 ? w.pre_tc : nullptr, idx->grid};
+                !csort && idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter,
+                cfg.tc && idx->n > 0 ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr};
     void *args[] = {&a0};
     cudaKernelNodeParams kp{};
     kp.func = (void *)query_prep;
@@ -829,7 +904,7 @@ tdq_status run_search(tdq_index *idx, const tdq_segments *queries, const SearchS
     if (st != TDQ_OK) return st;
     if ((cfg.flags & TDQ_FLAG_OTHER_TRAJECTORIES) && !queries->traj_id)
         return set_error(TDQ_ERR_INVALID, "tdq_search: TDQ_FLAG_OTHER_TRAJECTORIES needs the queries' traj_id");
-    st = ensure_queries(w, nq);
+    st = ensure_queries(w, nq, idx->m);
     if (st != TDQ_OK) return st;
 
     QueryInput in{};

@@ -155,6 +155,8 @@ struct DevCounters {
     unsigned long long pair_done;      // blocks of the last pair kernel that have finished (the last one
                                        // copies the counters to the host mirror)
     unsigned long long mma_issued;     // tensor-core pre-test: MMAs issued
+    unsigned long long prep_done;      // blocks of query_prep that have finished (the last one scans the
+                                       // bin counts of the counting sort)
     unsigned int error;                // bit 0: invalid query input; bit 1: a pipeline wait ran out
     unsigned int pad;
 };
@@ -221,6 +223,11 @@ struct Workspace {
     uint4 *pre_tc = nullptr;     // per-query tensor-core record before sorting (2 x uint4 each)
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;
+    // counting sort of the query segments by temporal bin: per-bin counts
+    // (then offsets) and the candidate ranges in sorted order
+    uint32_t *bin_cnt = nullptr;
+    uint32_t bin_cap = 0;
+    int64_t *srt_lo = nullptr, *srt_hi = nullptr;
     QuerySoA q{};
     // tiles
     uint64_t t_cap = 0;
@@ -301,7 +308,11 @@ struct LaunchCfg {
 // search.cu: workspace sizing, parameters, and one search split into a part
 // that only enqueues device work (capturable in a CUDA graph) and a part that
 // reads the counters once the stream has reached the end of it.
-tdq_status ensure_queries(Workspace &w, uint64_t nq);
+// Search workspace for nq query segments against an index of m bins.
+tdq_status ensure_queries(Workspace &w, uint64_t nq, uint32_t m);
+// Bins up to which query segments are ordered by a counting sort (per-bin
+// counts, one scan) rather than the radix sort.
+constexpr uint32_t kCountSortMaxBins = 1u << 17;
 tdq_status ensure_survivors(Workspace &w, uint64_t cap);
 tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg);
 int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq);
