@@ -18,6 +18,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libtdq.so")
 BUILD_DIR = os.path.join(PKG, "_build")
+# The debug variant: every index computation of the search kernels checked
+# against its bounds (-DTDQ_DEBUG; a failed check is reported, never a
+# trap).  Built on request, for the tests.
+LIB_DEBUG = os.path.join(PKG, "libtdq_debug.so")
+BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,21 +44,27 @@ def _stale(target, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Build libtdq.so (debug=True: libtdq_debug.so, the bounds-checked
+    variant) if it is missing or older than its sources; returns its path."""
+    lib_path = LIB_DEBUG if debug else LIB
+    build_dir = BUILD_DIR_DEBUG if debug else BUILD_DIR
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "tdq.h"))
-    if not force and not _stale(LIB, srcs + headers + [__file__]):
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    if not force and not _stale(lib_path, srcs + headers + [__file__]):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I",
                      INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"] + list(extra_flags)
+    if debug:
+        common.append("-DTDQ_DEBUG")
     if verbose:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [cc, "-c", src, "-o", obj] + common
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -65,14 +76,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if verbose:
         for _, err in outs:
             sys.stderr.write(err)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in outs] + ARCH + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

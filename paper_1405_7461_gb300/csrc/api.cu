@@ -45,4 +45,8 @@ extern "C" void tdq_debug_fail_allocations(int64_t after) { g_alloc_countdown.st
 
 extern "C" const char *tdq_last_error(void) { return g_err; }
 
-extern "C" const char *tdq_version(void) { return "tdq 0.1 (sm_103a)"; }
+#ifdef TDQ_DEBUG
+extern "C" const char *tdq_version(void) { return "tdq 0.2 (sm_103a, bounds-checked debug build)"; }
+#else
+extern "C" const char *tdq_version(void) { return "tdq 0.2 (sm_103a)"; }
+#endif

@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
         }
         int64_t eb, ee;
         filter_run(args, t, ibeg, iend, eb, ee);
+        if (!TDQ_DBG(ctr, kDbgFilterRun, eb >= 0 && eb < ee && ee <= (int64_t)args.n_entries)) ee = eb;
         int nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)t * kQT);
         float my_c2g, my_w;
         stage_queries(args.q.sph[(int64_t)t * kQT + min(lane, nqt - 1)], lane < nqt, lane, qr, my_c2g, my_w);
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
             if (has_next) {
                 while (args.tile_work[tn + 1] == args.tile_work[tn]) tn++;
                 filter_run(args, tn, ibeg, iend, ebn, een);
+                if (!TDQ_DBG(ctr, kDbgFilterRun, ebn >= 0 && ebn < een && een <= (int64_t)args.n_entries)) een = ebn;
                 nqn = (int)min((uint64_t)kQT, nvalid - tn * kQT);
                 qn = args.q.sph[(int64_t)tn * kQT + min(lane, nqn - 1)];
             }
@@ -191,7 +193,9 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
                 {
                     const bool same = pe + kPass < ee;
                     const int64_t nb = same ? pe + kPass : ebn;
-                    const int left = (int)min(same ? ee - nb : een - nb, (int64_t)kPass);
+                    int left = (int)min(same ? ee - nb : een - nb, (int64_t)kPass);
+                    if (!TDQ_DBG(ctr, kDbgFilterNext, left <= 0 || (nb >= 0 && nb + left <= (int64_t)args.n_entries)))
+                        left = 0;
                     const float4 *ps = esph + nb + lane;
                     const float *pse = esphe + nb + lane;
 #pragma unroll
@@ -265,10 +269,12 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
                         const int bit = 31 - __clz(mk);
                         mk &= ~(1u << bit);
                         const uint2 sv = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
-                        if (!direct)
-                            sbuf[pos] = sv;
-                        else if (pos < fa.surv_cap)
+                        if (!TDQ_DBG(ctr, kDbgFilterQuery, (uint64_t)(q0 + 31 - bit) < nvalid)) {
+                        } else if (!direct) {
+                            if (TDQ_DBG(ctr, kDbgFilterBuf, pos < (unsigned long long)kSurvBuf)) sbuf[pos] = sv;
+                        } else if (pos < fa.surv_cap) {
                             fa.surv[pos] = sv;
+                        }
                         pos++;
                     }
                 }
@@ -333,7 +339,8 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
         const unsigned long long k = wb + lane;
         const bool valid = k < ns;
         const uint2 sv = valid ? fa.surv[k] : make_uint2(0u, 0u);
-        bool active = valid && args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
+        bool active = valid && TDQ_DBG(ctr, kDbgRefine, sv.x < args.n_entries && sv.y < args.nq_slots) &&
+                      args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
                       args.e.te_key[sv.x] > args.q.ts_key[sv.y];
         if (args.flags && active)
             active = pair_allowed(args.flags, args.q.qtraj[sv.y], args.q.qid[sv.y], args.e.traj_id[sv.x],

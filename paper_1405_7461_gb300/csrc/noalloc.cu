@@ -165,7 +165,8 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     TDQ_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), stream));
     const BinView bins = bin_view(idx);
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
-        PrepArgs{in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr, nullptr, idx->n > 0, false});
+        PrepArgs{in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr, nullptr, idx->n > 0, false, nullptr,
+                 TcGrid{}, nullptr, idx->n});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     if (idx->n > 0) {
         TDQ_CUDA(radix_sort_pairs(s->keys, s->vals, s->keys_alt, s->vals_alt, nq, s->hist, stream,
@@ -173,13 +174,17 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
         const GatherArgs ga{s->pre_dev, s->pre_sph, s->vals, nq, s->ctr, s->q, ntiles, chunk, s->tile_lo,
                             s->tile_hi, s->tile_work};
         query_gather<<<grid_for(nq), kBlock, 0, stream>>>(ga);
-        PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk, 0u, nullptr};
+        PairArgs pa{idx->e, s->q, s->tile_lo, s->tile_hi, s->tile_work, ntiles, s->ctr, *out, chunk, 0u, nullptr,
+                    idx->n, nq};
         TDQ_CUDA(launch_pair_kernel(pa, false, idx->sm_count, nullptr, 0, stream, nullptr, 0));
     }
     TDQ_CUDA(cudaGetLastError());
     DevCounters h{};
     TDQ_CUDA(cudaMemcpyAsync(&h, s->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream));
     TDQ_CUDA(cudaStreamSynchronize(stream));
+    if (h.error & 4u)
+        return set_error(TDQ_ERR_CUDA, "tdq_search_device_noalloc: debug build: index bounds check at site %u failed",
+                         h.debug_site);
     if (h.error & 1u)
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search_device_noalloc: invalid query segment (non-finite value, t_end <= t_start, "

@@ -57,6 +57,7 @@ struct PrepArgs {
     // an atomic on bin_cnt (zeroed beforehand, bins.m words), and the last
     // block turns the counts into offsets
     uint32_t *bin_cnt;
+    uint64_t n_entries;  // entries of the index (bound of the debug build's range check)
 };
 
 // Arguments of query_scatter (counting sort): every valid query segment's
@@ -72,6 +73,7 @@ struct ScatterArgs {
     QuerySoA q;
     uint4 *q_rec;              // may be null (tensor-core records)
     int64_t *srt_lo, *srt_hi;  // candidate ranges in sorted order
+    DevCounters *ctr;
 };
 
 // Arguments of query_gather (it reads workspace arrays only).
@@ -109,6 +111,8 @@ struct PairArgs {
     uint32_t chunk;
     uint32_t flags;  // TDQ_FLAG_* pair filters (0: every pair)
     DevCounters *publish;  // may be null: host mirror the last pair kernel copies the counters to
+    uint64_t n_entries;    // entries of the index, and query slots of the search (bounds of the debug
+    uint64_t nq_slots;     // build's checks)
 };
 
 // The pair filters of TDQ_FLAG_OTHER_TRAJECTORIES / TDQ_FLAG_UNORDERED_ONCE
@@ -138,6 +142,7 @@ struct TcArgs {
     uint64_t nsuper;
     uint2 *surv;
     uint64_t surv_cap;
+    uint64_t n_rec;  // entry records held (bound of the debug build's checks)
 };
 
 // Kernels launched from more than one file (defined in search.cu).

@@ -218,7 +218,13 @@ __global__ void query_prep(PrepArgs a)
         }
         pre[kPreSeg][i] = __longlong_as_double(in.seg_id[i]);
         pre[kPreTraj][i] = __longlong_as_double(in.traj_id ? in.traj_id[i] : 0);
-        if (valid && a.ranges) candidate_range(bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
+        if (valid && a.ranges) {
+            candidate_range(bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
+            if (!TDQ_DBG(ctr, kDbgRange, rhi <= rlo || (rlo >= 0 && rhi <= (int64_t)a.n_entries))) {
+                rlo = INT64_MAX;
+                rhi = INT64_MIN;
+            }
+        }
     }
     if (i < nq && a.ranges) {
         pre[kPreLo][i] = __longlong_as_double(rlo);
@@ -277,6 +283,7 @@ __global__ void query_scatter(ScatterArgs a)
     const int64_t ts = __double_as_longlong(a.pre[7][i]), te = __double_as_longlong(a.pre[8][i]);
     if (!(ts < te)) return;  // invalid or padding: not sorted
     const uint64_t k = (uint64_t)a.bin_off[a.keys[i]] + a.ranks[i];
+    if (!TDQ_DBG(a.ctr, kDbgScatterPos, k < a.ctr->valid_queries)) return;
     QuerySoA &q = a.q;
     q.px[k] = a.pre[0][i]; q.py[k] = a.pre[1][i]; q.pz[k] = a.pre[2][i];
     q.vx[k] = a.pre[3][i]; q.vy[k] = a.pre[4][i]; q.vz[k] = a.pre[5][i];
@@ -307,7 +314,7 @@ __global__ void query_gather(GatherArgs a)
             rlo = a.srt_lo[k];
             rhi = a.srt_hi[k];
         }
-    } else if (k < a.nq && k < a.ctr->valid_queries) {
+    } else if (k < a.nq && k < a.ctr->valid_queries && TDQ_DBG(a.ctr, kDbgGatherOrder, a.order[k] < a.nq)) {
         const uint32_t i = a.order[k];
         q.px[k] = a.pre[0][i]; q.py[k] = a.pre[1][i]; q.pz[k] = a.pre[2][i];
         q.vx[k] = a.pre[3][i]; q.vy[k] = a.pre[4][i]; q.vz[k] = a.pre[5][i];
@@ -472,11 +479,14 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_search_kernel(PairArgs
         const long long item = S.item;
         if ((unsigned long long)item >= total) break;
         const uint64_t t = (uint64_t)S.tile;
+        if (!TDQ_DBG(ctr, kDbgPlainTile, t < args.ntiles)) break;  // (S.tile: the block agrees)
         const int64_t e0 = args.tile_lo[t] + (int64_t)(item - (long long)args.tile_work[t]) * EC;
         const int64_t e1 = min(e0 + (int64_t)EC, args.tile_hi[t]);
         const int ne = (int)(e1 - e0);
         const uint64_t q0 = t * kQT;
         const int nqt = (int)min((uint64_t)kQT, nvalid - q0);
+        if (!TDQ_DBG(ctr, kDbgPlainChunk, e0 >= 0 && e0 < e1 && e1 <= (int64_t)args.n_entries)) break;
+        if (!TDQ_DBG(ctr, kDbgPlainQueries, nqt > 0 && q0 + nqt <= args.nq_slots)) break;
 
         // stage the tile's query segments
         if (tid < kQT) {
@@ -762,14 +772,14 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     const bool tc = cfg.tc && idx->n > 0;
     query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
         PrepArgs{in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr, fuse ? w.sort_fused_hist : nullptr,
-                 idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr});
+                 idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr, idx->n});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     const uint64_t nsuper = (nq + 127) / 128;
     if (idx->n > 0) {
         if (csort) {
             query_scatter<<<grid_for(nq), kBlock, 0, stream>>>(ScatterArgs{
                 pre, w.pre_sph, w.pre_tc, w.keys, w.vals, w.bin_cnt, nq, w.q, tc ? w.q.tc_rec : nullptr, w.srt_lo,
-                w.srt_hi});
+                w.srt_hi, w.ctr});
         } else if ((e = radix_sort_pairs(w.keys, w.vals, w.keys_alt, w.vals_alt, nq, w.sort_hist, stream,
                                          bin_key_bits(idx->m), &w.ctr->sort_n,
                                          fuse ? w.sort_fused_hist : nullptr)) != cudaSuccess) {
@@ -780,11 +790,11 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                             csort ? w.srt_lo : nullptr, csort ? w.srt_hi : nullptr};
         query_gather<<<grid_for(tc ? nsuper * 128 : nq), kBlock, 0, stream>>>(ga);
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags,
-                    w.ctr_host_dev};
+                    w.ctr_host_dev, idx->n, nq};
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
         if (tc)
             e = launch_tc_filter_kernels(TcArgs{pa, idx->e.tc_rec, w.q.tc_rec, w.st_lo, w.st_hi, w.st_work, nsuper,
-                                                w.surv, w.s_cap_pairs},
+                                                w.surv, w.s_cap_pairs, idx->n_rec},
                                          idx->sm_count, stream, events ? w.ev[2] : nullptr, evflags);
         else
             e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
@@ -811,6 +821,8 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
         return set_error(TDQ_ERR_INVALID,
                          "tdq_search: invalid query segment (non-finite value, t_end <= t_start, d < 0 or NaN, "
                          "NaN window or t0 > t1)");
+    if (h.error & 4u)
+        return set_error(TDQ_ERR_CUDA, "tdq_search: debug build: index bounds check at site %u failed", h.debug_site);
     if (h.error & 2u)
         return set_error(TDQ_ERR_TIMEOUT,
                          "tdq_search: a wait of the tensor-core pre-test pipeline ran out of time (the search "
@@ -866,7 +878,7 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
     const bool csort = idx->n > 0 && idx->m <= kCountSortMaxBins;
     PrepArgs a0{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, w.vals, w.ctr,
                 !csort && idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter,
-                cfg.tc && idx->n > 0 ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr};
+                cfg.tc && idx->n > 0 ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr, idx->n};
     void *args[] = {&a0};
     cudaKernelNodeParams kp{};
     kp.func = (void *)query_prep;

@@ -271,6 +271,11 @@ __device__ bool tc_load_all(const TcArgs &a, TcSmem &sm, unsigned long long ibeg
     bool ok = true;
     b_loaded = 0;
     while (h) {
+        if (!TDQ_DBG(a.p.ctr, kDbgTcRecords, r.p0 >= 0 && (uint64_t)(r.p0 + (int64_t)kTcM * (p + 1)) <= a.n_rec) ||
+            !TDQ_DBG(a.p.ctr, kDbgTcSuper, r.s < a.nsuper)) {
+            ok = false;
+            break;
+        }
         if (p == 0) {
             const uint32_t bb = rix & 1;
             if (rix >= 2 && !(ok = bar_wait(&sm.b_free[bb], ((rix - 2) >> 1) & 1, abort))) break;
@@ -489,11 +494,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
                     if (!hit) continue;
                     uint32_t m = signs32(k ? v1 : v0);
                     if (nq[k] < 32) m &= (1u << nq[k]) - 1u;
+                    const uint32_t e = (uint32_t)(r.p0 + el);
+                    const uint32_t q0 = (uint32_t)((r.s * kTcTiles + 2 * half + k) * kQT);
+                    // (the highest set bit of m is the last query slot used)
+                    if (m && !TDQ_DBG(ctr, kDbgTcSurvivor, e < args.n_entries && q0 + 32 - __clz(m) <= nvalid)) m = 0u;
                     const int cnt = __popc(m);
                     if (!cnt) continue;
                     int pos = (int)atoms_add_u32(nsurv_s, (uint32_t)cnt);
-                    const uint32_t e = (uint32_t)(r.p0 + el);
-                    const uint32_t q0 = (uint32_t)((r.s * kTcTiles + 2 * half + k) * kQT);
                     while (m) {
                         const int bit = __ffs(m) - 1;
                         m &= m - 1;

@@ -157,9 +157,46 @@ struct DevCounters {
     unsigned long long mma_issued;     // tensor-core pre-test: MMAs issued
     unsigned long long prep_done;      // blocks of query_prep that have finished (the last one scans the
                                        // bin counts of the counting sort)
-    unsigned int error;                // bit 0: invalid query input; bit 1: a pipeline wait ran out
-    unsigned int pad;
+    unsigned int error;                // bit 0: invalid query input; bit 1: a pipeline wait ran out;
+                                       // bit 2 (debug build): an index bounds check failed
+    unsigned int debug_site;           // debug build: the first failed check's site (TdqDebugSite)
 };
+
+// Bounds checks of the debug build (compiled with -DTDQ_DEBUG; the GPU
+// counterpart of a memory checker, which this library's tests cannot use).
+// TDQ_DBG(ctr, site, cond) is the constant true in normal builds; in the
+// debug build it evaluates cond and, when it fails, sets error bit 2 and
+// records the first failing site, so that the guarded access is skipped and
+// the host reports TDQ_ERR_CUDA naming the site -- never a trap.
+enum TdqDebugSite : unsigned {
+    kDbgPlainTile = 1,      // plain kernel: tile index < tiles
+    kDbgPlainChunk = 2,     // plain kernel: entry chunk inside the entries
+    kDbgPlainQueries = 3,   // plain kernel: the tile's query slots inside the sorted queries
+    kDbgFilterRun = 4,      // FP32 pre-test: a run's entries inside the entries
+    kDbgFilterNext = 5,     // FP32 pre-test: the prefetched pass inside the entries
+    kDbgFilterQuery = 6,    // FP32 pre-test: a survivor's query inside the valid queries
+    kDbgFilterBuf = 7,      // FP32 pre-test: survivor buffer slot
+    kDbgRefine = 8,         // refine: a survivor's entry and query positions
+    kDbgGatherOrder = 9,    // query_gather: sorted order inside the query slots
+    kDbgScatterPos = 10,    // query_scatter: sorted position inside the valid queries
+    kDbgRange = 11,         // query_prep: candidate range inside the entries
+    kDbgTcRecords = 12,     // tensor-core pre-test: a pass's entry records inside the records
+    kDbgTcSuper = 13,       // tensor-core pre-test: supertile index
+    kDbgTcSurvivor = 14,    // tensor-core pre-test: a survivor's entry and query positions
+};
+#ifdef TDQ_DEBUG
+__device__ __forceinline__ bool dbg_check(DevCounters *c, unsigned site, bool ok)
+{
+    if (!ok) {
+        atomicOr(&c->error, 4u);
+        atomicCAS(&c->debug_site, 0u, site);
+    }
+    return ok;
+}
+#define TDQ_DBG(ctr, site, cond) (::tdq::dbg_check((ctr), (site), (cond)))
+#else
+#define TDQ_DBG(ctr, site, cond) (true)
+#endif
 
 // Sorted entry segments in device memory (structure of arrays).
 struct EntrySoA {
