@@ -410,6 +410,25 @@ tdq_status tdq_server_create(tdq_index *idx, const tdq_server_params *params, td
 tdq_status tdq_server_submit(tdq_server *srv, const tdq_segments *queries, double d, double t0, double t1,
                              uint64_t *ticket);
 
+/* Queue `count` requests in one call (the paper's setting of many users
+ * querying one resident database, Sec. 3; one call instead of one per
+ * request, so that a caller's per-call cost does not bound the server).
+ * Request k is query segments [offsets[k], offsets[k+1]) of `queries` (host
+ * memory, copied; offsets has count + 1 non-decreasing entries starting at
+ * 0 and ending at queries->n) with threshold d[k] and window [t0[k], t1[k]].
+ * Every request is validated as by tdq_server_submit before any is queued:
+ * on an error nothing is queued and TDQ_ERR_INVALID names the first bad
+ * request.  tickets (count entries) receive the requests' tickets, for
+ * tdq_server_wait. */
+tdq_status tdq_server_submit_many(tdq_server *srv, const tdq_segments *queries, const uint64_t *offsets,
+                                  uint64_t count, const double *d, const double *t0, const double *t1,
+                                  uint64_t *tickets);
+
+/* Wait (timeout_ms < 0: no limit) until every request submitted so far has
+ * finished its search (its results then wait for tdq_server_wait).
+ * TDQ_ERR_TIMEOUT if not in time. */
+tdq_status tdq_server_drain(tdq_server *srv, int64_t timeout_ms);
+
 /* Wait for a request (timeout_ms < 0: no limit) and take its results (host,
  * library-owned, release with tdq_results_free) and timings.
  * TDQ_ERR_TIMEOUT if not done in time (the request stays queued/running and

@@ -319,6 +319,91 @@ extern "C" tdq_status tdq_server_submit(tdq_server *s, const tdq_segments *queri
     return TDQ_OK;
 }
 
+extern "C" tdq_status tdq_server_submit_many(tdq_server *s, const tdq_segments *queries, const uint64_t *offsets,
+                                             uint64_t count, const double *d, const double *t0, const double *t1,
+                                             uint64_t *tickets)
+{
+    if (!s || !queries || !offsets || !d || !t0 || !t1 || !tickets)
+        return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: NULL argument");
+    if (queries->on_device)
+        return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: queries must be in host memory");
+    if (count == 0) return TDQ_OK;
+    const double *cols[8] = {queries->xs, queries->ys, queries->zs, queries->ts,
+                             queries->xe, queries->ye, queries->ze, queries->te};
+    for (int c = 0; c < 8; c++)
+        if (!cols[c]) return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: query column %d is NULL", c);
+    if (!queries->seg_id) return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: seg_id is NULL");
+    if (offsets[0] != 0 || offsets[count] != queries->n)
+        return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: offsets must run from 0 to queries->n");
+    // validate every request first: all or nothing is queued
+    for (uint64_t k = 0; k < count; k++) {
+        const uint64_t a = offsets[k], b = offsets[k + 1];
+        if (b < a || b - a == 0 || b - a > s->prm.max_batch_query_segments)
+            return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: request %llu needs 1..%llu query segments",
+                             (unsigned long long)k, (unsigned long long)s->prm.max_batch_query_segments);
+        tdq_segments sub = *queries;
+        sub.xs = cols[0] + a; sub.ys = cols[1] + a; sub.zs = cols[2] + a; sub.ts = cols[3] + a;
+        sub.xe = cols[4] + a; sub.ye = cols[5] + a; sub.ze = cols[6] + a; sub.te = cols[7] + a;
+        sub.seg_id = queries->seg_id + a;
+        sub.n = b - a;
+        if (!valid_request(&sub, d[k], t0[k], t1[k]))
+            return set_error(TDQ_ERR_INVALID,
+                             "tdq_server_submit_many: request %llu: invalid query segment, threshold or window",
+                             (unsigned long long)k);
+    }
+    std::vector<Request *> made;
+    made.reserve(count);
+    for (uint64_t k = 0; k < count; k++) {
+        Request *r = new (std::nothrow) Request();
+        if (!r) {
+            for (Request *x : made) delete x;
+            return set_error(TDQ_ERR_NOMEM, "tdq_server_submit_many: host allocation failed");
+        }
+        const uint64_t a = offsets[k];
+        r->n = offsets[k + 1] - a;
+        for (int c = 0; c < 8; c++) r->cols[c].assign(cols[c] + a, cols[c] + a + r->n);
+        r->seg_id.assign(queries->seg_id + a, queries->seg_id + a + r->n);
+        r->d = d[k];
+        r->t0 = t0[k];
+        r->t1 = t1[k];
+        made.push_back(r);
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) {
+            for (Request *x : made) delete x;
+            return set_error(TDQ_ERR_INVALID, "tdq_server_submit_many: server is stopping");
+        }
+        const Clock::time_point now = Clock::now();
+        for (uint64_t k = 0; k < count; k++) {
+            Request *r = made[k];
+            r->t_submit = now;
+            r->est_bytes = estimate_bytes(s, r->n);
+            r->ticket = s->next_ticket++;
+            s->reqs[r->ticket] = r;
+            s->queue.push_back(r);
+            tickets[k] = r->ticket;
+        }
+        s->st.requests_submitted += count;
+    }
+    s->cv_work.notify_all();
+    return TDQ_OK;
+}
+
+extern "C" tdq_status tdq_server_drain(tdq_server *s, int64_t timeout_ms)
+{
+    if (!s) return set_error(TDQ_ERR_INVALID, "tdq_server_drain: NULL argument");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto idle = [&] { return s->queue.empty() && s->running_batches == 0; };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, idle);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle)) {
+        return set_error(TDQ_ERR_TIMEOUT, "tdq_server_drain: requests still queued or running after %lld ms",
+                         (long long)timeout_ms);
+    }
+    return TDQ_OK;
+}
+
 extern "C" tdq_status tdq_server_wait(tdq_server *s, uint64_t ticket, int64_t timeout_ms, tdq_results **out,
                                       tdq_request_info *info)
 {

@@ -145,6 +145,8 @@ SIGNATURES = {
     "tdq_autotune": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
     "tdq_server_create": (ctypes.c_int, [P, P, P]),
     "tdq_server_submit": (ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]),
+    "tdq_server_submit_many": (ctypes.c_int, [P, P, P, ctypes.c_uint64, P, P, P, P]),
+    "tdq_server_drain": (ctypes.c_int, [P, ctypes.c_int64]),
     "tdq_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_int64, P, P]),
     "tdq_server_get_stats": (ctypes.c_int, [P, P]),
     "tdq_server_free": (None, [P]),
@@ -680,6 +682,29 @@ class Server:
         t = ctypes.c_uint64()
         _check(load().tdq_server_submit(self._h, ctypes.byref(s), float(d), float(t0), float(t1), ctypes.byref(t)))
         return int(t.value)
+
+    def submit_many(self, queries, d, t0, t1) -> list:
+        """tdq_server_submit_many: queue several requests in one call;
+        queries is a list of Segments (one per request), d / t0 / t1 one
+        value per request.  Returns their tickets."""
+        k = len(queries)
+        if k == 0:
+            return []
+        cat = Segments.concat(list(queries))
+        offs = np.zeros(k + 1, np.uint64)
+        offs[1:] = np.cumsum([len(q) for q in queries])
+        dd, a0, a1 = (np.ascontiguousarray(np.asarray(x, np.float64)) for x in (d, t0, t1))
+        assert len(dd) == len(a0) == len(a1) == k
+        tickets = np.zeros(k, np.uint64)
+        q = HostSegments(cat)
+        s = q.struct()
+        _check(load().tdq_server_submit_many(self._h, ctypes.byref(s), offs.ctypes.data, k, dd.ctypes.data,
+                                             a0.ctypes.data, a1.ctypes.data, tickets.ctypes.data))
+        return [int(t) for t in tickets]
+
+    def drain(self, timeout_ms: int = -1) -> None:
+        """tdq_server_drain: wait until every submitted request has been searched."""
+        _check(load().tdq_server_drain(self._h, int(timeout_ms)))
 
     def wait(self, ticket: int, timeout_ms: int = -1):
         """Results and timing info of a request (raises TdqError with

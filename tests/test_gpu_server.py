@@ -112,6 +112,31 @@ def test_memory_cap_admits_one_request_at_a_time(tdq, db, requests):
             _same(g, tdq.search(idx, rq.query, rq.d, rq.t0, rq.t1))
 
 
+def test_submit_many_equals_one_by_one_and_is_all_or_nothing(tdq, db, requests):
+    """tdq_server_submit_many queues many requests in one call: each
+    request's results equal those of its own submit; a batch holding one
+    invalid request queues nothing; tdq_server_drain returns once every
+    request has been searched."""
+    rq = requests[:24]
+    with tdq.build_index(db) as idx, tdq.Server(idx, lanes=2) as srv:
+        one = [srv.wait(srv.submit(r.query, r.d, r.t0, r.t1))[0] for r in rq]
+        tickets = srv.submit_many([r.query for r in rq], [r.d for r in rq], [r.t0 for r in rq], [r.t1 for r in rq])
+        srv.drain()
+        st = srv.stats()
+        assert st["requests_completed"] == 2 * len(rq) and st["queued"] == 0
+        many = [srv.wait(t, 0)[0] for t in tickets]  # done already: no waiting
+        bad_d = [r.d for r in rq]
+        bad_d[5] = -1.0
+        before = srv.stats()["requests_submitted"]
+        with pytest.raises(tdq.TdqError) as ei:
+            srv.submit_many([r.query for r in rq], bad_d, [r.t0 for r in rq], [r.t1 for r in rq])
+        assert ei.value.status == tdq.TDQ_ERR_INVALID and "request 5" in str(ei.value)
+        assert srv.stats()["requests_submitted"] == before
+    assert sum(len(a) for a in one) > 0
+    for a, b in zip(one, many):
+        _same(a, b)
+
+
 def test_timeouts_and_invalid_requests_are_reported_on_the_host(tdq, db, requests):
     with tdq.build_index(db) as idx, tdq.Server(idx, lanes=1, max_batch_query_segments=512) as srv:
         rq = requests[0]
