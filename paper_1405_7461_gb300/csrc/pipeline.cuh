@@ -60,6 +60,25 @@ struct PrepArgs {
     uint64_t n_entries;  // entries of the index (bound of the debug build's range check)
 };
 
+// Query slots up to which a search is prepared in one launch
+// (query_prep_small): blocks of kSmallPrep threads whose first
+// kSmallPrepWarps warps prepare a slot each, the last block sorting and
+// planning all of them.
+constexpr int kSmallPrep = 1024;
+constexpr int kSmallPrepWarps = 4;
+
+// Arguments of query_prep_small: those of query_prep (keys: the slots' sort
+// words; vals, sort_hist and bin_cnt unused), the sorted query columns and
+// the tile plan.
+struct SmallPrepArgs {
+    PrepArgs p;
+    double *cols[kPreCols];  // the pre columns (p.pre's table, by value)
+    QuerySoA q;
+    int64_t *tile_lo, *tile_hi;
+    unsigned long long *tile_work;  // exclusive offsets of the tiles' chunks, the total last; ntiles + 1
+    uint32_t chunk;
+};
+
 // Arguments of query_scatter (counting sort): every valid query segment's
 // columns to its sorted position bin offset + rank.
 struct ScatterArgs {

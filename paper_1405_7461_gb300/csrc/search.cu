@@ -121,31 +121,30 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     if (count_overlaps && jhi >= 0) n_overlap = (unsigned long long)(b_lo - c_lo);
 }
 
-// Validate and clip every query segment into the pre columns (see kPreCols;
-// keys stored bitwise in the double arrays); with a.ranges also its candidate
-// range and, with a.count_overlaps, its exact temporal-overlap count.
-__global__ void query_prep(PrepArgs a)
+// One query slot's preparation: validation and clipping into the pre
+// columns (see kPreCols; keys stored bitwise in the double arrays), the FP32
+// bounding sphere (and with a.pre_tc the tensor-core record), the sort key
+// -- the temporal bin of the clipped start, bins.m for invalid segments and
+// padding -- and, with a.ranges, the candidate range (also into the pre
+// columns) and with a.count_overlaps the exact temporal-overlap count.
+// Returns whether the slot holds a valid segment with a non-empty clipped
+// span.  Slots at or beyond nreal are padding: empty, not errors.
+__device__ __forceinline__ bool prep_slot(const PrepArgs &a, uint64_t i, uint64_t nreal, uint64_t &key,
+                                          unsigned long long &n_overlap)
 {
     const QueryInput &in = a.in;
-    const uint64_t nq = a.nq;
     const BinView &bins = a.bins;
     double *const *pre = a.pre;
     DevCounters *ctr = a.ctr;
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
     int64_t rlo = INT64_MAX, rhi = INT64_MIN;
-    unsigned long long n_overlap = 0;
-    uint32_t digit = 256;  // low byte of the sort key (256: not sorted)
-    // slots at or beyond the device-side count are padding: empty, not errors
-    const uint64_t nreal = in.n_real ? in.n_real : nq;
-    if (i == 0) ctr->sort_n = nreal < nq ? nreal : nq;
-    if (i < nq && i >= nreal) {
+    key = bins.m;
+    n_overlap = 0;
+    if (i >= nreal) {
         pre[7][i] = __longlong_as_double(INT64_MAX);
         pre[8][i] = __longlong_as_double(INT64_MIN);
         a.pre_sph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        a.keys[i] = (uint64_t)bins.m;
-        a.vals[i] = (uint32_t)i;
-    } else if (i < nq) {
+    } else {
         bool ok = true;
         double c[8];
 #pragma unroll
@@ -204,17 +203,9 @@ __global__ void query_prep(PrepArgs a)
         // sort key: the temporal bin of the clipped start, in FP32 (it only
         // groups the segments into tiles of 32 that span few bins); invalid
         // segments sort last
-        uint64_t key = bins.m;
         if (valid) {
             const float f = floorf(__double2float_rn(key_double(cs) - bins.t_min) * bins.inv_width_f);
             key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
-        }
-        a.keys[i] = key;
-        if (a.bin_cnt) {
-            if (valid) a.vals[i] = atomicAdd(&a.bin_cnt[key], 1u);
-        } else {
-            a.vals[i] = (uint32_t)i;
-            digit = (uint32_t)(key & 0xff);
         }
         pre[kPreSeg][i] = __longlong_as_double(in.seg_id[i]);
         pre[kPreTraj][i] = __longlong_as_double(in.traj_id ? in.traj_id[i] : 0);
@@ -226,9 +217,39 @@ __global__ void query_prep(PrepArgs a)
             }
         }
     }
-    if (i < nq && a.ranges) {
+    if (a.ranges) {
         pre[kPreLo][i] = __longlong_as_double(rlo);
         pre[kPreHi][i] = __longlong_as_double(rhi);
+    }
+    return valid;
+}
+
+// Validate and clip every query segment into the pre columns (prep_slot),
+// with its sort key and place: the counting sort's rank inside its bin, or
+// the radix sort's first digit counts.
+__global__ void query_prep(PrepArgs a)
+{
+    const uint64_t nq = a.nq;
+    DevCounters *ctr = a.ctr;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false;
+    unsigned long long n_overlap = 0;
+    uint32_t digit = 256;  // low byte of the sort key (256: not sorted)
+    // slots at or beyond the device-side count are padding: empty, not errors
+    const uint64_t nreal = a.in.n_real ? a.in.n_real : nq;
+    if (i == 0) ctr->sort_n = nreal < nq ? nreal : nq;
+    if (i < nq) {
+        uint64_t key;
+        valid = prep_slot(a, i, nreal, key, n_overlap);
+        a.keys[i] = key;
+        if (i >= nreal) {
+            a.vals[i] = (uint32_t)i;
+        } else if (a.bin_cnt) {
+            if (valid) a.vals[i] = atomicAdd(&a.bin_cnt[key], 1u);
+        } else {
+            a.vals[i] = (uint32_t)i;
+            digit = (uint32_t)(key & 0xff);
+        }
     }
     const unsigned vm = __ballot_sync(kFull, valid);
 #pragma unroll
@@ -246,7 +267,7 @@ __global__ void query_prep(PrepArgs a)
         __syncthreads();
         if (last) {
             __threadfence();
-            block_exclusive_scan<uint32_t, kBlock, 8>(a.bin_cnt, bins.m, nullptr);
+            block_exclusive_scan<uint32_t, kBlock, 8>(a.bin_cnt, a.bins.m, nullptr);
         }
     } else if (a.sort_hist) {  // this block's keys lie in one sort tile (blockDim divides kSortTileKeys)
         __shared__ uint32_t h[256];
@@ -257,6 +278,149 @@ __global__ void query_prep(PrepArgs a)
         uint32_t *th = a.sort_hist + (uint64_t)blockIdx.x * blockDim.x / kSortTileKeys * 256;
         for (int d = threadIdx.x; d < 256; d += blockDim.x)
             if (h[d]) atomicAdd(&th[d], h[d]);
+    }
+}
+
+// A search of at most kSmallPrep query slots is prepared in one launch: the
+// first kSmallPrepWarps warps of each block prepare kSmallPrepWarps x 32
+// slots (prep_slot) -- one warp per scheduler of an SM, as the per-slot
+// FP64 arithmetic is a long dependent chain on a narrow FP64 pipe -- and the
+// block that finishes last sorts the valid segments by (bin, slot) in shared
+// memory, writes the sorted columns and plans the tiles.  This replaces the
+// bin counters' clear and the three kernels of the multi-block preparation,
+// whose fixed costs dominate small searches (a serving request).  The sort
+// is a bitonic network over the 64-bit words (bin << 32 | slot), invalid
+// slots all ones, on the next power of two above the slots: exchanges
+// between lanes by shuffles, between warps through shared memory.
+__global__ void __launch_bounds__(kSmallPrep) query_prep_small(SmallPrepArgs s)
+{
+    const PrepArgs &a = s.p;
+    DevCounters *ctr = a.ctr;
+    __shared__ unsigned long long sk[kSmallPrep];
+    __shared__ unsigned long long tw[kSmallPrep / kQT];
+    __shared__ int wv[kSmallPrep / 32];
+    __shared__ bool last;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint64_t nq = a.nq;  // at most kSmallPrep (host-checked)
+    // slots at or beyond the device-side count are padding: not prepared, not sorted
+    const uint64_t nreal = a.in.n_real && a.in.n_real < nq ? a.in.n_real : nq;
+    if (warp < kSmallPrepWarps) {
+        const uint64_t i = (uint64_t)blockIdx.x * (kSmallPrepWarps * 32) + t;
+        bool valid = false;
+        unsigned long long n_overlap = 0;
+        uint64_t key = a.bins.m;
+        if (i < nreal) {
+            valid = prep_slot(a, i, nreal, key, n_overlap);
+            a.keys[i] = valid ? (key << 32) | i : ~0ull;  // sort word (bins.m < 2^32)
+        }
+        const unsigned vm = __ballot_sync(kFull, valid);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
+        if (lane == 0) {
+            if (vm) atomicAdd(&ctr->valid_queries, (unsigned long long)__popc(vm));
+            if (n_overlap) atomicAdd(&ctr->overlap_pairs, n_overlap);
+        }
+    }
+    if (gridDim.x > 1) __threadfence();
+    __syncthreads();
+    // one block: it is the last; more: the one that finishes last goes on
+    if (t == 0) last = gridDim.x == 1 || atomicAdd(&ctr->prep_done, 1ULL) == (unsigned long long)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    if (gridDim.x > 1) __threadfence();
+    // the last block: every slot's pre columns and sort word are in place
+    const int nvalid = (int)*(volatile unsigned long long *)&ctr->valid_queries;
+    unsigned long long v = (uint64_t)t < nreal ? *(volatile unsigned long long *)&a.keys[t] : ~0ull;
+    // The slots of a request come in time order, so that their bins are
+    // mostly in order already: the valid words are compacted in slot order
+    // (a block scan of the valid flags) and, if their bins never decrease,
+    // that is the sorted order; else the network sorts them.
+    const bool vt = v != ~0ull;
+    const unsigned vb = __ballot_sync(kFull, vt);
+    if (lane == 0) wv[warp] = __popc(vb);
+    __syncthreads();
+    int pos = __popc(vb & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; w++) pos += wv[w];
+    if (vt) sk[pos] = v;
+    __syncthreads();
+    const bool in_order = __syncthreads_and(t + 1 >= nvalid || (sk[t] >> 32) <= (sk[t + 1] >> 32));
+    int n2 = in_order ? 0 : 2;
+    while (n2 && (uint64_t)n2 < nreal) n2 <<= 1;  // block-uniform
+    if (in_order) v = t < nvalid ? sk[t] : ~0ull;
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            unsigned long long o;
+            if (j >= 32) {
+                __syncthreads();  // the previous exchange's reads are done
+                sk[t] = v;
+                __syncthreads();
+                o = sk[t ^ j];
+            } else if ((warp << 5) < n2) {  // whole warps (lanes at or above n2 hold all ones)
+                o = __shfl_xor_sync(kFull, v, j);
+            } else {
+                o = v;
+            }
+            // the lower slot of a pair keeps the minimum in an ascending run
+            // (threads at or above n2 hold all ones among themselves)
+            v = (((t & j) == 0) == ((t & k) == 0)) ? min(v, o) : max(v, o);
+        }
+    }
+    // sorted position t: the slot of the t-th valid segment (in bin order)
+    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
+    if (t < nvalid) {
+        const uint32_t sl = (uint32_t)v;
+        if (TDQ_DBG(ctr, kDbgSmallSlot, (uint64_t)sl < nreal)) {
+            double *const *pre = s.cols;
+            QuerySoA &q = s.q;
+            q.px[t] = pre[0][sl]; q.py[t] = pre[1][sl]; q.pz[t] = pre[2][sl];
+            q.vx[t] = pre[3][sl]; q.vy[t] = pre[4][sl]; q.vz[t] = pre[5][sl];
+            q.d2[t] = pre[6][sl];
+            q.ts_key[t] = __double_as_longlong(pre[7][sl]);
+            q.te_key[t] = __double_as_longlong(pre[8][sl]);
+            q.qid[t] = __double_as_longlong(pre[kPreSeg][sl]);
+            if (q.qtraj) q.qtraj[t] = __double_as_longlong(pre[kPreTraj][sl]);
+            q.sph[t] = a.pre_sph[sl];
+            rlo = __double_as_longlong(pre[kPreLo][sl]);
+            rhi = __double_as_longlong(pre[kPreHi][sl]);
+        }
+    }
+    // tile plan: warp w plans tile w (the union of its members' ranges, cut
+    // into chunks), then warp 0 turns the chunk counts into offsets
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rlo = min(rlo, (int64_t)__shfl_xor_sync(kFull, (long long)rlo, o));
+        rhi = max(rhi, (int64_t)__shfl_xor_sync(kFull, (long long)rhi, o));
+    }
+    const int ntiles = (int)((nq + kQT - 1) / kQT);
+    if (lane == 0) {
+        unsigned long long w = 0;
+        if (warp < ntiles) {
+            if (rhi > rlo) {
+                w = (unsigned long long)((rhi - rlo + s.chunk - 1) / s.chunk);
+            } else {
+                rlo = 0;
+                rhi = 0;
+            }
+            s.tile_lo[warp] = rlo;
+            s.tile_hi[warp] = rhi;
+        }
+        tw[warp] = w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long x = tw[lane];
+        unsigned long long incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane < ntiles) s.tile_work[lane] = incl - x;
+        if (lane == 31) {
+            s.tile_work[ntiles] = incl;
+            ctr->work_items = incl;
+            ctr->sort_n = nreal < nq ? nreal : nq;
+        }
     }
 }
 
@@ -735,13 +899,54 @@ tdq_status parse_params(const tdq_search_params *params, LaunchCfg *cfg)
     return TDQ_OK;
 }
 
+namespace {
+
+// Whether a search of nq query slots is prepared by query_prep_small (not
+// for the tensor-core pre-test, whose supertile records and plan come from
+// the multi-block preparation).
+bool small_prep(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
+{
+    return idx->n > 0 && !cfg.tc && nq >= 1 && nq <= (uint64_t)kSmallPrep;
+}
+
+// The preparation kernel's arguments (a launch and the re-binding of a
+// captured one build them here alike).
+PrepArgs prep_args(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq, const LaunchCfg &cfg)
+{
+    const bool csort = idx->n > 0 && idx->m <= kCountSortMaxBins;
+    const bool fuse = !csort && idx->n > 0 && sort_fusable(nq);
+    const bool tc = cfg.tc && idx->n > 0;
+    return PrepArgs{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, w.vals, w.ctr,
+                    fuse ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid,
+                    csort ? w.bin_cnt : nullptr, idx->n};
+}
+
+unsigned small_prep_blocks(uint64_t nq)
+{
+    const uint64_t per = (uint64_t)kSmallPrepWarps * 32;
+    return (unsigned)((nq + per - 1) / per);
+}
+
+SmallPrepArgs small_prep_args(const tdq_index *idx, Workspace &w, const QueryInput &in, uint64_t nq,
+                              const LaunchCfg &cfg)
+{
+    PrepArgs p{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, nullptr, w.ctr, nullptr, true, cfg.filter,
+               nullptr, idx->grid, nullptr, idx->n};
+    SmallPrepArgs sa{p, {}, w.q, w.tile_lo, w.tile_hi, w.tile_work, cfg.chunk};
+    for (int c = 0; c < kPreCols; c++) sa.cols[c] = w.pre[c];
+    return sa;
+}
+
+}  // namespace
+
 int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
 {
+    if (small_prep(idx, cfg, nq)) return 1 + (cfg.filter ? 2 : 1);  // query_prep_small, the pair kernel(s)
     // without entries: query_prep and publish_counters; with entries:
     // query_prep, the sort of the query keys (counting sort: query_scatter;
     // else the radix sort's kernels), query_gather and the pair kernel
     // (filter mode: filter and refine), whose last block publishes the
-    // counters
+    // counters; a small search: query_prep_small and the pair kernel(s)
     const int sort = idx->m <= kCountSortMaxBins ? 1 : sort_kernel_launches(nq, bin_key_bits(idx->m), true);
     return idx->n > 0 ? 2 + sort + (cfg.filter ? 2 : 1) : 2;
 }
@@ -757,9 +962,10 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     const unsigned evflags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     // the counters, and with the radix sort's small path its two fused
     // histograms (counting sort: the bin counts)
-    const bool csort = idx->n > 0 && idx->m <= kCountSortMaxBins;
+    const bool small = small_prep(idx, cfg, nq);
+    const bool csort = !small && idx->n > 0 && idx->m <= kCountSortMaxBins;
     if (csort && (!w.bin_cnt || w.bin_cap < idx->m)) return cudaErrorInvalidValue;  // workspace not sized
-    const bool fuse = !csort && idx->n > 0 && sort_fusable(nq);
+    const bool fuse = !small && !csort && idx->n > 0 && sort_fusable(nq);
     const uint64_t sort_tiles = (nq + kSortTileKeys - 1) / kSortTileKeys;
     e = cudaMemsetAsync(w.ctr, 0, fuse ? kCtrBytes + 2 * sort_tiles * 256 * sizeof(uint32_t) : sizeof(DevCounters),
                         stream);
@@ -768,15 +974,17 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
         return e;
     if (events && (e = cudaEventRecordWithFlags(w.ev[0], stream, evflags)) != cudaSuccess) return e;
     double *const *pre = w.pre_dev;
-    const BinView bins = bin_view(idx);
     const bool tc = cfg.tc && idx->n > 0;
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
-        PrepArgs{in, nq, bins, pre, w.pre_sph, w.keys, w.vals, w.ctr, fuse ? w.sort_fused_hist : nullptr,
-                 idx->n > 0, cfg.filter, tc ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr, idx->n});
+    if (small)
+        query_prep_small<<<small_prep_blocks(nq), kSmallPrep, 0, stream>>>(small_prep_args(idx, w, in, nq, cfg));
+    else
+        query_prep<<<grid_for(nq), kBlock, 0, stream>>>(prep_args(idx, w, in, nq, cfg));
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     const uint64_t nsuper = (nq + 127) / 128;
     if (idx->n > 0) {
-        if (csort) {
+        if (small) {
+            // sorted and planned already
+        } else if (csort) {
             query_scatter<<<grid_for(nq), kBlock, 0, stream>>>(ScatterArgs{
                 pre, w.pre_sph, w.pre_tc, w.keys, w.vals, w.bin_cnt, nq, w.q, tc ? w.q.tc_rec : nullptr, w.srt_lo,
                 w.srt_hi, w.ctr});
@@ -785,10 +993,12 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                          fuse ? w.sort_fused_hist : nullptr)) != cudaSuccess) {
             return e;
         }
-        const GatherArgs ga{pre, w.pre_sph, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk, w.tile_lo, w.tile_hi,
-                            w.tile_work, w.pre_tc, tc ? w.q.tc_rec : nullptr, w.st_lo, w.st_hi, w.st_work, nsuper,
-                            csort ? w.srt_lo : nullptr, csort ? w.srt_hi : nullptr};
-        query_gather<<<grid_for(tc ? nsuper * 128 : nq), kBlock, 0, stream>>>(ga);
+        if (!small) {
+            const GatherArgs ga{pre, w.pre_sph, w.vals, nq, w.ctr, w.q, ntiles, cfg.chunk, w.tile_lo, w.tile_hi,
+                                w.tile_work, w.pre_tc, tc ? w.q.tc_rec : nullptr, w.st_lo, w.st_hi, w.st_work, nsuper,
+                                csort ? w.srt_lo : nullptr, csort ? w.srt_hi : nullptr};
+            query_gather<<<grid_for(tc ? nsuper * 128 : nq), kBlock, 0, stream>>>(ga);
+        }
         PairArgs pa{idx->e, w.q, w.tile_lo, w.tile_hi, w.tile_work, ntiles, w.ctr, out, cfg.chunk, cfg.flags,
                     w.ctr_host_dev, idx->n, nq};
         if (events && (e = cudaEventRecordWithFlags(w.ev[1], stream, evflags)) != cudaSuccess) return e;
@@ -865,7 +1075,7 @@ cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
         if ((e = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp;
         if ((e = cudaGraphKernelNodeGetParams(nodes[k], &kp)) != cudaSuccess) break;
-        if (kp.func == (void *)query_prep) out->prep = nodes[k];
+        if (kp.func == (void *)query_prep || kp.func == (void *)query_prep_small) out->prep = nodes[k];
     }
     free(nodes);
     if (e == cudaSuccess && !out->prep) e = cudaErrorInvalidValue;
@@ -875,16 +1085,22 @@ cudaError_t find_input_nodes(cudaGraph_t g, GraphInputNodes *out)
 cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, const tdq_index *idx, Workspace &w,
                         const QueryInput &in, uint64_t nq, const LaunchCfg &cfg)
 {
-    const bool csort = idx->n > 0 && idx->m <= kCountSortMaxBins;
-    PrepArgs a0{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, w.vals, w.ctr,
-                !csort && idx->n > 0 && sort_fusable(nq) ? w.sort_fused_hist : nullptr, idx->n > 0, cfg.filter,
-                cfg.tc && idx->n > 0 ? w.pre_tc : nullptr, idx->grid, csort ? w.bin_cnt : nullptr, idx->n};
-    void *args[] = {&a0};
     cudaKernelNodeParams kp{};
+    kp.sharedMemBytes = 0;
+    if (small_prep(idx, cfg, nq)) {  // the node captured for this size is query_prep_small
+        SmallPrepArgs a0 = small_prep_args(idx, w, in, nq, cfg);
+        void *args[] = {&a0};
+        kp.func = (void *)query_prep_small;
+        kp.gridDim = dim3(small_prep_blocks(nq));
+        kp.blockDim = dim3(kSmallPrep);
+        kp.kernelParams = args;
+        return cudaGraphExecKernelNodeSetParams(exec, nodes.prep, &kp);
+    }
+    PrepArgs a0 = prep_args(idx, w, in, nq, cfg);
+    void *args[] = {&a0};
     kp.func = (void *)query_prep;
     kp.gridDim = dim3(grid_for(nq));
     kp.blockDim = dim3(kBlock);
-    kp.sharedMemBytes = 0;
     kp.kernelParams = args;
     return cudaGraphExecKernelNodeSetParams(exec, nodes.prep, &kp);
 }

@@ -183,6 +183,7 @@ enum TdqDebugSite : unsigned {
     kDbgTcRecords = 12,     // tensor-core pre-test: a pass's entry records inside the records
     kDbgTcSuper = 13,       // tensor-core pre-test: supertile index
     kDbgTcSurvivor = 14,    // tensor-core pre-test: a survivor's entry and query positions
+    kDbgSmallSlot = 15,     // query_prep_small: sorted slot inside the query slots
 };
 #ifdef TDQ_DEBUG
 __device__ __forceinline__ bool dbg_check(DevCounters *c, unsigned site, bool ok)

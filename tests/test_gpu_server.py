@@ -58,7 +58,15 @@ def test_results_same_alone_and_in_the_mix(tdq, db, requests, mode_name):
                 assert info["latency_ms"] >= info["run_ms"] >= 0
             st_alone = srv.stats()
             assert st_alone["batches"] == len(requests)
-            # the mix: all requests submitted from two threads at once
+            # the mix, 1: all requests queued in one call, so that the lanes
+            # admit several into each batch
+            tickets = srv.submit_many([rq.query for rq in requests], [rq.d for rq in requests],
+                                      [rq.t0 for rq in requests], [rq.t1 for rq in requests])
+            mixed = [srv.wait(t)[0] for t in tickets]
+            st_many = srv.stats()
+            assert st_many["batches"] - st_alone["batches"] < len(requests)  # requests shared batches
+            # the mix, 2: all requests submitted from two threads at once (they
+            # share batches or not, as the timing falls)
             tickets = [None] * len(requests)
 
             def submitter(ks):
@@ -71,12 +79,12 @@ def test_results_same_alone_and_in_the_mix(tdq, db, requests, mode_name):
                 t.start()
             for t in ths:
                 t.join()
-            mixed = [srv.wait(t)[0] for t in tickets]
+            mixed2 = [srv.wait(t)[0] for t in tickets]
             st = srv.stats()
-        assert st["requests_completed"] == 2 * len(requests)
-        assert st["batches"] - st_alone["batches"] < len(requests)  # requests shared batches
-        for a, m in zip(alone, mixed):
+        assert st["requests_completed"] == 3 * len(requests)
+        for a, m, m2 in zip(alone, mixed, mixed2):
             _same(a, m)
+            _same(a, m2)
         # each request against a direct search with its own d and window
         for rq, a in zip(requests[:8], alone[:8]):
             ref = tdq.search(idx, rq.query, rq.d, rq.t0, rq.t1)
