@@ -372,7 +372,7 @@ def roofline(mode, tot, n_launch, n_entries):
         r["achieved_candidates"] = ach_c
         r["frac_candidates"] = ach_c / peak
         r["work_unit_candidates"] = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per candidate pair of the ranges"
-        r["refine_kernel_ms_avg"] = tot["refine_ms"] / n_launch
+        r["kernel_includes"] = "the FP64 refinement of the pre-test's survivors (each warp refines its own)"
         hbm_bytes = FILTER_BYTES_PER_ENTRY * n_entries
     else:
         hbm_bytes = PLAIN_BYTES_PER_CANDIDATE * tot["interactions"] / n_launch

@@ -32,11 +32,20 @@ namespace {
 // subtracted and the 32u R^2 by which R_j^2 exceeds the exact bound (the
 // radii carry a factor 1 + 2^-20); R >= 2^-60 keeps every quantity normal.
 // Segments beyond 2^60 in magnitude carry a zero sphere and E = -inf, or an
-// infinite radius and K = -inf, and are never rejected.  The survivors
-// (entry, query) are appended to a list through a per-warp shared-memory
-// buffer (one atomic per 256 survivors: dense workloads pass many pairs to
-// the refinement, and per-lane atomics on one counter would serialise);
-// traj_dist_refine_kernel then evaluates them in FP64.
+// infinite radius and K = -inf, and are never rejected.
+//
+// The survivors (entry, query) collect in a per-warp shared-memory buffer,
+// and then (kInline false) go to a list with one atomic per 256 of them
+// (dense workloads pass many pairs to the refinement, and per-lane atomics
+// on one counter would serialise), which traj_dist_refine_kernel evaluates
+// in FP64 over the whole grid.  A small search (kInline true: at most
+// kSmallPrep query slots, few survivors) saves that launch: once a warp's
+// buffer holds kRefineAt survivors (a dense pass fills it in rounds), the
+// warp refines them itself, as the refine kernel does (refine_due,
+// refine_batch), and the block that finishes last copies the counters to
+// the host mirror.  (On a large batch the in-kernel refinement was measured
+// slower than the separate kernel: the FP64 batches stall the warps' FP32
+// work and leave more partial batches.)
 
 // Warps per block of the filter kernel.  It has no block-wide step, but the
 // warps of a block take adjacent item ranges, whose entry records largely
@@ -44,8 +53,36 @@ namespace {
 constexpr int kFilterWarps = 8;
 constexpr int kFilterThreads = 32 * kFilterWarps;
 constexpr int kPer = 4;            // entries per lane per pass
-constexpr int kSurvBuf = 256;      // survivors a warp buffers before one atomic on the list
+constexpr int kSurvBuf = 256;      // survivors a warp buffers
+constexpr int kRefineAt = 64;      // kInline: buffered survivors at which the warp refines them
 constexpr int kPass = 32 * kPer;   // entries per pass
+
+// FP64 evaluation (Sec. 5, Algorithm 1) of one batch of queued survivors,
+// one per lane, and the append of the hits (the whole warp); the FP64 pipe
+// is busy for a warp instruction whatever the number of active lanes, so
+// that survivors are evaluated in full batches of 32 wherever possible.
+__device__ __forceinline__ void refine_batch(const PairArgs &args, uint2 sv, bool active, uint64_t cap, int lane,
+                                             unsigned lt_mask)
+{
+    const int64_t ek = sv.x, qk = sv.y;
+    const PairEval r = eval_pair_fp64(active, args.e.ts_key[ek], args.e.te_key[ek], args.q.ts_key[qk],
+                                      args.q.te_key[qk], args.e.px[ek], args.e.py[ek], args.e.pz[ek], args.e.vx[ek],
+                                      args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk], args.q.pz[qk],
+                                      args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
+    append_hits(r, args.ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
+}
+
+// The exact span-key check (and the pair filters) of one survivor: whether
+// its FP64 evaluation is due.
+__device__ __forceinline__ bool refine_due(const PairArgs &args, uint2 sv)
+{
+    if (!TDQ_DBG(args.ctr, kDbgRefine, sv.x < args.n_entries && sv.y < args.nq_slots)) return false;
+    bool due = args.e.ts_key[sv.x] < args.q.te_key[sv.y] && args.e.te_key[sv.x] > args.q.ts_key[sv.y];
+    if (args.flags && due)
+        due = pair_allowed(args.flags, args.q.qtraj[sv.y], args.q.qid[sv.y], args.e.traj_id[sv.x],
+                           args.e.seg_id[sv.x]);
+    return due;
+}
 
 // One entry's pre-test terms, each duplicated into both halves of a paired
 // FP32 operand.
@@ -104,15 +141,24 @@ __device__ __forceinline__ void stage_queries(float4 s, bool real, int lane, flo
         qr[lane] = make_float4(X, r1, Y, r2);
 }
 
+template <bool kInline>
 __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(FilterArgs fa)
 {
     const PairArgs &args = fa.p;
     __shared__ float4 qr_all[kFilterWarps][kQT];
     __shared__ uint2 sbuf_all[kFilterWarps][kSurvBuf];
+    __shared__ uint2 queue_all[kInline ? kFilterWarps : 1][64];
+    __shared__ uint2 pool[kInline ? kFilterWarps * 32 : 1];
+    __shared__ int pooled;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *qr = qr_all[warp];
-    uint2 *sbuf = sbuf_all[warp];  // this warp's survivors not yet in the list
+    uint2 *sbuf = sbuf_all[warp];   // this warp's survivors not yet listed (refined)
+    uint2 *queue = queue_all[kInline ? warp : 0];  // kInline: survivors due for the FP64 code, < 32 between batches
     int nbuf = 0;                   // (warp-uniform)
+    int queued = 0;                 // (warp-uniform)
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t cap = args.out.capacity;
+    if (threadIdx.x == 0) pooled = 0;
     float *qrf = reinterpret_cast<float *>(qr);
     const int k_slot = (lane >> 1) * 8 + 6 + (lane & 1);  // this lane's K in qr[2i+1].zw
     DevCounters *ctr = args.ctr;
@@ -125,7 +171,7 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
     const unsigned long long iend = min(ibeg + per, total);
     const float4 *esph = args.e.sph;
     const float *esphe = args.e.sph_e;
-    unsigned long long n_inter = 0;
+    unsigned long long n_inter = 0, n_surv = 0, n_fp64 = 0;
     // moves the buffered survivors to the list (called by the whole warp)
     auto flush_survivors = [&]() {
         if (nbuf == 0) return;
@@ -135,6 +181,30 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
         __syncwarp();
         for (int i = lane; i < nbuf; i += 32)
             if (base + i < fa.surv_cap) fa.surv[base + i] = sbuf[i];
+        __syncwarp();
+        nbuf = 0;
+    };
+    // kInline: refines the buffered survivors (called by the whole warp)
+    auto refine_buffered = [&]() {
+        for (int b = 0; b < nbuf; b += 32) {
+            const bool valid = b + lane < nbuf;
+            const uint2 sv = valid ? sbuf[b + lane] : make_uint2(0u, 0u);
+            const bool due = valid && refine_due(args, sv);
+            const unsigned am = __ballot_sync(kFull, due);
+            if (due) queue[queued + __popc(am & lt_mask)] = sv;
+            queued += __popc(am);
+            n_fp64 += __popc(am);
+            __syncwarp();
+            if (queued >= 32) {
+                const uint2 qv = queue[lane];
+                const uint2 rest = lane + 32 < queued ? queue[lane + 32] : make_uint2(0u, 0u);
+                __syncwarp();
+                if (lane + 32 < queued) queue[lane] = rest;
+                queued -= 32;
+                __syncwarp();
+                refine_batch(args, qv, true, cap, lane, lt_mask);
+            }
+        }
         __syncwarp();
         nbuf = 0;
     };
@@ -239,10 +309,8 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
                     any |= m[k];
                 }
                 if (!__any_sync(kFull, any != 0u)) continue;
-                // append the warp's survivors: ranks by a warp scan, then into
-                // the warp's buffer (flushed to the list with one atomic per
-                // kSurvBuf survivors), or, for a pass with more survivors than
-                // the buffer holds, straight to the list
+                // the warp's survivors: ranks by a warp scan, then into the
+                // warp's buffer
                 int cnt = 0;
 #pragma unroll
                 for (int k = 0; k < kPer; k++) cnt += __popc(m[k]);
@@ -253,32 +321,70 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
                     if (lane >= o) incl += y;
                 }
                 const int total = __shfl_sync(kFull, incl, 31);
-                if (nbuf + total > kSurvBuf) flush_survivors();
-                const bool direct = total > kSurvBuf;
-                unsigned long long pos = nbuf + (incl - cnt);
-                if (direct) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)total);
-                    pos = __shfl_sync(kFull, base, 0) + (incl - cnt);
-                }
-#pragma unroll
-                for (int k = 0; k < kPer; k++) {
-                    unsigned mk = m[k];
-                    const uint32_t ek = (uint32_t)(pe + lane + 32 * k);
-                    while (mk) {
-                        const int bit = 31 - __clz(mk);
-                        mk &= ~(1u << bit);
-                        const uint2 sv = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
-                        if (!TDQ_DBG(ctr, kDbgFilterQuery, (uint64_t)(q0 + 31 - bit) < nvalid)) {
-                        } else if (!direct) {
-                            if (TDQ_DBG(ctr, kDbgFilterBuf, pos < (unsigned long long)kSurvBuf)) sbuf[pos] = sv;
-                        } else if (pos < fa.surv_cap) {
-                            fa.surv[pos] = sv;
-                        }
-                        pos++;
+                if constexpr (!kInline) {
+                    // (flushed to the list with one atomic per kSurvBuf
+                    // survivors), or, for a pass with more survivors than the
+                    // buffer holds, straight to the list
+                    if (nbuf + total > kSurvBuf) flush_survivors();
+                    const bool direct = total > kSurvBuf;
+                    unsigned long long pos = nbuf + (incl - cnt);
+                    if (direct) {
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)total);
+                        pos = __shfl_sync(kFull, base, 0) + (incl - cnt);
                     }
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) {
+                        unsigned mk = m[k];
+                        const uint32_t ek = (uint32_t)(pe + lane + 32 * k);
+                        while (mk) {
+                            const int bit = 31 - __clz(mk);
+                            mk &= ~(1u << bit);
+                            const uint2 sv = make_uint2(ek, (uint32_t)(q0 + 31 - bit));
+                            if (!TDQ_DBG(ctr, kDbgFilterQuery, (uint64_t)(q0 + 31 - bit) < nvalid)) {
+                            } else if (!direct) {
+                                if (TDQ_DBG(ctr, kDbgFilterBuf, pos < (unsigned long long)kSurvBuf)) sbuf[pos] = sv;
+                            } else if (pos < fa.surv_cap) {
+                                fa.surv[pos] = sv;
+                            }
+                            pos++;
+                        }
+                    }
+                    if (!direct) nbuf += total;
+                    continue;
                 }
-                if (!direct) nbuf += total;
+                // kInline: a pass with more survivors than the buffer has room
+                // for fills it in rounds, each full buffer refined before the
+                // next round
+                n_surv += (unsigned long long)total;
+                for (int done = 0; done < total;) {
+                    if (nbuf == kSurvBuf) refine_buffered();
+                    const int take = min(total - done, kSurvBuf - nbuf);
+                    int r = incl - cnt;  // this lane's first rank in the pass
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) {
+                        unsigned mk = m[k];
+                        const uint32_t ek = (uint32_t)(pe + lane + 32 * k);
+                        while (mk) {
+                            const int bit = 31 - __clz(mk);
+                            mk &= ~(1u << bit);
+                            if (r >= done && r < done + take) {
+                                const int pos = nbuf + (r - done);
+                                // (debug build: a failed check leaves a survivor
+                                // that the refinement's own check drops)
+                                if (TDQ_DBG(ctr, kDbgFilterBuf, pos < kSurvBuf))
+                                    sbuf[pos] = TDQ_DBG(ctr, kDbgFilterQuery, (uint64_t)(q0 + 31 - bit) < nvalid)
+                                                    ? make_uint2(ek, (uint32_t)(q0 + 31 - bit))
+                                                    : make_uint2(0xffffffffu, 0xffffffffu);
+                            }
+                            r++;
+                        }
+                    }
+                    __syncwarp();
+                    nbuf += take;
+                    done += take;
+                }
+                if (nbuf >= kRefineAt) refine_buffered();
             }
             if (!has_next) break;
             t = tn;
@@ -287,11 +393,40 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
             nqt = nqn;
             stage_queries(qn, lane < nqt, lane, qr, my_c2g, my_w);
         }
-        flush_survivors();
+        if constexpr (kInline)
+            refine_buffered();
+        else
+            flush_survivors();
+    }
+    if constexpr (!kInline) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_inter += __shfl_xor_sync(kFull, n_inter, o);
+        if (lane == 0 && n_inter) atomicAdd(&ctr->interactions, n_inter);
+        return;
+    }
+    // kInline: pool the warps' remainders and run them as full batches (the
+    // last one partial)
+    __syncthreads();
+    if (queued > 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&pooled, queued);
+        base = __shfl_sync(kFull, base, 0);
+        if (lane < queued) pool[base + lane] = queue[lane];
+    }
+    __syncthreads();
+    const int np = pooled;
+    for (int bt = warp; bt * 32 < np; bt += kFilterWarps) {
+        const bool active = bt * 32 + lane < np;
+        refine_batch(args, active ? pool[bt * 32 + lane] : make_uint2(0u, 0u), active, cap, lane, lt_mask);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_inter += __shfl_xor_sync(kFull, n_inter, o);
-    if (lane == 0 && n_inter) atomicAdd(&ctr->interactions, n_inter);
+    if (lane == 0) {
+        if (n_inter) atomicAdd(&ctr->interactions, n_inter);
+        if (n_surv) atomicAdd(&ctr->survivors, n_surv);
+        if (n_fp64) atomicAdd(&ctr->fp64_pairs, n_fp64);
+    }
+    publish_when_last(ctr, args.publish);
 }
 
 // FP64 evaluation of the filter's survivors.  The pre-test ignores time, so
@@ -305,17 +440,6 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
 // partial batch.  The block that finishes last copies the counters to the
 // host mirror.
 constexpr int kRefineWarps = kPairThreads / 32;
-
-__device__ __forceinline__ void refine_batch(const PairArgs &args, uint2 sv, bool active, uint64_t cap, int lane,
-                                             unsigned lt_mask)
-{
-    const int64_t ek = sv.x, qk = sv.y;
-    const PairEval r = eval_pair_fp64(active, args.e.ts_key[ek], args.e.te_key[ek], args.q.ts_key[qk],
-                                      args.q.te_key[qk], args.e.px[ek], args.e.py[ek], args.e.pz[ek], args.e.vx[ek],
-                                      args.e.vy[ek], args.e.vz[ek], args.q.px[qk], args.q.py[qk], args.q.pz[qk],
-                                      args.q.vx[qk], args.q.vy[qk], args.q.vz[qk], args.q.d2[qk]);
-    append_hits(r, args.ctr, args.out, cap, args.q.qid[qk], args.e.seg_id[ek], lane, lt_mask);
-}
 
 __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterArgs fa)
 {
@@ -339,12 +463,7 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
         const unsigned long long k = wb + lane;
         const bool valid = k < ns;
         const uint2 sv = valid ? fa.surv[k] : make_uint2(0u, 0u);
-        bool active = valid && TDQ_DBG(ctr, kDbgRefine, sv.x < args.n_entries && sv.y < args.nq_slots) &&
-                      args.e.ts_key[sv.x] < args.q.te_key[sv.y] &&
-                      args.e.te_key[sv.x] > args.q.ts_key[sv.y];
-        if (args.flags && active)
-            active = pair_allowed(args.flags, args.q.qtraj[sv.y], args.q.qid[sv.y], args.e.traj_id[sv.x],
-                                  args.e.seg_id[sv.x]);
+        const bool active = valid && refine_due(args, sv);
         const unsigned am = __ballot_sync(kFull, active);
         if (active) queue[queued + __popc(am & lt_mask)] = sv;
         queued += __popc(am);
@@ -380,20 +499,24 @@ __global__ void __launch_bounds__(kPairThreads) traj_dist_refine_kernel(FilterAr
 
 }  // namespace
 
-// The filter mode's two kernels as persistent grids (as many CTAs as fit on
+// The filter mode's kernels as persistent grids (as many CTAs as fit on
 // every SM at once): the FP32 pre-test, then the FP64 refinement of its
-// survivors; mid (may be null) is recorded between them with the flags
-// evflags.
+// survivors -- in the pre-test kernel itself for a small search (inline) --
+// with mid (may be null) recorded between them with the flags evflags.
 cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream_t stream, cudaEvent_t mid,
-                                  unsigned evflags)
+                                  unsigned evflags, bool inline_refine)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_dist_filter_kernel, kFilterThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, inline_refine ? traj_dist_filter_kernel<true> : traj_dist_filter_kernel<false>, kFilterThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    traj_dist_filter_kernel<<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
+    if (inline_refine)
+        traj_dist_filter_kernel<true><<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
+    else
+        traj_dist_filter_kernel<false><<<sm_count * per_sm, kFilterThreads, 0, stream>>>(fa);
     if (mid && (e = cudaEventRecordWithFlags(mid, stream, evflags)) != cudaSuccess) return e;
-    return launch_refine_kernel(fa, sm_count, stream);
+    return inline_refine ? cudaGetLastError() : launch_refine_kernel(fa, sm_count, stream);
 }
 
 cudaError_t launch_refine_kernel(const FilterArgs &fa, int sm_count, cudaStream_t stream)
@@ -409,7 +532,8 @@ cudaError_t launch_refine_kernel(const FilterArgs &fa, int sm_count, cudaStream_
 cudaError_t load_filter_module()
 {
     cudaFuncAttributes fa;
-    return cudaFuncGetAttributes(&fa, traj_dist_filter_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, traj_dist_filter_kernel<false>);
+    return e != cudaSuccess ? e : cudaFuncGetAttributes(&fa, traj_dist_filter_kernel<true>);
 }
 
 }  // namespace tdq

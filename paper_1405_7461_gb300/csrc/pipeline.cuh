@@ -171,11 +171,12 @@ __global__ void query_scatter(ScatterArgs a);
 __global__ void publish_counters(const DevCounters *src, DevCounters *dst);
 
 // Pair kernel of the requested mode as a persistent grid (search.cu); the
-// filter mode's pair (filter.cu).
+// filter mode's pair (filter.cu), with inline_refine the pre-test kernel
+// refining its own survivors (a small search).
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
-                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags);
+                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags, bool inline_refine = false);
 cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream_t stream, cudaEvent_t mid,
-                                  unsigned evflags);
+                                  unsigned evflags, bool inline_refine);
 // The FP64 refine kernel of the filter modes alone (filter.cu).
 cudaError_t launch_refine_kernel(const FilterArgs &fa, int sm_count, cudaStream_t stream);
 // The tensor-core pre-test, then the refine kernel (tcfilter.cu).

@@ -762,9 +762,10 @@ size_t pair_smem_bytes(uint32_t chunk)
 // mid (filter mode, may be null): event recorded between the filter and the
 // refine kernel with the flags evflags.
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
-                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags)
+                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags, bool inline_refine)
 {
-    if (filter) return launch_filter_kernels(FilterArgs{pa, surv, surv_cap}, sm_count, stream, mid, evflags);
+    if (filter)
+        return launch_filter_kernels(FilterArgs{pa, surv, surv_cap}, sm_count, stream, mid, evflags, inline_refine);
     const size_t smem = pair_smem_bytes(pa.chunk);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(traj_dist_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -941,12 +942,13 @@ SmallPrepArgs small_prep_args(const tdq_index *idx, Workspace &w, const QueryInp
 
 int search_kernel_launches(const tdq_index *idx, const LaunchCfg &cfg, uint64_t nq)
 {
-    if (small_prep(idx, cfg, nq)) return 1 + (cfg.filter ? 2 : 1);  // query_prep_small, the pair kernel(s)
+    if (small_prep(idx, cfg, nq)) return 2;  // query_prep_small, the pair kernel (refining its own survivors)
     // without entries: query_prep and publish_counters; with entries:
     // query_prep, the sort of the query keys (counting sort: query_scatter;
     // else the radix sort's kernels), query_gather and the pair kernel
-    // (filter mode: filter and refine), whose last block publishes the
-    // counters; a small search: query_prep_small and the pair kernel(s)
+    // (filter modes: the pre-test and the refine kernel), whose last block
+    // publishes the counters; a small search: query_prep_small and the pair
+    // kernel
     const int sort = idx->m <= kCountSortMaxBins ? 1 : sort_kernel_launches(nq, bin_key_bits(idx->m), true);
     return idx->n > 0 ? 2 + sort + (cfg.filter ? 2 : 1) : 2;
 }
@@ -1008,7 +1010,7 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                          idx->sm_count, stream, events ? w.ev[2] : nullptr, evflags);
         else
             e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
-                                   events ? w.ev[2] : nullptr, evflags);
+                                   events ? w.ev[2] : nullptr, evflags, small);
         if (e != cudaSuccess) return e;
         if (events && (e = cudaEventRecordWithFlags(cfg.filter ? w.ev[4] : w.ev[2], stream, evflags)) != cudaSuccess)
             return e;
@@ -1037,7 +1039,8 @@ tdq_status finish_search(const tdq_index *idx, const Workspace &w, const LaunchC
         return set_error(TDQ_ERR_TIMEOUT,
                          "tdq_search: a wait of the tensor-core pre-test pipeline ran out of time (the search "
                          "was abandoned; its results are incomplete)");
-    if (cfg.filter && idx->n > 0 && h.survivors > w.s_cap_pairs) {
+    // (a small search's FP32 pre-test refines its survivors in place; else they are listed)
+    if (cfg.filter && !small_prep(idx, cfg, nq) && h.survivors > w.s_cap_pairs) {
         *surv_overflow = true;
         return TDQ_OK;
     }

@@ -461,7 +461,10 @@ def test_filter_keeps_touching_stationary_spheres(tdq, offset, mode):
 def test_filter_survivor_list_overflow_is_regrown(tdq, mode):
     """A cluster where every pair survives the pre-test: 1.3 M survivors
     overflow the initial survivor list (2^20 pairs), which is grown and the
-    search re-run; the results equal the plain FP64 mode's."""
+    search re-run; the results equal the plain FP64 mode's.  (64 query
+    segments: a small search, whose FP32 pre-test refines the survivors in
+    place instead -- up to 4,096 in a pass of 128 entries, which fill its
+    warp's buffer in rounds.)"""
     rng = np.random.default_rng(21)
     ent = workloads.random_segments(rng, 20_000, box=0.2, t_span=0.5, max_dur=20.0, max_speed=0.01)
     qry = workloads.random_segments(rng, 64, box=0.2, t_span=0.5, max_dur=20.0, max_speed=0.01)

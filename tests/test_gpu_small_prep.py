@@ -84,11 +84,11 @@ def test_one_block_and_multi_block_preparation_agree(tdq, entries, n, mode_name,
     for k in ("query_segments", "overlap_pairs", "results"):
         assert ss[k] == sl[k], k
     # one launch prepares a batch of at most 1,024 slots: query_prep_small,
-    # then the pair kernel (filter mode: the pre-test and the refine)
-    pair_launches = 2 if mode == tdq.MODE_FP32_FILTER else 1
+    # then the pair kernel (filter mode: the pre-test, which refines its own
+    # survivors)
     if n <= 1024:
-        assert ss["kernel_launches"] == 1 + pair_launches
-    assert sl["kernel_launches"] > 1 + pair_launches
+        assert ss["kernel_launches"] == 2
+    assert sl["kernel_launches"] > 2
     ref = oracle.search_sweep_per_query(entries, q, d, t0, t1)
     qo = np.argsort(q.seg_id)
     got = {"qi": qo[np.searchsorted(q.seg_id[qo], rs.query_seg_id)], "ei": rs.entry_seg_id.copy(),
