@@ -46,6 +46,16 @@ namespace {
 // the host mirror.  (On a large batch the in-kernel refinement was measured
 // slower than the separate kernel: the FP64 batches stall the warps' FP32
 // work and leave more partial batches.)
+//
+// A small search is typically one trajectory's segments in time order, so
+// that a tile's 32 segments span 32 time steps and its union range is many
+// times each segment's own candidate range (Sec. 4's wasteful
+// interactions).  The small-search kernel therefore also holds every lane's
+// query segment's own range and, per pass, skips the segments whose range
+// misses the pass's entries: a pass that none meets is skipped, and with at
+// most kSparseAt segments left only their pairs are evaluated.  (Measured on
+// the large batch, whose tiles hold segments of nearly the same time, the
+// per-pass test cost more than it saved.)
 
 // Warps per block of the filter kernel.  It has no block-wide step, but the
 // warps of a block take adjacent item ranges, whose entry records largely
@@ -55,6 +65,7 @@ constexpr int kFilterThreads = 32 * kFilterWarps;
 constexpr int kPer = 4;            // entries per lane per pass
 constexpr int kSurvBuf = 256;      // survivors a warp buffers
 constexpr int kRefineAt = 64;      // kInline: buffered survivors at which the warp refines them
+constexpr int kSparseAt = 16;      // kInline: active query segments of a pass up to which only their pairs run
 constexpr int kPass = 32 * kPer;   // entries per pass
 
 // FP64 evaluation (Sec. 5, Algorithm 1) of one batch of queued survivors,
@@ -225,6 +236,13 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
         int nqt = (int)min((uint64_t)kQT, nvalid - (uint64_t)t * kQT);
         float my_c2g, my_w;
         stage_queries(args.q.sph[(int64_t)t * kQT + min(lane, nqt - 1)], lane < nqt, lane, qr, my_c2g, my_w);
+        // kInline with q_lo: this lane's query segment's own candidate range
+        // (an empty one past the tile's last segment)
+        int64_t my_lo = INT64_MAX, my_hi = INT64_MIN;
+        if (kInline && fa.q_lo && lane < nqt) {
+            my_lo = fa.q_lo[(int64_t)t * kQT + lane];
+            my_hi = fa.q_hi[(int64_t)t * kQT + lane];
+        }
         float4 ns[kPer];
         float nse[kPer];
 #pragma unroll
@@ -241,12 +259,17 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
             int64_t ebn = 0, een = 0;
             int nqn = 0;
             float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+            int64_t lon = INT64_MAX, hin = INT64_MIN;
             if (has_next) {
                 while (args.tile_work[tn + 1] == args.tile_work[tn]) tn++;
                 filter_run(args, tn, ibeg, iend, ebn, een);
                 if (!TDQ_DBG(ctr, kDbgFilterRun, ebn >= 0 && ebn < een && een <= (int64_t)args.n_entries)) een = ebn;
                 nqn = (int)min((uint64_t)kQT, nvalid - tn * kQT);
                 qn = args.q.sph[(int64_t)tn * kQT + min(lane, nqn - 1)];
+                if (kInline && fa.q_lo && lane < nqn) {
+                    lon = fa.q_lo[(int64_t)tn * kQT + lane];
+                    hin = fa.q_hi[(int64_t)tn * kQT + lane];
+                }
             }
             const int64_t q0 = (int64_t)t * kQT;
             const unsigned qvalid = 0xffffffffu << (kQT - nqt);  // bit 31-j <-> query j
@@ -275,6 +298,15 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
                         nse[k] = in ? pse[32 * k] : 0.f;
                     }
                 }
+                // kInline with q_lo: the tile's query segments whose own
+                // candidate range meets this pass (bit 31-j <-> query j);
+                // none: the pass is skipped
+                unsigned act = qvalid;
+                if (kInline && fa.q_lo) {
+                    const int64_t pend = min(pe + kPass, ee);
+                    act = __brev(__ballot_sync(kFull, my_lo < pend && my_hi > pe));
+                    if (act == 0u) continue;
+                }
                 // radii are non-negative: their bit patterns order like the values
                 const float wmax = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(wl)));
                 const float Rj = __fadd_ru(wmax, my_w);
@@ -282,30 +314,53 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
                 __syncwarp();  // the previous pass's K are no longer read
                 qrf[k_slot] = Kj;
                 __syncwarp();
-                // two independent mask chains per entry (queries 0-15 and
-                // 16-31), joined afterwards: the funnel shifts of one chain
-                // depend on each other
-                unsigned m[kPer], mh[kPer];
+                unsigned m[kPer];
+                // every query pair: two independent mask chains per entry
+                // (queries 0-15 and 16-31), joined afterwards -- the funnel
+                // shifts of one chain depend on each other
+                auto dense_masks = [&]() {
+                    unsigned mh[kPer];
 #pragma unroll
-                for (int k = 0; k < kPer; k++) m[k] = mh[k] = 0u;
+                    for (int k = 0; k < kPer; k++) m[k] = mh[k] = 0u;
 #pragma unroll
-                for (int j = 0; j < kQT; j += 2) {
-                    const float4 qa = qr[j], qb = qr[j + 1];
+                    for (int j = 0; j < kQT; j += 2) {
+                        const float4 qa = qr[j], qb = qr[j + 1];
 #pragma unroll
-                    for (int k = 0; k < kPer; k++) {
-                        const float2 v = sphere_gap_pair(ed[k], qa, qb);
-                        unsigned &mm = j < kQT / 2 ? mh[k] : m[k];
-                        mm = __funnelshift_l(__float_as_uint(v.x), mm, 1);
-                        mm = __funnelshift_l(__float_as_uint(v.y), mm, 1);
+                        for (int k = 0; k < kPer; k++) {
+                            const float2 v = sphere_gap_pair(ed[k], qa, qb);
+                            unsigned &mm = j < kQT / 2 ? mh[k] : m[k];
+                            mm = __funnelshift_l(__float_as_uint(v.x), mm, 1);
+                            mm = __funnelshift_l(__float_as_uint(v.y), mm, 1);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) m[k] = __byte_perm(m[k], mh[k], 0x5410);
+                };
+                if constexpr (!kInline) {
+                    dense_masks();
+                } else if (__popc(act) > kSparseAt) {
+                    dense_masks();
+                } else {
+                    // the active query pairs only, each sign bit put in place
+#pragma unroll
+                    for (int k = 0; k < kPer; k++) m[k] = 0u;
+                    for (unsigned rem = act; rem;) {
+                        const int j = __clz(rem) & ~1;  // the pair's first query
+                        rem &= ~(0xc0000000u >> j);
+                        const float4 qa = qr[j], qb = qr[j + 1];
+#pragma unroll
+                        for (int k = 0; k < kPer; k++) {
+                            const float2 v = sphere_gap_pair(ed[k], qa, qb);
+                            m[k] |= ((__float_as_uint(v.x) >> 31) << (31 - j)) |
+                                    ((__float_as_uint(v.y) >> 31) << (30 - j));
+                        }
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < kPer; k++) m[k] = __byte_perm(m[k], mh[k], 0x5410);
                 unsigned any = 0u;
                 const int here = (int)min(ee - pe, (int64_t)kPass);
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
-                    m[k] = lane + 32 * k < here ? (m[k] & qvalid) : 0u;
+                    m[k] = lane + 32 * k < here ? (m[k] & qvalid & act) : 0u;
                     any |= m[k];
                 }
                 if (!__any_sync(kFull, any != 0u)) continue;
@@ -391,6 +446,8 @@ __global__ void __launch_bounds__(kFilterThreads, 2) traj_dist_filter_kernel(Fil
             eb = ebn;
             ee = een;
             nqt = nqn;
+            my_lo = lon;
+            my_hi = hin;
             stage_queries(qn, lane < nqt, lane, qr, my_c2g, my_w);
         }
         if constexpr (kInline)

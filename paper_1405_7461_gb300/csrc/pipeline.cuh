@@ -76,6 +76,7 @@ struct SmallPrepArgs {
     QuerySoA q;
     int64_t *tile_lo, *tile_hi;
     unsigned long long *tile_work;  // exclusive offsets of the tiles' chunks, the total last; ntiles + 1
+    int64_t *srt_lo, *srt_hi;       // every sorted segment's candidate range (for the pre-test)
     uint32_t chunk;
 };
 
@@ -148,6 +149,10 @@ struct FilterArgs {
     PairArgs p;
     uint2 *surv;            // survivor list: (sorted entry position, sorted query position)
     uint64_t surv_cap;
+    // may be null: every sorted query segment's own candidate range (a small
+    // search), by which the pre-test skips the segments whose range misses a
+    // pass of entries
+    const int64_t *q_lo, *q_hi;
 };
 
 // The tensor-core pre-test's arguments (tcfilter.cu): the pair arguments
@@ -174,7 +179,8 @@ __global__ void publish_counters(const DevCounters *src, DevCounters *dst);
 // filter mode's pair (filter.cu), with inline_refine the pre-test kernel
 // refining its own survivors (a small search).
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
-                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags, bool inline_refine = false);
+                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags, bool inline_refine = false,
+                               const int64_t *q_lo = nullptr, const int64_t *q_hi = nullptr);
 cudaError_t launch_filter_kernels(const FilterArgs &fa, int sm_count, cudaStream_t stream, cudaEvent_t mid,
                                   unsigned evflags, bool inline_refine);
 // The FP64 refine kernel of the filter modes alone (filter.cu).

@@ -382,6 +382,8 @@ __global__ void __launch_bounds__(kSmallPrep) query_prep_small(SmallPrepArgs s)
             q.sph[t] = a.pre_sph[sl];
             rlo = __double_as_longlong(pre[kPreLo][sl]);
             rhi = __double_as_longlong(pre[kPreHi][sl]);
+            s.srt_lo[t] = rlo;
+            s.srt_hi[t] = rhi;
         }
     }
     // tile plan: warp w plans tile w (the union of its members' ranges, cut
@@ -762,10 +764,12 @@ size_t pair_smem_bytes(uint32_t chunk)
 // mid (filter mode, may be null): event recorded between the filter and the
 // refine kernel with the flags evflags.
 cudaError_t launch_pair_kernel(const PairArgs &pa, bool filter, int sm_count, uint2 *surv, uint64_t surv_cap,
-                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags, bool inline_refine)
+                               cudaStream_t stream, cudaEvent_t mid, unsigned evflags, bool inline_refine,
+                               const int64_t *q_lo, const int64_t *q_hi)
 {
     if (filter)
-        return launch_filter_kernels(FilterArgs{pa, surv, surv_cap}, sm_count, stream, mid, evflags, inline_refine);
+        return launch_filter_kernels(FilterArgs{pa, surv, surv_cap, q_lo, q_hi}, sm_count, stream, mid, evflags,
+                                     inline_refine);
     const size_t smem = pair_smem_bytes(pa.chunk);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(traj_dist_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -933,7 +937,7 @@ SmallPrepArgs small_prep_args(const tdq_index *idx, Workspace &w, const QueryInp
 {
     PrepArgs p{in, nq, bin_view(idx), w.pre_dev, w.pre_sph, w.keys, nullptr, w.ctr, nullptr, true, cfg.filter,
                nullptr, idx->grid, nullptr, idx->n};
-    SmallPrepArgs sa{p, {}, w.q, w.tile_lo, w.tile_hi, w.tile_work, cfg.chunk};
+    SmallPrepArgs sa{p, {}, w.q, w.tile_lo, w.tile_hi, w.tile_work, w.srt_lo, w.srt_hi, cfg.chunk};
     for (int c = 0; c < kPreCols; c++) sa.cols[c] = w.pre[c];
     return sa;
 }
@@ -1010,7 +1014,8 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
                                          idx->sm_count, stream, events ? w.ev[2] : nullptr, evflags);
         else
             e = launch_pair_kernel(pa, cfg.filter, idx->sm_count, w.surv, w.s_cap_pairs, stream,
-                                   events ? w.ev[2] : nullptr, evflags, small);
+                                   events ? w.ev[2] : nullptr, evflags, small, small ? w.srt_lo : nullptr,
+                                   small ? w.srt_hi : nullptr);
         if (e != cudaSuccess) return e;
         if (events && (e = cudaEventRecordWithFlags(cfg.filter ? w.ev[4] : w.ev[2], stream, evflags)) != cudaSuccess)
             return e;

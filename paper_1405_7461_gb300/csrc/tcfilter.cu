@@ -546,7 +546,7 @@ cudaError_t launch_tc_filter_kernels(const TcArgs &ta, int sm_count, cudaStream_
     if (e != cudaSuccess) return e;
     traj_dist_tc_filter_kernel<<<sm_count * 2, kTcThreads, kTcSmemRequest, stream>>>(ta);
     if (mid && (e = cudaEventRecordWithFlags(mid, stream, evflags)) != cudaSuccess) return e;
-    return launch_refine_kernel(FilterArgs{ta.p, ta.surv, ta.surv_cap}, sm_count, stream);
+    return launch_refine_kernel(FilterArgs{ta.p, ta.surv, ta.surv_cap, nullptr, nullptr}, sm_count, stream);
 }
 
 cudaError_t load_tc_module()
