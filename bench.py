@@ -372,7 +372,7 @@ def roofline(mode, tot, n_launch, n_entries):
         r["achieved_candidates"] = ach_c
         r["frac_candidates"] = ach_c / peak
         r["work_unit_candidates"] = f"{FLOPS_PER_CANDIDATE_FP32} FP32 flops per candidate pair of the ranges"
-        r["kernel_includes"] = "the FP64 refinement of the pre-test's survivors (each warp refines its own)"
+        r["refine_kernel_ms_avg"] = tot["refine_ms"] / n_launch
         hbm_bytes = FILTER_BYTES_PER_ENTRY * n_entries
     else:
         hbm_bytes = PLAIN_BYTES_PER_CANDIDATE * tot["interactions"] / n_launch
@@ -472,13 +472,30 @@ def batching_section(args, tdq, torch, stream, with_oracle=False):
         ms.append(ev0.elapsed_time(ev1))
         pairs += p
     plan.free()
+    # the plain FP64 path on the same batches, one step (for the batched
+    # path's speedup over it)
+    plan = tdq.Plan(idx, b, mode=tdq.MODE_FP64, entry_chunk=tun["entry_chunk"],
+                    result_capacity=tun["result_capacity"])
+    for k in {0, len(batches) - 1}:  # capture the graphs of both batch sizes before timing
+        a, e = batches[k]
+        plan.search(subs[k], dd[a:e], t0[a:e], t1[a:e], stream=stream)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    p64, _ = run()
+    ev1.record(stream)
+    ev1.synchronize()
+    ms64 = ev0.elapsed_time(ev1)
+    plan.free()
     idx.free()
     tot = sum(ms) / 1e3
     out = {"workload": "batching_walks: %d walks x 300 points (%d entries), %d query trajectories (%d segments), "
                        "own d and window each" % (args.batch_n_traj, len(w.entries), args.batch_n_queries, n),
            "tuning": tun, "autotune_s": tune_s, "batches_per_step": len(batches),
            "pair_tests_per_s": pairs / tot, "queries_per_s": len(ms) * args.batch_n_queries / tot,
-           "ms_per_step": 1e3 * tot / len(ms)}
+           "ms_per_step": 1e3 * tot / len(ms),
+           "plain_fp64": {"pair_tests_per_s": p64 / (ms64 / 1e3), "queries_per_s": args.batch_n_queries / (ms64 / 1e3),
+                          "ms_per_step": ms64, "steps": 1}}
+    out["speedup_vs_plain_fp64"] = out["queries_per_s"] / out["plain_fp64"]["queries_per_s"]
     if with_oracle:
         from oracle import oracle
 
@@ -532,8 +549,13 @@ def serving_section(args, tdq, torch, with_oracle=False):
     its own d and window; p50/p99 latency and queries/s of the serving loop,
     its saturation throughput, and the plain FP64 search issued one query at
     a time for comparison."""
+    import gc
     import threading
 
+    # the sections before this one leave large host arrays behind: collect
+    # them now, and keep the collector from pausing the Python client (the
+    # submitter and the collecting thread) during the timed open loop
+    gc.collect()
     db = workloads.serving_database(n_traj=args.serve_n_traj, n_points=500)
     reqs = workloads.serving_requests(n_requests=int(args.serve_rate * args.serve_seconds),
                                       rate_per_s=args.serve_rate, n_points=500)
@@ -541,8 +563,16 @@ def serving_section(args, tdq, torch, with_oracle=False):
     del db
     srv = tdq.Server(idx, max_batch_query_segments=65536, memory_cap_bytes=16 << 30, lanes=3,
                      mode=tdq.MODE_FP32_FILTER, results_per_query_segment=1.0)
-    for rq in reqs[:50]:  # warm up (graph capture per size class)
+    # warm up: graph capture per size class and lane -- requests one at a
+    # time, then bursts that the lanes batch into every larger class
+    for rq in reqs[:50]:
         srv.wait(srv.submit(rq.query, rq.d, rq.t0, rq.t1))
+    for n_burst in (8, 32, 128, 512):
+        for rep in range(3):
+            ws = reqs[50 + rep * n_burst:50 + (rep + 1) * n_burst]
+            for t in srv.submit_many([rq.query for rq in ws], [rq.d for rq in ws], [rq.t0 for rq in ws],
+                                     [rq.t1 for rq in ws]):
+                srv.wait(t)
     tickets = [None] * len(reqs)
     lat = np.zeros(len(reqs))
 
@@ -554,17 +584,22 @@ def serving_section(args, tdq, torch, with_oracle=False):
                 time.sleep(delay)
             tickets[k] = srv.submit(rq.query, rq.d, rq.t0, rq.t1)
 
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
     th = threading.Thread(target=submitter)
     th.start()
     n_results = 0
-    for k in range(len(reqs)):
-        while tickets[k] is None:
-            time.sleep(0.0002)
-        res, info = srv.wait(tickets[k])
-        lat[k] = info["latency_ms"]
-        n_results += len(res)
-    th.join()
+    try:
+        for k in range(len(reqs)):
+            while tickets[k] is None:
+                time.sleep(0.0002)
+            res, info = srv.wait(tickets[k])
+            lat[k] = info["latency_ms"]
+            n_results += len(res)
+        th.join()
+    finally:
+        gc.enable()
     wall = time.perf_counter() - t0
     st = srv.stats()
     # saturation: a burst of all requests at once from the Python client
@@ -933,6 +968,11 @@ def main():
                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / e_dt}
 
     with_oracle = not args.no_cpu_baseline
+    # the latency measurement first, before the sections that leave large
+    # host and device allocations behind
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_section(args, tdq, torch, with_oracle)
     tiny = None
     if rank == 0 and world == 1 and not args.no_tiny:
         tiny = tiny_section(args, tdq, torch, stream, with_oracle)
@@ -942,9 +982,6 @@ def main():
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
         batching = batching_section(args, tdq, torch, stream, with_oracle)
-    serving = None
-    if rank == 0 and world == 1 and not args.no_serving:
-        serving = serving_section(args, tdq, torch, with_oracle)
     self_join = None
     if rank == 0 and world == 1 and not args.no_self_join:
         self_join = self_join_section(args, tdq, torch)

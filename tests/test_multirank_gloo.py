@@ -103,7 +103,7 @@ def test_roofline_arithmetic():
     assert f["frac"] == pytest.approx(f["achieved"] / 80547.84)
     assert f["achieved_candidates"] == pytest.approx(7 * 2e9 / 1e-3 / 1e9)  # 7 flops per candidate
     assert f["frac_candidates"] == pytest.approx(f["achieved_candidates"] / 80547.84)
-    assert "refinement" in f["kernel_includes"]  # the pre-test kernel refines its own survivors
+    assert f["refine_kernel_ms_avg"] == 0.25
     assert f["hbm"]["algorithmic_bytes_per_launch"] == 20 * 1000  # the 20 B record of each entry
     assert f["hbm"]["frac"] == pytest.approx(f["hbm"]["achieved_gbs"] / bench.hbm_peak_gbs())
     assert bench.roofline("fp64", dict(tot, kernel_ms=0.0), 2, 1000) is None
