@@ -21,13 +21,16 @@
 //   warp 9, one thread: the MMA issuer -- the MMA of each pass into one of
 //     two accumulator stages (256 TMEM columns), its completion signalled
 //     through the stage's mbarrier by tcgen05.commit;
-//   warps 0-7: the epilogue -- warp w reads accumulator lanes
-//     32 (w % 4) .. + 31 (one entry each) and the 32 columns of each of its
-//     tiles 2 (w / 4) and 2 (w / 4) + 1 whose own range meets the pass, with
-//     tcgen05.ld, hands the stage back at once, ORs each tile's 32 values
-//     and, only where a sign bit is set (v < 0: the spheres can meet), builds
-//     the entry's 32-bit survivor mask and appends the survivors (entry,
-//     query) through a per-warp shared-memory buffer.
+//   warps 0-7: the epilogue, two groups of four -- group w / 4 takes the
+//     passes of its accumulator stage (every other pass), so that two passes
+//     are looked at at once; warp w reads accumulator lanes 32 (w % 4) .. + 31
+//     (one entry each) and the 32 columns of each of the four tiles whose own
+//     range meets the pass, two tiles at a time with tcgen05.ld (one wait per
+//     pair), ORs each tile's 32 values and, only where a sign bit is set
+//     (v < 0: the spheres can meet), builds the entry's 32-bit survivor mask,
+//     hands the stage back once all four tiles are read, and then appends the
+//     survivors (entry, query) through a per-warp shared-memory buffer at
+//     ranks taken by a warp scan.
 // Tiles whose own range misses a pass are skipped.  Every wait is bounded;
 // a wait that runs out sets error bit 2 (reported as TDQ_ERR_TIMEOUT) and the
 // CTA winds down, waiting for its own copies and MMAs in flight before it
@@ -45,6 +48,7 @@ constexpr int kTcN = 128;                   // query slots per supertile (MMA N)
 constexpr int kTcTiles = kTcN / kQT;        // tiles of 32 per supertile
 constexpr int kTcAStages = 8;               // ring of entry-record stages
 constexpr int kTcAcc = 2;                   // accumulator stages (256 TMEM columns; two CTAs fill an SM)
+constexpr int kTcGroupWarps = kTcEpiWarps / kTcAcc;  // epilogue warps per accumulator stage (one per lane quarter)
 constexpr uint32_t kTcPassBytes = kTcM * 32;
 constexpr uint32_t kTcBBytes = kTcN * 32;
 constexpr uint32_t kTcCols = kTcAcc * kTcN;  // tensor-memory columns per CTA
@@ -63,7 +67,7 @@ struct TcSmem {
     uint4 a[kTcAStages][kTcPassBytes / 16];
     uint4 b[2][kTcBBytes / 16];
     uint2 surv[kTcEpiWarps][kTcSurvBuf];
-    int nsurv[kTcEpiWarps];  // survivors in each warp's buffer
+    int4 tiles[kTcEpiWarps][kTcTiles];  // each epilogue warp's copy of the run's tiles: (segments, lo, hi) rel. to p0
     unsigned long long a_full[kTcAStages], mma_done[kTcAStages];
     unsigned long long acc_empty[kTcAcc];
     unsigned long long b_full[2], b_free[2], drain;
@@ -73,26 +77,6 @@ struct TcSmem {
 static_assert(sizeof(TcSmem) + 1024 <= kTcSmemRequest, "shared memory layout fits the request");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory word access by 32-bit shared-space address (the shared
-// block is reached through a realigned pointer, which the compiler no longer
-// knows to be shared).
-__device__ __forceinline__ uint32_t atoms_add_u32(uint32_t saddr, uint32_t x)
-{
-    uint32_t old;
-    asm volatile("atom.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(saddr), "r"(x) : "memory");
-    return old;
-}
-__device__ __forceinline__ uint32_t lds_u32(uint32_t saddr)
-{
-    uint32_t x;
-    asm volatile("ld.volatile.shared::cta.u32 %0, [%1];" : "=r"(x) : "r"(saddr) : "memory");
-    return x;
-}
-__device__ __forceinline__ void sts_u32(uint32_t saddr, uint32_t x)
-{
-    asm volatile("st.volatile.shared::cta.u32 [%0], %1;" ::"r"(saddr), "r"(x) : "memory");
-}
 
 __device__ __forceinline__ void bar_init(unsigned long long *b, uint32_t count)
 {
@@ -170,9 +154,9 @@ __device__ __forceinline__ void tc_commit(unsigned long long *b)
 
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 32 consecutive accumulator columns of this warp's 32 lanes into v[0..31],
-// and the wait for them.
-__device__ __forceinline__ void tc_load32(uint32_t taddr, uint32_t *v)
+// 32 consecutive accumulator columns of this warp's 32 lanes into v[0..31]
+// (tc_wait_ld waits for them).
+__device__ __forceinline__ void tc_load32_nowait(uint32_t taddr, uint32_t *v)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                  "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -183,7 +167,6 @@ __device__ __forceinline__ void tc_load32(uint32_t taddr, uint32_t *v)
                    "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                  : "r"(taddr)
                  : "memory");
-    tc_wait_ld();
 }
 
 // Sign bits of 32 words as a mask (bit j = sign of v[j]): four independent
@@ -353,14 +336,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
             bar_init(&sm.a_full[i], 1);
             bar_init(&sm.mma_done[i], 1);
         }
-        for (int i = 0; i < kTcAcc; i++) bar_init(&sm.acc_empty[i], kTcEpiWarps);
+        for (int i = 0; i < kTcAcc; i++) bar_init(&sm.acc_empty[i], kTcGroupWarps);
         for (int i = 0; i < 2; i++) {
             bar_init(&sm.b_full[i], 1);
             bar_init(&sm.b_free[i], 1);
         }
         bar_init(&sm.drain, 1);
         sm.abort = 0;
-        for (int i = 0; i < kTcEpiWarps; i++) sm.nsurv[i] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -409,113 +391,153 @@ __global__ void __launch_bounds__(kTcThreads, 2) traj_dist_tc_filter_kernel(TcAr
         }
     } else {
         // epilogue warp: accumulator lanes 32 quarter .. 32 quarter + 31 (one
-        // entry each) and the columns of tiles 2 half and 2 half + 1
-        const int quarter = warp & 3, half = warp >> 2;
+        // entry each), all four tiles, of the passes of its group (the passes
+        // g with g % kTcAcc == group, i.e. its accumulator stage): the two
+        // groups work on two passes at once
+        const int quarter = warp & 3, group = warp / kTcGroupWarps;
         uint2 *sbuf = sm.surv[warp];
-        const uint32_t nsurv_s = smem_addr(&sm.nsurv[warp]);  // this warp's buffer count (shared space)
+        int nbuf = 0;  // (warp-uniform)
         unsigned long long n_inter = 0;
         const uint64_t nvalid = ctr->valid_queries;
         // moves the buffered survivors to the list (called by the whole warp)
         auto flush = [&]() {
-            __syncwarp();
-            const int nb = min((int)lds_u32(nsurv_s), kTcSurvBuf);
-            if (nb == 0) return;
+            if (nbuf == 0) return;
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)nb);
+            if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)nbuf);
             base = __shfl_sync(kFull, base, 0);
-            for (int i = lane; i < nb; i += 32)
+            __syncwarp();
+            for (int i = lane; i < nbuf; i += 32)
                 if (base + i < a.surv_cap) a.surv[base + i] = sbuf[i];
             __syncwarp();
-            if (lane == 0) sts_u32(nsurv_s, 0u);
-            __syncwarp();
+            nbuf = 0;
         };
         TcRun r;
         bool h = tc_first_run(a, ibeg, iend, r);
         uint32_t p = 0;
         uint64_t gm = 0;
-        // this warp's two tiles in the current run: query segments, and the
-        // part of each tile's own range inside the run, relative to p0
-        int nq[2] = {0, 0};
-        int32_t tlo[2] = {0, 0}, thi[2] = {0, 0};
+        // the run's four tiles (lane k computes tile k): query segments, and
+        // the part of the tile's own range inside the run, relative to p0
+        int4 *tiles = sm.tiles[warp];
         auto run_tiles = [&]() {
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const uint64_t t = r.s * kTcTiles + 2 * half + k;
+            __syncwarp();  // the previous run's tiles are no longer read
+            if (lane < kTcTiles) {
+                const uint64_t t = r.s * kTcTiles + lane;
                 const int64_t left = (int64_t)nvalid - (int64_t)t * kQT;
                 int n = t < args.ntiles ? (int)max((int64_t)0, min(left, (int64_t)kQT)) : 0;
                 const int64_t lo = n ? max(args.tile_lo[t], r.eb) : 0, hi = n ? min(args.tile_hi[t], r.ee) : 0;
                 if (hi <= lo) n = 0;
-                nq[k] = n;
-                tlo[k] = (int32_t)(lo - r.p0);
-                thi[k] = (int32_t)(hi - r.p0);
+                tiles[lane] = make_int4(n, (int32_t)(lo - r.p0), (int32_t)(hi - r.p0), 0);
                 // candidates: the tile's range inside this run, times its query segments
-                if (quarter == 0 && lane == 0 && n) n_inter += (unsigned long long)(hi - lo) * (unsigned long long)n;
+                if (quarter == 0 && group == 0 && n) n_inter += (unsigned long long)(hi - lo) * (unsigned long long)n;
             }
+            __syncwarp();
+        };
+        // one tile's survivor mask of this lane's entry el (relative to p0):
+        // bit j set where the value of query slot j is negative (v < 0: the
+        // spheres can meet); the OR of the 32 values decides whether the
+        // mask needs building at all
+        auto mask_of = [&](int k, const uint32_t *v, bool act, int32_t el) -> uint32_t {
+            if (!act) return 0u;
+            const int4 ti = tiles[k];
+            const bool hit = el >= ti.y && el < ti.z && (or32(v) >> 31);
+            if (!__any_sync(kFull, hit)) return 0u;
+            uint32_t m = 0u;
+            if (hit) {
+                m = signs32(v);
+                if (ti.x < 32) m &= (1u << ti.x) - 1u;
+            }
+            return m;
+        };
+        // the survivors (entry, query) of one tile's masks into the warp's
+        // buffer at ranks taken by a warp scan, the buffer flushed to the list
+        // when full; a tile with more survivors than the buffer holds goes
+        // straight to the list
+        auto append = [&](int k, uint32_t m, int32_t el) {
+            if (!__any_sync(kFull, m != 0u)) return;
+            const uint32_t e = (uint32_t)(r.p0 + el);
+            const uint32_t q0 = (uint32_t)((r.s * kTcTiles + k) * kQT);
+            // (the highest set bit of m is the last query slot used)
+            if (m && !TDQ_DBG(ctr, kDbgTcSurvivor, e < args.n_entries && q0 + 32 - __clz(m) <= nvalid)) m = 0u;
+            const int cnt = __popc(m);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) return;
+            if (nbuf + total > kTcSurvBuf) flush();
+            const bool direct = total > kTcSurvBuf;
+            unsigned long long pos = nbuf + (incl - cnt);
+            if (direct) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&ctr->survivors, (unsigned long long)total);
+                pos = __shfl_sync(kFull, base, 0) + (incl - cnt);
+            }
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                const uint2 sv = make_uint2(e, q0 + bit);
+                if (!direct) {
+                    if (TDQ_DBG(ctr, kDbgTcSurvivor, pos < (unsigned long long)kTcSurvBuf)) sbuf[pos] = sv;
+                } else if (pos < a.surv_cap) {
+                    a.surv[pos] = sv;
+                }
+                pos++;
+            }
+            __syncwarp();
+            if (!direct) nbuf += total;
         };
         if (h) run_tiles();
         while (h) {
-            const uint32_t acc = (uint32_t)(gm % kTcAcc);
-            // the pass's MMA is done: one lane waits, the warp follows its
-            // verdict (the tensor-memory loads below need all 32 lanes)
-            int got = 0;
-            if (lane == 0) got = bar_wait(&sm.mma_done[gm % kTcAStages], (uint32_t)((gm / kTcAStages) & 1), abort);
-            got = __shfl_sync(kFull, got, 0);
-            if (!got) {
-                if (lane == 0) {
-                    atomicOr(&ctr->error, 2u);
-                    *abort = 1;
-                }
-                break;
-            }
-            // the pass's entries relative to p0; which of the two tiles' own
-            // ranges meet them (warp-uniform)
-            const int32_t pr = (int32_t)(kTcM * p);
-            const bool act0 = nq[0] > 0 && tlo[0] < pr + kTcM && thi[0] > pr;
-            const bool act1 = nq[1] > 0 && tlo[1] < pr + kTcM && thi[1] > pr;
-            uint32_t v0[kQT], v1[kQT];
-            const uint32_t tcol = tmem + ((uint32_t)(32 * quarter) << 16) + acc * kTcN + 2 * half * kQT;
-            tc_fence_after();
-            if (act0) tc_load32(tcol, v0);
-            if (act1) tc_load32(tcol + kQT, v1);
-            // the stage goes back to the MMA issuer before the values are looked at
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) bar_arrive(&sm.acc_empty[acc]);
-            const int32_t el = pr + 32 * quarter + lane;  // this lane's entry, relative to p0
-            // common case: none of the values is negative
-            const bool hit0 = act0 && el >= tlo[0] && el < thi[0] && (or32(v0) >> 31);
-            const bool hit1 = act1 && el >= tlo[1] && el < thi[1] && (or32(v1) >> 31);
-            if (__any_sync(kFull, hit0 || hit1)) {
-                // some entry may meet some query segment: the lanes that hit
-                // append their survivors at places taken with a shared atomic
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    const bool hit = k ? hit1 : hit0;
-                    if (!hit) continue;
-                    uint32_t m = signs32(k ? v1 : v0);
-                    if (nq[k] < 32) m &= (1u << nq[k]) - 1u;
-                    const uint32_t e = (uint32_t)(r.p0 + el);
-                    const uint32_t q0 = (uint32_t)((r.s * kTcTiles + 2 * half + k) * kQT);
-                    // (the highest set bit of m is the last query slot used)
-                    if (m && !TDQ_DBG(ctr, kDbgTcSurvivor, e < args.n_entries && q0 + 32 - __clz(m) <= nvalid)) m = 0u;
-                    const int cnt = __popc(m);
-                    if (!cnt) continue;
-                    int pos = (int)atoms_add_u32(nsurv_s, (uint32_t)cnt);
-                    while (m) {
-                        const int bit = __ffs(m) - 1;
-                        m &= m - 1;
-                        const uint2 sv = make_uint2(e, q0 + bit);
-                        if (pos < kTcSurvBuf) {
-                            sbuf[pos] = sv;
-                        } else {  // the buffer is full: straight to the list
-                            const unsigned long long kk = atomicAdd(&ctr->survivors, 1ULL);
-                            if (kk < a.surv_cap) a.surv[kk] = sv;
-                        }
-                        pos++;
+            if ((int)(gm % kTcAcc) == group) {
+                const uint32_t acc = (uint32_t)group;
+                // the pass's MMA is done: one lane waits, the warp follows its
+                // verdict (the tensor-memory loads below need all 32 lanes)
+                int got = 0;
+                if (lane == 0)
+                    got = bar_wait(&sm.mma_done[gm % kTcAStages], (uint32_t)((gm / kTcAStages) & 1), abort);
+                got = __shfl_sync(kFull, got, 0);
+                if (!got) {
+                    if (lane == 0) {
+                        atomicOr(&ctr->error, 2u);
+                        *abort = 1;
                     }
+                    break;
                 }
+                // the pass's entries relative to p0; which tiles' own ranges
+                // meet them (warp-uniform)
+                const int32_t pr = (int32_t)(kTcM * p);
+                unsigned act = 0u;  // bit k: tile k's own range meets the pass
+#pragma unroll
+                for (int k = 0; k < kTcTiles; k++) {
+                    const int4 ti = tiles[k];
+                    act |= (ti.x > 0 && ti.y < pr + kTcM && ti.z > pr) ? 1u << k : 0u;
+                }
+                const int32_t el = pr + 32 * quarter + lane;  // this lane's entry, relative to p0
+                const uint32_t tcol = tmem + ((uint32_t)(32 * quarter) << 16) + acc * kTcN;
+                uint32_t v0[kQT], v1[kQT];
+                tc_fence_after();
+                // tiles 0 and 1 (one wait for both loads), looked at while
+                // the accumulator is still held
+                if (act & 1u) tc_load32_nowait(tcol, v0);
+                if (act & 2u) tc_load32_nowait(tcol + kQT, v1);
+                if (act & 3u) tc_wait_ld();
+                const uint32_t m0 = mask_of(0, v0, act & 1u, el), m1 = mask_of(1, v1, act & 2u, el);
+                // tiles 2 and 3, then the stage goes back to the MMA issuer;
+                // the survivors are appended after that
+                if (act & 4u) tc_load32_nowait(tcol + 2 * kQT, v0);
+                if (act & 8u) tc_load32_nowait(tcol + 3 * kQT, v1);
+                if (act & 12u) tc_wait_ld();
+                const uint32_t m2 = mask_of(2, v0, act & 4u, el), m3 = mask_of(3, v1, act & 8u, el);
+                tc_fence_before();
                 __syncwarp();
-                if ((int)lds_u32(nsurv_s) >= kTcSurvBuf / 2) flush();
+                if (lane == 0) bar_arrive(&sm.acc_empty[acc]);
+                append(0, m0, el);
+                append(1, m1, el);
+                append(2, m2, el);
+                append(3, m3, el);
             }
             gm++;
             if (++p == r.np) {
