@@ -172,6 +172,28 @@ __global__ void te_bin_assign(const int64_t *te_sorted, uint64_t n, double t_min
         for (int64_t j = bk + 1; j <= (int64_t)m; j++) te_bin_begin[j] = (int64_t)n;
 }
 
+// Each bin's smallest time key under bin_of: bin_lo_key[b] = the smallest key
+// k of a non-NaN time whose bin is >= b (b = 1 .. m-1; bin_of is monotone in
+// time), by bisection over the keys of -inf .. +inf; bin_lo_key[0] =
+// INT64_MIN, bin_lo_key[m] = INT64_MAX.  The bin of a time with key k is
+// then the last b with bin_lo_key[b] <= k, exactly bin_of's.
+__global__ void bin_bounds(double t_min, double width, uint32_t m, int64_t *bin_lo_key)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > m) return;
+    if (b == 0 || b == m) {
+        bin_lo_key[b] = b == 0 ? INT64_MIN : INT64_MAX;
+        return;
+    }
+    int64_t lo = okey(__longlong_as_double((long long)0xfff0000000000000ULL));  // -inf
+    int64_t hi = okey(__longlong_as_double((long long)0x7ff0000000000000ULL));  // +inf: bin m - 1 >= b
+    while (lo < hi) {
+        const int64_t mid = lo + (int64_t)(((uint64_t)hi - (uint64_t)lo) >> 1);
+        if (bin_of(key_double(mid), t_min, width, m) >= (int64_t)b) hi = mid; else lo = mid + 1;
+    }
+    bin_lo_key[b] = lo;
+}
+
 // Prefix maximum of the bin ends (one block).
 __global__ void __launch_bounds__(1024) bin_prefix_max(const int64_t *bin_end_key, uint32_t m, int64_t *pmax)
 {
@@ -282,7 +304,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
     idx->n_rec = (n + 7) / 8 * 8 + 128;  // whole groups of 8, and room for a pass of 128 from any group
     uint64_t ebytes = 12 * carve_bytes(n, 8) + carve_bytes(n, 4) + carve_bytes(n, 16) +
                       carve_bytes(2 * idx->n_rec, 16);
-    uint64_t bbytes = 2 * carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
+    uint64_t bbytes = 3 * carve_bytes(m + 1, 8) + 2 * carve_bytes(m, 8);
     if (dev_alloc(&idx->e_block, ebytes) != cudaSuccess || dev_alloc(&idx->b_block, bbytes) != cudaSuccess) {
         cudaGetLastError();
         tdq_index_free(idx);
@@ -305,6 +327,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         idx->bin_end_key = carve<int64_t>(q, m);
         idx->bin_pmax_key = carve<int64_t>(q, m);
         idx->te_bin_begin = carve<int64_t>(q, m + 1);
+        idx->bin_lo_key = carve<int64_t>(q, m + 1);
     }
 
     // Temporary build memory: staged input (host case), sort buffers, scratch.
@@ -391,6 +414,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
             int64_t bmin = key_from_bits(kmin), bmax = key_from_bits(kmax);
             memcpy(&idx->t_min, &bmin, 8);
             memcpy(&idx->t_max, &bmax, 8);
+            idx->tmin_key = kmin;
             idx->width = (idx->t_max - idx->t_min) / (double)m;
             memcpy(&idx->max_dur, &back[3], 8);
             double box[6];
@@ -414,6 +438,7 @@ extern "C" tdq_status tdq_build_index(const tdq_segments *entries, const tdq_ind
         bin_assign<<<grid_for(n), kBlock, 0, stream>>>(idx->e.ts_key, idx->e.te_key, n, idx->t_min, idx->width, m,
                                                        idx->bin_begin, idx->bin_end_key);
         bin_prefix_max<<<1, 1024, 0, stream>>>(idx->bin_end_key, m, idx->bin_pmax_key);
+        bin_bounds<<<grid_for((uint64_t)m + 1), kBlock, 0, stream>>>(idx->t_min, idx->width, m, idx->bin_lo_key);
         // t_end keys in ascending order: #overlaps(q) = #{ts < q.te} - #{te <= q.ts}
         te_keys<<<grid_for(n), kBlock, 0, stream>>>(idx->e.te_key, n, keys, vals);
         if (radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, hist, stream) != cudaSuccess) {

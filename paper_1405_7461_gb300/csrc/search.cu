@@ -73,16 +73,17 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     //  C  (count_overlaps) #{t_end <= cs}, likewise inside the bin of cs in
     //     the sorted t_end keys (bin table te_bin_begin).
     const double te = key_double(ce), ts = key_double(cs);
-    // Last bin that can hold an entry starting before the query end.
-    const int64_t jhi = le0(te - bins.t_min) ? -1 : bin_of(te, bins.t_min, bins.width, bins.m);
+    // Last bin that can hold an entry starting before the query end (none
+    // when the query ends at or before the first entry start).
+    const int64_t jhi = ce <= bins.tmin_key ? -1 : bin_of_key(bins, ce, te);
     const int64_t m = bins.m;
-    const int64_t bts = bin_of(ts, bins.t_min, bins.width, bins.m);  // exact: C relies on it
+    const int64_t bts = bin_of_key(bins, cs, ts);  // exact: C relies on it
     int64_t a_lo, a_hi;
     {
         // the lower end only needs to be about right: it is verified
-        const double f0 = floor((ts - bins.max_dur - bins.t_min) * bins.inv_width) - 1.0;
         const int64_t hb = bts + 1 < m ? bts + 1 : m - 1;
-        int64_t b0 = f0 > 0.0 ? (f0 < (double)(m - 1) ? (int64_t)f0 : m - 1) : 0;
+        int64_t b0 = bts - bins.dur_bins - 1;
+        if (b0 < 0) b0 = 0;
         if (b0 > hb) b0 = hb;
         const bool below = b0 > 0 && bins.bin_pmax_key[b0 - 1] > cs;  // the answer lies before b0
         const bool above = !below && bins.bin_pmax_key[hb] <= cs;     // the answer lies after hb
@@ -93,7 +94,7 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     if (jhi >= 0) {
         b_lo = bins.bin_begin[jhi];
         b_hi = bins.bin_begin[jhi + 1];
-        if (count_overlaps && !le0(ts - bins.t_min)) {
+        if (count_overlaps && cs > bins.tmin_key) {
             c_lo = bins.te_bin_begin[bts];
             c_hi = bins.te_bin_begin[bts + 1];
         }

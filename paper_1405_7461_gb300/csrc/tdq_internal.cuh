@@ -314,6 +314,8 @@ struct tdq_index {
     int64_t *bin_begin = nullptr;   // m + 1 sorted positions
     int64_t *bin_end_key = nullptr; // m, largest t_end key (INT64_MIN when empty)
     int64_t *bin_pmax_key = nullptr;// m, prefix max of bin_end_key
+    int64_t *bin_lo_key = nullptr;  // m + 1: the smallest time key of each bin under bin_of (INT64_MIN, ..., INT64_MAX)
+    int64_t tmin_key = 0;           // time key of t_min
     int64_t *te_bin_begin = nullptr;// m + 1: first position in e.te_sorted whose t_end lies in bin >= b
     tdq::TcGrid grid{};             // integer grid of the tensor-core pre-test (over the entries' centers)
     uint64_t n_rec = 0;             // tensor-core records held (n rounded up to 8, plus one pass of 128)
