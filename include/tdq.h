@@ -130,7 +130,9 @@ typedef struct {
  * hits, temporal misses and temporal-hit/spatial-misses). */
 typedef struct {
     uint64_t query_segments;    /* query segments searched (after validation) */
-    uint64_t interactions;      /* candidate pairs visited by the kernel (tile x chunk) */
+    uint64_t interactions;      /* candidate pairs of the tiles' ranges (tile x chunk; a search of at most
+                                   1,024 query segments in the FP32 filter mode tests only the pairs of
+                                   each segment's own range among them) */
     uint64_t overlap_pairs;     /* pairs whose common span (inside the window) has positive length */
     uint64_t fp64_pairs;        /* pairs evaluated in FP64 (all overlap pairs in FP64 mode) */
     uint64_t results;           /* pairs within d (alpha * interactions) */
@@ -141,7 +143,9 @@ typedef struct {
     double total_ms;            /* device time of the whole search on its stream */
     uint64_t filter_survivors;  /* filter modes: pairs that passed the pre-test (0 in FP64 mode) */
     double refine_ms;           /* filter modes: device time of the FP64 refine kernel (pair_kernel_ms then
-                                   covers the pre-test kernel alone) */
+                                   covers the pre-test kernel alone); ~0 for a search of at most 1,024
+                                   query segments in the FP32 filter mode, whose pre-test kernel refines its
+                                   own survivors */
     uint64_t mma_issued;        /* TDQ_MODE_TC_FILTER: tensor-core MMAs issued (each 128 entries x 128 query
                                    slots x 16 record elements) */
 } tdq_stats;
@@ -236,16 +240,18 @@ tdq_status tdq_search_device_batched(tdq_index *idx, const tdq_segments *queries
  * synchronize the whole device.  Build the index beforehand; then this call
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
  * It runs the plain FP64 kernels of tdq_search_device, with the same
- * arguments, results and errors, but keeps its per-search scratch in one
- * fixed file-scope device array of about 1.5 MiB, held by the device until
- * the process exits.
+ * arguments, results and errors in that mode, but keeps its per-search
+ * scratch in one fixed file-scope device array of about 1.5 MiB, held by the
+ * device until the process exits.
  *  - Modes: only TDQ_MODE_FP64 with no pair filters.  The filter modes
  *    (whose survivor list has no fixed bound) and any TDQ_FLAG_* are
  *    rejected with TDQ_ERR_INVALID.
  *  - Synchronous: the call copies the counters back to the host and waits
- *    for its stream before it returns.  CUDA loads device code and arrays lazily; tdq_build_index
- * loads all of the library's device code (this array included) on the
- * index's device, so no search call -- this one in particular -- loads any.
+ *    for its stream before it returns.
+ *  - Device code: CUDA loads device code and arrays lazily; tdq_build_index
+ *    loads all of the library's device code (this array included) on the
+ *    index's device, so that no search call -- this one in particular --
+ *    loads any.
  *  - Limit: at most 8192 query segments per call; more is rejected with
  *    TDQ_ERR_INVALID and a message naming the limit.
  *  - The first call on a device resolves the array's device address
