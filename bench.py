@@ -164,7 +164,8 @@ def config_dict(args, w, extra=None):
     c = {"workload": "scale_random_walk: %d walks (%d entry segments), %d query trajectories (%d segments), "
                      "d in {1,5,15}, full window" % (args.n_traj, len(w.entries), args.n_queries, len(w.queries)),
          "entry_segments": len(w.entries), "query_segments": len(w.queries), "d_values": list(w.d_values),
-         "bin_count": 10000, "l2": "flushed (256 MiB write) between timed GPU steps",
+         "bin_count": 10000, "entry_chunk": HEADLINE_ENTRY_CHUNK,
+         "l2": "flushed (256 MiB write) between timed GPU steps",
          "warmup_rule": "W steps, then more until %.1f s of wall time" % WARMUP_MIN_S}
     if extra:
         c.update(extra)
@@ -387,14 +388,22 @@ def roofline(mode, tot, n_launch, n_entries):
 HEADLINE_RESULT_CAPACITY = 1 << 22
 
 
+# entry chunk of the headline plan: the unit in which the pre-test's warps
+# split the tiles' ranges.  On this batch (70,785 query segments, L2 flushed
+# before each search) chunks of 256 / 512 / 1024 / 2048 entries gave a
+# pre-test of 236 / 235 / 223 / 230 us.
+HEADLINE_ENTRY_CHUNK = 1024
+
+
 def headline_plan(tdq, idx, n_query_segments, host_results=False, mode=None):
     """The plan the headline (device inputs, device results) and the
     end-to-end leg (pinned host inputs read in place, results written into a
     page-locked host buffer: host_results) time: the FP32 pre-test mode (or
-    `mode`), one batch of all thresholds' query segments, default bin count
-    and chunk."""
+    `mode`), one batch of all thresholds' query segments, the default bin
+    count and HEADLINE_ENTRY_CHUNK."""
     return tdq.Plan(idx, n_query_segments, mode=tdq.MODE_FP32_FILTER if mode is None else mode,
-                    result_capacity=HEADLINE_RESULT_CAPACITY, host_results=host_results)
+                    entry_chunk=HEADLINE_ENTRY_CHUNK, result_capacity=HEADLINE_RESULT_CAPACITY,
+                    host_results=host_results)
 
 
 def pinned_copy(torch, a):
