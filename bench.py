@@ -975,6 +975,42 @@ def main():
                "path": "pinned host queries read in place by the kernels; results written by the kernels into a "
                        "page-locked host buffer (tdq_plan host_results), read there; counters through mapped memory",
                "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / e_dt}
+        # the same step through the plain host call tdq_search (the boundary's
+        # search: one call per threshold, host queries in, library-owned host
+        # results out), as a caller without plans makes it
+        qh1 = tdq.HostSegments(workloads.Segments(*[pinned_copy(torch, w.queries[c]) for c in workloads.COLUMNS],
+                                                  pinned_copy(torch, w.queries.seg_id),
+                                                  pinned_copy(torch, w.queries.traj_id)))
+        def host_step():
+            n_pairs, n_res = 0, 0
+            for d in w.d_values:
+                r = tdq.search(idx, qh1, d, *w.window, mode=tdq.MODE_FP32_FILTER)
+                n_pairs += tdq.get_stats(idx)["overlap_pairs"]
+                n_res += len(r)
+                del r
+            return n_pairs, n_res
+        t_w = time.perf_counter()
+        for _ in range(max(args.warmup, 1)):
+            host_step()
+        while time.perf_counter() - t_w < args.min_warmup_s:
+            host_step()
+        barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h_pairs = h_res = 0
+        for _ in range(args.steps):
+            p_, r_ = host_step()
+            h_pairs += p_
+            h_res += r_
+        torch.cuda.synchronize()
+        h_dt, h_pairs = reduce_over_ranks(time.perf_counter() - t, h_pairs, device="cuda")
+        e2e["tdq_search"] = {
+            "value": h_pairs / h_dt, "unit": "pair tests/s", "host_memory": "pinned",
+            "h2d_bytes_per_step": len(w.queries) * 80 * len(w.d_values),
+            "d2h_bytes_per_step": 32 * h_res // args.steps,
+            "path": "tdq_search per threshold (FP32 pre-test mode): pinned host queries read in place, results "
+                    "copied into library-owned page-locked host arrays (tdq_results), one call after another",
+            "queries_per_s": world * args.steps * len(w.d_values) * args.n_queries / h_dt}
 
     with_oracle = not args.no_cpu_baseline
     # the latency measurement first, before the sections that leave large
