@@ -274,7 +274,8 @@ tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segments *queries
  * its own threshold d and window [t0, t1] -- as one CUDA graph launch: the
  * whole search (counter reset, query preparation and sort, candidate ranges,
  * tiles, pair kernels, overlap count, counter read-back) is captured once per
- * power-of-two size class of the batch and replayed.  The plan owns its
+ * size class of the batch (powers of two up to the plan's largest batch, and
+ * that batch size itself) and replayed.  The plan owns its
  * workspace, staging buffers and a result buffer (device memory, or with
  * host_results page-locked host memory); it keeps a pointer
  * to the index (free the plan before the index).  One search at a time per

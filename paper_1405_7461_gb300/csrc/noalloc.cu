@@ -164,7 +164,7 @@ extern "C" tdq_status tdq_search_device_noalloc(tdq_index *idx, const tdq_segmen
     // the array keeps the previous call's contents: clear the counters
     TDQ_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), stream));
     const BinView bins = bin_view(idx);
-    query_prep<<<grid_for(nq), kBlock, 0, stream>>>(
+    query_prep<<<prep_grid(nq), kBlock, 0, stream>>>(
         PrepArgs{in, nq, bins, s->pre_dev, s->pre_sph, s->keys, s->vals, s->ctr, nullptr, idx->n > 0, false, nullptr,
                  TcGrid{}, nullptr, idx->n});
     const uint64_t ntiles = (nq + kQT - 1) / kQT;

@@ -196,6 +196,10 @@ struct TcArgs {
 };
 
 // Kernels launched from more than one file (defined in search.cu).
+// query_prep: blocks of kBlock threads, each block kPrepSlots query slots
+// (prep_grid blocks for nq slots).
+constexpr int kPrepSlots = kBlock / 2;
+inline unsigned prep_grid(uint64_t nq) { return grid_for(nq, kPrepSlots); }
 __global__ void query_prep(PrepArgs a);
 __global__ void query_gather(GatherArgs a);
 __global__ void query_scatter(ScatterArgs a);

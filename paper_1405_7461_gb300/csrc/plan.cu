@@ -5,9 +5,10 @@
 // tdq_plan_search stages the batch, then replays the whole search -- counter
 // reset, query preparation and sort, candidate ranges, tiles, pair kernels,
 // overlap count, counter read-back -- as one CUDA graph launch.  Graphs are
-// captured once per power-of-two size class of the batch (the slots past the
-// batch's real size are empty padding), so batches of uneven size reuse a
-// few graphs.  Per batch, the kernel that reads the input (query
+// captured once per size class of the batch -- powers of two up to the
+// plan's largest batch, and that size itself (the slots past the batch's real
+// size are empty padding) -- so batches of uneven size reuse a few graphs and
+// full batches run no padding.  Per batch, the kernel that reads the input (query
 // preparation) is re-pointed at it (device and page-locked host inputs in
 // place, other host inputs through staging buffers) and told the batch's real
 // size, without re-capturing.  The paper processes a query
@@ -322,7 +323,10 @@ extern "C" tdq_status tdq_plan_search(tdq_plan *p, const tdq_segments *queries, 
             in = staged_input(p);
         }
     }
-    const uint64_t cls = size_class(nq);
+    // the batch's size class: a power of two (from kMinClass) up to the plan's
+    // largest batch, which is a class of its own (a plan sized for exactly
+    // its batches runs no padding slots)
+    const uint64_t cls = size_class(nq) < p->max_q ? size_class(nq) : p->max_q;
     in.n_real = nq;
     for (int attempt = 0;; attempt++) {
         if (p->use_graph) {

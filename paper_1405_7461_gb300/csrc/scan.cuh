@@ -8,11 +8,14 @@
 namespace tdq {
 
 // Every thread of the block calls it.  Each iteration stages kThreads * kPer
-// counters in shared memory with coalesced loads (one padding word per 32
-// against bank conflicts), scans kPer consecutive counters per thread, scans
-// the thread sums across the block, writes the prefixes back and stores them
-// coalesced; a carry links the iterations.  The data is read through L2
-// (other blocks may have written it).  total (may be null) receives the sum.
+// counters in shared memory (one padding word per 32 against bank
+// conflicts), scans kPer consecutive counters per thread, scans the thread
+// sums across the block, writes the prefixes back and stores them
+// coalesced; a carry links the iterations.  The counters of the next
+// iteration are loaded (coalesced) while the current ones are scanned, so
+// that a load's latency is paid once rather than once per iteration.  The
+// data is read through L2 (other blocks may have written it).  total (may be
+// null) receives the sum.
 template <typename T, int kThreads, int kPer>
 __device__ __forceinline__ void block_exclusive_scan(T *data, uint64_t n, T *total)
 {
@@ -25,11 +28,18 @@ __device__ __forceinline__ void block_exclusive_scan(T *data, uint64_t n, T *tot
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto pad = [](int i) { return i + (i >> 5); };
     if (tid == 0) carry = 0;
+    T nxt[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+        const int i = j * kThreads + tid;
+        nxt[j] = (uint64_t)i < n ? __ldcg(data + i) : (T)0;
+    }
     for (uint64_t start = 0; start < n; start += kChunk) {
 #pragma unroll
         for (int j = 0; j < kPer; j++) {
             const int i = j * kThreads + tid;
-            buf[pad(i)] = start + i < n ? __ldcg(data + start + i) : (T)0;
+            buf[pad(i)] = nxt[j];
+            nxt[j] = start + kChunk + i < n ? __ldcg(data + start + kChunk + i) : (T)0;
         }
         __syncthreads();
         T v[kPer];

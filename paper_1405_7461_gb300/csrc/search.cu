@@ -122,126 +122,163 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     if (count_overlaps && jhi >= 0) n_overlap = (unsigned long long)(b_lo - c_lo);
 }
 
-// One query slot's preparation: validation and clipping into the pre
-// columns (see kPreCols; keys stored bitwise in the double arrays), the FP32
-// bounding sphere (and with a.pre_tc the tensor-core record), the sort key
-// -- the temporal bin of the clipped start, bins.m for invalid segments and
-// padding -- and, with a.ranges, the candidate range (also into the pre
-// columns) and with a.count_overlaps the exact temporal-overlap count.
-// Returns whether the slot holds a valid segment with a non-empty clipped
-// span.  Slots at or beyond nreal are padding: empty, not errors.
-__device__ __forceinline__ bool prep_slot(const PrepArgs &a, uint64_t i, uint64_t nreal, uint64_t &key,
-                                          unsigned long long &n_overlap)
+// One real query slot's input, validated and clipped to its window
+// (Sec. 4): the eight columns, d, the start key and the clipped span keys
+// [cs, ce).  ok: every value finite, t_end > t_start, d >= 0, the window
+// ordered and free of NaN; valid: ok with a non-empty clipped span.
+struct SlotIn {
+    double c[8];
+    double d;
+    int64_t ks, cs, ce;
+    bool ok, valid;
+};
+
+__device__ __forceinline__ SlotIn slot_input(const QueryInput &in, uint64_t i)
 {
-    const QueryInput &in = a.in;
-    const BinView &bins = a.bins;
-    double *const *pre = a.pre;
-    DevCounters *ctr = a.ctr;
-    bool valid = false;
-    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
-    key = bins.m;
-    n_overlap = 0;
-    if (i >= nreal) {
-        pre[7][i] = __longlong_as_double(INT64_MAX);
-        pre[8][i] = __longlong_as_double(INT64_MIN);
-        a.pre_sph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-        bool ok = true;
-        double c[8];
+    SlotIn s;
+    bool ok = true;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            c[k] = in.c[k][i];
-            ok &= finite_bits(c[k]);
-        }
-        double d = in.d_arr ? in.d_arr[i] : in.d;
-        double t0 = in.t0_arr ? in.t0_arr[i] : in.t0;
-        double t1 = in.t1_arr ? in.t1_arr[i] : in.t1;
-        ok &= finite_bits(d) && ge0(d);
-        ok &= !is_nan_bits(t0) && !is_nan_bits(t1);
-        int64_t ks = okey(c[3]), ke = okey(c[7]);
-        ok &= ke > ks;
-        int64_t k0 = ok ? okey(t0) : 0, k1 = ok ? okey(t1) : 0;
-        ok &= k0 <= k1;
-        if (!ok) atomicOr(&ctr->error, 1u);
-        int64_t cs = max(ks, k0), ce = min(ke, k1);
-        valid = ok && cs < ce;
-        // one FP64 division per segment (the FP64 pipe is narrow)
-        const double inv = 1.0 / (c[7] - c[3]);
-        double vx = (c[4] - c[0]) * inv, vy = (c[5] - c[1]) * inv, vz = (c[6] - c[2]) * inv;
-        double px = c[0], py = c[1], pz = c[2];
-        if (valid && cs != ks) {  // the window cuts the start: position at the clipped start
-            double shift = key_double(cs) - c[3];
-            px = fma(vx, shift, px);
-            py = fma(vy, shift, py);
-            pz = fma(vz, shift, pz);
-        }
-        pre[0][i] = px; pre[1][i] = py; pre[2][i] = pz;
-        pre[3][i] = vx; pre[4][i] = vy; pre[5][i] = vz;
-        pre[6][i] = d * d;
-        // invalid segments get the empty span (ts' >= te'), like padding
-        pre[7][i] = __longlong_as_double(valid ? cs : INT64_MAX);
-        pre[8][i] = __longlong_as_double(valid ? ce : INT64_MIN);
-        // FP32 bounding sphere of the clipped segment, its radius widened by
-        // d (and a relative 2^-30 of d): the pre-test of the filter mode
-        float4 sp = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
-        if (valid) {
-            const double h = 0.5 * (key_double(ce) - key_double(cs));
-            const float dw = __double2float_ru(d);
-            sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), __fmul_ru(norm_ru(vx, vy, vz),
-                          __double2float_ru(h)), __fmaf_ru(dw, 0x1p-30f, dw));
-        }
-        a.pre_sph[i] = sp;
-        // tensor-core pre-test record of the clipped segment's sphere: center
-        // and radius in FP64, snapped to the index's grid
-        if (a.pre_tc && valid) {
-            const double h = 0.5 * (key_double(ce) - key_double(cs));
-            const double r = sqrt(fma(vz, vz, fma(vy, vy, vx * vx))) * h;
-            uint4 lo, hi;
-            tc_query_record(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), r, d, a.grid, lo, hi);
-            a.pre_tc[2 * i] = lo;
-            a.pre_tc[2 * i + 1] = hi;
-        }
-        // sort key: the temporal bin of the clipped start, in FP32 (it only
-        // groups the segments into tiles of 32 that span few bins); invalid
-        // segments sort last
-        if (valid) {
-            const float f = floorf(__double2float_rn(key_double(cs) - bins.t_min) * bins.inv_width_f);
-            key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
-        }
-        pre[kPreSeg][i] = __longlong_as_double(in.seg_id[i]);
-        pre[kPreTraj][i] = __longlong_as_double(in.traj_id ? in.traj_id[i] : 0);
-        if (valid && a.ranges) {
-            candidate_range(bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
-            if (!TDQ_DBG(ctr, kDbgRange, rhi <= rlo || (rlo >= 0 && rhi <= (int64_t)a.n_entries))) {
-                rlo = INT64_MAX;
-                rhi = INT64_MIN;
-            }
-        }
+    for (int k = 0; k < 8; k++) {
+        s.c[k] = in.c[k][i];
+        ok &= finite_bits(s.c[k]);
     }
-    if (a.ranges) {
-        pre[kPreLo][i] = __longlong_as_double(rlo);
-        pre[kPreHi][i] = __longlong_as_double(rhi);
-    }
-    return valid;
+    s.d = in.d_arr ? in.d_arr[i] : in.d;
+    const double t0 = in.t0_arr ? in.t0_arr[i] : in.t0;
+    const double t1 = in.t1_arr ? in.t1_arr[i] : in.t1;
+    ok &= finite_bits(s.d) && ge0(s.d);
+    ok &= !is_nan_bits(t0) && !is_nan_bits(t1);
+    s.ks = okey(s.c[3]);
+    const int64_t ke = okey(s.c[7]);
+    ok &= ke > s.ks;
+    const int64_t k0 = ok ? okey(t0) : 0, k1 = ok ? okey(t1) : 0;
+    ok &= k0 <= k1;
+    s.cs = max(s.ks, k0);
+    s.ce = min(ke, k1);
+    s.ok = ok;
+    s.valid = ok && s.cs < s.ce;
+    return s;
 }
 
-// Validate and clip every query segment into the pre columns (prep_slot),
-// with its sort key and place: the counting sort's rank inside its bin, or
-// the radix sort's first digit counts.
-__global__ void query_prep(PrepArgs a)
+// A padding slot (at or beyond the real count): an empty span, no sphere,
+// an empty range.
+__device__ __forceinline__ void slot_padding(const PrepArgs &a, uint64_t i)
 {
+    a.pre[7][i] = __longlong_as_double(INT64_MAX);
+    a.pre[8][i] = __longlong_as_double(INT64_MIN);
+    a.pre_sph[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The arithmetic of one real slot: the pre columns (see kPreCols; keys
+// stored bitwise in the double arrays), the FP32 bounding sphere (and with
+// a.pre_tc the tensor-core record) and the ids.  Returns the sort key: the
+// temporal bin of the clipped start, bins.m for an invalid segment.
+__device__ __forceinline__ uint64_t slot_arith(const PrepArgs &a, uint64_t i, const SlotIn &s)
+{
+    const BinView &bins = a.bins;
+    double *const *pre = a.pre;
+    const double *c = s.c;
+    const bool valid = s.valid;
+    const int64_t cs = s.cs, ce = s.ce;
+    // one FP64 division per segment (the FP64 pipe is narrow)
+    const double inv = 1.0 / (c[7] - c[3]);
+    double vx = (c[4] - c[0]) * inv, vy = (c[5] - c[1]) * inv, vz = (c[6] - c[2]) * inv;
+    double px = c[0], py = c[1], pz = c[2];
+    if (valid && cs != s.ks) {  // the window cuts the start: position at the clipped start
+        double shift = key_double(cs) - c[3];
+        px = fma(vx, shift, px);
+        py = fma(vy, shift, py);
+        pz = fma(vz, shift, pz);
+    }
+    pre[0][i] = px; pre[1][i] = py; pre[2][i] = pz;
+    pre[3][i] = vx; pre[4][i] = vy; pre[5][i] = vz;
+    pre[6][i] = s.d * s.d;
+    // invalid segments get the empty span (ts' >= te'), like padding
+    pre[7][i] = __longlong_as_double(valid ? cs : INT64_MAX);
+    pre[8][i] = __longlong_as_double(valid ? ce : INT64_MIN);
+    // FP32 bounding sphere of the clipped segment, its radius widened by
+    // d (and a relative 2^-30 of d): the pre-test of the filter mode
+    float4 sp = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+    if (valid) {
+        const double h = 0.5 * (key_double(ce) - key_double(cs));
+        const float dw = __double2float_ru(s.d);
+        sp = sphere32(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), __fmul_ru(norm_ru(vx, vy, vz),
+                      __double2float_ru(h)), __fmaf_ru(dw, 0x1p-30f, dw));
+    }
+    a.pre_sph[i] = sp;
+    // tensor-core pre-test record of the clipped segment's sphere: center
+    // and radius in FP64, snapped to the index's grid
+    if (a.pre_tc && valid) {
+        const double h = 0.5 * (key_double(ce) - key_double(cs));
+        const double r = sqrt(fma(vz, vz, fma(vy, vy, vx * vx))) * h;
+        uint4 lo, hi;
+        tc_query_record(fma(vx, h, px), fma(vy, h, py), fma(vz, h, pz), r, s.d, a.grid, lo, hi);
+        a.pre_tc[2 * i] = lo;
+        a.pre_tc[2 * i + 1] = hi;
+    }
+    pre[kPreSeg][i] = __longlong_as_double(a.in.seg_id[i]);
+    pre[kPreTraj][i] = __longlong_as_double(a.in.traj_id ? a.in.traj_id[i] : 0);
+    // sort key: the temporal bin of the clipped start, in FP32 (it only
+    // groups the segments into tiles of 32 that span few bins); invalid
+    // segments sort last
+    uint64_t key = bins.m;
+    if (valid) {
+        const float f = floorf(__double2float_rn(key_double(cs) - bins.t_min) * bins.inv_width_f);
+        key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
+    }
+    return key;
+}
+
+// The candidate range of one slot into the pre columns (kPreLo, kPreHi;
+// empty for an invalid slot) and, with a.count_overlaps, its exact number
+// of temporal-overlap pairs (returned).
+__device__ __forceinline__ unsigned long long slot_range(const PrepArgs &a, uint64_t i, bool valid, int64_t cs,
+                                                         int64_t ce)
+{
+    int64_t rlo = INT64_MAX, rhi = INT64_MIN;
+    unsigned long long n_overlap = 0;
+    if (valid) {
+        candidate_range(a.bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
+        if (!TDQ_DBG(a.ctr, kDbgRange, rhi <= rlo || (rlo >= 0 && rhi <= (int64_t)a.n_entries))) {
+            rlo = INT64_MAX;
+            rhi = INT64_MIN;
+        }
+    }
+    a.pre[kPreLo][i] = __longlong_as_double(rlo);
+    a.pre[kPreHi][i] = __longlong_as_double(rhi);
+    return n_overlap;
+}
+
+// Validate and clip every query segment into the pre columns, with its
+// sort key and place: the counting sort's rank inside its bin, or the radix
+// sort's first digit counts.  A block takes kPrepSlots slots in two roles:
+// its first kPrepSlots threads do the arithmetic of a slot each
+// (slot_arith: a chain of FP64 operations on the narrow FP64 pipe), the
+// other kPrepSlots threads the candidate ranges of the same slots
+// (slot_range: chains of dependent loads from the bin table), so that the
+// two chains run side by side rather than one after the other.
+__global__ void __launch_bounds__(kBlock, 4) query_prep(PrepArgs a)
+{
+    static_assert(2 * kPrepSlots == kBlock, "two roles of kPrepSlots threads");
     const uint64_t nq = a.nq;
     DevCounters *ctr = a.ctr;
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool arith = threadIdx.x < kPrepSlots;
+    const uint64_t i = (uint64_t)blockIdx.x * kPrepSlots + (threadIdx.x % kPrepSlots);
     bool valid = false;
     unsigned long long n_overlap = 0;
     uint32_t digit = 256;  // low byte of the sort key (256: not sorted)
     // slots at or beyond the device-side count are padding: empty, not errors
     const uint64_t nreal = a.in.n_real ? a.in.n_real : nq;
-    if (i == 0) ctr->sort_n = nreal < nq ? nreal : nq;
-    if (i < nq) {
-        uint64_t key;
-        valid = prep_slot(a, i, nreal, key, n_overlap);
+    if (i == 0 && arith) ctr->sort_n = nreal < nq ? nreal : nq;
+    if (i < nq && arith) {
+        uint64_t key = a.bins.m;
+        if (i >= nreal) {
+            slot_padding(a, i);
+        } else {
+            const SlotIn s = slot_input(a.in, i);
+            if (!s.ok) atomicOr(&ctr->error, 1u);
+            key = slot_arith(a, i, s);
+            valid = s.valid;
+        }
         a.keys[i] = key;
         if (i >= nreal) {
             a.vals[i] = (uint32_t)i;
@@ -251,7 +288,19 @@ __global__ void query_prep(PrepArgs a)
             a.vals[i] = (uint32_t)i;
             digit = (uint32_t)(key & 0xff);
         }
+    } else if (i < nq && a.ranges) {
+        bool v = false;
+        int64_t cs = 0, ce = 0;
+        if (i < nreal) {
+            const SlotIn s = slot_input(a.in, i);
+            v = s.valid;
+            cs = s.cs;
+            ce = s.ce;
+        }
+        n_overlap = slot_range(a, i, v, cs, ce);
     }
+    // (the arithmetic threads count the valid segments, the range threads
+    // the overlap pairs)
     const unsigned vm = __ballot_sync(kFull, valid);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
@@ -268,25 +317,27 @@ __global__ void query_prep(PrepArgs a)
         __syncthreads();
         if (last) {
             __threadfence();
-            block_exclusive_scan<uint32_t, kBlock, 8>(a.bin_cnt, a.bins.m, nullptr);
+            block_exclusive_scan<uint32_t, kBlock, 16>(a.bin_cnt, a.bins.m, nullptr);
         }
-    } else if (a.sort_hist) {  // this block's keys lie in one sort tile (blockDim divides kSortTileKeys)
+    } else if (a.sort_hist) {  // this block's keys lie in one sort tile (kPrepSlots divides kSortTileKeys)
+        static_assert(kSortTileKeys % kPrepSlots == 0, "a block's slots lie in one sort tile");
         __shared__ uint32_t h[256];
         for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
         __syncthreads();
         if (digit < 256) atomicAdd(&h[digit], 1u);
         __syncthreads();
-        uint32_t *th = a.sort_hist + (uint64_t)blockIdx.x * blockDim.x / kSortTileKeys * 256;
+        uint32_t *th = a.sort_hist + (uint64_t)blockIdx.x * kPrepSlots / kSortTileKeys * 256;
         for (int d = threadIdx.x; d < 256; d += blockDim.x)
             if (h[d]) atomicAdd(&th[d], h[d]);
     }
 }
 
-// A search of at most kSmallPrep query slots is prepared in one launch: the
-// first kSmallPrepWarps warps of each block prepare kSmallPrepWarps x 32
-// slots (prep_slot) -- one warp per scheduler of an SM, as the per-slot
-// FP64 arithmetic is a long dependent chain on a narrow FP64 pipe -- and the
-// block that finishes last sorts the valid segments by (bin, slot) in shared
+// A search of at most kSmallPrep query slots is prepared in one launch: each
+// block prepares kSmallPrepWarps x 32 slots -- the first kSmallPrepWarps
+// warps their arithmetic (slot_arith, one warp per scheduler of an SM, as
+// the per-slot FP64 arithmetic is a long dependent chain on a narrow FP64
+// pipe), the next kSmallPrepWarps warps their candidate ranges (slot_range)
+// at the same time -- and the block that finishes last sorts the valid segments by (bin, slot) in shared
 // memory, writes the sorted columns and plans the tiles.  This replaces the
 // bin counters' clear and the three kernels of the multi-block preparation,
 // whose fixed costs dominate small searches (a serving request).  The sort
@@ -305,14 +356,24 @@ __global__ void __launch_bounds__(kSmallPrep) query_prep_small(SmallPrepArgs s)
     const uint64_t nq = a.nq;  // at most kSmallPrep (host-checked)
     // slots at or beyond the device-side count are padding: not prepared, not sorted
     const uint64_t nreal = a.in.n_real && a.in.n_real < nq ? a.in.n_real : nq;
-    if (warp < kSmallPrepWarps) {
-        const uint64_t i = (uint64_t)blockIdx.x * (kSmallPrepWarps * 32) + t;
+    if (warp < 2 * kSmallPrepWarps) {
+        // warps 0 .. kSmallPrepWarps-1: the arithmetic of the block's slots;
+        // the next kSmallPrepWarps warps: their candidate ranges (the two
+        // chains side by side, as in query_prep)
+        const bool arith = warp < kSmallPrepWarps;
+        const uint64_t i = (uint64_t)blockIdx.x * (kSmallPrepWarps * 32) + (t % (kSmallPrepWarps * 32));
         bool valid = false;
         unsigned long long n_overlap = 0;
-        uint64_t key = a.bins.m;
         if (i < nreal) {
-            valid = prep_slot(a, i, nreal, key, n_overlap);
-            a.keys[i] = valid ? (key << 32) | i : ~0ull;  // sort word (bins.m < 2^32)
+            const SlotIn in = slot_input(a.in, i);
+            if (arith) {
+                if (!in.ok) atomicOr(&ctr->error, 1u);
+                const uint64_t key = slot_arith(a, i, in);
+                valid = in.valid;
+                a.keys[i] = valid ? (key << 32) | i : ~0ull;  // sort word (bins.m < 2^32)
+            } else if (a.ranges) {
+                n_overlap = slot_range(a, i, in.valid, in.cs, in.ce);
+            }
         }
         const unsigned vm = __ballot_sync(kFull, valid);
 #pragma unroll
@@ -985,7 +1046,7 @@ cudaError_t enqueue_search(const tdq_index *idx, Workspace &w, const QueryInput 
     if (small)
         query_prep_small<<<small_prep_blocks(nq), kSmallPrep, 0, stream>>>(small_prep_args(idx, w, in, nq, cfg));
     else
-        query_prep<<<grid_for(nq), kBlock, 0, stream>>>(prep_args(idx, w, in, nq, cfg));
+        query_prep<<<prep_grid(nq), kBlock, 0, stream>>>(prep_args(idx, w, in, nq, cfg));
     const uint64_t ntiles = (nq + kQT - 1) / kQT;
     const uint64_t nsuper = (nq + 127) / 128;
     if (idx->n > 0) {
@@ -1108,7 +1169,7 @@ cudaError_t bind_inputs(cudaGraphExec_t exec, const GraphInputNodes &nodes, cons
     PrepArgs a0 = prep_args(idx, w, in, nq, cfg);
     void *args[] = {&a0};
     kp.func = (void *)query_prep;
-    kp.gridDim = dim3(grid_for(nq));
+    kp.gridDim = dim3(prep_grid(nq));
     kp.blockDim = dim3(kBlock);
     kp.kernelParams = args;
     return cudaGraphExecKernelNodeSetParams(exec, nodes.prep, &kp);
