@@ -874,18 +874,22 @@ def main():
     modes["tcfilter"] = tdq.MODE_TC_FILTER
 
     def step(mode):
+        # the step's searches; returns the bookkeeping to run once the step's
+        # end is recorded (a batched step's statistics are read afterwards;
+        # unbatched searches share the index's statistics, read after each)
         t = {"pairs": 0, "interactions": 0, "results": 0, "launches": 0, "kernel_ms": 0.0, "fp64_pairs": 0,
              "survivors": 0, "refine_ms": 0.0, "mma": 0}
         if mode in ("batched", "batched_tc"):
             p = plan if mode == "batched" else plantc
-            cnt = p.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
-            stats = [p.stats()]
-            t["results"] = cnt
-        else:
-            stats = []
-            for d in w.d_values:
-                t["results"] += tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=modes[mode])
-                stats.append(tdq.get_stats(idx))
+            t["results"] = p.search(q3dev, d3dev, t03dev, t13dev, stream=stream)
+            return lambda: tally(t, [p.stats()])
+        stats = []
+        for d in w.d_values:
+            t["results"] += tdq.search_device(idx, qdev, d, *w.window, buf, stream=stream, mode=modes[mode])
+            stats.append(tdq.get_stats(idx))
+        return lambda: tally(t, stats)
+
+    def tally(t, stats):
         for s in stats:
             t["pairs"] += s["overlap_pairs"]
             t["interactions"] += s["interactions"]
@@ -902,9 +906,9 @@ def main():
         # a few sub-millisecond steps do not bring the GPU to its steady clocks
         t_w = time.perf_counter()
         for _ in range(args.warmup):
-            step(mode)
+            step(mode)()
         while time.perf_counter() - t_w < args.min_warmup_s:
-            step(mode)
+            step(mode)()
         torch.cuda.synchronize()
         barrier()
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -913,10 +917,11 @@ def main():
         for _ in range(args.steps):
             flush.zero_()
             ev0.record(stream)
-            out = step(mode)
+            collect = step(mode)
             ev1.record(stream)
             ev1.synchronize()
             ms.append(ev0.elapsed_time(ev1))
+            out = collect()
             tot = out if tot is None else {k: tot[k] + out[k] for k in tot}
         torch.cuda.synchronize()
         barrier()
@@ -960,15 +965,16 @@ def main():
         barrier()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        e_pairs = 0
         d2h = 0
         for _ in range(args.steps):
             eplan.search(q3h, d3h, t03h, t13h, stream=stream)
             r = eplan.results(view=True)
-            e_pairs += eplan.stats()["overlap_pairs"]
             d2h += 32 * len(r) + 64
         torch.cuda.synchronize()
-        e_dt, e_pairs = reduce_over_ranks(time.perf_counter() - t, e_pairs, device="cuda")
+        e_dt = time.perf_counter() - t
+        # (every step searches the same batch: the last one's count of pairs)
+        e_pairs = args.steps * eplan.stats()["overlap_pairs"]
+        e_dt, e_pairs = reduce_over_ranks(e_dt, e_pairs, device="cuda")
         eplan.free()
         e2e = {"value": e_pairs / e_dt, "unit": "pair tests/s", "host_memory": "pinned",
                "h2d_bytes_per_step": len(q3) * 96, "d2h_bytes_per_step": d2h // args.steps,
