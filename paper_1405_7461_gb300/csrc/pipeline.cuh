@@ -23,7 +23,6 @@ struct BinView {
     double inv_width;   // 1 / width (for estimates that are verified afterwards)
     double max_dur;     // longest entry duration
     uint32_t m;
-    float inv_width_f;  // 1 / width in FP32 (for sort keys only)
     int64_t tmin_key;   // time key of t_min
     int64_t dur_bins;   // bins a longest entry can span, rounded up (for estimates that are verified afterwards)
 };
@@ -33,21 +32,21 @@ inline BinView bin_view(const tdq_index *idx)
     const double inv = idx->width > 0.0 ? 1.0 / idx->width : 0.0;
     const double db = ceil(idx->max_dur * inv) + 1.0;
     return BinView{idx->bin_begin, idx->bin_pmax_key, idx->e.ts_key, idx->e.te_sorted, idx->te_bin_begin,
-                   idx->bin_lo_key, idx->t_min, idx->width, inv, idx->max_dur, idx->m,
-                   idx->width > 0.0 ? (float)(1.0 / idx->width) : 0.f, idx->tmin_key,
+                   idx->bin_lo_key, idx->t_min, idx->width, inv, idx->max_dur, idx->m, idx->tmin_key,
                    db < (double)idx->m ? (int64_t)db : (int64_t)idx->m};
 }
 
 // The bin of the time t (key k) under bin_of -- floor((t - t_min) / width),
 // clamped to [0, m) -- without its FP64 division: an estimate by one
-// multiplication, checked against the table of each bin's smallest key (the
-// bin is the last b with bin_lo_key[b] <= k), and if it is off (a degenerate
-// width, extreme magnitudes) a bisection of that table.
+// multiplication and one rounding conversion (downward, saturating; the
+// clamp in integers), checked against the table of each bin's smallest key
+// (the bin is the last b with bin_lo_key[b] <= k), and if it is off (a
+// degenerate width, extreme magnitudes) a bisection of that table.
 __device__ __forceinline__ int64_t bin_of_key(const BinView &bins, int64_t k, double t)
 {
     const int64_t m = bins.m;
-    const double f = floor((t - bins.t_min) * bins.inv_width);
-    const int64_t b = f > 0.0 ? (f < (double)(m - 1) ? (int64_t)f : m - 1) : 0;
+    const long long f = __double2ll_rd((t - bins.t_min) * bins.inv_width);
+    const int64_t b = f > 0 ? (f < m - 1 ? (int64_t)f : m - 1) : 0;
     const int64_t lo = bins.bin_lo_key[b], hi = bins.bin_lo_key[b + 1];
     if (k >= lo && k < hi) return b;
     int64_t a = k < lo ? 0 : b + 1, z = k < lo ? b : m;  // bin_lo_key[a] <= k < bin_lo_key[z]

@@ -55,7 +55,8 @@ __device__ __forceinline__ bool is_nan_bits(double x)
 // q.t_end} - #{t_end <= q.t_start} (the second set lies inside the first
 // because t_end > t_start).
 __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs, int64_t ce, bool count_overlaps,
-                                                int64_t &rlo, int64_t &rhi, unsigned long long &n_overlap)
+                                                int64_t &rlo, int64_t &rhi, unsigned long long &n_overlap,
+                                                int64_t &bin_start)
 {
     // Three binary searches, advanced together so that their loads overlap
     // (each thread's searches are a chain of dependent loads):
@@ -78,6 +79,7 @@ __device__ __forceinline__ void candidate_range(const BinView &bins, int64_t cs,
     const int64_t jhi = ce <= bins.tmin_key ? -1 : bin_of_key(bins, ce, te);
     const int64_t m = bins.m;
     const int64_t bts = bin_of_key(bins, cs, ts);  // exact: C relies on it
+    bin_start = bts;
     int64_t a_lo, a_hi;
     {
         // the lower end only needs to be about right: it is verified
@@ -170,11 +172,9 @@ __device__ __forceinline__ void slot_padding(const PrepArgs &a, uint64_t i)
 
 // The arithmetic of one real slot: the pre columns (see kPreCols; keys
 // stored bitwise in the double arrays), the FP32 bounding sphere (and with
-// a.pre_tc the tensor-core record) and the ids.  Returns the sort key: the
-// temporal bin of the clipped start, bins.m for an invalid segment.
-__device__ __forceinline__ uint64_t slot_arith(const PrepArgs &a, uint64_t i, const SlotIn &s)
+// a.pre_tc the tensor-core record) and the ids.
+__device__ __forceinline__ void slot_arith(const PrepArgs &a, uint64_t i, const SlotIn &s)
 {
-    const BinView &bins = a.bins;
     double *const *pre = a.pre;
     const double *c = s.c;
     const bool valid = s.valid;
@@ -217,27 +217,23 @@ __device__ __forceinline__ uint64_t slot_arith(const PrepArgs &a, uint64_t i, co
     }
     pre[kPreSeg][i] = __longlong_as_double(a.in.seg_id[i]);
     pre[kPreTraj][i] = __longlong_as_double(a.in.traj_id ? a.in.traj_id[i] : 0);
-    // sort key: the temporal bin of the clipped start, in FP32 (it only
-    // groups the segments into tiles of 32 that span few bins); invalid
-    // segments sort last
-    uint64_t key = bins.m;
-    if (valid) {
-        const float f = floorf(__double2float_rn(key_double(cs) - bins.t_min) * bins.inv_width_f);
-        key = f < 0.f ? 0 : (f < (float)(bins.m - 1) ? (uint64_t)f : (uint64_t)(bins.m - 1));
-    }
-    return key;
 }
 
 // The candidate range of one slot into the pre columns (kPreLo, kPreHi;
 // empty for an invalid slot) and, with a.count_overlaps, its exact number
-// of temporal-overlap pairs (returned).
+// of temporal-overlap pairs (returned); its sort key into `key`: the
+// temporal bin of the clipped start (exact, found by the lookup), bins.m
+// for an invalid segment (sorted last).
 __device__ __forceinline__ unsigned long long slot_range(const PrepArgs &a, uint64_t i, bool valid, int64_t cs,
-                                                         int64_t ce)
+                                                         int64_t ce, uint64_t &key)
 {
     int64_t rlo = INT64_MAX, rhi = INT64_MIN;
     unsigned long long n_overlap = 0;
+    key = a.bins.m;
     if (valid) {
-        candidate_range(a.bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap);
+        int64_t bin = 0;
+        candidate_range(a.bins, cs, ce, a.count_overlaps, rlo, rhi, n_overlap, bin);
+        key = (uint64_t)bin;
         if (!TDQ_DBG(a.ctr, kDbgRange, rhi <= rlo || (rlo >= 0 && rhi <= (int64_t)a.n_entries))) {
             rlo = INT64_MAX;
             rhi = INT64_MIN;
@@ -254,8 +250,9 @@ __device__ __forceinline__ unsigned long long slot_range(const PrepArgs &a, uint
 // its first kPrepSlots threads do the arithmetic of a slot each
 // (slot_arith: a chain of FP64 operations on the narrow FP64 pipe), the
 // other kPrepSlots threads the candidate ranges of the same slots
-// (slot_range: chains of dependent loads from the bin table), so that the
-// two chains run side by side rather than one after the other.
+// (slot_range: chains of dependent loads from the bin table) and, from the
+// bin of the clipped start the lookup finds, the sort keys and places, so
+// that the two chains run side by side rather than one after the other.
 __global__ void __launch_bounds__(kBlock, 4) query_prep(PrepArgs a)
 {
     static_assert(2 * kPrepSlots == kBlock, "two roles of kPrepSlots threads");
@@ -270,23 +267,17 @@ __global__ void __launch_bounds__(kBlock, 4) query_prep(PrepArgs a)
     const uint64_t nreal = a.in.n_real ? a.in.n_real : nq;
     if (i == 0 && arith) ctr->sort_n = nreal < nq ? nreal : nq;
     if (i < nq && arith) {
-        uint64_t key = a.bins.m;
         if (i >= nreal) {
             slot_padding(a, i);
         } else {
             const SlotIn s = slot_input(a.in, i);
             if (!s.ok) atomicOr(&ctr->error, 1u);
-            key = slot_arith(a, i, s);
+            slot_arith(a, i, s);
             valid = s.valid;
         }
-        a.keys[i] = key;
-        if (i >= nreal) {
+        if (!a.ranges) {  // an index without entries: nothing is sorted
+            a.keys[i] = a.bins.m;
             a.vals[i] = (uint32_t)i;
-        } else if (a.bin_cnt) {
-            if (valid) a.vals[i] = atomicAdd(&a.bin_cnt[key], 1u);
-        } else {
-            a.vals[i] = (uint32_t)i;
-            digit = (uint32_t)(key & 0xff);
         }
     } else if (i < nq && a.ranges) {
         bool v = false;
@@ -297,10 +288,20 @@ __global__ void __launch_bounds__(kBlock, 4) query_prep(PrepArgs a)
             cs = s.cs;
             ce = s.ce;
         }
-        n_overlap = slot_range(a, i, v, cs, ce);
+        uint64_t key;
+        n_overlap = slot_range(a, i, v, cs, ce, key);
+        a.keys[i] = key;
+        if (i >= nreal) {
+            a.vals[i] = (uint32_t)i;
+        } else if (a.bin_cnt) {
+            if (v) a.vals[i] = atomicAdd(&a.bin_cnt[key], 1u);
+        } else {
+            a.vals[i] = (uint32_t)i;
+            digit = (uint32_t)(key & 0xff);
+        }
     }
     // (the arithmetic threads count the valid segments, the range threads
-    // the overlap pairs)
+    // the overlap pairs and the radix sort's digits)
     const unsigned vm = __ballot_sync(kFull, valid);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_overlap += __shfl_xor_sync(kFull, n_overlap, o);
@@ -368,11 +369,12 @@ __global__ void __launch_bounds__(kSmallPrep) query_prep_small(SmallPrepArgs s)
             const SlotIn in = slot_input(a.in, i);
             if (arith) {
                 if (!in.ok) atomicOr(&ctr->error, 1u);
-                const uint64_t key = slot_arith(a, i, in);
+                slot_arith(a, i, in);
                 valid = in.valid;
-                a.keys[i] = valid ? (key << 32) | i : ~0ull;  // sort word (bins.m < 2^32)
             } else if (a.ranges) {
-                n_overlap = slot_range(a, i, in.valid, in.cs, in.ce);
+                uint64_t key;
+                n_overlap = slot_range(a, i, in.valid, in.cs, in.ce, key);
+                a.keys[i] = in.valid ? (key << 32) | i : ~0ull;  // sort word (bins.m < 2^32)
             }
         }
         const unsigned vm = __ballot_sync(kFull, valid);
